@@ -1,0 +1,358 @@
+"""Pins for the FP64 oracle: checks against mathematics that does not come
+from the oracle itself (closed forms, library routines, finite differences,
+invariants, brute force).  CPU only."""
+import numpy as np
+import pytest
+import scipy.linalg as sl
+
+import oracle as orc
+import scenegen
+
+
+def _rand_rotvec(rng, theta):
+    axis = rng.normal(size=3)
+    return theta * axis / np.linalg.norm(axis)
+
+
+ANGLES = [0.0, 1e-12, 1e-9, 3e-5, 2e-4, 0.05, 0.099, 0.101, 0.3, 1.0, 2.5,
+          np.pi - 1e-6]
+
+
+@pytest.mark.parametrize("theta", ANGLES)
+def test_rodrigues_is_matrix_exponential(theta):
+    """R(omega) = expm([omega]_x) (scipy's Pade expm, a library routine)."""
+    rng = np.random.default_rng(int(theta * 1e6) % 1000 + 7)
+    w = _rand_rotvec(rng, theta)
+    R = orc.rodrigues(w)
+    E = sl.expm(orc.skew(w))
+    assert np.max(np.abs(R - E)) < 2e-15
+    assert np.max(np.abs(R @ R.T - np.eye(3))) < 2e-15
+
+
+@pytest.mark.parametrize("theta", ANGLES)
+def test_left_jacobian_by_series(theta):
+    """J_l(w) = sum_n [w]_x^n / (n+1)!  (its defining power series)."""
+    rng = np.random.default_rng(11)
+    w = _rand_rotvec(rng, theta)
+    K = orc.skew(w)
+    S = np.zeros((3, 3))
+    term = np.eye(3)
+    fact = 1.0
+    for n in range(60):
+        fact *= (n + 1)
+        S += term / fact
+        term = term @ K
+    assert np.max(np.abs(orc.left_jacobian(w) - S)) < 5e-15
+
+
+def test_left_jacobian_perturbation_identity():
+    """R(w + d) R(w)^T = expm([J_l(w) d]_x) + O(|d|^2), checked by central
+    differences of R(w + e d)."""
+    rng = np.random.default_rng(3)
+    for theta in [1e-7, 0.02, 0.7, 2.9]:
+        w = _rand_rotvec(rng, theta)
+        d = rng.normal(size=3)
+        e = 1e-6
+        dR = (orc.rodrigues(w + e * d) - orc.rodrigues(w - e * d)) / (2 * e)
+        lhs = dR @ orc.rodrigues(w).T
+        rhs = orc.skew(orc.left_jacobian(w) @ d)
+        assert np.max(np.abs(lhs - rhs)) < 1e-8
+
+
+def test_projection_closed_forms():
+    """Hand-computed pixels of the BAL camera."""
+    cams = np.zeros((3, 9))
+    cams[:, 5] = -5.0
+    cams[:, 6] = 500.0
+    cams[1, 7] = 0.1                       # k1
+    cams[2, 1] = np.pi / 2                 # rotation about y by 90 degrees
+    pts = np.array([[1.0, 0.0, 0.0], [0.0, 0.0, 1.0]])
+    ci = np.array([0, 1, 2, 2])
+    pi = np.array([0, 0, 0, 1])
+    out = orc.project(cams, pts, ci, pi)
+    # X_cam = (1,0,-5): p = -(1,0)/(-5) = (0.2, 0); pixel 500 * 0.2
+    assert np.allclose(out[0], [100.0, 0.0], atol=1e-12)
+    # |p|^2 = 0.04, distortion 1 + 0.1 * 0.04
+    assert np.allclose(out[1], [100.4, 0.0], atol=1e-12)
+    # R_y(pi/2) (1,0,0) = (0,0,-1): X_cam = (0,0,-6), on the optical axis
+    assert np.allclose(out[2], [0.0, 0.0], atol=1e-12)
+    # R_y(pi/2) (0,0,1) = (1,0,0): X_cam = (1,0,-5)
+    assert np.allclose(out[3], [100.0, 0.0], atol=1e-10)
+
+
+def _random_cameras(rng, n, thetas):
+    cams = np.zeros((n, 9))
+    for i in range(n):
+        cams[i, 0:3] = _rand_rotvec(rng, thetas[i % len(thetas)])
+    cams[:, 3:5] = rng.normal(0, 0.5, size=(n, 2))
+    cams[:, 5] = -5.0 + rng.normal(0, 0.3, size=n)
+    cams[:, 6] = 400.0 + 200.0 * rng.random(n)
+    cams[:, 7] = rng.normal(0, 0.05, size=n)
+    cams[:, 8] = rng.normal(0, 0.02, size=n)
+    return cams
+
+
+def test_jacobian_matches_central_differences():
+    """Analytic Jc, Jp against central differences of the residual, including
+    the small-angle branches and a rotation near pi."""
+    rng = np.random.default_rng(5)
+    thetas = [0.0, 1e-9, 5e-5, 0.05, 0.5, 2.0, np.pi - 1e-4]
+    C = len(thetas)
+    cams = _random_cameras(rng, C, thetas)
+    # points in front of each camera: X = R^T (X_cam - t) with X_cam[2] < 0
+    pts, ci, pi = [], [], []
+    for i in range(C):
+        R = orc.rodrigues(cams[i, 0:3])
+        for _ in range(4):
+            Xc = np.array([rng.normal(0, 1.0), rng.normal(0, 1.0), -4.0 - 2 * rng.random()])
+            pts.append(R.T @ (Xc - cams[i, 3:6]))
+            ci.append(i)
+            pi.append(len(pts) - 1)
+    pts = np.array(pts)
+    ci = np.array(ci)
+    pi = np.array(pi)
+    pix = rng.normal(0, 50, size=(len(ci), 2))
+    r, Jc, Jp = orc.linearize(cams, pts, ci, pi, pix)
+    assert np.allclose(r, orc.residuals(cams, pts, ci, pi, pix), atol=0, rtol=0)
+    for k in range(len(ci)):
+        for a in range(9):
+            h = 1e-6 * max(1.0, abs(cams[ci[k], a]))
+            cp = cams.copy()
+            cm = cams.copy()
+            cp[ci[k], a] += h
+            cm[ci[k], a] -= h
+            fd = (orc.residuals(cp, pts, ci[k:k + 1], pi[k:k + 1], pix[k:k + 1]) -
+                  orc.residuals(cm, pts, ci[k:k + 1], pi[k:k + 1], pix[k:k + 1]))[0] / (2 * h)
+            scale = max(1.0, np.max(np.abs(Jc[k, :, a])))
+            assert np.max(np.abs(fd - Jc[k, :, a])) < 2e-6 * scale, (k, a)
+        for a in range(3):
+            h = 1e-6 * max(1.0, abs(pts[pi[k], a]))
+            pp = pts.copy()
+            pm = pts.copy()
+            pp[pi[k], a] += h
+            pm[pi[k], a] -= h
+            fd = (orc.residuals(cams, pp, ci[k:k + 1], pi[k:k + 1], pix[k:k + 1]) -
+                  orc.residuals(cams, pm, ci[k:k + 1], pi[k:k + 1], pix[k:k + 1]))[0] / (2 * h)
+            scale = max(1.0, np.max(np.abs(Jp[k, :, a])))
+            assert np.max(np.abs(fd - Jp[k, :, a])) < 2e-6 * scale, (k, a)
+
+
+def _tiny_scene(seed, C=4, P=12, noise=1.0, delta=0.0, outliers=0.0):
+    sc = scenegen.ring_scene(C, P, seed=seed, view_p=0.5, noise_px=noise,
+                             outlier_frac=outliers, huber_delta=delta)
+    pix = orc.pixels_from_scene(sc)
+    return sc, pix
+
+
+def test_huber_with_large_delta_is_plain_loss():
+    sc, pix = _tiny_scene(1)
+    a = orc.assemble(sc.cams_init, sc.points_init, sc.cam_idx, sc.pt_idx, pix, 0.0)
+    b = orc.assemble(sc.cams_init, sc.points_init, sc.cam_idx, sc.pt_idx, pix, 1e9)
+    for key in ("U", "V", "W", "gc", "gp"):
+        assert np.array_equal(a[key], b[key])
+    assert a["F"] == b["F"]
+
+
+def test_huber_closed_form():
+    rho, w = orc.huber(np.array([0.25, 1.0, 4.0, 9.0]), 1.0)
+    assert np.allclose(rho, [0.25, 1.0, 3.0, 5.0])       # 2*sqrt(s) - 1 outside
+    assert np.allclose(w, [1.0, 1.0, 0.5, 1.0 / 3.0])     # rho'(s) = 1/sqrt(s)
+
+
+@pytest.mark.parametrize("delta,outliers", [(0.0, 0.0), (1.0, 0.3)])
+def test_block_assembly_equals_dense(delta, outliers):
+    """U, V, W, g from the per-observation blocks equal J^T J and J^T r of the
+    dense weighted Jacobian (brute force)."""
+    sc, pix = _tiny_scene(2, C=5, P=15, delta=delta, outliers=outliers)
+    args = (sc.cams_init, sc.points_init, sc.cam_idx, sc.pt_idx, pix, delta)
+    blk = orc.assemble(*args)
+    J, rw = orc.dense_jacobian(*args)
+    H = J.T @ J
+    g = J.T @ rw
+    C, P = sc.C, sc.P
+    scale = np.max(np.abs(H))
+    for i in range(C):
+        assert np.max(np.abs(H[9 * i:9 * i + 9, 9 * i:9 * i + 9] - blk["U"][i])) < 1e-13 * scale
+        assert np.max(np.abs(g[9 * i:9 * i + 9] - blk["gc"][i])) < 1e-13 * np.max(np.abs(g))
+    for j in range(P):
+        o = 9 * C + 3 * j
+        assert np.max(np.abs(H[o:o + 3, o:o + 3] - blk["V"][j])) < 1e-13 * scale
+        assert np.max(np.abs(g[o:o + 3] - blk["gp"][j])) < 1e-13 * np.max(np.abs(g))
+    Wsum = np.zeros((C, P, 9, 3))
+    for k in range(sc.O):
+        Wsum[sc.cam_idx[k], sc.pt_idx[k]] += blk["W"][k]
+    for i in range(C):
+        for j in range(P):
+            o = 9 * C + 3 * j
+            assert np.max(np.abs(H[9 * i:9 * i + 9, o:o + 3] - Wsum[i, j])) < 1e-13 * scale
+    # camera-camera blocks of H vanish: no residual touches two cameras
+    for i in range(C):
+        for l in range(C):
+            if i != l:
+                assert np.all(H[9 * i:9 * i + 9, 9 * l:9 * l + 9] == 0.0)
+
+
+def test_schur_solve_equals_dense_solve():
+    """Schur complement + Cholesky + back-substitution solves the full damped
+    system exactly (textbook block elimination), and tight PCG agrees."""
+    sc, pix = _tiny_scene(3, C=5, P=20, delta=1.0, outliers=0.2)
+    lam = 1e-3
+    args = (sc.cams_init, sc.points_init, sc.cam_idx, sc.pt_idx, pix)
+    blk = orc.assemble(*args, 1.0)
+    dc_d, dp_d = orc.dense_lm_delta(*args, lam, delta=1.0)
+    opts = orc.LMOptions(solver="cholesky", huber_delta=1.0)
+    dc, dp, _, _ = orc.solve_damped(blk, sc.cam_idx, sc.pt_idx, lam, opts)
+    sc_ = np.max(np.abs(dc_d))
+    assert np.max(np.abs(dc - dc_d)) < 1e-9 * sc_
+    assert np.max(np.abs(dp - dp_d)) < 1e-9 * max(np.max(np.abs(dp_d)), sc_)
+    opts = orc.LMOptions(solver="pcg", pcg_tol=1e-15, pcg_maxiter=9 * sc.C * 4,
+                         huber_delta=1.0)
+    dc2, dp2, its, rel = orc.solve_damped(blk, sc.cam_idx, sc.pt_idx, lam, opts)
+    assert np.max(np.abs(dc2 - dc_d)) < 1e-7 * sc_
+    # residual of the full system
+    J, rw = orc.dense_jacobian(*args, 1.0)
+    H = J.T @ J
+    g = J.T @ rw
+    Hs = H + np.diag(orc.damp_diag(np.diag(H), lam, 1e-6, 1e32))
+    d = np.concatenate([dc.reshape(-1), dp.reshape(-1)])
+    assert np.linalg.norm(Hs @ d + g) < 1e-10 * np.linalg.norm(g)
+
+
+def test_implicit_schur_matvec_and_block_jacobi():
+    sc, pix = _tiny_scene(4, C=6, P=25)
+    lam = 1e-2
+    blk = orc.assemble(sc.cams_init, sc.points_init, sc.cam_idx, sc.pt_idx, pix)
+    S, b, Us, Vinv = orc.schur_explicit(blk, sc.cam_idx, sc.pt_idx, lam)
+    rng = np.random.default_rng(0)
+    x = rng.normal(size=(sc.C, 9))
+    Sx = orc.schur_matvec(x, Us, Vinv, blk["W"], sc.cam_idx, sc.pt_idx)
+    assert np.max(np.abs(Sx.reshape(-1) - S @ x.reshape(-1))) < 1e-11 * np.max(np.abs(S @ x.reshape(-1)))
+    M = orc.block_jacobi(Us, Vinv, blk["W"], sc.cam_idx, sc.pt_idx)
+    for i in range(sc.C):
+        Sii = S[9 * i:9 * i + 9, 9 * i:9 * i + 9]
+        assert np.max(np.abs(M[i] @ Sii - np.eye(9))) < 1e-8
+    assert np.all(np.linalg.eigvalsh(S) > 0)
+
+
+def test_pcg_terminates_in_n_steps_on_spd():
+    """CG on an SPD n x n system reaches the solution in at most n steps
+    (exact arithmetic); checked against numpy's dense solve."""
+    rng = np.random.default_rng(8)
+    n = 30
+    Q = rng.normal(size=(n, n))
+    A = Q @ Q.T / n + np.diag(np.linspace(0.5, 3.0, n))
+    b = rng.normal(size=n)
+    Dinv = 1.0 / np.diag(A)
+    x, its, rel = orc.pcg(lambda v: A @ v, lambda v: Dinv * v, b, 1e-13, 4 * n)
+    assert its <= n
+    assert np.max(np.abs(x - np.linalg.solve(A, b))) < 1e-9 * np.max(np.abs(x))
+    x1, its1, _ = orc.pcg(lambda v: A @ v, lambda v: Dinv * v, b, 1e-13, 1)
+    # one step is the exact line minimisation along the preconditioned gradient
+    z = Dinv * b
+    assert np.allclose(x1, (b @ z) / (z @ A @ z) * z, rtol=1e-12, atol=0)
+
+
+def test_model_reduction_closed_form_for_exact_step():
+    """With (H + lambda D) Delta = -g solved exactly,
+    -g^T Delta - 1/2 Delta^T H Delta = 1/2 (-g^T Delta + lambda Delta^T D Delta)."""
+    sc, pix = _tiny_scene(5, C=5, P=20)
+    lam = 0.3
+    args = (sc.cams_init, sc.points_init, sc.cam_idx, sc.pt_idx, pix)
+    blk = orc.assemble(*args)
+    dc, dp, _, _ = orc.solve_damped(blk, sc.cam_idx, sc.pt_idx, lam,
+                                    orc.LMOptions(solver="cholesky"))
+    dL = orc.model_reduction(blk, dc, dp, sc.cam_idx, sc.pt_idx)
+    J, rw = orc.dense_jacobian(*args)
+    H = J.T @ J
+    g = J.T @ rw
+    D = np.clip(np.diag(H), 1e-6, 1e32)
+    d = np.concatenate([dc.reshape(-1), dp.reshape(-1)])
+    ref = 0.5 * (-(g @ d) + lam * d @ (D * d))
+    assert abs(dL - ref) < 1e-10 * abs(ref)
+    assert dL > 0
+
+
+def test_gain_ratio_tends_to_one_for_small_steps():
+    sc, pix = _tiny_scene(6, C=4, P=20)
+    args = (sc.cams_init, sc.points_init, sc.cam_idx, sc.pt_idx, pix)
+    blk = orc.assemble(*args)
+    F = orc.cost(*args)
+    for lam, tol in [(1e4, 1e-2), (1e6, 1e-4)]:
+        dc, dp, _, _ = orc.solve_damped(blk, sc.cam_idx, sc.pt_idx, lam,
+                                        orc.LMOptions(solver="cholesky"))
+        Ft = orc.cost(sc.cams_init + dc, sc.points_init + dp, sc.cam_idx, sc.pt_idx, pix)
+        dL = orc.model_reduction(blk, dc, dp, sc.cam_idx, sc.pt_idx)
+        assert abs((F - Ft) / dL - 1.0) < tol
+
+
+def test_cost_is_gauge_invariant():
+    """F is unchanged by a global similarity applied to cameras and points."""
+    sc, pix = _tiny_scene(7, C=6, P=40)
+    from scipy.spatial.transform import Rotation
+    Q = Rotation.from_rotvec([0.3, -0.2, 0.5]).as_matrix()
+    cams2, pts2 = orc.gauge_transform(sc.cams_init, sc.points_init, 1.7, Q,
+                                      np.array([0.4, -1.0, 0.25]))
+    F1 = orc.cost(sc.cams_init, sc.points_init, sc.cam_idx, sc.pt_idx, pix)
+    F2 = orc.cost(cams2, pts2, sc.cam_idx, sc.pt_idx, pix)
+    assert abs(F1 - F2) < 1e-11 * F1
+
+
+def test_jacobian_has_seven_dim_gauge_null_space():
+    """At a noise-free solution J has a 7-dimensional null space (rotation,
+    translation, scale of the whole scene): the 7 smallest singular values are
+    far below the 8th.  A wrong sign or index in Jc/Jp breaks this."""
+    sc, _ = _tiny_scene(8, C=5, P=30, noise=0.0)
+    pix = orc.project(sc.cams_gt, sc.points_gt, sc.cam_idx, sc.pt_idx)
+    J, _ = orc.dense_jacobian(sc.cams_gt, sc.points_gt, sc.cam_idx, sc.pt_idx, pix)
+    s = np.linalg.svd(J, compute_uv=False)
+    assert s[-7] < 1e-9 * s[0]
+    assert s[-8] > 1e-6 * s[0]
+
+
+def test_noise_free_lm_reaches_zero_cost():
+    sc = scenegen.ring_scene(8, 200, seed=9, view_p=0.3, noise_px=0.0)
+    pix = orc.pixels_from_scene(sc)
+    opts = orc.LMOptions(solver="cholesky")
+    _, _, trace = orc.lm(sc.cams_init, sc.points_init, sc.cam_idx, sc.pt_idx, pix, 30, opts)
+    F0 = trace[0]["cost"]
+    Ffinal = min(t["cost_trial"] for t in trace if t["accepted"])
+    assert F0 > 1.0
+    assert Ffinal < 1e-20 * sc.O
+
+
+def test_lm_accepted_costs_are_monotone():
+    sc = scenegen.config_scene("ba16")
+    pix = orc.pixels_from_scene(sc)
+    opts = orc.LMOptions(solver="cholesky")
+    _, _, trace = orc.lm(sc.cams_init, sc.points_init, sc.cam_idx, sc.pt_idx, pix, 8, opts)
+    costs = [trace[0]["cost"]] + [t["cost_trial"] for t in trace if t["accepted"]]
+    assert all(b <= a for a, b in zip(costs, costs[1:]))
+    assert costs[-1] < 0.1 * costs[0]
+    # with 1 px noise the converged mean squared error is about 2 sigma^2 * (1 - dof/2O)
+    mse = 2.0 * costs[-1] / sc.O
+    assert 1.5 < mse < 2.2
+
+
+def _counting_sort(keys, n):
+    counts = [0] * n
+    for k in keys:
+        counts[k] += 1
+    rowptr = [0]
+    for c in counts:
+        rowptr.append(rowptr[-1] + c)
+    cursor = rowptr[:-1].copy()
+    perm = [0] * len(keys)
+    for i, k in enumerate(keys):
+        perm[cursor[k]] = i
+        cursor[k] += 1
+    return perm, rowptr
+
+
+@pytest.mark.parametrize("n,O", [(1, 0), (1, 5), (7, 50), (300, 2000), (5000, 3000)])
+def test_csr_build_is_stable_counting_sort(n, O):
+    rng = np.random.default_rng(n + O)
+    keys = rng.integers(0, n, size=O)
+    perm, rowptr = orc.csr_build(keys, n)
+    p2, r2 = _counting_sort(keys.tolist(), n)
+    assert perm.tolist() == p2
+    assert rowptr.tolist() == r2
