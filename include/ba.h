@@ -1,0 +1,244 @@
+/*
+ * ba.h -- C ABI of the GB300 (sm_103a) Levenberg-Marquardt bundle-adjustment
+ * library.
+ *
+ * The library solves the non-linear least-squares problem of Eq. 1 (Sec.
+ * III-A): minimise, over cameras theta_c and points X_j, the sum over the
+ * OBSERVED (camera, point) pairs k of rho(|pi(theta_c(k), X_p(k)) - x_k|^2),
+ * with the LM iteration of Alg. 1 / Eq. 2 (Sec. III-B).
+ *
+ * Camera model (the BAL camera of the paper's benchmark data, Sec. V): a
+ * camera is 9 numbers (omega[3] angle-axis, t[3], f, k1, k2).  A point X
+ * maps to X_cam = R(omega) X + t, p = -X_cam[0:2] / X_cam[2],
+ * pi = f (1 + k1 |p|^2 + k2 |p|^4) p.  All parameters update additively.
+ *
+ * Conventions shared by every entry point:
+ *  - Floating-point arrays have the type selected by ba_options.precision:
+ *    double for BA_PREC_F64, float for BA_PREC_F32.  Reductions (normal-
+ *    equation sums, dot products, costs, the gain ratio) are FP64 in both.
+ *  - cams is [C][9], points [P][3], pixels [O][2], row-major, contiguous.
+ *    cam_idx / pt_idx are int32 [O].
+ *  - Pointers marked "any" may be host (pageable or pinned) or device
+ *    memory; they are copied with a stream-ordered copy.  Pointers marked
+ *    "dev" must be device memory of the current device.  The caller owns
+ *    every pointer it passes; the library never keeps one.
+ *  - stream is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    All work is ordered on it; only calls documented as synchronising
+ *    block the host.
+ *  - Every call returns a ba_status; on failure ba_last_error() returns a
+ *    message for the calling thread.  No call aborts, traps or spins
+ *    without a bound.
+ */
+#ifndef BA_GB300_H
+#define BA_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ba_problem ba_problem; /* opaque, owned by the library */
+
+typedef enum {
+  BA_OK = 0,
+  BA_ERR_INVALID_ARG = 1, /* bad size, pointer, index or option */
+  BA_ERR_CUDA = 2,        /* a CUDA runtime call failed */
+  BA_ERR_NONFINITE = 3,   /* a non-finite parameter, pixel or cost */
+  BA_ERR_TIMEOUT = 4,     /* a bounded device wait ran out */
+  BA_ERR_NOT_CONVERGED = 5,
+  BA_ERR_OOM = 6,         /* device allocation failed */
+  BA_ERR_STATE = 7        /* call not valid in the problem's current state */
+} ba_status;
+
+enum { BA_PREC_F64 = 0, BA_PREC_F32 = 1 };
+
+/* Solver options.  up/down are the trust-region factors of the paper's
+ * minimum code example (TrustRegion(up=2.0, down=0.5**4), Sec. IV); its
+ * PCG(tol=1e-4, maxiter=250) gives pcg_tol / pcg_maxiter.  diag_min/diag_max
+ * are the bounds of diagonal clamping (Sec. IV-B).  The remaining constants
+ * are this library's readings of a paper that gives none. */
+typedef struct {
+  int precision;       /* BA_PREC_F64 or BA_PREC_F32 */
+  double huber_delta;  /* > 0: Huber loss on |r| with this delta (pixels) */
+  double lambda0;      /* initial damping, 1e-4 */
+  double up;           /* lambda /= up after a very good step, 2 */
+  double down;         /* lambda /= down after a bad or rejected step, 1/16 */
+  double rho_good;     /* gain ratio above which lambda shrinks, 0.75 */
+  double rho_bad;      /* gain ratio below which lambda grows, 0.25 */
+  double lambda_min;   /* 1e-16 */
+  double lambda_max;   /* 1e32 */
+  double diag_min;     /* clamp of diag(J^T J) before lambda scaling, 1e-6 */
+  double diag_max;     /* 1e32 */
+  int pcg_maxiter;     /* PCG iterations per LM trial, 250 */
+  double pcg_tol;      /* stop when |r|_2 <= pcg_tol |b|_2, 1e-4 */
+  int use_graph;       /* 1: ba_solve replays a captured CUDA graph */
+  int max_stats;       /* capacity of the per-trial statistics ring, 4096 */
+} ba_options;
+
+/* Statistics of one LM trial (Alg. 1, one pass of the loop body). */
+typedef struct {
+  double cost;        /* F(theta) before the trial, F = 1/2 sum rho(|r|^2) */
+  double cost_trial;  /* F(theta + Delta) */
+  double model;       /* Delta L = -g^T Delta - 1/2 sum_k w_k |J_k Delta|^2 */
+  double rho;         /* (cost - cost_trial) / model */
+  double lambda;      /* damping used by this trial */
+  double pcg_rel_res; /* |r|/|b| of the reduced system at exit */
+  int32_t accepted;   /* 1 if theta <- theta + Delta */
+  int32_t pcg_iters;  /* PCG iterations run */
+  int32_t precond_fallbacks; /* cameras whose block-Jacobi block was not SPD */
+  int32_t reserved;
+} ba_iter_stats;
+
+/* Fill *opt with the defaults listed above. */
+ba_status ba_options_default(ba_options* opt);
+
+/* Create a problem (C cameras, P points, O observations), run the cached
+ * symbolic phase (Sec. IV-B: stable device radix sorts of the observations
+ * by camera and by point) and evaluate the initial cost.
+ * cams (any, [C][9]), points (any, [P][3]), cam_idx / pt_idx (any, int32
+ * [O]), pixels (any, [O][2]) are copied.  Errors: BA_ERR_INVALID_ARG for
+ * C, P or O < 1, a NULL pointer, an index out of range or bad options;
+ * BA_ERR_NONFINITE for a non-finite parameter, pixel or initial cost;
+ * BA_ERR_OOM.  Synchronises the stream.  On error *out is NULL. */
+ba_status ba_problem_create(ba_problem** out, int C, int P, int O,
+                            const void* cams, const void* points,
+                            const int32_t* cam_idx, const int32_t* pt_idx,
+                            const void* pixels, const ba_options* opt,
+                            void* stream);
+
+/* Free a problem and everything it owns (NULL is accepted). */
+ba_status ba_problem_destroy(ba_problem* h);
+
+/* One LM trial (Alg. 1 loop body): linearise if theta changed (a1, a2),
+ * damp and reduce (a3), solve the reduced camera system by block-Jacobi PCG
+ * with implicit S x (a4), back-substitute (a5), evaluate the trial and
+ * accept or reject it, update lambda (a6).  No host synchronisation. */
+ba_status ba_lm_step(ba_problem* h, void* stream);
+
+/* iters LM trials; with use_graph the trial is captured once as a CUDA graph
+ * (App. B) and replayed.  No host synchronisation. */
+ba_status ba_solve(ba_problem* h, int iters, void* stream);
+
+/* Copy the current (last accepted) parameters to cams_out [C][9] and
+ * points_out [P][3] (any). Either may be NULL. */
+ba_status ba_get_params(ba_problem* h, void* cams_out, void* points_out,
+                        void* stream);
+
+/* Replace the parameters (any; either may be NULL to keep it) and
+ * re-evaluate the cost; the next trial re-linearises.  lambda is kept. */
+ba_status ba_set_params(ba_problem* h, const void* cams, const void* points,
+                        void* stream);
+
+/* Replace the observed pixels (any, [O][2]); the observation structure is
+ * kept, the cost is re-evaluated and the next trial re-linearises. */
+ba_status ba_set_pixels(ba_problem* h, const void* pixels, void* stream);
+
+/* Copy up to cap statistics records (oldest first among the last cap
+ * trials) to host_out; *n_out = number copied.  Synchronises the stream of
+ * the problem.  Returns BA_ERR_NONFINITE if a trial since the last call saw
+ * a non-finite trial cost (such trials are rejected, theta is unchanged). */
+ba_status ba_get_stats(ba_problem* h, ba_iter_stats* host_out, int cap,
+                       int* n_out);
+
+/* Current cost F(theta) and damping lambda, copied to the host.
+ * Synchronises. */
+ba_status ba_get_scalars(ba_problem* h, double* cost, double* lambda);
+
+/* Checkpoint: the number of doubles ba_get_state writes (9C + 3P + 4). */
+size_t ba_state_size(const ba_problem* h);
+/* Write theta, cost, lambda and the trial counter to host_state (host,
+ * ba_state_size doubles; parameters converted to double).  Synchronises. */
+ba_status ba_get_state(ba_problem* h, double* host_state);
+/* Restore a state written by ba_get_state on a problem with the same
+ * C, P, O and precision.  Synchronises. */
+ba_status ba_set_state(ba_problem* h, const double* host_state);
+
+/* Thread-local message of the last failing call ("" if none). */
+const char* ba_last_error(void);
+
+/* ---- step-level entry points (same arithmetic as ba_lm_step) ---------- */
+
+/* Copy the cached symbolic phase (Sec. IV-B): perm_cam [O] lists the
+ * observations in camera order (ties by observation index), rowptr_cam
+ * [C+1]; likewise perm_pt [O], rowptr_pt [P+1].  All dev, int32. */
+ba_status ba_get_csr(ba_problem* h, int32_t* perm_cam, int32_t* rowptr_cam,
+                     int32_t* perm_pt, int32_t* rowptr_pt, void* stream);
+
+/* a1 + a2 at the current theta: residuals, Jacobian blocks (Sec. III-C), the
+ * block normal equations (Alg. 1: A = J^T J and J^T R), then copy
+ *   U [C][9][9], V [P][3][3], gc [C][9], gp [P][3]  (dev, double; any may be
+ *   NULL), and per observation, in input order, the weighted blocks
+ *   sqrt(w) Jc [O][2][9], sqrt(w) Jp [O][2][3] and w [O] (dev, precision
+ *   type; any may be NULL). */
+ba_status ba_linearize(ba_problem* h, double* U, double* V, double* gc,
+                       double* gp, void* Jc, void* Jp, void* w,
+                       void* stream);
+
+/* y = S x for the reduced camera system damped with lambda (Eq. 2 with the
+ * Schur complement of the point blocks), never forming S.  x, y: dev double
+ * [C][9].  Uses the linearisation of the last ba_linearize / LM trial. */
+ba_status ba_schur_matvec(ba_problem* h, double lambda, const double* x,
+                          double* y, void* stream);
+
+/* One damped solve (Eq. 2) at the current linearisation: block-Jacobi PCG
+ * on the reduced system with the given maxiter / tol, then back-
+ * substitution.  dc (dev double [C][9]), dp (dev, precision type, [P][3]);
+ * iters / rel_res (host, may be NULL) get the PCG count and |r|/|b|.
+ * Synchronises. */
+ba_status ba_damped_solve(ba_problem* h, double lambda, int maxiter,
+                          double tol, double* dc, void* dp, int* iters,
+                          double* rel_res, void* stream);
+
+/* ---- stand-alone operations -------------------------------------------- */
+
+/* pixels_out[k] = pi(cams[cam_idx[k]], points[pt_idx[k]]) for k < O.
+ * All pointers dev; precision selects float or double.  Indices are not
+ * checked (they must be in range). */
+ba_status ba_project(int precision, int C, int P, int O, const void* cams,
+                     const void* points, const int32_t* cam_idx,
+                     const int32_t* pt_idx, void* pixels_out, void* stream);
+
+/* Stable sort of n keys in [0, n_keys) (the symbolic phase, Sec. IV-B):
+ * perm_out [n] (dev) lists indices in key order, ties by index; rowptr_out
+ * [n_keys + 1] (dev) are the key ranges.  n may be 0.  Keys out of range
+ * give BA_ERR_INVALID_ARG.  Allocates its scratch on the device and
+ * synchronises the stream. */
+ba_status ba_csr_build(const int32_t* keys, int n, int n_keys,
+                       int32_t* perm_out, int32_t* rowptr_out, void* stream);
+
+/* Number of kernel launches the library has issued in this process (for
+ * launch accounting in benchmarks; graph replays count every node). */
+uint64_t ba_kernel_launch_count(void);
+
+/* Kernel classes timed by ba_profile_trials. */
+enum {
+  BA_K_LIN_CAM = 0,   /* a1+a2 camera-major linearisation pass */
+  BA_K_LIN_PT = 1,    /* a1+a2 point-major linearisation pass */
+  BA_K_SCHUR_CAM = 2, /* a3 camera-major Schur / block-Jacobi pass */
+  BA_K_PASS_A = 3,    /* a4 PCG pass A (point-major, W^T p) */
+  BA_K_PASS_B = 4,    /* a4 PCG pass B (camera-major, W t) */
+  BA_K_COST = 5,      /* a6 trial cost + model reduction pass */
+  BA_K_BACKSUB = 6,   /* a5 back-substitution pass */
+  BA_K_OTHER = 7,     /* per-camera / per-point / scalar kernels */
+  BA_K_COUNT = 8
+};
+
+typedef struct {
+  double ms[BA_K_COUNT];        /* summed device time (CUDA events) */
+  int64_t launches[BA_K_COUNT]; /* launches that did work */
+  double trial_ms;              /* event time of the whole trials */
+} ba_kernel_times;
+
+/* Run iters LM trials (same arithmetic and state changes as ba_solve) with
+ * direct launches and a CUDA event pair around every kernel, on the
+ * problem's stream, and sum the durations per kernel class into *out (host).
+ * PCG launches after convergence (which exit at once) are not counted.
+ * Synchronises. */
+ba_status ba_profile_trials(ba_problem* h, int iters, ba_kernel_times* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BA_GB300_H */

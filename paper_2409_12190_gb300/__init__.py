@@ -1,0 +1,267 @@
+"""GB300 (sm_103a) Levenberg-Marquardt bundle adjustment.
+
+A thin Python binding over the C ABI of ``libba_gb300.so`` (include/ba.h):
+torch tensors supply device memory and streams, every computation runs in
+the library's CUDA kernels.  There is no CPU fallback: without the built
+library every call raises.
+
+    import torch, paper_2409_12190_gb300 as ba
+    prob = ba.Problem(cams, points, cam_idx, pt_idx, pixels,
+                      ba.Options(precision="f32", huber_delta=1.0))
+    prob.solve(20)
+    cams, points = prob.params()
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import dataclasses
+
+import torch
+
+from . import _lib
+from ._lib import BAError, BA_PREC_F32, BA_PREC_F64
+
+__all__ = ["Options", "Problem", "project", "csr_build", "kernel_launch_count",
+           "BAError", "library_path"]
+
+library_path = _lib.LIB_PATH
+
+
+def _L():
+    return _lib.load()
+
+
+def _stream(stream=None) -> ct.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ct.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return None if t is None else ct.c_void_p(t.data_ptr())
+
+
+@dataclasses.dataclass
+class Options:
+    """Solver options (see ba_options in include/ba.h)."""
+    precision: str = "f64"          # "f64" or "f32"
+    huber_delta: float = 0.0
+    lambda0: float = 1e-4
+    up: float = 2.0
+    down: float = 0.0625
+    rho_good: float = 0.75
+    rho_bad: float = 0.25
+    lambda_min: float = 1e-16
+    lambda_max: float = 1e32
+    diag_min: float = 1e-6
+    diag_max: float = 1e32
+    pcg_maxiter: int = 250
+    pcg_tol: float = 1e-4
+    use_graph: bool = True
+    max_stats: int = 4096
+
+    @property
+    def dtype(self):
+        return torch.float32 if self.precision == "f32" else torch.float64
+
+    def to_c(self) -> _lib.ba_options:
+        o = _lib.ba_options()
+        _lib.check(_L().ba_options_default(ct.byref(o)))
+        if self.precision not in ("f32", "f64"):
+            raise ValueError("precision must be 'f32' or 'f64'")
+        o.precision = BA_PREC_F32 if self.precision == "f32" else BA_PREC_F64
+        for f in ("huber_delta", "lambda0", "up", "down", "rho_good", "rho_bad", "lambda_min",
+                  "lambda_max", "diag_min", "diag_max", "pcg_tol"):
+            setattr(o, f, float(getattr(self, f)))
+        o.pcg_maxiter = int(self.pcg_maxiter)
+        o.use_graph = int(bool(self.use_graph))
+        o.max_stats = int(self.max_stats)
+        return o
+
+
+def _dev(t, dtype, device):
+    t = torch.as_tensor(t)
+    return t.to(device=device, dtype=dtype).contiguous()
+
+
+class Problem:
+    """One bundle-adjustment problem resident on the GPU.
+
+    cams [C, 9] (omega, t, f, k1, k2), points [P, 3], cam_idx / pt_idx [O]
+    int32, pixels [O, 2]; any device (copied), float dtype converted to the
+    options' precision."""
+
+    def __init__(self, cams, points, cam_idx, pt_idx, pixels, options: Options | None = None,
+                 device="cuda", stream=None):
+        self.options = options or Options()
+        self.dtype = self.options.dtype
+        self.device = torch.device(device)
+        cams = _dev(cams, self.dtype, self.device)
+        points = _dev(points, self.dtype, self.device)
+        ci = _dev(cam_idx, torch.int32, self.device)
+        pi = _dev(pt_idx, torch.int32, self.device)
+        px = _dev(pixels, self.dtype, self.device)
+        self.C, self.P, self.O = int(cams.shape[0]), int(points.shape[0]), int(ci.shape[0])
+        h = ct.c_void_p()
+        o = self.options.to_c()
+        _lib.check(_L().ba_problem_create(ct.byref(h), self.C, self.P, self.O, _ptr(cams),
+                                          _ptr(points), _ptr(ci), _ptr(pi), _ptr(px), ct.byref(o),
+                                          _stream(stream)))
+        self._h = h
+
+    # -- lifetime ---------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            _L().ba_problem_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- LM -----------------------------------------------------------------
+    def lm_step(self, stream=None):
+        _lib.check(_L().ba_lm_step(self._h, _stream(stream)))
+
+    def solve(self, iters: int, stream=None):
+        _lib.check(_L().ba_solve(self._h, int(iters), _stream(stream)))
+
+    def params(self, stream=None):
+        cams = torch.empty((self.C, 9), dtype=self.dtype, device=self.device)
+        pts = torch.empty((self.P, 3), dtype=self.dtype, device=self.device)
+        _lib.check(_L().ba_get_params(self._h, _ptr(cams), _ptr(pts), _stream(stream)))
+        return cams, pts
+
+    def get_params_into(self, cams_out, points_out, stream=None):
+        """Copy theta into caller tensors (device or pinned host)."""
+        _lib.check(_L().ba_get_params(self._h, _ptr(cams_out), _ptr(points_out), _stream(stream)))
+
+    def set_params(self, cams=None, points=None, stream=None):
+        c = None if cams is None else cams.contiguous()
+        p = None if points is None else points.contiguous()
+        for t in (c, p):
+            if t is not None and t.dtype != self.dtype:
+                raise TypeError(f"expected {self.dtype}")
+        _lib.check(_L().ba_set_params(self._h, _ptr(c), _ptr(p), _stream(stream)))
+
+    def set_pixels(self, pixels, stream=None):
+        px = pixels.contiguous()
+        if px.dtype != self.dtype:
+            raise TypeError(f"expected {self.dtype}")
+        _lib.check(_L().ba_set_pixels(self._h, _ptr(px), _stream(stream)))
+
+    def stats(self, cap: int = 4096, raise_nonfinite: bool = True):
+        buf = (_lib.ba_iter_stats * cap)()
+        n = ct.c_int()
+        st = _L().ba_get_stats(self._h, buf, cap, ct.byref(n))
+        out = [dict(cost=s.cost, cost_trial=s.cost_trial, model=s.model, rho=s.rho, lam=s.lambda_,
+                    pcg_rel_res=s.pcg_rel_res, accepted=bool(s.accepted), pcg_iters=s.pcg_iters,
+                    precond_fallbacks=s.precond_fallbacks) for s in buf[:n.value]]
+        if st != _lib.BA_OK and (raise_nonfinite or st != 3):
+            _lib.check(st)
+        return out
+
+    def scalars(self):
+        c, l = ct.c_double(), ct.c_double()
+        _lib.check(_L().ba_get_scalars(self._h, ct.byref(c), ct.byref(l)))
+        return c.value, l.value
+
+    def get_state(self):
+        n = _L().ba_state_size(self._h)
+        out = torch.empty(n, dtype=torch.float64)
+        _lib.check(_L().ba_get_state(self._h, _ptr(out)))
+        return out
+
+    def set_state(self, state):
+        s = torch.as_tensor(state, dtype=torch.float64).contiguous().cpu()
+        if s.numel() != _L().ba_state_size(self._h):
+            raise ValueError("state size mismatch")
+        _lib.check(_L().ba_set_state(self._h, _ptr(s)))
+
+    def profile_trials(self, iters: int):
+        """Run iters LM trials with a CUDA event pair around every launch;
+        returns {kernel class: (total ms, launches)} and the trials' total ms."""
+        t = _lib.ba_kernel_times()
+        _lib.check(_L().ba_profile_trials(self._h, int(iters), ct.byref(t)))
+        per = {name: (t.ms[i], int(t.launches[i])) for i, name in enumerate(_lib.BA_K_NAMES)}
+        return per, t.trial_ms
+
+    # -- step-level -----------------------------------------------------------
+    def csr(self, stream=None):
+        d = self.device
+        pc = torch.empty(self.O, dtype=torch.int32, device=d)
+        rc = torch.empty(self.C + 1, dtype=torch.int32, device=d)
+        pp = torch.empty(self.O, dtype=torch.int32, device=d)
+        rp = torch.empty(self.P + 1, dtype=torch.int32, device=d)
+        _lib.check(_L().ba_get_csr(self._h, _ptr(pc), _ptr(rc), _ptr(pp), _ptr(rp), _stream(stream)))
+        return pc, rc, pp, rp
+
+    def linearize(self, blocks=True, jacobians=True, stream=None):
+        d = self.device
+        f64 = torch.float64
+        out = {}
+        if blocks:
+            out["U"] = torch.empty((self.C, 9, 9), dtype=f64, device=d)
+            out["V"] = torch.empty((self.P, 3, 3), dtype=f64, device=d)
+            out["gc"] = torch.empty((self.C, 9), dtype=f64, device=d)
+            out["gp"] = torch.empty((self.P, 3), dtype=f64, device=d)
+        if jacobians:
+            out["Jc"] = torch.empty((self.O, 2, 9), dtype=self.dtype, device=d)
+            out["Jp"] = torch.empty((self.O, 2, 3), dtype=self.dtype, device=d)
+            out["w"] = torch.empty((self.O,), dtype=self.dtype, device=d)
+        g = out.get
+        _lib.check(_L().ba_linearize(self._h, _ptr(g("U")), _ptr(g("V")), _ptr(g("gc")),
+                                     _ptr(g("gp")), _ptr(g("Jc")), _ptr(g("Jp")), _ptr(g("w")),
+                                     _stream(stream)))
+        return out
+
+    def schur_matvec(self, lam: float, x, stream=None):
+        x = x.to(device=self.device, dtype=torch.float64).contiguous()
+        y = torch.empty_like(x)
+        _lib.check(_L().ba_schur_matvec(self._h, float(lam), _ptr(x), _ptr(y), _stream(stream)))
+        return y
+
+    def damped_solve(self, lam: float, maxiter: int, tol: float, stream=None):
+        dc = torch.empty((self.C, 9), dtype=torch.float64, device=self.device)
+        dp = torch.empty((self.P, 3), dtype=self.dtype, device=self.device)
+        it = ct.c_int()
+        rel = ct.c_double()
+        _lib.check(_L().ba_damped_solve(self._h, float(lam), int(maxiter), float(tol), _ptr(dc),
+                                        _ptr(dp), ct.byref(it), ct.byref(rel), _stream(stream)))
+        return dc, dp, it.value, rel.value
+
+
+def project(cams, points, cam_idx, pt_idx, stream=None):
+    """pi(theta_c(k), X_p(k)) for every observation (device tensors)."""
+    if cams.dtype not in (torch.float32, torch.float64) or points.dtype != cams.dtype:
+        raise TypeError("cams and points must share a float32/float64 dtype")
+    prec = BA_PREC_F32 if cams.dtype == torch.float32 else BA_PREC_F64
+    cams, points = cams.contiguous(), points.contiguous()
+    ci = cam_idx.to(torch.int32).contiguous()
+    pi = pt_idx.to(torch.int32).contiguous()
+    out = torch.empty((ci.shape[0], 2), dtype=cams.dtype, device=cams.device)
+    _lib.check(_L().ba_project(prec, cams.shape[0], points.shape[0], ci.shape[0], _ptr(cams),
+                               _ptr(points), _ptr(ci), _ptr(pi), _ptr(out), _stream(stream)))
+    return out
+
+
+def csr_build(keys, n_keys: int, stream=None):
+    """Stable sort of int32 device keys in [0, n_keys): (perm, rowptr)."""
+    k = keys.to(torch.int32).contiguous()
+    perm = torch.empty(k.shape[0], dtype=torch.int32, device=k.device)
+    rowptr = torch.empty(n_keys + 1, dtype=torch.int32, device=k.device)
+    _lib.check(_L().ba_csr_build(_ptr(k) if k.numel() else None, k.shape[0], int(n_keys),
+                                 _ptr(perm) if k.numel() else None, _ptr(rowptr), _stream(stream)))
+    return perm, rowptr
+
+
+def kernel_launch_count() -> int:
+    return int(_L().ba_kernel_launch_count())

@@ -1,0 +1,122 @@
+"""ctypes declarations of the C ABI in include/ba.h (argument marshalling only)."""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libba_gb300.so")
+
+BA_OK = 0
+STATUS_NAMES = {0: "BA_OK", 1: "BA_ERR_INVALID_ARG", 2: "BA_ERR_CUDA", 3: "BA_ERR_NONFINITE",
+                4: "BA_ERR_TIMEOUT", 5: "BA_ERR_NOT_CONVERGED", 6: "BA_ERR_OOM", 7: "BA_ERR_STATE"}
+BA_PREC_F64 = 0
+BA_PREC_F32 = 1
+
+
+class ba_options(ct.Structure):
+    _fields_ = [
+        ("precision", ct.c_int),
+        ("huber_delta", ct.c_double),
+        ("lambda0", ct.c_double),
+        ("up", ct.c_double),
+        ("down", ct.c_double),
+        ("rho_good", ct.c_double),
+        ("rho_bad", ct.c_double),
+        ("lambda_min", ct.c_double),
+        ("lambda_max", ct.c_double),
+        ("diag_min", ct.c_double),
+        ("diag_max", ct.c_double),
+        ("pcg_maxiter", ct.c_int),
+        ("pcg_tol", ct.c_double),
+        ("use_graph", ct.c_int),
+        ("max_stats", ct.c_int),
+    ]
+
+
+class ba_iter_stats(ct.Structure):
+    _fields_ = [
+        ("cost", ct.c_double),
+        ("cost_trial", ct.c_double),
+        ("model", ct.c_double),
+        ("rho", ct.c_double),
+        ("lambda_", ct.c_double),
+        ("pcg_rel_res", ct.c_double),
+        ("accepted", ct.c_int32),
+        ("pcg_iters", ct.c_int32),
+        ("precond_fallbacks", ct.c_int32),
+        ("reserved", ct.c_int32),
+    ]
+
+
+BA_K_NAMES = ["lin_cam", "lin_pt", "schur_cam", "pass_a", "pass_b", "cost", "backsub", "other"]
+
+
+class ba_kernel_times(ct.Structure):
+    _fields_ = [("ms", ct.c_double * 8), ("launches", ct.c_int64 * 8), ("trial_ms", ct.c_double)]
+
+
+_VP = ct.c_void_p
+_I = ct.c_int
+_D = ct.c_double
+_S = ct.c_int  # ba_status
+
+# name -> (restype, argtypes)
+SIGNATURES = {
+    "ba_options_default": (_S, [ct.POINTER(ba_options)]),
+    "ba_problem_create": (_S, [ct.POINTER(_VP), _I, _I, _I, _VP, _VP, _VP, _VP, _VP,
+                               ct.POINTER(ba_options), _VP]),
+    "ba_problem_destroy": (_S, [_VP]),
+    "ba_lm_step": (_S, [_VP, _VP]),
+    "ba_solve": (_S, [_VP, _I, _VP]),
+    "ba_get_params": (_S, [_VP, _VP, _VP, _VP]),
+    "ba_set_params": (_S, [_VP, _VP, _VP, _VP]),
+    "ba_set_pixels": (_S, [_VP, _VP, _VP]),
+    "ba_get_stats": (_S, [_VP, ct.POINTER(ba_iter_stats), _I, ct.POINTER(_I)]),
+    "ba_get_scalars": (_S, [_VP, ct.POINTER(_D), ct.POINTER(_D)]),
+    "ba_state_size": (ct.c_size_t, [_VP]),
+    "ba_get_state": (_S, [_VP, _VP]),
+    "ba_set_state": (_S, [_VP, _VP]),
+    "ba_last_error": (ct.c_char_p, []),
+    "ba_get_csr": (_S, [_VP, _VP, _VP, _VP, _VP, _VP]),
+    "ba_linearize": (_S, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "ba_schur_matvec": (_S, [_VP, _D, _VP, _VP, _VP]),
+    "ba_damped_solve": (_S, [_VP, _D, _I, _D, _VP, _VP, ct.POINTER(_I), ct.POINTER(_D), _VP]),
+    "ba_project": (_S, [_I, _I, _I, _I, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "ba_csr_build": (_S, [_VP, _I, _I, _VP, _VP, _VP]),
+    "ba_kernel_launch_count": (ct.c_uint64, []),
+    "ba_profile_trials": (_S, [_VP, _I, ct.POINTER(ba_kernel_times)]),
+}
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load the shared library; raises if it has not been built."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise ImportError(
+            f"{p} not found: build it first with "
+            "`python -c 'import __graft_entry__ as g; g.build()'` (nvcc, sm_103a)")
+    lib = ct.CDLL(p)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    if path is None:
+        _lib = lib
+    return lib
+
+
+class BAError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def check(status: int):
+    if status != BA_OK:
+        raise BAError(status, load().ba_last_error().decode(errors="replace"))

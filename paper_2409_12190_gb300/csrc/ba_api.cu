@@ -1,0 +1,892 @@
+// C ABI of the LM bundle-adjustment library (include/ba.h): the problem
+// object, its device buffers, the stream-ordered LM trial and its CUDA graph.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "ba.h"
+#include "ba_internal.h"
+#include "ba_kernels.cuh"
+
+namespace ba {
+
+static std::atomic<uint64_t> g_launches{0};
+static thread_local bool g_capturing = false;
+
+void count_launch(uint64_t n) {
+  if (!g_capturing) g_launches.fetch_add(n, std::memory_order_relaxed);
+}
+
+}  // namespace ba
+
+namespace {
+
+thread_local std::string g_err;
+
+ba_status fail(ba_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return st;
+}
+
+#define CU(call)                                                                       \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess) {                                                           \
+      ba_status s_ = (e_ == cudaErrorMemoryAllocation) ? BA_ERR_OOM : BA_ERR_CUDA;      \
+      return fail(s_, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                  __LINE__);                                                           \
+    }                                                                                  \
+  } while (0)
+
+inline unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+struct ba_problem {
+  int C = 0, P = 0, O = 0, prec = 0;
+  size_t tsize = 8;
+  ba_options opt{};
+  cudaStream_t s = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  std::vector<void*> allocs;
+  // structure (symbolic phase)
+  int32_t *cam_idx = nullptr, *pt_idx = nullptr;
+  int32_t *perm_cam = nullptr, *rowptr_cam = nullptr, *perm_pt = nullptr, *rowptr_pt = nullptr;
+  int32_t *cm_pt = nullptr, *pm_cam = nullptr;
+  void *cm_px = nullptr, *pm_px = nullptr, *px_in = nullptr;
+  int npieces = 0;
+  int32_t *piece_cam = nullptr, *piece_beg = nullptr, *piece_end = nullptr, *cam_piece_ptr = nullptr;
+  // parameters, double-buffered (current / trial)
+  void *cams = nullptr, *pts = nullptr;
+  // linearisation
+  void *camtab = nullptr, *Jcm = nullptr, *Jpm = nullptr;
+  double *U = nullptr, *gc = nullptr, *V = nullptr, *gp = nullptr;
+  void *Vinv = nullptr, *y0 = nullptr;
+  // PCG
+  double *Minv = nullptr, *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
+  void *pT = nullptr, *xT = nullptr, *tpt = nullptr, *dp = nullptr;
+  double* part = nullptr;
+  int ncb = 0, npb = 0;
+  double *dot_pq = nullptr, *dot_rz = nullptr, *dot_rr = nullptr, *dot_bb = nullptr;
+  double *dot_gc = nullptr, *dot_gp = nullptr;
+  ba::DevState* st = nullptr;
+  ba_iter_stats* stats = nullptr;
+  int cap = 0;
+  // graph of one trial
+  cudaGraphExec_t gexec = nullptr;
+  size_t gnodes = 0;
+  // per-launch CUDA events (ba_profile_trials only)
+  struct ProfRec {
+    int kind, trial, k;
+    cudaEvent_t a, b;
+  };
+  std::vector<ProfRec>* prof = nullptr;
+  int prof_trial = 0;
+
+  template <typename X>
+  cudaError_t alloc(X** ptr, size_t bytes) {
+    void* v = nullptr;
+    cudaError_t e = cudaMalloc(&v, bytes > 0 ? bytes : 16);
+    if (e == cudaSuccess) {
+      allocs.push_back(v);
+      *ptr = static_cast<X*>(v);
+    }
+    return e;
+  }
+  ~ba_problem() {
+    if (gexec) cudaGraphExecDestroy(gexec);
+    for (void* v : allocs) cudaFree(v);
+    if (ev_in) cudaEventDestroy(ev_in);
+    if (ev_out) cudaEventDestroy(ev_out);
+    if (s) cudaStreamDestroy(s);
+  }
+};
+
+namespace {
+
+using namespace ba;
+
+// Order the problem's internal stream after the caller's stream.
+ba_status enter(ba_problem* h, void* stream) {
+  CU(cudaEventRecord(h->ev_in, (cudaStream_t)stream));
+  CU(cudaStreamWaitEvent(h->s, h->ev_in, 0));
+  return BA_OK;
+}
+// Order the caller's stream after the problem's internal stream.
+ba_status leave(ba_problem* h, void* stream) {
+  CU(cudaEventRecord(h->ev_out, h->s));
+  CU(cudaStreamWaitEvent((cudaStream_t)stream, h->ev_out, 0));
+  return BA_OK;
+}
+
+// Event pair around one launch when profiling is on (no-op otherwise).
+struct Prof {
+  ba_problem* h;
+  ba_problem::ProfRec rec{};
+  Prof(ba_problem* hh, int kind, int k = -1) : h(hh) {
+    if (!h->prof) return;
+    rec.kind = kind;
+    rec.trial = h->prof_trial;
+    rec.k = k;
+    cudaEventCreate(&rec.a);
+    cudaEventCreate(&rec.b);
+    cudaEventRecord(rec.a, h->s);
+  }
+  ~Prof() {
+    if (!h->prof) return;
+    cudaEventRecord(rec.b, h->s);
+    h->prof->push_back(rec);
+  }
+};
+
+template <typename T>
+void enqueue_lin(ba_problem* h, int gate) {
+  cudaStream_t s = h->s;
+  const T delta = (T)(h->opt.huber_delta > 0 ? h->opt.huber_delta : 0.0);
+  {
+    Prof pr(h, BA_K_OTHER, -2);
+    k_cam_prep<T><<<nblk(h->C, 128), 128, 0, s>>>(h->C, (const T*)h->cams, h->st, gate, (T*)h->camtab);
+  }
+  {
+    Prof pr(h, BA_K_LIN_CAM, -2);
+    k_lin_cam<T><<<h->npieces, PIECE_THREADS, 0, s>>>(
+        h->piece_cam, h->piece_beg, h->piece_end, h->cm_pt, (const T*)h->cm_px, (const T*)h->pts,
+        (const T*)h->camtab, h->st, gate, delta, h->O, h->P, (T*)h->Jcm, h->part);
+  }
+  {
+    Prof pr(h, BA_K_OTHER, -2);
+    k_cam_combine_lin<<<nblk(h->C, 128), 128, 0, s>>>(h->C, h->cam_piece_ptr, h->part, h->st, gate, h->U, h->gc);
+  }
+  {
+    Prof pr(h, BA_K_LIN_PT, -2);
+    k_lin_pt<T><<<nblk(h->P, PT_THREADS), PT_THREADS, 0, s>>>(
+        h->P, h->O, h->rowptr_pt, h->pm_cam, (const T*)h->pm_px, (const T*)h->pts, (const T*)h->camtab, h->st,
+        gate, delta, (T*)h->Jpm, h->V, h->gp);
+  }
+  count_launch(4);
+}
+
+template <typename T>
+void enqueue_solve(ba_problem* h, const double* lam_ptr, int maxiter, double tol) {
+  cudaStream_t s = h->s;
+  const double dmin = h->opt.diag_min, dmax = h->opt.diag_max;
+  {
+    Prof pr(h, BA_K_OTHER);
+    k_pt_damp<T><<<nblk(h->P, PT_THREADS), PT_THREADS, 0, s>>>(h->P, h->V, h->gp, lam_ptr, dmin, dmax,
+                                                              (T*)h->Vinv, (T*)h->y0);
+  }
+  {
+    Prof pr(h, BA_K_SCHUR_CAM);
+    k_schur_cam<T><<<h->npieces, PIECE_THREADS, 0, s>>>(h->piece_cam, h->piece_beg, h->piece_end, h->cm_pt,
+                                                       (const T*)h->Jcm, (const T*)h->camtab, (const T*)h->Vinv,
+                                                       (const T*)h->y0, h->O, h->part);
+  }
+  {
+    Prof pr(h, BA_K_OTHER);
+    k_cam_combine_schur<T><<<h->ncb, CAM_THREADS, 0, s>>>(
+        h->C, h->cam_piece_ptr, h->part, h->U, h->gc, lam_ptr, dmin, dmax, h->Minv, h->x, h->r, h->z, h->p,
+        (T*)h->pT, h->dot_rz + h->ncb, h->dot_bb, h->st);
+  }
+  count_launch(3);
+  for (int k = 0; k < maxiter; ++k) {
+    {
+      Prof pr(h, BA_K_PASS_A, k);
+      k_pass_a<T, 0><<<nblk(h->P, PT_THREADS), PT_THREADS, 0, s>>>(
+          h->P, h->O, h->rowptr_pt, h->pm_cam, (const T*)h->Jpm, (const T*)h->camtab, (const T*)h->pT,
+          (const T*)h->Vinv, h->st, 1, (T*)h->tpt, nullptr, nullptr, nullptr, nullptr);
+    }
+    {
+      Prof pr(h, BA_K_PASS_B, k);
+      k_pass_b<T><<<h->npieces, PIECE_THREADS, 0, s>>>(h->piece_cam, h->piece_beg, h->piece_end, h->cm_pt,
+                                                      (const T*)h->Jcm, (const T*)h->camtab, (const T*)h->tpt,
+                                                      h->st, 1, h->O, h->part);
+    }
+    {
+      Prof pr(h, BA_K_OTHER, k);
+      k_pcg_q<<<h->ncb, CAM_THREADS, 0, s>>>(h->C, h->cam_piece_ptr, h->part, h->U, lam_ptr, dmin, dmax, h->p,
+                                             h->q, h->dot_pq, h->st, 1);
+    }
+    {
+      Prof pr(h, BA_K_OTHER, k);
+      k_pcg_update<<<h->ncb, CAM_THREADS, 0, s>>>(h->C, h->ncb, k, h->dot_pq, h->dot_rz, h->dot_rr, h->p, h->q,
+                                                  h->x, h->r, h->z, h->Minv, h->st);
+    }
+    {
+      Prof pr(h, BA_K_OTHER, k);
+      k_pcg_direction<T><<<h->ncb, CAM_THREADS, 0, s>>>(h->C, h->ncb, k, tol, h->dot_rz, h->dot_rr, h->dot_bb,
+                                                       h->z, h->p, (T*)h->pT, h->st);
+    }
+    count_launch(5);
+  }
+  {
+    Prof pr(h, BA_K_OTHER);
+    k_cam_trial<T><<<h->ncb, CAM_THREADS, 0, s>>>(h->C, h->x, h->gc, (T*)h->cams, h->st, (T*)h->xT, h->dot_gc);
+  }
+  {
+    Prof pr(h, BA_K_BACKSUB);
+    k_pass_a<T, 1><<<h->npb, PT_THREADS, 0, s>>>(h->P, h->O, h->rowptr_pt, h->pm_cam, (const T*)h->Jpm,
+                                                 (const T*)h->camtab, (const T*)h->xT, (const T*)h->Vinv, h->st,
+                                                 0, (T*)h->dp, (const T*)h->y0, h->gp, (T*)h->pts, h->dot_gp);
+  }
+  count_launch(2);
+}
+
+template <typename T>
+void enqueue_trial(ba_problem* h) {
+  enqueue_lin<T>(h, 1);
+  enqueue_solve<T>(h, &h->st->lam, h->opt.pcg_maxiter, h->opt.pcg_tol);
+  const T delta = (T)(h->opt.huber_delta > 0 ? h->opt.huber_delta : 0.0);
+  {
+    Prof pr(h, BA_K_COST);
+    k_cost_cam<T, true><<<h->npieces, PIECE_THREADS, 0, h->s>>>(
+        h->piece_cam, h->piece_beg, h->piece_end, h->cm_pt, (const T*)h->cm_px, (const T*)h->cams,
+        (const T*)h->pts, h->st, 1, delta, h->C, h->P, h->O, (const T*)h->Jcm, (const T*)h->camtab,
+        (const T*)h->xT, (const T*)h->dp, h->part);
+  }
+  const ba_options& o = h->opt;
+  {
+    Prof pr(h, BA_K_OTHER);
+    k_lm_control<<<1, 256, 0, h->s>>>(h->npieces, h->part, h->ncb, h->dot_gc, h->npb, h->dot_gp, o.up, o.down,
+                                      o.rho_good, o.rho_bad, o.lambda_min, o.lambda_max, h->st, h->stats, h->cap);
+  }
+  count_launch(2);
+}
+
+template <typename T>
+void enqueue_cost(ba_problem* h) {
+  const T delta = (T)(h->opt.huber_delta > 0 ? h->opt.huber_delta : 0.0);
+  k_cost_cam<T, false><<<h->npieces, PIECE_THREADS, 0, h->s>>>(
+      h->piece_cam, h->piece_beg, h->piece_end, h->cm_pt, (const T*)h->cm_px, (const T*)h->cams,
+      (const T*)h->pts, h->st, 0, delta, h->C, h->P, h->O, nullptr, nullptr, nullptr, nullptr, h->part);
+  k_cost_finalize<<<1, 256, 0, h->s>>>(h->npieces, h->part, h->st);
+  count_launch(2);
+}
+
+void enqueue_trial_any(ba_problem* h) {
+  if (h->prec == BA_PREC_F32) enqueue_trial<float>(h);
+  else enqueue_trial<double>(h);
+}
+
+ba_status check_options(const ba_options* o) {
+  if (o->precision != BA_PREC_F64 && o->precision != BA_PREC_F32)
+    return fail(BA_ERR_INVALID_ARG, "precision must be BA_PREC_F64 or BA_PREC_F32");
+  if (!(o->lambda0 > 0) || !(o->up > 1) || !(o->down > 0 && o->down < 1) || !(o->lambda_min > 0) ||
+      !(o->lambda_max >= o->lambda_min) || !(o->diag_min >= 0) || !(o->diag_max >= o->diag_min))
+    return fail(BA_ERR_INVALID_ARG, "damping options out of range");
+  if (o->pcg_maxiter < 0 || o->pcg_maxiter > 100000 || !(o->pcg_tol >= 0))
+    return fail(BA_ERR_INVALID_ARG, "pcg_maxiter must be in [0, 100000] and pcg_tol >= 0");
+  if (o->max_stats < 1 || o->max_stats > (1 << 24)) return fail(BA_ERR_INVALID_ARG, "max_stats out of range");
+  if (!(o->huber_delta >= 0) && !(o->huber_delta <= 0))
+    return fail(BA_ERR_INVALID_ARG, "huber_delta is NaN");
+  return BA_OK;
+}
+
+template <typename T>
+ba_status create_impl(ba_problem* h, const void* cams, const void* points, const int32_t* cam_idx,
+                      const int32_t* pt_idx, const void* pixels) {
+  const long long C = h->C, P = h->P, O = h->O;
+  const size_t ts = sizeof(T);
+  cudaStream_t s = h->s;
+  CU(h->alloc(&h->st, sizeof(DevState)));
+  CU(cudaMemsetAsync(h->st, 0, sizeof(DevState), s));
+  {
+    DevState init{};
+    init.lam = h->opt.lambda0;
+    init.lam_probe = h->opt.lambda0;
+    init.need_lin = 1;
+    CU(cudaMemcpyAsync(h->st, &init, sizeof(DevState), cudaMemcpyHostToDevice, s));
+  }
+  CU(h->alloc(&h->cams, 2 * 9 * C * ts));
+  CU(h->alloc(&h->pts, 2 * 3 * P * ts));
+  CU(h->alloc(&h->cam_idx, O * 4));
+  CU(h->alloc(&h->pt_idx, O * 4));
+  CU(h->alloc(&h->px_in, 2 * O * ts));
+  CU(cudaMemcpyAsync(h->cams, cams, 9 * C * ts, cudaMemcpyDefault, s));
+  CU(cudaMemcpyAsync(h->pts, points, 3 * P * ts, cudaMemcpyDefault, s));
+  CU(cudaMemcpyAsync(h->cam_idx, cam_idx, O * 4, cudaMemcpyDefault, s));
+  CU(cudaMemcpyAsync(h->pt_idx, pt_idx, O * 4, cudaMemcpyDefault, s));
+  CU(cudaMemcpyAsync(h->px_in, pixels, 2 * O * ts, cudaMemcpyDefault, s));
+  const long long nv = std::max(O, std::max(9 * C, 3 * P));
+  k_validate<T><<<nblk(nv, 256), 256, 0, s>>>(h->C, h->P, h->O, (const T*)h->cams, (const T*)h->pts,
+                                              h->cam_idx, h->pt_idx, (const T*)h->px_in, h->st);
+  count_launch();
+  int err = 0;
+  CU(cudaMemcpyAsync(&err, &h->st->err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CU(cudaStreamSynchronize(s));
+  if (err & 1) return fail(BA_ERR_INVALID_ARG, "observation index out of range");
+  if (err & 2) return fail(BA_ERR_NONFINITE, "non-finite camera, point or pixel value");
+
+  // symbolic phase: stable sorts by camera and by point
+  CU(h->alloc(&h->perm_cam, O * 4));
+  CU(h->alloc(&h->perm_pt, O * 4));
+  CU(h->alloc(&h->rowptr_cam, (C + 1) * 4));
+  CU(h->alloc(&h->rowptr_pt, (P + 1) * 4));
+  void* scratch = nullptr;
+  CU(cudaMalloc(&scratch, csr_scratch_bytes(h->O)));
+  cudaError_t e1 = csr_build_async(h->cam_idx, h->O, h->C, h->perm_cam, h->rowptr_cam, scratch, &h->st->err, s);
+  cudaError_t e2 = csr_build_async(h->pt_idx, h->O, h->P, h->perm_pt, h->rowptr_pt, scratch, &h->st->err, s);
+  cudaError_t e3 = cudaStreamSynchronize(s);
+  cudaFree(scratch);
+  CU(e1);
+  CU(e2);
+  CU(e3);
+
+  // pieces: each camera's slots cut into runs of at most PIECE
+  std::vector<int32_t> rp(C + 1);
+  CU(cudaMemcpy(rp.data(), h->rowptr_cam, (C + 1) * 4, cudaMemcpyDeviceToHost));
+  std::vector<int32_t> pc, pb, pe, cpp(C + 1);
+  for (long long c = 0; c < C; ++c) {
+    cpp[c] = (int32_t)pc.size();
+    const int n = rp[c + 1] - rp[c];
+    const int k = (n + PIECE - 1) / PIECE;
+    for (int i = 0; i < k; ++i) {
+      pc.push_back((int32_t)c);
+      pb.push_back(rp[c] + (int)((long long)n * i / k));
+      pe.push_back(rp[c] + (int)((long long)n * (i + 1) / k));
+    }
+  }
+  cpp[C] = (int32_t)pc.size();
+  h->npieces = (int)pc.size();
+  CU(h->alloc(&h->piece_cam, pc.size() * 4));
+  CU(h->alloc(&h->piece_beg, pc.size() * 4));
+  CU(h->alloc(&h->piece_end, pc.size() * 4));
+  CU(h->alloc(&h->cam_piece_ptr, (C + 1) * 4));
+  CU(cudaMemcpy(h->piece_cam, pc.data(), pc.size() * 4, cudaMemcpyHostToDevice));
+  CU(cudaMemcpy(h->piece_beg, pb.data(), pb.size() * 4, cudaMemcpyHostToDevice));
+  CU(cudaMemcpy(h->piece_end, pe.data(), pe.size() * 4, cudaMemcpyHostToDevice));
+  CU(cudaMemcpy(h->cam_piece_ptr, cpp.data(), (C + 1) * 4, cudaMemcpyHostToDevice));
+
+  // observation data in both orders
+  CU(h->alloc(&h->cm_pt, O * 4));
+  CU(h->alloc(&h->pm_cam, O * 4));
+  CU(h->alloc(&h->cm_px, 2 * O * ts));
+  CU(h->alloc(&h->pm_px, 2 * O * ts));
+  k_gather_obs<T><<<nblk(O, 256), 256, 0, s>>>(h->O, h->perm_cam, h->perm_pt, h->cam_idx, h->pt_idx,
+                                               (const T*)h->px_in, h->cm_pt, (T*)h->cm_px, h->pm_cam,
+                                               (T*)h->pm_px);
+  count_launch();
+
+  // linearisation and solver buffers
+  CU(h->alloc(&h->camtab, CT * C * ts));
+  CU(h->alloc(&h->Jcm, (size_t)NPLANE * O * ts));
+  CU(h->alloc(&h->Jpm, (size_t)NPLANE * O * ts));
+  CU(h->alloc(&h->U, 45 * C * 8));
+  CU(h->alloc(&h->gc, 9 * C * 8));
+  CU(h->alloc(&h->V, 6 * P * 8));
+  CU(h->alloc(&h->gp, 3 * P * 8));
+  CU(h->alloc(&h->Vinv, 6 * P * ts));
+  CU(h->alloc(&h->y0, 3 * P * ts));
+  CU(h->alloc(&h->Minv, 45 * C * 8));
+  CU(h->alloc(&h->x, 9 * C * 8));
+  CU(h->alloc(&h->r, 9 * C * 8));
+  CU(h->alloc(&h->z, 9 * C * 8));
+  CU(h->alloc(&h->p, 9 * C * 8));
+  CU(h->alloc(&h->q, 9 * C * 8));
+  CU(h->alloc(&h->pT, 9 * C * ts));
+  CU(h->alloc(&h->xT, 9 * C * ts));
+  CU(h->alloc(&h->tpt, 3 * P * ts));
+  CU(h->alloc(&h->dp, 3 * P * ts));
+  CU(h->alloc(&h->part, (size_t)PART * std::max(h->npieces, 1) * 8));
+  h->ncb = (int)nblk(C, CAM_THREADS);
+  h->npb = (int)nblk(P, PT_THREADS);
+  CU(h->alloc(&h->dot_pq, h->ncb * 8));
+  CU(h->alloc(&h->dot_rz, 2 * h->ncb * 8));
+  CU(h->alloc(&h->dot_rr, h->ncb * 8));
+  CU(h->alloc(&h->dot_bb, h->ncb * 8));
+  CU(h->alloc(&h->dot_gc, h->ncb * 8));
+  CU(h->alloc(&h->dot_gp, h->npb * 8));
+  h->cap = h->opt.max_stats;
+  CU(h->alloc(&h->stats, (size_t)h->cap * sizeof(ba_iter_stats)));
+  CU(cudaMemsetAsync(h->stats, 0, (size_t)h->cap * sizeof(ba_iter_stats), s));
+  CU(cudaMemsetAsync(h->x, 0, 9 * C * 8, s));
+  CU(cudaMemsetAsync(h->dp, 0, 3 * P * ts, s));
+  CU(cudaMemsetAsync(h->xT, 0, 9 * C * ts, s));
+
+  enqueue_cost<T>(h);
+  CU(cudaGetLastError());
+  CU(cudaMemcpyAsync(&err, &h->st->err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CU(cudaStreamSynchronize(s));
+  if (err & 2) return fail(BA_ERR_NONFINITE, "non-finite initial cost");
+  return BA_OK;
+}
+
+ba_status run_cost(ba_problem* h) {
+  if (h->prec == BA_PREC_F32) enqueue_cost<float>(h);
+  else enqueue_cost<double>(h);
+  CU(cudaGetLastError());
+  return BA_OK;
+}
+
+ba_status set_flag(ba_problem* h, size_t offset, int value) {
+  // write one int of DevState (pageable source: copied before return)
+  CU(cudaMemcpyAsync(reinterpret_cast<char*>(h->st) + offset, &value, sizeof(int), cudaMemcpyHostToDevice, h->s));
+  CU(cudaStreamSynchronize(h->s));
+  return BA_OK;
+}
+
+ba_status set_probe_lambda(ba_problem* h, double lam) {
+  CU(cudaMemcpyAsync(&h->st->lam_probe, &lam, sizeof(double), cudaMemcpyHostToDevice, h->s));
+  CU(cudaStreamSynchronize(h->s));
+  return BA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ba_status ba_options_default(ba_options* o) {
+  if (!o) return fail(BA_ERR_INVALID_ARG, "NULL options");
+  o->precision = BA_PREC_F64;
+  o->huber_delta = 0.0;
+  o->lambda0 = 1e-4;
+  o->up = 2.0;
+  o->down = 0.0625;
+  o->rho_good = 0.75;
+  o->rho_bad = 0.25;
+  o->lambda_min = 1e-16;
+  o->lambda_max = 1e32;
+  o->diag_min = 1e-6;
+  o->diag_max = 1e32;
+  o->pcg_maxiter = 250;
+  o->pcg_tol = 1e-4;
+  o->use_graph = 1;
+  o->max_stats = 4096;
+  return BA_OK;
+}
+
+ba_status ba_problem_create(ba_problem** out, int C, int P, int O, const void* cams, const void* points,
+                            const int32_t* cam_idx, const int32_t* pt_idx, const void* pixels,
+                            const ba_options* opt, void* stream) {
+  if (!out) return fail(BA_ERR_INVALID_ARG, "NULL output handle");
+  *out = nullptr;
+  if (C < 1 || P < 1 || O < 1) return fail(BA_ERR_INVALID_ARG, "C, P and O must be >= 1 (got %d, %d, %d)", C, P, O);
+  if (!cams || !points || !cam_idx || !pt_idx || !pixels) return fail(BA_ERR_INVALID_ARG, "NULL input array");
+  ba_options o;
+  if (opt) o = *opt;
+  else ba_options_default(&o);
+  ba_status st = check_options(&o);
+  if (st != BA_OK) return st;
+  ba_problem* h = new (std::nothrow) ba_problem();
+  if (!h) return fail(BA_ERR_OOM, "host allocation failed");
+  h->C = C;
+  h->P = P;
+  h->O = O;
+  h->prec = o.precision;
+  h->tsize = o.precision == BA_PREC_F32 ? 4 : 8;
+  h->opt = o;
+  cudaError_t e = cudaStreamCreateWithFlags(&h->s, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    delete h;
+    return fail(BA_ERR_CUDA, "stream/event creation failed: %s", cudaGetErrorString(e));
+  }
+  st = enter(h, stream);
+  if (st == BA_OK) {
+    st = h->prec == BA_PREC_F32 ? create_impl<float>(h, cams, points, cam_idx, pt_idx, pixels)
+                                : create_impl<double>(h, cams, points, cam_idx, pt_idx, pixels);
+  }
+  if (st != BA_OK) {
+    std::string msg = g_err;
+    cudaStreamSynchronize(h->s);
+    delete h;
+    g_err = msg;
+    return st;
+  }
+  *out = h;
+  return BA_OK;
+}
+
+ba_status ba_problem_destroy(ba_problem* h) {
+  if (!h) return BA_OK;
+  cudaStreamSynchronize(h->s);
+  delete h;
+  return BA_OK;
+}
+
+ba_status ba_lm_step(ba_problem* h, void* stream) {
+  if (!h) return fail(BA_ERR_INVALID_ARG, "NULL problem");
+  ba_status st = enter(h, stream);
+  if (st != BA_OK) return st;
+  enqueue_trial_any(h);
+  CU(cudaGetLastError());
+  return leave(h, stream);
+}
+
+ba_status ba_solve(ba_problem* h, int iters, void* stream) {
+  if (!h) return fail(BA_ERR_INVALID_ARG, "NULL problem");
+  if (iters < 0) return fail(BA_ERR_INVALID_ARG, "iters < 0");
+  ba_status st = enter(h, stream);
+  if (st != BA_OK) return st;
+  if (!h->opt.use_graph) {
+    for (int i = 0; i < iters; ++i) enqueue_trial_any(h);
+    CU(cudaGetLastError());
+    return leave(h, stream);
+  }
+  if (!h->gexec && iters > 0) {
+    cudaGraph_t g = nullptr;
+    CU(cudaStreamBeginCapture(h->s, cudaStreamCaptureModeThreadLocal));
+    ba::g_capturing = true;
+    enqueue_trial_any(h);
+    ba::g_capturing = false;
+    cudaError_t e = cudaStreamEndCapture(h->s, &g);
+    if (e != cudaSuccess) return fail(BA_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
+    size_t n = 0;
+    cudaGraphGetNodes(g, nullptr, &n);
+    h->gnodes = n;
+    e = cudaGraphInstantiate(&h->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      h->gexec = nullptr;
+      return fail(BA_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
+    }
+  }
+  for (int i = 0; i < iters; ++i) {
+    CU(cudaGraphLaunch(h->gexec, h->s));
+    count_launch(h->gnodes);
+  }
+  return leave(h, stream);
+}
+
+ba_status ba_get_params(ba_problem* h, void* cams_out, void* points_out, void* stream) {
+  if (!h) return fail(BA_ERR_INVALID_ARG, "NULL problem");
+  ba_status st = enter(h, stream);
+  if (st != BA_OK) return st;
+  int cur = 0;
+  CU(cudaMemcpyAsync(&cur, &h->st->cur, sizeof(int), cudaMemcpyDeviceToHost, h->s));
+  CU(cudaStreamSynchronize(h->s));
+  const size_t cb = 9ull * h->C * h->tsize, pb = 3ull * h->P * h->tsize;
+  if (cams_out)
+    CU(cudaMemcpyAsync(cams_out, (char*)h->cams + cur * cb, cb, cudaMemcpyDefault, h->s));
+  if (points_out)
+    CU(cudaMemcpyAsync(points_out, (char*)h->pts + cur * pb, pb, cudaMemcpyDefault, h->s));
+  return leave(h, stream);
+}
+
+ba_status ba_set_params(ba_problem* h, const void* cams, const void* points, void* stream) {
+  if (!h) return fail(BA_ERR_INVALID_ARG, "NULL problem");
+  ba_status st = enter(h, stream);
+  if (st != BA_OK) return st;
+  int cur = 0;
+  CU(cudaMemcpyAsync(&cur, &h->st->cur, sizeof(int), cudaMemcpyDeviceToHost, h->s));
+  CU(cudaStreamSynchronize(h->s));
+  const size_t cb = 9ull * h->C * h->tsize, pb = 3ull * h->P * h->tsize;
+  if (cams) CU(cudaMemcpyAsync((char*)h->cams + cur * cb, cams, cb, cudaMemcpyDefault, h->s));
+  if (points) CU(cudaMemcpyAsync((char*)h->pts + cur * pb, points, pb, cudaMemcpyDefault, h->s));
+  st = set_flag(h, offsetof(DevState, need_lin), 1);
+  if (st != BA_OK) return st;
+  st = run_cost(h);
+  if (st != BA_OK) return st;
+  return leave(h, stream);
+}
+
+ba_status ba_set_pixels(ba_problem* h, const void* pixels, void* stream) {
+  if (!h || !pixels) return fail(BA_ERR_INVALID_ARG, "NULL argument");
+  ba_status st = enter(h, stream);
+  if (st != BA_OK) return st;
+  CU(cudaMemcpyAsync(h->px_in, pixels, 2ull * h->O * h->tsize, cudaMemcpyDefault, h->s));
+  if (h->prec == BA_PREC_F32)
+    k_gather_obs<float><<<nblk(h->O, 256), 256, 0, h->s>>>(h->O, h->perm_cam, h->perm_pt, h->cam_idx, h->pt_idx,
+                                                           (const float*)h->px_in, h->cm_pt, (float*)h->cm_px,
+                                                           h->pm_cam, (float*)h->pm_px);
+  else
+    k_gather_obs<double><<<nblk(h->O, 256), 256, 0, h->s>>>(h->O, h->perm_cam, h->perm_pt, h->cam_idx,
+                                                            h->pt_idx, (const double*)h->px_in, h->cm_pt,
+                                                            (double*)h->cm_px, h->pm_cam, (double*)h->pm_px);
+  count_launch();
+  st = set_flag(h, offsetof(DevState, need_lin), 1);
+  if (st != BA_OK) return st;
+  st = run_cost(h);
+  if (st != BA_OK) return st;
+  return leave(h, stream);
+}
+
+ba_status ba_get_stats(ba_problem* h, ba_iter_stats* host_out, int cap, int* n_out) {
+  if (!h || (cap > 0 && !host_out)) return fail(BA_ERR_INVALID_ARG, "NULL argument");
+  DevState ds;
+  CU(cudaMemcpyAsync(&ds, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, h->s));
+  CU(cudaStreamSynchronize(h->s));
+  const long long avail = std::min<long long>(ds.trials, h->cap);
+  const long long n = std::min<long long>(avail, cap > 0 ? cap : 0);
+  for (long long i = 0; i < n; ++i) {
+    const long long t = ds.trials - n + i;
+    CU(cudaMemcpy(host_out + i, h->stats + (t % h->cap), sizeof(ba_iter_stats), cudaMemcpyDeviceToHost));
+  }
+  if (n_out) *n_out = (int)n;
+  if (ds.nonfinite > 0) {
+    ba_status st = set_flag(h, offsetof(DevState, nonfinite), 0);
+    if (st != BA_OK) return st;
+    return fail(BA_ERR_NONFINITE, "%d trial(s) produced a non-finite cost and were rejected", ds.nonfinite);
+  }
+  return BA_OK;
+}
+
+ba_status ba_get_scalars(ba_problem* h, double* cost, double* lambda) {
+  if (!h) return fail(BA_ERR_INVALID_ARG, "NULL problem");
+  DevState ds;
+  CU(cudaMemcpyAsync(&ds, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, h->s));
+  CU(cudaStreamSynchronize(h->s));
+  if (cost) *cost = ds.F;
+  if (lambda) *lambda = ds.lam;
+  return BA_OK;
+}
+
+size_t ba_state_size(const ba_problem* h) { return h ? 9ull * h->C + 3ull * h->P + 4 : 0; }
+
+ba_status ba_get_state(ba_problem* h, double* out) {
+  if (!h || !out) return fail(BA_ERR_INVALID_ARG, "NULL argument");
+  DevState ds;
+  CU(cudaMemcpyAsync(&ds, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, h->s));
+  CU(cudaStreamSynchronize(h->s));
+  const size_t nc = 9ull * h->C, np = 3ull * h->P;
+  std::vector<char> buf((nc + np) * h->tsize);
+  CU(cudaMemcpy(buf.data(), (char*)h->cams + ds.cur * nc * h->tsize, nc * h->tsize, cudaMemcpyDeviceToHost));
+  CU(cudaMemcpy(buf.data() + nc * h->tsize, (char*)h->pts + ds.cur * np * h->tsize, np * h->tsize,
+                cudaMemcpyDeviceToHost));
+  for (size_t i = 0; i < nc + np; ++i)
+    out[i] = h->prec == BA_PREC_F32 ? (double)((float*)buf.data())[i] : ((double*)buf.data())[i];
+  out[nc + np] = ds.F;
+  out[nc + np + 1] = ds.lam;
+  out[nc + np + 2] = (double)ds.trials;
+  out[nc + np + 3] = (double)ds.need_lin;
+  return BA_OK;
+}
+
+ba_status ba_set_state(ba_problem* h, const double* in) {
+  if (!h || !in) return fail(BA_ERR_INVALID_ARG, "NULL argument");
+  const size_t nc = 9ull * h->C, np = 3ull * h->P;
+  std::vector<char> buf((nc + np) * h->tsize);
+  for (size_t i = 0; i < nc + np; ++i) {
+    if (h->prec == BA_PREC_F32) ((float*)buf.data())[i] = (float)in[i];
+    else ((double*)buf.data())[i] = in[i];
+  }
+  DevState ds;
+  CU(cudaMemcpyAsync(&ds, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, h->s));
+  CU(cudaStreamSynchronize(h->s));
+  CU(cudaMemcpy((char*)h->cams + ds.cur * nc * h->tsize, buf.data(), nc * h->tsize, cudaMemcpyHostToDevice));
+  CU(cudaMemcpy((char*)h->pts + ds.cur * np * h->tsize, buf.data() + nc * h->tsize, np * h->tsize,
+                cudaMemcpyHostToDevice));
+  ds.F = in[nc + np];
+  ds.lam = in[nc + np + 1];
+  ds.trials = (long long)in[nc + np + 2];
+  ds.need_lin = 1;
+  ds.nonfinite = 0;
+  CU(cudaMemcpy(h->st, &ds, sizeof(DevState), cudaMemcpyHostToDevice));
+  return BA_OK;
+}
+
+const char* ba_last_error(void) { return g_err.c_str(); }
+
+ba_status ba_get_csr(ba_problem* h, int32_t* perm_cam, int32_t* rowptr_cam, int32_t* perm_pt, int32_t* rowptr_pt,
+                     void* stream) {
+  if (!h) return fail(BA_ERR_INVALID_ARG, "NULL problem");
+  ba_status st = enter(h, stream);
+  if (st != BA_OK) return st;
+  if (perm_cam) CU(cudaMemcpyAsync(perm_cam, h->perm_cam, 4ull * h->O, cudaMemcpyDeviceToDevice, h->s));
+  if (rowptr_cam) CU(cudaMemcpyAsync(rowptr_cam, h->rowptr_cam, 4ull * (h->C + 1), cudaMemcpyDeviceToDevice, h->s));
+  if (perm_pt) CU(cudaMemcpyAsync(perm_pt, h->perm_pt, 4ull * h->O, cudaMemcpyDeviceToDevice, h->s));
+  if (rowptr_pt) CU(cudaMemcpyAsync(rowptr_pt, h->rowptr_pt, 4ull * (h->P + 1), cudaMemcpyDeviceToDevice, h->s));
+  return leave(h, stream);
+}
+
+ba_status ba_linearize(ba_problem* h, double* U, double* V, double* gc, double* gp, void* Jc, void* Jp, void* w,
+                       void* stream) {
+  if (!h) return fail(BA_ERR_INVALID_ARG, "NULL problem");
+  ba_status st = enter(h, stream);
+  if (st != BA_OK) return st;
+  st = set_flag(h, offsetof(DevState, need_lin), 1);
+  if (st != BA_OK) return st;
+  const double dl = h->opt.huber_delta > 0 ? h->opt.huber_delta : 0.0;
+  if (h->prec == BA_PREC_F32) {
+    enqueue_lin<float>(h, 1);
+    if (Jc || Jp || w)
+      k_export_lin<float><<<nblk(h->O, 256), 256, 0, h->s>>>(h->O, h->P, h->perm_cam, h->cam_idx, h->cm_pt,
+                                                              (const float*)h->cm_px, (const float*)h->Jcm,
+                                                              (const float*)h->camtab, (const float*)h->pts, h->st,
+                                                              (float)dl, (float*)Jc, (float*)Jp, (float*)w);
+  } else {
+    enqueue_lin<double>(h, 1);
+    if (Jc || Jp || w)
+      k_export_lin<double><<<nblk(h->O, 256), 256, 0, h->s>>>(h->O, h->P, h->perm_cam, h->cam_idx, h->cm_pt,
+                                                               (const double*)h->cm_px, (const double*)h->Jcm,
+                                                               (const double*)h->camtab, (const double*)h->pts,
+                                                               h->st, dl, (double*)Jc, (double*)Jp, (double*)w);
+  }
+  if (U) k_unpack_sym<<<nblk(81ll * h->C, 256), 256, 0, h->s>>>(h->C, 9, h->U, U);
+  if (V) k_unpack_sym<<<nblk(9ll * h->P, 256), 256, 0, h->s>>>(h->P, 3, h->V, V);
+  if (gc) CU(cudaMemcpyAsync(gc, h->gc, 72ull * h->C, cudaMemcpyDeviceToDevice, h->s));
+  if (gp) CU(cudaMemcpyAsync(gp, h->gp, 24ull * h->P, cudaMemcpyDeviceToDevice, h->s));
+  count_launch(3);
+  CU(cudaGetLastError());
+  return leave(h, stream);
+}
+
+ba_status ba_schur_matvec(ba_problem* h, double lambda, const double* x, double* y, void* stream) {
+  if (!h || !x || !y) return fail(BA_ERR_INVALID_ARG, "NULL argument");
+  ba_status st = enter(h, stream);
+  if (st != BA_OK) return st;
+  st = set_probe_lambda(h, lambda);
+  if (st != BA_OK) return st;
+  const double* lp = &h->st->lam_probe;
+  const double dmin = h->opt.diag_min, dmax = h->opt.diag_max;
+  CU(cudaMemcpyAsync(h->p, x, 72ull * h->C, cudaMemcpyDeviceToDevice, h->s));
+  if (h->prec == BA_PREC_F32) {
+    using T = float;
+    enqueue_lin<T>(h, 1);
+    k_pt_damp<T><<<nblk(h->P, PT_THREADS), PT_THREADS, 0, h->s>>>(h->P, h->V, h->gp, lp, dmin, dmax, (T*)h->Vinv,
+                                                                 (T*)h->y0);
+    k_cast_vec<T><<<nblk(9ll * h->C, 256), 256, 0, h->s>>>(9ll * h->C, h->p, (T*)h->pT);
+    k_pass_a<T, 0><<<h->npb, PT_THREADS, 0, h->s>>>(h->P, h->O, h->rowptr_pt, h->pm_cam, (const T*)h->Jpm,
+                                                    (const T*)h->camtab, (const T*)h->pT, (const T*)h->Vinv, h->st,
+                                                    0, (T*)h->tpt, nullptr, nullptr, nullptr, nullptr);
+    k_pass_b<T><<<h->npieces, PIECE_THREADS, 0, h->s>>>(h->piece_cam, h->piece_beg, h->piece_end, h->cm_pt,
+                                                       (const T*)h->Jcm, (const T*)h->camtab, (const T*)h->tpt,
+                                                       h->st, 0, h->O, h->part);
+  } else {
+    using T = double;
+    enqueue_lin<T>(h, 1);
+    k_pt_damp<T><<<nblk(h->P, PT_THREADS), PT_THREADS, 0, h->s>>>(h->P, h->V, h->gp, lp, dmin, dmax, (T*)h->Vinv,
+                                                                 (T*)h->y0);
+    k_cast_vec<T><<<nblk(9ll * h->C, 256), 256, 0, h->s>>>(9ll * h->C, h->p, (T*)h->pT);
+    k_pass_a<T, 0><<<h->npb, PT_THREADS, 0, h->s>>>(h->P, h->O, h->rowptr_pt, h->pm_cam, (const T*)h->Jpm,
+                                                    (const T*)h->camtab, (const T*)h->pT, (const T*)h->Vinv, h->st,
+                                                    0, (T*)h->tpt, nullptr, nullptr, nullptr, nullptr);
+    k_pass_b<T><<<h->npieces, PIECE_THREADS, 0, h->s>>>(h->piece_cam, h->piece_beg, h->piece_end, h->cm_pt,
+                                                       (const T*)h->Jcm, (const T*)h->camtab, (const T*)h->tpt,
+                                                       h->st, 0, h->O, h->part);
+  }
+  k_pcg_q<<<h->ncb, CAM_THREADS, 0, h->s>>>(h->C, h->cam_piece_ptr, h->part, h->U, lp, dmin, dmax, h->p, h->q,
+                                            nullptr, h->st, 0);
+  count_launch(5);
+  CU(cudaMemcpyAsync(y, h->q, 72ull * h->C, cudaMemcpyDeviceToDevice, h->s));
+  CU(cudaGetLastError());
+  return leave(h, stream);
+}
+
+ba_status ba_damped_solve(ba_problem* h, double lambda, int maxiter, double tol, double* dc, void* dp, int* iters,
+                          double* rel_res, void* stream) {
+  if (!h) return fail(BA_ERR_INVALID_ARG, "NULL problem");
+  if (maxiter < 0 || maxiter > 100000 || !(tol >= 0)) return fail(BA_ERR_INVALID_ARG, "bad maxiter/tol");
+  ba_status st = enter(h, stream);
+  if (st != BA_OK) return st;
+  st = set_probe_lambda(h, lambda);
+  if (st != BA_OK) return st;
+  const double* lp = &h->st->lam_probe;
+  if (h->prec == BA_PREC_F32) {
+    enqueue_lin<float>(h, 1);
+    enqueue_solve<float>(h, lp, maxiter, tol);
+  } else {
+    enqueue_lin<double>(h, 1);
+    enqueue_solve<double>(h, lp, maxiter, tol);
+  }
+  CU(cudaGetLastError());
+  if (dc) CU(cudaMemcpyAsync(dc, h->x, 72ull * h->C, cudaMemcpyDeviceToDevice, h->s));
+  if (dp) CU(cudaMemcpyAsync(dp, h->dp, 3ull * h->P * h->tsize, cudaMemcpyDeviceToDevice, h->s));
+  DevState ds;
+  CU(cudaMemcpyAsync(&ds, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, h->s));
+  CU(cudaStreamSynchronize(h->s));
+  if (iters) *iters = ds.pcg_iters;
+  if (rel_res) *rel_res = ds.pcg_rel;
+  return leave(h, stream);
+}
+
+ba_status ba_project(int precision, int C, int P, int O, const void* cams, const void* points,
+                     const int32_t* cam_idx, const int32_t* pt_idx, void* out, void* stream) {
+  if (C < 1 || P < 1 || O < 0) return fail(BA_ERR_INVALID_ARG, "bad sizes");
+  if (O == 0) return BA_OK;
+  if (!cams || !points || !cam_idx || !pt_idx || !out) return fail(BA_ERR_INVALID_ARG, "NULL argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (precision == BA_PREC_F32)
+    k_project<float><<<nblk(O, 256), 256, 0, s>>>(O, (const float*)cams, (const float*)points, cam_idx, pt_idx,
+                                                  (float*)out);
+  else if (precision == BA_PREC_F64)
+    k_project<double><<<nblk(O, 256), 256, 0, s>>>(O, (const double*)cams, (const double*)points, cam_idx, pt_idx,
+                                                   (double*)out);
+  else
+    return fail(BA_ERR_INVALID_ARG, "bad precision");
+  count_launch();
+  CU(cudaGetLastError());
+  return BA_OK;
+}
+
+ba_status ba_csr_build(const int32_t* keys, int n, int n_keys, int32_t* perm_out, int32_t* rowptr_out,
+                       void* stream) {
+  if (n < 0 || n_keys < 1) return fail(BA_ERR_INVALID_ARG, "n must be >= 0 and n_keys >= 1");
+  if ((n > 0 && (!keys || !perm_out)) || !rowptr_out) return fail(BA_ERR_INVALID_ARG, "NULL argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  void* scratch = nullptr;
+  CU(cudaMalloc(&scratch, ba::csr_scratch_bytes(n)));
+  int* d_err = reinterpret_cast<int*>(static_cast<char*>(scratch) + ba::csr_scratch_bytes(n) - 256);
+  cudaError_t e = cudaMemsetAsync(d_err, 0, sizeof(int), s);
+  if (e == cudaSuccess) e = ba::csr_build_async(keys, n, n_keys, perm_out, rowptr_out, scratch, d_err, s);
+  int err = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&err, d_err, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(scratch);
+  if (e != cudaSuccess) return fail(BA_ERR_CUDA, "csr build failed: %s", cudaGetErrorString(e));
+  if (err) return fail(BA_ERR_INVALID_ARG, "key out of range [0, %d)", n_keys);
+  return BA_OK;
+}
+
+uint64_t ba_kernel_launch_count(void) { return ba::g_launches.load(); }
+
+ba_status ba_profile_trials(ba_problem* h, int iters, ba_kernel_times* out) {
+  if (!h || !out || iters < 0) return fail(BA_ERR_INVALID_ARG, "bad argument");
+  memset(out, 0, sizeof(*out));
+  DevState ds;
+  CU(cudaMemcpyAsync(&ds, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, h->s));
+  CU(cudaStreamSynchronize(h->s));
+  const long long t0 = ds.trials;
+  const int lin0 = ds.need_lin;
+  std::vector<ba_problem::ProfRec> recs;
+  cudaEvent_t ea, eb;
+  CU(cudaEventCreate(&ea));
+  CU(cudaEventCreate(&eb));
+  h->prof = &recs;
+  CU(cudaEventRecord(ea, h->s));
+  for (int i = 0; i < iters; ++i) {
+    h->prof_trial = i;
+    enqueue_trial_any(h);
+  }
+  CU(cudaEventRecord(eb, h->s));
+  h->prof = nullptr;
+  cudaError_t e = cudaStreamSynchronize(h->s);
+  std::vector<ba_iter_stats> st(iters);
+  for (int i = 0; i < iters && e == cudaSuccess; ++i)
+    e = cudaMemcpy(&st[i], h->stats + ((t0 + i) % h->cap), sizeof(ba_iter_stats), cudaMemcpyDeviceToHost);
+  float tm = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&tm, ea, eb);
+  out->trial_ms = tm;
+  for (auto& r : recs) {
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, r.a, r.b);
+    const bool lin = r.trial == 0 ? lin0 != 0 : st[r.trial - 1].accepted != 0;
+    bool did = true;
+    if (r.k == -2) did = lin;                          // gated linearisation kernels
+    else if (r.k >= 0) did = r.k < st[r.trial].pcg_iters;  // PCG launches after convergence exit at once
+    if (did) {
+      out->ms[r.kind] += ms;
+      out->launches[r.kind] += 1;
+    }
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  cudaEventDestroy(ea);
+  cudaEventDestroy(eb);
+  if (e != cudaSuccess) return fail(BA_ERR_CUDA, "profiling failed: %s", cudaGetErrorString(e));
+  return BA_OK;
+}
+
+}  // extern "C"

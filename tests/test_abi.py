@@ -1,0 +1,64 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU and exports every
+entry point include/ba.h declares (no compute calls)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2409_12190_gb300 import build as b
+    path = b.build()
+    return ctypes.CDLL(path)
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "ba.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(ba_[a-z_]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for n in ("ba_problem_create", "ba_lm_step", "ba_solve", "ba_get_params", "ba_get_stats",
+              "ba_problem_destroy", "ba_last_error", "ba_csr_build", "ba_project"):
+        assert n in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_signatures_cover_header():
+    from paper_2409_12190_gb300 import _lib
+    assert set(_declared()) <= set(_lib.SIGNATURES)
+
+
+def test_options_default_without_gpu(lib):
+    from paper_2409_12190_gb300 import _lib
+    L = _lib.load()
+    o = _lib.ba_options()
+    assert L.ba_options_default(ctypes.byref(o)) == 0
+    assert o.up == 2.0 and o.down == 0.0625 and o.pcg_maxiter == 250 and o.pcg_tol == 1e-4
+    assert o.lambda0 == 1e-4 and o.diag_min == 1e-6
+
+
+def test_struct_layouts_match_header():
+    from paper_2409_12190_gb300 import _lib
+    assert ctypes.sizeof(_lib.ba_iter_stats) == 6 * 8 + 4 * 4
+    assert ctypes.sizeof(_lib.ba_options) == 8 * 11 + 8 + 8 + 8  # int+pad, 10 doubles, ...
+
+
+def test_argument_errors_need_no_gpu(lib):
+    from paper_2409_12190_gb300 import _lib
+    L = _lib.load()
+    h = ctypes.c_void_p()
+    assert L.ba_problem_create(ctypes.byref(h), 0, 1, 1, None, None, None, None, None, None, None) == 1
+    assert b"must be >= 1" in L.ba_last_error()
+    assert L.ba_csr_build(None, -1, 3, None, None, None) == 1
+    assert L.ba_lm_step(None, None) == 1

@@ -1,0 +1,98 @@
+"""a1-a5 step by step against the FP64 oracle: projection, residuals and
+Jacobian blocks, block assembly, implicit Schur products, damped solve."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as orc
+import paper_2409_12190_gb300 as ba
+import scenegen
+from gpu_helpers import np64, problem, rel_err, small_ring
+
+pytestmark = pytest.mark.gpu
+
+# FP64 path: identical formulas, different association order -> ~1e-13;
+# FP32 path: float per-observation arithmetic -> a few float ulps of the
+# block scale.
+TOL = {"f64": 1e-11, "f32": 3e-5}
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_project(prec):
+    sc = small_ring(huber=False)
+    dt = torch.float64 if prec == "f64" else torch.float32
+    out = ba.project(torch.tensor(sc.cams_gt, dtype=dt, device="cuda"),
+                     torch.tensor(sc.points_gt, dtype=dt, device="cuda"),
+                     torch.from_numpy(sc.cam_idx).cuda(), torch.from_numpy(sc.pt_idx).cuda())
+    ref = orc.project(sc.cams_gt, sc.points_gt, sc.cam_idx, sc.pt_idx)
+    assert rel_err(np64(out), ref) < (1e-13 if prec == "f64" else 2e-6)
+
+
+def _scenes():
+    a = scenegen.config_scene("ba16")
+    b = scenegen.ring_scene(12, 400, seed=11, view_p=0.3, outlier_frac=0.2,
+                            outlier_px=20.0, huber_delta=1.0)
+    return {"plain": a, "huber": b}
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("kind", ["plain", "huber"])
+def test_linearize_and_assemble(prec, kind):
+    sc = _scenes()[kind]
+    pix = orc.pixels_from_scene(sc)
+    with problem(sc, pix, prec) as prob:
+        out = prob.linearize()
+    ref = orc.assemble(sc.cams_init, sc.points_init, sc.cam_idx, sc.pt_idx, pix, sc.huber_delta)
+    sw = np.sqrt(ref["w"])
+    tol = TOL[prec]
+    assert rel_err(np64(out["w"]), ref["w"]) < tol
+    assert rel_err(np64(out["Jc"]), sw[:, None, None] * ref["Jc"]) < tol
+    assert rel_err(np64(out["Jp"]), sw[:, None, None] * ref["Jp"]) < tol
+    for key in ("U", "V", "gc", "gp"):
+        assert rel_err(np64(out[key]), ref[key]) < 10 * tol, key
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_schur_matvec(prec):
+    sc = scenegen.config_scene("ba16")
+    pix = orc.pixels_from_scene(sc)
+    lam = 1e-3
+    blk = orc.assemble(sc.cams_init, sc.points_init, sc.cam_idx, sc.pt_idx, pix)
+    S, _, _, _ = orc.schur_explicit(blk, sc.cam_idx, sc.pt_idx, lam)
+    rng = np.random.default_rng(0)
+    with problem(sc, pix, prec) as prob:
+        for _ in range(3):
+            x = rng.normal(size=(sc.C, 9)) * np.array([1e-3] * 6 + [1.0, 1e-3, 1e-3])
+            y = prob.schur_matvec(lam, torch.from_numpy(x).cuda())
+            ref = S @ x.reshape(-1)
+            assert rel_err(np64(y).reshape(-1), ref) < (1e-10 if prec == "f64" else 1e-4)
+
+
+def test_damped_solve_matches_dense_cholesky():
+    sc = scenegen.config_scene("ba16")
+    pix = orc.pixels_from_scene(sc)
+    lam = 1e-3
+    blk = orc.assemble(sc.cams_init, sc.points_init, sc.cam_idx, sc.pt_idx, pix)
+    dc_ref, dp_ref, _, _ = orc.solve_damped(blk, sc.cam_idx, sc.pt_idx, lam,
+                                           orc.LMOptions(solver="cholesky"))
+    with problem(sc, pix, "f64") as prob:
+        dc, dp, its, rel = prob.damped_solve(lam, 9 * sc.C * 3, 1e-13)
+    assert rel <= 1e-13 and its > 0
+    assert rel_err(np64(dc), dc_ref) < 1e-8
+    assert rel_err(np64(dp), dp_ref) < 1e-8
+
+
+def test_damped_solve_truncated_pcg_matches_oracle_pcg():
+    """Same PCG algorithm, same stopping rule: same iterate."""
+    sc = small_ring()
+    pix = orc.pixels_from_scene(sc)
+    lam = 1e-4
+    blk = orc.assemble(sc.cams_init, sc.points_init, sc.cam_idx, sc.pt_idx, pix, sc.huber_delta)
+    opts = orc.LMOptions(solver="pcg", pcg_tol=1e-4, pcg_maxiter=50)
+    dc_ref, dp_ref, its_ref, rel_ref = orc.solve_damped(blk, sc.cam_idx, sc.pt_idx, lam, opts)
+    with problem(sc, pix, "f64") as prob:
+        dc, dp, its, rel = prob.damped_solve(lam, 50, 1e-4)
+    assert its == its_ref
+    assert abs(rel - rel_ref) < 1e-8 * max(rel_ref, 1e-30) + 1e-14
+    assert rel_err(np64(dc), dc_ref) < 1e-9
+    assert rel_err(np64(dp), dp_ref) < 1e-9
