@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--profile-trials", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--points", type=int, default=0,
+                    help="profiling only: same recipe with fewer points")
     return ap.parse_args()
 
 
@@ -227,7 +229,10 @@ def run_ours(args):
             import torch.distributed as dist
             dist.barrier()
 
-    scene = scenegen.config_scene(WORKLOAD)
+    if args.points:
+        scene = scenegen.ring_scene(4000, args.points, seed=3, view_p=1.0 / 5.7, name="ba4000-small")
+    else:
+        scene = scenegen.config_scene(WORKLOAD)
     C, P, O = scene.C, scene.P, scene.O
     ci = torch.from_numpy(scene.cam_idx).to(dev)
     pi = torch.from_numpy(scene.pt_idx).to(dev)
@@ -331,7 +336,7 @@ def run_ours(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "cameras": C, "points": P, "observations": O,
+            "config": {"workload": scene.name, "cameras": C, "points": P, "observations": O,
                        "precision": "f32 per-observation, f64 reductions", "loss": "squared",
                        "pcg": f"block-Jacobi, maxiter {PCG_MAXITER}, tol {PCG_TOL}",
                        "pcg_iters_mean": statistics.mean(pcg) if pcg else None,

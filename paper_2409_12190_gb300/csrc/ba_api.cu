@@ -64,7 +64,9 @@ struct ba_problem {
   // structure (symbolic phase)
   int32_t *cam_idx = nullptr, *pt_idx = nullptr;
   int32_t *perm_cam = nullptr, *rowptr_cam = nullptr, *perm_pt = nullptr, *rowptr_pt = nullptr;
-  int32_t *cm_pt = nullptr, *pm_cam = nullptr;
+  int32_t *cm_pt = nullptr, *pm_cam = nullptr, *pm_pt = nullptr;
+  int nchunks = 0;
+  int32_t* pchunk = nullptr;  // [nchunks + 1] first point of each point chunk
   void *cm_px = nullptr, *pm_px = nullptr, *px_in = nullptr;
   int npieces = 0;
   int32_t *piece_cam = nullptr, *piece_beg = nullptr, *piece_end = nullptr, *cam_piece_ptr = nullptr;
@@ -171,9 +173,9 @@ void enqueue_lin(ba_problem* h, int gate) {
   }
   {
     Prof pr(h, BA_K_LIN_PT, -2);
-    k_lin_pt<T><<<nblk(h->P, PT_THREADS), PT_THREADS, 0, s>>>(
-        h->P, h->O, h->rowptr_pt, h->pm_cam, (const T*)h->pm_px, (const T*)h->pts, (const T*)h->camtab, h->st,
-        gate, delta, (T*)h->Jpm, h->V, h->gp);
+    k_lin_pt<T><<<h->nchunks, CHUNK_THREADS, CHUNK_SLOTS * 9 * sizeof(T), s>>>(
+        h->pchunk, h->O, h->rowptr_pt, h->pm_cam, h->pm_pt, (const T*)h->pm_px, (const T*)h->pts,
+        (const T*)h->camtab, h->st, h->P, gate, delta, (T*)h->Jpm, h->V, h->gp);
   }
   count_launch(4);
 }
@@ -203,9 +205,9 @@ void enqueue_solve(ba_problem* h, const double* lam_ptr, int maxiter, double tol
   for (int k = 0; k < maxiter; ++k) {
     {
       Prof pr(h, BA_K_PASS_A, k);
-      k_pass_a<T, 0><<<nblk(h->P, PT_THREADS), PT_THREADS, 0, s>>>(
-          h->P, h->O, h->rowptr_pt, h->pm_cam, (const T*)h->Jpm, (const T*)h->camtab, (const T*)h->pT,
-          (const T*)h->Vinv, h->st, 1, (T*)h->tpt, nullptr, nullptr, nullptr, nullptr);
+      k_pass_a<T, 0><<<h->nchunks, CHUNK_THREADS, CHUNK_SLOTS * 3 * sizeof(T), s>>>(
+          h->pchunk, h->P, h->O, h->rowptr_pt, h->pm_cam, (const T*)h->Jpm, (const T*)h->camtab,
+          (const T*)h->pT, (const T*)h->Vinv, h->st, 1, (T*)h->tpt, nullptr, nullptr, nullptr, nullptr);
     }
     {
       Prof pr(h, BA_K_PASS_B, k);
@@ -236,9 +238,9 @@ void enqueue_solve(ba_problem* h, const double* lam_ptr, int maxiter, double tol
   }
   {
     Prof pr(h, BA_K_BACKSUB);
-    k_pass_a<T, 1><<<h->npb, PT_THREADS, 0, s>>>(h->P, h->O, h->rowptr_pt, h->pm_cam, (const T*)h->Jpm,
-                                                 (const T*)h->camtab, (const T*)h->xT, (const T*)h->Vinv, h->st,
-                                                 0, (T*)h->dp, (const T*)h->y0, h->gp, (T*)h->pts, h->dot_gp);
+    k_pass_a<T, 1><<<h->nchunks, CHUNK_THREADS, CHUNK_SLOTS * 3 * sizeof(T), s>>>(
+        h->pchunk, h->P, h->O, h->rowptr_pt, h->pm_cam, (const T*)h->Jpm, (const T*)h->camtab,
+        (const T*)h->xT, (const T*)h->Vinv, h->st, 0, (T*)h->dp, (const T*)h->y0, h->gp, (T*)h->pts, h->dot_gp);
   }
   count_launch(2);
 }
@@ -258,7 +260,7 @@ void enqueue_trial(ba_problem* h) {
   const ba_options& o = h->opt;
   {
     Prof pr(h, BA_K_OTHER);
-    k_lm_control<<<1, 256, 0, h->s>>>(h->npieces, h->part, h->ncb, h->dot_gc, h->npb, h->dot_gp, o.up, o.down,
+    k_lm_control<<<1, 256, 0, h->s>>>(h->npieces, h->part, h->ncb, h->dot_gc, h->nchunks, h->dot_gp, o.up, o.down,
                                       o.rho_good, o.rho_bad, o.lambda_min, o.lambda_max, h->st, h->stats, h->cap);
   }
   count_launch(2);
@@ -368,14 +370,37 @@ ba_status create_impl(ba_problem* h, const void* cams, const void* points, const
   CU(cudaMemcpy(h->piece_end, pe.data(), pe.size() * 4, cudaMemcpyHostToDevice));
   CU(cudaMemcpy(h->cam_piece_ptr, cpp.data(), (C + 1) * 4, cudaMemcpyHostToDevice));
 
+  // point chunks: runs of whole points with at most CHUNK_SLOTS observations
+  // and CHUNK_PTS points (a point with more observations is a chunk alone)
+  {
+    std::vector<int32_t> rq(P + 1);
+    CU(cudaMemcpy(rq.data(), h->rowptr_pt, (P + 1) * 4, cudaMemcpyDeviceToHost));
+    std::vector<int32_t> pch;
+    long long j = 0;
+    while (j < P) {
+      pch.push_back((int32_t)j);
+      long long e = j + 1;
+      while (e < P && e - j < CHUNK_PTS && rq[e + 1] - rq[j] <= CHUNK_SLOTS) ++e;
+      j = e;
+    }
+    pch.push_back((int32_t)P);
+    h->nchunks = (int)pch.size() - 1;
+    CU(h->alloc(&h->pchunk, pch.size() * 4));
+    CU(cudaMemcpy(h->pchunk, pch.data(), pch.size() * 4, cudaMemcpyHostToDevice));
+  }
+  if (sizeof(T) * CHUNK_SLOTS * 9 > 48 * 1024)
+    CU(cudaFuncSetAttribute(k_lin_pt<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)(sizeof(T) * CHUNK_SLOTS * 9)));
+
   // observation data in both orders
   CU(h->alloc(&h->cm_pt, O * 4));
   CU(h->alloc(&h->pm_cam, O * 4));
+  CU(h->alloc(&h->pm_pt, O * 4));
   CU(h->alloc(&h->cm_px, 2 * O * ts));
   CU(h->alloc(&h->pm_px, 2 * O * ts));
   k_gather_obs<T><<<nblk(O, 256), 256, 0, s>>>(h->O, h->perm_cam, h->perm_pt, h->cam_idx, h->pt_idx,
                                                (const T*)h->px_in, h->cm_pt, (T*)h->cm_px, h->pm_cam,
-                                               (T*)h->pm_px);
+                                               h->pm_pt, (T*)h->pm_px);
   count_launch();
 
   // linearisation and solver buffers
@@ -406,7 +431,7 @@ ba_status create_impl(ba_problem* h, const void* cams, const void* points, const
   CU(h->alloc(&h->dot_rr, h->ncb * 8));
   CU(h->alloc(&h->dot_bb, h->ncb * 8));
   CU(h->alloc(&h->dot_gc, h->ncb * 8));
-  CU(h->alloc(&h->dot_gp, h->npb * 8));
+  CU(h->alloc(&h->dot_gp, std::max(h->nchunks, 1) * 8));
   h->cap = h->opt.max_stats;
   CU(h->alloc(&h->stats, (size_t)h->cap * sizeof(ba_iter_stats)));
   CU(cudaMemsetAsync(h->stats, 0, (size_t)h->cap * sizeof(ba_iter_stats), s));
@@ -600,11 +625,12 @@ ba_status ba_set_pixels(ba_problem* h, const void* pixels, void* stream) {
   if (h->prec == BA_PREC_F32)
     k_gather_obs<float><<<nblk(h->O, 256), 256, 0, h->s>>>(h->O, h->perm_cam, h->perm_pt, h->cam_idx, h->pt_idx,
                                                            (const float*)h->px_in, h->cm_pt, (float*)h->cm_px,
-                                                           h->pm_cam, (float*)h->pm_px);
+                                                           h->pm_cam, h->pm_pt, (float*)h->pm_px);
   else
     k_gather_obs<double><<<nblk(h->O, 256), 256, 0, h->s>>>(h->O, h->perm_cam, h->perm_pt, h->cam_idx,
                                                             h->pt_idx, (const double*)h->px_in, h->cm_pt,
-                                                            (double*)h->cm_px, h->pm_cam, (double*)h->pm_px);
+                                                            (double*)h->cm_px, h->pm_cam, h->pm_pt,
+                                                            (double*)h->pm_px);
   count_launch();
   st = set_flag(h, offsetof(DevState, need_lin), 1);
   if (st != BA_OK) return st;
@@ -748,9 +774,9 @@ ba_status ba_schur_matvec(ba_problem* h, double lambda, const double* x, double*
     k_pt_damp<T><<<nblk(h->P, PT_THREADS), PT_THREADS, 0, h->s>>>(h->P, h->V, h->gp, lp, dmin, dmax, (T*)h->Vinv,
                                                                  (T*)h->y0);
     k_cast_vec<T><<<nblk(9ll * h->C, 256), 256, 0, h->s>>>(9ll * h->C, h->p, (T*)h->pT);
-    k_pass_a<T, 0><<<h->npb, PT_THREADS, 0, h->s>>>(h->P, h->O, h->rowptr_pt, h->pm_cam, (const T*)h->Jpm,
-                                                    (const T*)h->camtab, (const T*)h->pT, (const T*)h->Vinv, h->st,
-                                                    0, (T*)h->tpt, nullptr, nullptr, nullptr, nullptr);
+    k_pass_a<T, 0><<<h->nchunks, CHUNK_THREADS, CHUNK_SLOTS * 3 * sizeof(T), h->s>>>(
+        h->pchunk, h->P, h->O, h->rowptr_pt, h->pm_cam, (const T*)h->Jpm, (const T*)h->camtab, (const T*)h->pT,
+        (const T*)h->Vinv, h->st, 0, (T*)h->tpt, nullptr, nullptr, nullptr, nullptr);
     k_pass_b<T><<<h->npieces, PIECE_THREADS, 0, h->s>>>(h->piece_cam, h->piece_beg, h->piece_end, h->cm_pt,
                                                        (const T*)h->Jcm, (const T*)h->camtab, (const T*)h->tpt,
                                                        h->st, 0, h->O, h->part);
@@ -760,9 +786,9 @@ ba_status ba_schur_matvec(ba_problem* h, double lambda, const double* x, double*
     k_pt_damp<T><<<nblk(h->P, PT_THREADS), PT_THREADS, 0, h->s>>>(h->P, h->V, h->gp, lp, dmin, dmax, (T*)h->Vinv,
                                                                  (T*)h->y0);
     k_cast_vec<T><<<nblk(9ll * h->C, 256), 256, 0, h->s>>>(9ll * h->C, h->p, (T*)h->pT);
-    k_pass_a<T, 0><<<h->npb, PT_THREADS, 0, h->s>>>(h->P, h->O, h->rowptr_pt, h->pm_cam, (const T*)h->Jpm,
-                                                    (const T*)h->camtab, (const T*)h->pT, (const T*)h->Vinv, h->st,
-                                                    0, (T*)h->tpt, nullptr, nullptr, nullptr, nullptr);
+    k_pass_a<T, 0><<<h->nchunks, CHUNK_THREADS, CHUNK_SLOTS * 3 * sizeof(T), h->s>>>(
+        h->pchunk, h->P, h->O, h->rowptr_pt, h->pm_cam, (const T*)h->Jpm, (const T*)h->camtab, (const T*)h->pT,
+        (const T*)h->Vinv, h->st, 0, (T*)h->tpt, nullptr, nullptr, nullptr, nullptr);
     k_pass_b<T><<<h->npieces, PIECE_THREADS, 0, h->s>>>(h->piece_cam, h->piece_beg, h->piece_end, h->cm_pt,
                                                        (const T*)h->Jcm, (const T*)h->camtab, (const T*)h->tpt,
                                                        h->st, 0, h->O, h->part);

@@ -18,9 +18,11 @@
 // Reductions.  Every sum over observations is taken in a fixed order: a
 // camera's observations are cut into pieces of at most PIECE slots, one CTA
 // per piece reduces its slots (per-thread partials, warp shuffles, then the
-// warps in order) and a per-camera kernel adds the pieces in order; a point's
-// observations are summed sequentially by one thread.  No global atomics are
-// used on the numeric path, so every result is bitwise reproducible.
+// warps in order) and a per-camera kernel adds the pieces in order; points
+// are grouped into chunks of at most CHUNK_SLOTS observations, one CTA per
+// chunk computes one observation per thread into shared memory and one
+// thread per point adds its observations in slot order.  No global atomics
+// are used on the numeric path, so every result is bitwise reproducible.
 // Per-observation arithmetic is in T; per-thread partial sums are in T; all
 // cross-thread sums, dot products, costs and the gain ratio are in double.
 #pragma once
@@ -40,6 +42,9 @@ constexpr int CAM_THREADS = 128;
 constexpr int NPLANE = 18;
 constexpr int CT = 24;               // camera table: R[9], Jl[9], t[3], f, k1, k2
 constexpr int PART = 64;             // doubles per piece partial (54 used)
+constexpr int CHUNK_SLOTS = 1024;    // max point-major slots per point chunk
+constexpr int CHUNK_PTS = 1024;      // max points per point chunk
+constexpr int CHUNK_THREADS = 256;
 
 // Device-resident LM / PCG state; every field is written by exactly one
 // thread of one kernel and read by later kernels.
@@ -321,7 +326,7 @@ template <typename T>
 __global__ void k_gather_obs(int O, const int32_t* __restrict__ perm_cam, const int32_t* __restrict__ perm_pt,
                              const int32_t* __restrict__ ci, const int32_t* __restrict__ pi,
                              const T* __restrict__ px, int32_t* __restrict__ cm_pt, T* __restrict__ cm_px,
-                             int32_t* __restrict__ pm_cam, T* __restrict__ pm_px) {
+                             int32_t* __restrict__ pm_cam, int32_t* __restrict__ pm_pt, T* __restrict__ pm_px) {
   const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= O) return;
   const int k = perm_cam[s];
@@ -330,6 +335,7 @@ __global__ void k_gather_obs(int O, const int32_t* __restrict__ perm_cam, const 
   cm_px[O + s] = px[2LL * k + 1];
   const int k2 = perm_pt[s];
   pm_cam[s] = ci[k2];
+  pm_pt[s] = pi[k2];
   pm_px[s] = px[2LL * k2];
   pm_px[O + s] = px[2LL * k2 + 1];
 }
@@ -419,44 +425,91 @@ __global__ void k_cam_combine_lin(int C, const int32_t* __restrict__ cam_piece_p
   }
 }
 
-// Point-major pass: write the planes, V (6) and gp (3) per point.
+// Point-major pass over one chunk of points: write the planes, V (6) and
+// gp (3) per point.  One thread per observation (coalesced plane stores);
+// each observation's 9 contributions go to shared memory and one thread per
+// point adds its observations in slot order.  A point with more than
+// CHUNK_SLOTS observations is a chunk of its own and is reduced by the block.
 template <typename T>
-__global__ void __launch_bounds__(PT_THREADS)
-k_lin_pt(int P, int O, const int32_t* __restrict__ rowptr_pt, const int32_t* __restrict__ pm_cam,
-         const T* __restrict__ pm_px, const T* __restrict__ pts_buf, const T* __restrict__ camtab,
-         const DevState* __restrict__ st, int gate, T delta, T* __restrict__ Jpm,
-         double* __restrict__ V, double* __restrict__ gp) {
+__device__ __forceinline__ void lin_pt_obs(int q, int O, const int32_t* __restrict__ pm_cam,
+                                           const int32_t* __restrict__ pm_pt, const T* __restrict__ pm_px,
+                                           const T* __restrict__ pts, const T* __restrict__ camtab, T delta,
+                                           T* __restrict__ Jpm, T (&v)[9]) {
+  const int j = pm_pt[q];
+  const T* ct = camtab + (long long)CT * pm_cam[q];
+  T ctl[CT];
+#pragma unroll
+  for (int i = 0; i < CT; ++i) ctl[i] = ct[i];
+  Lin<T> o;
+  lin_obs(ctl, pts[3LL * j], pts[3LL * j + 1], pts[3LL * j + 2], pm_px[q], pm_px[(long long)O + q], delta, o);
+  T pl[NPLANE];
+  lin_to_planes(o, pl);
+#pragma unroll
+  for (int p = 0; p < NPLANE; ++p) Jpm[(long long)p * O + q] = pl[p];
+  T Jp[6];
+  jp_from(o.A, ctl, Jp);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+#pragma unroll
+    for (int b = a; b < 3; ++b) v[sym3(a, b)] = Jp[a] * Jp[b] + Jp[3 + a] * Jp[3 + b];
+    v[6 + a] = Jp[a] * o.r0 + Jp[3 + a] * o.r1;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(CHUNK_THREADS)
+k_lin_pt(const int32_t* __restrict__ pchunk, int O, const int32_t* __restrict__ rowptr_pt,
+         const int32_t* __restrict__ pm_cam, const int32_t* __restrict__ pm_pt, const T* __restrict__ pm_px,
+         const T* __restrict__ pts_buf, const T* __restrict__ camtab, const DevState* __restrict__ st, int P,
+         int gate, T delta, T* __restrict__ Jpm, double* __restrict__ V, double* __restrict__ gp) {
   if (gate && !st->need_lin) return;
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= P) return;
-  const T* X = pts_buf + (long long)st->cur * 3 * P + 3LL * j;
-  const T X0 = X[0], X1 = X[1], X2 = X[2];
-  T v[6] = {0, 0, 0, 0, 0, 0}, g[3] = {0, 0, 0};
-  const int q1 = rowptr_pt[j + 1];
-  for (int q = rowptr_pt[j]; q < q1; ++q) {
-    const T* ct = camtab + (long long)CT * pm_cam[q];
-    T ctl[CT];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sv = reinterpret_cast<T*>(smem_raw);  // [CHUNK_SLOTS][9]
+  const T* pts = pts_buf + (long long)st->cur * 3 * P;
+  const int j0 = pchunk[blockIdx.x], j1 = pchunk[blockIdx.x + 1];
+  const int s0 = rowptr_pt[j0], s1 = rowptr_pt[j1];
+  if (s1 - s0 <= CHUNK_SLOTS) {
+    for (int q = s0 + threadIdx.x; q < s1; q += CHUNK_THREADS) {
+      T v[9];
+      lin_pt_obs(q, O, pm_cam, pm_pt, pm_px, pts, camtab, delta, Jpm, v);
 #pragma unroll
-    for (int i = 0; i < CT; ++i) ctl[i] = ct[i];
-    Lin<T> o;
-    lin_obs(ctl, X0, X1, X2, pm_px[q], pm_px[(long long)O + q], delta, o);
-    T pl[NPLANE];
-    lin_to_planes(o, pl);
+      for (int i = 0; i < 9; ++i) sv[(q - s0) * 9 + i] = v[i];
+    }
+    __syncthreads();
+    for (int j = j0 + threadIdx.x; j < j1; j += CHUNK_THREADS) {
+      T acc[9];
 #pragma unroll
-    for (int p = 0; p < NPLANE; ++p) Jpm[(long long)p * O + q] = pl[p];
-    T Jp[6];
-    jp_from(o.A, ctl, Jp);
+      for (int i = 0; i < 9; ++i) acc[i] = T(0);
+      const int q1 = rowptr_pt[j + 1];
+      for (int q = rowptr_pt[j]; q < q1; ++q)
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
+        for (int i = 0; i < 9; ++i) acc[i] += sv[(q - s0) * 9 + i];
 #pragma unroll
-      for (int b = a; b < 3; ++b) v[sym3(a, b)] += Jp[a] * Jp[b] + Jp[3 + a] * Jp[3 + b];
-      g[a] += Jp[a] * o.r0 + Jp[3 + a] * o.r1;
+      for (int i = 0; i < 6; ++i) V[6LL * j + i] = (double)acc[i];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) gp[3LL * j + i] = (double)acc[6 + i];
+    }
+  } else {
+    T acc[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) acc[i] = T(0);
+    for (int q = s0 + threadIdx.x; q < s1; q += CHUNK_THREADS) {
+      T v[9];
+      lin_pt_obs(q, O, pm_cam, pm_pt, pm_px, pts, camtab, delta, Jpm, v);
+#pragma unroll
+      for (int i = 0; i < 9; ++i) acc[i] += v[i];
+    }
+    double d[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) d[i] = (double)acc[i];
+    block_sum_all<9>(d);
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int i = 0; i < 6; ++i) V[6LL * j0 + i] = d[i];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) gp[3LL * j0 + i] = d[6 + i];
     }
   }
-#pragma unroll
-  for (int i = 0; i < 6; ++i) V[6LL * j + i] = (double)v[i];
-#pragma unroll
-  for (int i = 0; i < 3; ++i) gp[3LL * j + i] = (double)g[i];
 }
 
 // ---------------------------------------------------------------------------
@@ -699,68 +752,108 @@ k_cam_combine_schur(int C, const int32_t* __restrict__ cam_piece_ptr, const doub
 // a4: PCG iteration k (S p through two passes, then the vector updates)
 // ---------------------------------------------------------------------------
 
-// Pass A (point-major): t_j = V*_j^{-1} sum_{k in pt j} Jp_k^T (Jc_k p_c(k)).
-// With out_mode 1 (back-substitution): dp_j = -(y0_j + t_j), the trial point
-// theta_p + dp_j is written and gp_j . dp_j is reduced per block.
+// Pass A (point-major): t_j = V*_j^{-1} sum_{k in pt j} Jp_k^T (Jc_k p_c(k)),
+// over one chunk of points (thread per observation, shared-memory segmented
+// sum per point as in k_lin_pt).  With MODE 1 (back-substitution) it forms
+// dp_j = -(y0_j + t_j), writes the trial point theta_p + dp_j and reduces
+// gp_j . dp_j per chunk.
+template <typename T>
+__device__ __forceinline__ void pass_a_obs(int q, long long O, const int32_t* __restrict__ pm_cam,
+                                           const T* __restrict__ Jpm, const T* __restrict__ camtab,
+                                           const T* __restrict__ xc, T& z0, T& z1, T& z2) {
+  const int c = pm_cam[q];
+  T pl[NPLANE];
+  load_planes(Jpm, O, q, pl);
+  const T* xv = xc + 9LL * c;
+  T j0[9], j1[9];
+  jc_rows(pl, j0, j1);
+  T e0 = 0, e1 = 0;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const T xi = xv[i];
+    e0 += j0[i] * xi;
+    e1 += j1[i] * xi;
+  }
+  const T a0 = pl[0] * e0 + pl[3] * e1;
+  const T a1 = pl[1] * e0 + pl[4] * e1;
+  const T a2 = pl[2] * e0 + pl[5] * e1;
+  const T* R = camtab + (long long)CT * c;
+  z0 = R[0] * a0 + R[3] * a1 + R[6] * a2;
+  z1 = R[1] * a0 + R[4] * a1 + R[7] * a2;
+  z2 = R[2] * a0 + R[5] * a1 + R[8] * a2;
+}
+
 template <typename T, int MODE>
-__global__ void __launch_bounds__(PT_THREADS)
-k_pass_a(int P, int O, const int32_t* __restrict__ rowptr_pt, const int32_t* __restrict__ pm_cam,
-         const T* __restrict__ Jpm, const T* __restrict__ camtab, const T* __restrict__ xc,
-         const T* __restrict__ Vinv, const DevState* __restrict__ st, int check_done,
-         T* __restrict__ out, const T* __restrict__ y0, const double* __restrict__ gp,
-         T* __restrict__ pts_buf, double* __restrict__ dot_gp) {
+__device__ __forceinline__ double pass_a_point(int j, int P, T z0, T z1, T z2, const T* __restrict__ Vinv,
+                                               T* __restrict__ out, const T* __restrict__ y0,
+                                               const double* __restrict__ gp, T* __restrict__ pts_buf, int cur) {
+  const T* vi = Vinv + 6LL * j;
+  const T t0 = vi[0] * z0 + vi[1] * z1 + vi[2] * z2;
+  const T t1 = vi[1] * z0 + vi[3] * z1 + vi[4] * z2;
+  const T t2 = vi[2] * z0 + vi[4] * z1 + vi[5] * z2;
+  if (MODE == 0) {
+    out[3LL * j] = t0;
+    out[3LL * j + 1] = t1;
+    out[3LL * j + 2] = t2;
+    return 0.0;
+  }
+  const T d0 = -(y0[3LL * j] + t0), d1 = -(y0[3LL * j + 1] + t1), d2 = -(y0[3LL * j + 2] + t2);
+  out[3LL * j] = d0;
+  out[3LL * j + 1] = d1;
+  out[3LL * j + 2] = d2;
+  const T* src = pts_buf + (long long)cur * 3 * P + 3LL * j;
+  T* dst = pts_buf + (long long)(1 - cur) * 3 * P + 3LL * j;
+  dst[0] = src[0] + d0;
+  dst[1] = src[1] + d1;
+  dst[2] = src[2] + d2;
+  return gp[3LL * j] * (double)d0 + gp[3LL * j + 1] * (double)d1 + gp[3LL * j + 2] * (double)d2;
+}
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(CHUNK_THREADS)
+k_pass_a(const int32_t* __restrict__ pchunk, int P, int O, const int32_t* __restrict__ rowptr_pt,
+         const int32_t* __restrict__ pm_cam, const T* __restrict__ Jpm, const T* __restrict__ camtab,
+         const T* __restrict__ xc, const T* __restrict__ Vinv, const DevState* __restrict__ st, int check_done,
+         T* __restrict__ out, const T* __restrict__ y0, const double* __restrict__ gp, T* __restrict__ pts_buf,
+         double* __restrict__ dot_gp) {
   if (MODE == 0 && check_done && st->pcg_done) return;
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sz = reinterpret_cast<T*>(smem_raw);  // [CHUNK_SLOTS][3]
+  const int cur = MODE == 1 ? st->cur : 0;
+  const int j0 = pchunk[blockIdx.x], j1 = pchunk[blockIdx.x + 1];
+  const int s0 = rowptr_pt[j0], s1 = rowptr_pt[j1];
   double gd = 0.0;
-  if (j < P) {
-    T z0 = 0, z1 = 0, z2 = 0;
-    const int q1 = rowptr_pt[j + 1];
-    for (int q = rowptr_pt[j]; q < q1; ++q) {
-      const int c = pm_cam[q];
-      T pl[NPLANE];
-      load_planes(Jpm, O, q, pl);
-      const T* xv = xc + 9LL * c;
-      T xl[9];
-#pragma unroll
-      for (int i = 0; i < 9; ++i) xl[i] = xv[i];
-      T j0[9], j1[9];
-      jc_rows(pl, j0, j1);
-      T e0 = 0, e1 = 0;
-#pragma unroll
-      for (int i = 0; i < 9; ++i) {
-        e0 += j0[i] * xl[i];
-        e1 += j1[i] * xl[i];
+  if (s1 - s0 <= CHUNK_SLOTS) {
+    for (int q = s0 + threadIdx.x; q < s1; q += CHUNK_THREADS) {
+      T z0, z1, z2;
+      pass_a_obs(q, O, pm_cam, Jpm, camtab, xc, z0, z1, z2);
+      sz[(q - s0) * 3] = z0;
+      sz[(q - s0) * 3 + 1] = z1;
+      sz[(q - s0) * 3 + 2] = z2;
+    }
+    __syncthreads();
+    for (int j = j0 + threadIdx.x; j < j1; j += CHUNK_THREADS) {
+      T z0 = 0, z1 = 0, z2 = 0;
+      const int q1 = rowptr_pt[j + 1];
+      for (int q = rowptr_pt[j]; q < q1; ++q) {
+        z0 += sz[(q - s0) * 3];
+        z1 += sz[(q - s0) * 3 + 1];
+        z2 += sz[(q - s0) * 3 + 2];
       }
-      // A^T e, then R^T
-      const T a0 = pl[0] * e0 + pl[3] * e1;
-      const T a1 = pl[1] * e0 + pl[4] * e1;
-      const T a2 = pl[2] * e0 + pl[5] * e1;
-      const T* R = camtab + (long long)CT * c;
-      z0 += R[0] * a0 + R[3] * a1 + R[6] * a2;
-      z1 += R[1] * a0 + R[4] * a1 + R[7] * a2;
-      z2 += R[2] * a0 + R[5] * a1 + R[8] * a2;
+      gd += pass_a_point<T, MODE>(j, P, z0, z1, z2, Vinv, out, y0, gp, pts_buf, cur);
     }
-    const T* vi = Vinv + 6LL * j;
-    const T t0 = vi[0] * z0 + vi[1] * z1 + vi[2] * z2;
-    const T t1 = vi[1] * z0 + vi[3] * z1 + vi[4] * z2;
-    const T t2 = vi[2] * z0 + vi[4] * z1 + vi[5] * z2;
-    if (MODE == 0) {
-      out[3LL * j] = t0;
-      out[3LL * j + 1] = t1;
-      out[3LL * j + 2] = t2;
-    } else {
-      const T d0 = -(y0[3LL * j] + t0), d1 = -(y0[3LL * j + 1] + t1), d2 = -(y0[3LL * j + 2] + t2);
-      out[3LL * j] = d0;
-      out[3LL * j + 1] = d1;
-      out[3LL * j + 2] = d2;
-      const int cur = st->cur;
-      const T* src = pts_buf + (long long)cur * 3 * P + 3LL * j;
-      T* dst = pts_buf + (long long)(1 - cur) * 3 * P + 3LL * j;
-      dst[0] = src[0] + d0;
-      dst[1] = src[1] + d1;
-      dst[2] = src[2] + d2;
-      gd = gp[3LL * j] * (double)d0 + gp[3LL * j + 1] * (double)d1 + gp[3LL * j + 2] * (double)d2;
+  } else {
+    T z0 = 0, z1 = 0, z2 = 0;
+    for (int q = s0 + threadIdx.x; q < s1; q += CHUNK_THREADS) {
+      T a0, a1, a2;
+      pass_a_obs(q, O, pm_cam, Jpm, camtab, xc, a0, a1, a2);
+      z0 += a0;
+      z1 += a1;
+      z2 += a2;
     }
+    double d[3] = {(double)z0, (double)z1, (double)z2};
+    block_sum_all<3>(d);
+    if (threadIdx.x == 0) gd = pass_a_point<T, MODE>(j0, P, (T)d[0], (T)d[1], (T)d[2], Vinv, out, y0, gp, pts_buf, cur);
   }
   if (MODE == 1) {
     double v[1] = {gd};
@@ -786,6 +879,7 @@ k_pass_b(const int32_t* __restrict__ piece_cam, const int32_t* __restrict__ piec
 #pragma unroll
   for (int i = 0; i < 9; ++i) acc[i] = T(0);
   const int end = piece_end[b];
+#pragma unroll 4
   for (int s = piece_beg[b] + threadIdx.x; s < end; s += PIECE_THREADS) {
     const int j = cm_pt[s];
     T pl[NPLANE];
