@@ -208,6 +208,26 @@ ba_status ba_project(int precision, int C, int P, int O, const void* cams,
 ba_status ba_csr_build(const int32_t* keys, int n, int n_keys,
                        int32_t* perm_out, int32_t* rowptr_out, void* stream);
 
+/* Largest n accepted by ba_csr_build_noalloc. */
+#define BA_NOALLOC_MAX_KEYS (1 << 20)
+
+/* ba_csr_build without any device allocation, for callers that may not
+ * allocate device memory while they run (real-time loops where cudaMalloc /
+ * cudaFree could stall the device, processes whose device memory belongs to
+ * another allocator, code allowed to allocate only at start-up).  The paper
+ * has no counterpart: it is an interface choice of this library.
+ * Same arguments, output and errors as ba_csr_build (keys, perm_out,
+ * rowptr_out dev; n in [0, BA_NOALLOC_MAX_KEYS], larger n gives
+ * BA_ERR_INVALID_ARG); synchronises the stream.  Its scratch is one fixed
+ * __device__ array of about 17 MB that every GPU loading the library holds
+ * until exit; the first call on a device looks up that array's device
+ * address with the device current, so make the first call before any
+ * stream capture.  All calls share the array: calls whose GPU work overlaps
+ * race and must be serialised by the caller. */
+ba_status ba_csr_build_noalloc(const int32_t* keys, int n, int n_keys,
+                               int32_t* perm_out, int32_t* rowptr_out,
+                               void* stream);
+
 /* Number of kernel launches the library has issued in this process (for
  * launch accounting in benchmarks; graph replays count every node). */
 uint64_t ba_kernel_launch_count(void);

@@ -84,6 +84,7 @@ SIGNATURES = {
     "ba_damped_solve": (_S, [_VP, _D, _I, _D, _VP, _VP, ct.POINTER(_I), ct.POINTER(_D), _VP]),
     "ba_project": (_S, [_I, _I, _I, _I, _VP, _VP, _VP, _VP, _VP, _VP]),
     "ba_csr_build": (_S, [_VP, _I, _I, _VP, _VP, _VP]),
+    "ba_csr_build_noalloc": (_S, [_VP, _I, _I, _VP, _VP, _VP]),
     "ba_kernel_launch_count": (ct.c_uint64, []),
     "ba_profile_trials": (_S, [_VP, _I, ct.POINTER(ba_kernel_times)]),
 }

@@ -54,6 +54,20 @@ inline unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
 
+namespace ba {
+
+ba_status set_error(ba_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return st;
+}
+
+}  // namespace ba
+
 struct ba_problem {
   int C = 0, P = 0, O = 0, prec = 0;
   size_t tsize = 8;

@@ -5,10 +5,15 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include "ba.h"
+
 namespace ba {
 
 // Launch accounting (ba_kernel_launch_count).
 void count_launch(uint64_t n = 1);
+
+// Record a message for ba_last_error() and return st.
+ba_status set_error(ba_status st, const char* fmt, ...);
 
 // Stable radix sort + row pointers (ba_sort.cu).  scratch must hold
 // csr_scratch_bytes(n) bytes; d_err gets bit 0 set for a key outside
