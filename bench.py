@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--profile-trials", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--jacobian", choices=["auto", "recompute", "store"], default="auto")
     ap.add_argument("--points", type=int, default=0,
                     help="profiling only: same recipe with fewer points")
     return ap.parse_args()
@@ -157,26 +158,39 @@ class ClockSampler:
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
 
 
-def algorithmic_bytes(kind, C, P, O, npieces, tsize):
-    """Compulsory bytes of one launch: every array element the kernel must
-    read or write, each counted once (per-observation planes and indices,
-    per-point / per-camera vectors)."""
-    planes = 18 * tsize
-    if kind == "pass_b":      # planes + point index per obs; t per point; piece partials
-        return O * (planes + 4) + P * 3 * tsize + npieces * 9 * 8 + C * 9 * tsize
-    if kind == "pass_a":      # planes + camera index per obs; rowptr, V*^-1, t out per point
-        return O * (planes + 4) + P * (4 + 6 * tsize + 3 * tsize) + C * 18 * tsize
-    if kind == "lin_cam":     # pixel + point index in, planes out; points once; partials
-        return O * (2 * tsize + 4 + planes) + P * 3 * tsize + npieces * 54 * 8
+def algorithmic_bytes(kind, C, P, O, npieces, tsize, mf, huber=False):
+    """Compulsory HBM bytes of one launch: every array element the kernel
+    must read or write, each counted once (per-observation planes, indices
+    and weights; per-point / per-camera vectors once)."""
+    ob = 18 * tsize if not mf else (tsize if huber else 0)   # planes or sqrt(w)
+    if kind == "pass_b":   # cm_pt; point record (X, t) per point; camera table; partials
+        return O * (4 + ob) + P * 8 * tsize + npieces * 9 * 8 + C * 16 * tsize
+    if kind == "pass_a1":  # cm_pt (+ sqrt(w)) or planes in, one 4-vector out per obs; points once
+        return O * (4 + ob + 4 * tsize) + (P * 4 * tsize if mf else 0) + C * (16 + 12) * tsize
+    if kind == "pass_a2":  # order map + one 4-vector per obs; rowptr, V*^-1, t out per point
+        return O * (4 + 4 * tsize) + P * (4 + 6 * tsize + 4 * tsize)
+    if kind == "lin_cam":  # pixels + point index in; planes / weights out; points once; partials
+        return O * (2 * tsize + 4 + ob) + P * 3 * tsize + npieces * 54 * 8
     if kind == "lin_pt":
-        return O * (2 * tsize + 4 + planes) + P * (4 + 3 * tsize + 9 * 8) + C * 24 * tsize
+        return O * (2 * tsize + 8 + ob) + P * (4 + 3 * tsize + 9 * 8) + C * 32 * tsize
     if kind == "schur_cam":
-        return O * (planes + 4) + P * 9 * tsize + npieces * 54 * 8
-    if kind == "cost":
-        return O * (2 * tsize + 4 + planes) + P * 6 * tsize + npieces * 2 * 8
-    if kind == "backsub":
-        return O * (planes + 4) + P * (4 + 9 * tsize + 3 * 8 + 9 * tsize) + C * 9 * tsize
+        return O * (4 + ob) + P * ((3 * tsize if mf else 0) + 9 * tsize) + npieces * 54 * 8
+    if kind == "cost":     # pixels, point index, (model) planes; trial + current points, dp
+        return O * (2 * tsize + 4 + ob) + P * 9 * tsize + npieces * 2 * 8
+    if kind == "backsub":  # A1 + A2 of the back-substitution (two launches per trial)
+        return (O * (4 + ob + 4 * tsize) + (P * 4 * tsize if mf else 0)
+                + O * (4 + 4 * tsize) + P * (4 + 6 * tsize + 3 * tsize + 3 * 8 + 9 * tsize)) // 2
     return 0
+
+
+# FP32 operations per observation of the recompute-mode passes (an FMA counts
+# two): the factored Jacobian (61) plus the pass's products.
+FLOPS_PER_OBS = {"pass_b": 119, "pass_a1": 113}
+
+
+def fp32_peak_tflops(sm_mhz):
+    """152 SMs x 128 FP32 lanes x 2 flops per FMA x clock."""
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
 def kernel_source_hash():
@@ -239,7 +253,9 @@ def run_ours(args):
     cams_gt = torch.tensor(scene.cams_gt, dtype=torch.float32, device=dev)
     pts_gt = torch.tensor(scene.points_gt, dtype=torch.float32, device=dev)
     pix = ba.project(cams_gt, pts_gt, ci, pi) + torch.tensor(scene.noise, dtype=torch.float32, device=dev)
-    opts = ba.Options(precision="f32", pcg_maxiter=PCG_MAXITER, pcg_tol=PCG_TOL, use_graph=True)
+    opts = ba.Options(precision="f32", pcg_maxiter=PCG_MAXITER, pcg_tol=PCG_TOL, use_graph=True,
+                      jacobian=args.jacobian)
+    mf = args.jacobian in ("auto", "recompute")
     prob = ba.Problem(scene.cams_init, scene.points_init, ci, pi, pix, opts, device=dev)
     torch.cuda.synchronize()
 
@@ -278,23 +294,37 @@ def run_ours(args):
     npieces = sum(max(1, math.ceil(n / 2048)) if n > 0 else 0 for n in np.bincount(scene.cam_idx, minlength=C))
     total = sum(v[0] for v in per.values())
     kernels = {}
+    peak, peak_kind = peaks()
+    sm_mhz = (clk or {}).get("sm_max_mhz") or 2070.0
+    alu_peak = fp32_peak_tflops(sm_mhz)
     for name, (kms, n) in per.items():
         if n == 0:
             continue
-        b = algorithmic_bytes(name, C, P, O, npieces, tsize)
+        b = algorithmic_bytes(name, C, P, O, npieces, tsize, mf)
         avg = kms / n
         kernels[name] = {"launches": n, "avg_us": 1000.0 * avg, "share": kms / total,
                          "gbs": (b / (avg / 1000.0) / 1e9) if b else None}
+        if mf and name in FLOPS_PER_OBS:
+            kernels[name]["tflops"] = FLOPS_PER_OBS[name] * O / (avg / 1000.0) / 1e12
     dom = max((k for k in kernels if kernels[k]["gbs"]), key=lambda k: per[k][0])
-    peak, peak_kind = peaks()
     src_hash = kernel_source_hash()
     ach = kernels[dom]["gbs"]
     roofline = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak, "unit": "GB/s",
                 "frac": ach / peak, "peak_source": peak_kind,
-                "bytes_per_launch": algorithmic_bytes(dom, C, P, O, npieces, tsize),
+                "bytes_per_launch": algorithmic_bytes(dom, C, P, O, npieces, tsize, mf),
                 "traffic": measured_traffic(dom, src_hash), "kernel_source": src_hash}
+    if "tflops" in kernels[dom]:
+        alu = {"achieved": kernels[dom]["tflops"], "peak": alu_peak, "unit": "TFLOP/s",
+               "frac": kernels[dom]["tflops"] / alu_peak,
+               "flops_per_launch": FLOPS_PER_OBS[dom] * O,
+               "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz"}
+        roofline["hbm"] = {k: roofline[k] for k in ("achieved", "peak", "unit", "frac")}
+        roofline["alu"] = alu
+        if alu["frac"] > roofline["frac"]:
+            roofline.update({"bound": "alu", "achieved": alu["achieved"], "peak": alu["peak"],
+                             "unit": alu["unit"], "frac": alu["frac"], "peak_source": alu["peak_source"]})
     # whole-iteration algorithmic bandwidth (bytes of all big passes / trial time)
-    it_bytes = sum(algorithmic_bytes(k, C, P, O, npieces, tsize) * per[k][1] for k in per)
+    it_bytes = sum(algorithmic_bytes(k, C, P, O, npieces, tsize, mf) * per[k][1] for k in per)
     roofline["iteration_gbs"] = it_bytes / (prof_ms / 1000.0) / 1e9
     roofline["iteration_frac"] = roofline["iteration_gbs"] / peak
 
@@ -344,7 +374,8 @@ def run_ours(args):
                        "l2": "inputs larger than L2 (each PCG pass streams >0.6 GB of "
                              "per-observation data; L2 129 MB)",
                        "parallelism": "replicas" if world > 1 else "single GPU",
-                       "graph": "one CUDA graph per LM trial"},
+                       "graph": "one CUDA graph per LM trial",
+                       "jacobian": "recomputed in every pass" if mf else "stored planes"},
             "gpu_launches": launches, "clocks": clk, "roofline": roofline,
             "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e}
     print(json.dumps(line), flush=True)

@@ -54,6 +54,14 @@ typedef enum {
 
 enum { BA_PREC_F64 = 0, BA_PREC_F32 = 1 };
 
+/* How the passes after the linearisation get the Jacobian blocks:
+ * BA_JAC_STORE writes them once per linearisation (18 numbers per
+ * observation, twice) and streams them; BA_JAC_RECOMPUTE rebuilds them in
+ * every pass from the parameters (no per-observation storage but sqrt(w)
+ * under a robust loss); BA_JAC_AUTO picks RECOMPUTE for BA_PREC_F32 and
+ * STORE for BA_PREC_F64.  Both give the same blocks up to rounding. */
+enum { BA_JAC_AUTO = 0, BA_JAC_RECOMPUTE = 1, BA_JAC_STORE = 2 };
+
 /* Solver options.  up/down are the trust-region factors of the paper's
  * minimum code example (TrustRegion(up=2.0, down=0.5**4), Sec. IV); its
  * PCG(tol=1e-4, maxiter=250) gives pcg_tol / pcg_maxiter.  diag_min/diag_max
@@ -75,6 +83,7 @@ typedef struct {
   double pcg_tol;      /* stop when |r|_2 <= pcg_tol |b|_2, 1e-4 */
   int use_graph;       /* 1: ba_solve replays a captured CUDA graph */
   int max_stats;       /* capacity of the per-trial statistics ring, 4096 */
+  int jacobian_mode;   /* BA_JAC_AUTO, BA_JAC_RECOMPUTE or BA_JAC_STORE */
 } ba_options;
 
 /* Statistics of one LM trial (Alg. 1, one pass of the loop body). */
@@ -237,12 +246,13 @@ enum {
   BA_K_LIN_CAM = 0,   /* a1+a2 camera-major linearisation pass */
   BA_K_LIN_PT = 1,    /* a1+a2 point-major linearisation pass */
   BA_K_SCHUR_CAM = 2, /* a3 camera-major Schur / block-Jacobi pass */
-  BA_K_PASS_A = 3,    /* a4 PCG pass A (point-major, W^T p) */
+  BA_K_PASS_A = 3,    /* a4 PCG pass A1 (camera-major, Jp^T Jc p per observation) */
   BA_K_PASS_B = 4,    /* a4 PCG pass B (camera-major, W t) */
   BA_K_COST = 5,      /* a6 trial cost + model reduction pass */
-  BA_K_BACKSUB = 6,   /* a5 back-substitution pass */
+  BA_K_BACKSUB = 6,   /* a5 back-substitution passes */
   BA_K_OTHER = 7,     /* per-camera / per-point / scalar kernels */
-  BA_K_COUNT = 8
+  BA_K_PASS_A2 = 8,   /* a4 PCG pass A2 (point-major sum, V*^{-1}) */
+  BA_K_COUNT = 9
 };
 
 typedef struct {

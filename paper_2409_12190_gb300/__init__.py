@@ -59,6 +59,7 @@ class Options:
     pcg_tol: float = 1e-4
     use_graph: bool = True
     max_stats: int = 4096
+    jacobian: str = "auto"          # "auto", "recompute" or "store"
 
     @property
     def dtype(self):
@@ -76,6 +77,9 @@ class Options:
         o.pcg_maxiter = int(self.pcg_maxiter)
         o.use_graph = int(bool(self.use_graph))
         o.max_stats = int(self.max_stats)
+        if self.jacobian not in _lib.BA_JAC:
+            raise ValueError("jacobian must be 'auto', 'recompute' or 'store'")
+        o.jacobian_mode = _lib.BA_JAC[self.jacobian]
         return o
 
 

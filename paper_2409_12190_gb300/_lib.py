@@ -12,6 +12,7 @@ STATUS_NAMES = {0: "BA_OK", 1: "BA_ERR_INVALID_ARG", 2: "BA_ERR_CUDA", 3: "BA_ER
                 4: "BA_ERR_TIMEOUT", 5: "BA_ERR_NOT_CONVERGED", 6: "BA_ERR_OOM", 7: "BA_ERR_STATE"}
 BA_PREC_F64 = 0
 BA_PREC_F32 = 1
+BA_JAC = {"auto": 0, "recompute": 1, "store": 2}
 
 
 class ba_options(ct.Structure):
@@ -31,6 +32,7 @@ class ba_options(ct.Structure):
         ("pcg_tol", ct.c_double),
         ("use_graph", ct.c_int),
         ("max_stats", ct.c_int),
+        ("jacobian_mode", ct.c_int),
     ]
 
 
@@ -49,11 +51,11 @@ class ba_iter_stats(ct.Structure):
     ]
 
 
-BA_K_NAMES = ["lin_cam", "lin_pt", "schur_cam", "pass_a", "pass_b", "cost", "backsub", "other"]
+BA_K_NAMES = ["lin_cam", "lin_pt", "schur_cam", "pass_a1", "pass_b", "cost", "backsub", "other", "pass_a2"]
 
 
 class ba_kernel_times(ct.Structure):
-    _fields_ = [("ms", ct.c_double * 8), ("launches", ct.c_int64 * 8), ("trial_ms", ct.c_double)]
+    _fields_ = [("ms", ct.c_double * 9), ("launches", ct.c_int64 * 9), ("trial_ms", ct.c_double)]
 
 
 _VP = ct.c_void_p

@@ -70,15 +70,25 @@ ba_status set_error(ba_status st, const char* fmt, ...) {
 
 struct ba_problem {
   int C = 0, P = 0, O = 0, prec = 0;
+  bool mf = false;  // recompute the Jacobian factors in every pass
   size_t tsize = 8;
   ba_options opt{};
   cudaStream_t s = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   std::vector<void*> allocs;
   // structure (symbolic phase)
+  // Points are renumbered internally (sorted by the first camera that sees
+  // them) so that the points of one camera are close together in memory.
+  // pt_idx, perm_*, rowptr_pt and every per-point array use the internal
+  // numbering; pnew[new] = caller's index, pnewpos[caller's] = new.
   int32_t *cam_idx = nullptr, *pt_idx = nullptr;
   int32_t *perm_cam = nullptr, *rowptr_cam = nullptr, *perm_pt = nullptr, *rowptr_pt = nullptr;
+  int32_t *pnew = nullptr, *pnewpos = nullptr;
+  // the symbolic phase in the caller's numbering (ba_get_csr)
+  int32_t *xperm_cam = nullptr, *xperm_pt = nullptr, *xrowptr_pt = nullptr;
+  void* pts_tmp = nullptr;  // [P][3] staging for reordering parameters
   int32_t *cm_pt = nullptr, *pm_cam = nullptr, *pm_pt = nullptr;
+  int32_t* pm2cm = nullptr;  // camera-major slot of each point-major slot
   int nchunks = 0;
   int32_t* pchunk = nullptr;  // [nchunks + 1] first point of each point chunk
   void *cm_px = nullptr, *pm_px = nullptr, *px_in = nullptr;
@@ -87,12 +97,15 @@ struct ba_problem {
   // parameters, double-buffered (current / trial)
   void *cams = nullptr, *pts = nullptr;
   // linearisation
-  void *camtab = nullptr, *Jcm = nullptr, *Jpm = nullptr;
+  void *camtab = nullptr, *Jcm = nullptr;
+  void *ptab = nullptr;  // [P][8]: X, 0, t, 0
+  void *zbuf = nullptr;  // [O][4]: pass A1 output, camera-major
+  void *cm_sw = nullptr, *pm_sw = nullptr;  // sqrt(w) per observation (recompute mode, robust loss)
   double *U = nullptr, *gc = nullptr, *V = nullptr, *gp = nullptr;
   void *Vinv = nullptr, *y0 = nullptr;
   // PCG
   double *Minv = nullptr, *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
-  void *pT = nullptr, *xT = nullptr, *tpt = nullptr, *dp = nullptr;
+  void *pT = nullptr, *xT = nullptr, *dp = nullptr;
   double* part = nullptr;
   int ncb = 0, npb = 0;
   double *dot_pq = nullptr, *dot_rz = nullptr, *dot_rr = nullptr, *dot_bb = nullptr;
@@ -167,7 +180,7 @@ struct Prof {
   }
 };
 
-template <typename T>
+template <typename T, bool MF>
 void enqueue_lin(ba_problem* h, int gate) {
   cudaStream_t s = h->s;
   const T delta = (T)(h->opt.huber_delta > 0 ? h->opt.huber_delta : 0.0);
@@ -176,10 +189,14 @@ void enqueue_lin(ba_problem* h, int gate) {
     k_cam_prep<T><<<nblk(h->C, 128), 128, 0, s>>>(h->C, (const T*)h->cams, h->st, gate, (T*)h->camtab);
   }
   {
+    Prof pr(h, BA_K_OTHER, -2);
+    k_pt_prep<T><<<nblk(h->P, 256), 256, 0, s>>>(h->P, (const T*)h->pts, h->st, gate, (T*)h->ptab);
+  }
+  {
     Prof pr(h, BA_K_LIN_CAM, -2);
-    k_lin_cam<T><<<h->npieces, PIECE_THREADS, 0, s>>>(
+    k_lin_cam<T, !MF><<<h->npieces, PIECE_THREADS, 0, s>>>(
         h->piece_cam, h->piece_beg, h->piece_end, h->cm_pt, (const T*)h->cm_px, (const T*)h->pts,
-        (const T*)h->camtab, h->st, gate, delta, h->O, h->P, (T*)h->Jcm, h->part);
+        (const T*)h->camtab, h->st, gate, delta, h->O, h->P, (T*)h->Jcm, (T*)h->cm_sw, h->part);
   }
   {
     Prof pr(h, BA_K_OTHER, -2);
@@ -189,12 +206,64 @@ void enqueue_lin(ba_problem* h, int gate) {
     Prof pr(h, BA_K_LIN_PT, -2);
     k_lin_pt<T><<<h->nchunks, CHUNK_THREADS, CHUNK_SLOTS * 9 * sizeof(T), s>>>(
         h->pchunk, h->O, h->rowptr_pt, h->pm_cam, h->pm_pt, (const T*)h->pm_px, (const T*)h->pts,
-        (const T*)h->camtab, h->st, h->P, gate, delta, (T*)h->Jpm, h->V, h->gp);
+        (const T*)h->camtab, h->st, h->P, gate, delta, (T*)h->pm_sw, h->V, h->gp);
   }
-  count_launch(4);
+  count_launch(5);
 }
 
-template <typename T>
+// Passes A1, A2 (MODE 0) and B of S p for p in the pass form xc: t in the
+// point table, pass-B partials in h->part.  k = PCG iteration (profiling).
+template <typename T, bool MF>
+void enqueue_schur_product(ba_problem* h, const T* xc, int k, int check_done) {
+  cudaStream_t s = h->s;
+  {
+    Prof pr(h, BA_K_PASS_A, k);
+    k_pass_a1<T, MF><<<h->npieces, PIECE_THREADS, 0, s>>>(
+        h->piece_cam, h->piece_beg, h->piece_end, h->cm_pt, (const T*)h->Jcm, (const T*)h->cm_sw,
+        (const T*)h->ptab, (const T*)h->camtab, xc, h->st, check_done, h->O, (T*)h->zbuf);
+  }
+  {
+    Prof pr(h, BA_K_PASS_A2, k);
+    k_pass_a2<T, 0><<<h->nchunks, CHUNK_THREADS, CHUNK_SLOTS * 4 * sizeof(T), s>>>(
+        h->pchunk, h->P, h->rowptr_pt, h->pm2cm, (const T*)h->zbuf, (const T*)h->Vinv, h->st, check_done,
+        (T*)h->ptab, nullptr, nullptr, nullptr, nullptr, nullptr);
+  }
+  {
+    Prof pr(h, BA_K_PASS_B, k);
+    k_pass_b<T, MF><<<h->npieces, PIECE_THREADS, 0, s>>>(h->piece_cam, h->piece_beg, h->piece_end, h->cm_pt,
+                                                        (const T*)h->Jcm, (const T*)h->cm_sw, (const T*)h->ptab,
+                                                        (const T*)h->camtab, h->st, check_done, h->O, h->part);
+  }
+  count_launch(3);
+}
+
+// One PCG pass pair plus the vector updates of iteration k.
+template <typename T, bool MF>
+void enqueue_pcg_iter(ba_problem* h, const double* lam_ptr, int k, double tol) {
+  cudaStream_t s = h->s;
+  const double dmin = h->opt.diag_min, dmax = h->opt.diag_max;
+  enqueue_schur_product<T, MF>(h, (const T*)h->pT, k, 1);
+  {
+    Prof pr(h, BA_K_OTHER, k);
+    k_pcg_q<T, MF><<<h->ncb, VT, 0, s>>>(h->C, h->cam_piece_ptr, h->part, h->U, (const T*)h->camtab, lam_ptr,
+                                        dmin, dmax, h->p, h->q, h->dot_pq, h->st, 1);
+  }
+  count_launch(3);
+  {
+    Prof pr(h, BA_K_OTHER, k);
+    k_pcg_update<<<h->ncb, VT, 0, s>>>(h->C, h->ncb, k, h->dot_pq, h->dot_rz, h->dot_rr, h->p, h->q, h->x, h->r,
+                                       h->z, h->Minv, h->st);
+  }
+  {
+    Prof pr(h, BA_K_OTHER, k);
+    k_pcg_direction<T, MF><<<h->ncb, VT, 0, s>>>(h->C, h->ncb, k, tol, h->dot_rz, h->dot_rr,
+                                                         h->dot_bb, h->z, h->p, (const T*)h->camtab, (T*)h->pT,
+                                                         h->st);
+  }
+  count_launch(2);
+}
+
+template <typename T, bool MF>
 void enqueue_solve(ba_problem* h, const double* lam_ptr, int maxiter, double tol) {
   cudaStream_t s = h->s;
   const double dmin = h->opt.diag_min, dmax = h->opt.diag_max;
@@ -205,71 +274,49 @@ void enqueue_solve(ba_problem* h, const double* lam_ptr, int maxiter, double tol
   }
   {
     Prof pr(h, BA_K_SCHUR_CAM);
-    k_schur_cam<T><<<h->npieces, PIECE_THREADS, 0, s>>>(h->piece_cam, h->piece_beg, h->piece_end, h->cm_pt,
-                                                       (const T*)h->Jcm, (const T*)h->camtab, (const T*)h->Vinv,
-                                                       (const T*)h->y0, h->O, h->part);
+    k_schur_cam<T, MF><<<h->npieces, PIECE_THREADS, 0, s>>>(
+        h->piece_cam, h->piece_beg, h->piece_end, h->cm_pt, (const T*)h->Jcm, (const T*)h->camtab,
+        (const T*)h->pts, (const T*)h->cm_sw, h->st, h->P, (const T*)h->Vinv, (const T*)h->y0, h->O, h->part);
   }
   {
     Prof pr(h, BA_K_OTHER);
-    k_cam_combine_schur<T><<<h->ncb, CAM_THREADS, 0, s>>>(
-        h->C, h->cam_piece_ptr, h->part, h->U, h->gc, lam_ptr, dmin, dmax, h->Minv, h->x, h->r, h->z, h->p,
-        (T*)h->pT, h->dot_rz + h->ncb, h->dot_bb, h->st);
+    k_cam_combine_schur<T, MF><<<h->ncb, CAM_THREADS, 0, s>>>(
+        h->C, h->cam_piece_ptr, h->part, h->U, h->gc, (const T*)h->camtab, lam_ptr, dmin, dmax, h->Minv, h->x,
+        h->r, h->z, h->p, (T*)h->pT, h->dot_rz + h->ncb, h->dot_bb, h->st);
   }
   count_launch(3);
-  for (int k = 0; k < maxiter; ++k) {
-    {
-      Prof pr(h, BA_K_PASS_A, k);
-      k_pass_a<T, 0><<<h->nchunks, CHUNK_THREADS, CHUNK_SLOTS * 3 * sizeof(T), s>>>(
-          h->pchunk, h->P, h->O, h->rowptr_pt, h->pm_cam, (const T*)h->Jpm, (const T*)h->camtab,
-          (const T*)h->pT, (const T*)h->Vinv, h->st, 1, (T*)h->tpt, nullptr, nullptr, nullptr, nullptr);
-    }
-    {
-      Prof pr(h, BA_K_PASS_B, k);
-      k_pass_b<T><<<h->npieces, PIECE_THREADS, 0, s>>>(h->piece_cam, h->piece_beg, h->piece_end, h->cm_pt,
-                                                      (const T*)h->Jcm, (const T*)h->camtab, (const T*)h->tpt,
-                                                      h->st, 1, h->O, h->part);
-    }
-    {
-      Prof pr(h, BA_K_OTHER, k);
-      k_pcg_q<<<h->ncb, CAM_THREADS, 0, s>>>(h->C, h->cam_piece_ptr, h->part, h->U, lam_ptr, dmin, dmax, h->p,
-                                             h->q, h->dot_pq, h->st, 1);
-    }
-    {
-      Prof pr(h, BA_K_OTHER, k);
-      k_pcg_update<<<h->ncb, CAM_THREADS, 0, s>>>(h->C, h->ncb, k, h->dot_pq, h->dot_rz, h->dot_rr, h->p, h->q,
-                                                  h->x, h->r, h->z, h->Minv, h->st);
-    }
-    {
-      Prof pr(h, BA_K_OTHER, k);
-      k_pcg_direction<T><<<h->ncb, CAM_THREADS, 0, s>>>(h->C, h->ncb, k, tol, h->dot_rz, h->dot_rr, h->dot_bb,
-                                                       h->z, h->p, (T*)h->pT, h->st);
-    }
-    count_launch(5);
-  }
+  for (int k = 0; k < maxiter; ++k) enqueue_pcg_iter<T, MF>(h, lam_ptr, k, tol);
   {
     Prof pr(h, BA_K_OTHER);
-    k_cam_trial<T><<<h->ncb, CAM_THREADS, 0, s>>>(h->C, h->x, h->gc, (T*)h->cams, h->st, (T*)h->xT, h->dot_gc);
+    k_cam_trial<T, MF><<<h->ncb, CAM_THREADS, 0, s>>>(h->C, h->x, h->gc, (T*)h->cams, (const T*)h->camtab, h->st,
+                                                     (T*)h->xT, h->dot_gc);
   }
   {
     Prof pr(h, BA_K_BACKSUB);
-    k_pass_a<T, 1><<<h->nchunks, CHUNK_THREADS, CHUNK_SLOTS * 3 * sizeof(T), s>>>(
-        h->pchunk, h->P, h->O, h->rowptr_pt, h->pm_cam, (const T*)h->Jpm, (const T*)h->camtab,
-        (const T*)h->xT, (const T*)h->Vinv, h->st, 0, (T*)h->dp, (const T*)h->y0, h->gp, (T*)h->pts, h->dot_gp);
+    k_pass_a1<T, MF><<<h->npieces, PIECE_THREADS, 0, s>>>(
+        h->piece_cam, h->piece_beg, h->piece_end, h->cm_pt, (const T*)h->Jcm, (const T*)h->cm_sw,
+        (const T*)h->ptab, (const T*)h->camtab, (const T*)h->xT, h->st, 0, h->O, (T*)h->zbuf);
   }
-  count_launch(2);
+  {
+    Prof pr(h, BA_K_BACKSUB);
+    k_pass_a2<T, 1><<<h->nchunks, CHUNK_THREADS, CHUNK_SLOTS * 4 * sizeof(T), s>>>(
+        h->pchunk, h->P, h->rowptr_pt, h->pm2cm, (const T*)h->zbuf, (const T*)h->Vinv, h->st, 0, (T*)h->ptab,
+        (T*)h->dp, (const T*)h->y0, h->gp, (T*)h->pts, h->dot_gp);
+  }
+  count_launch(3);
 }
 
-template <typename T>
+template <typename T, bool MF>
 void enqueue_trial(ba_problem* h) {
-  enqueue_lin<T>(h, 1);
-  enqueue_solve<T>(h, &h->st->lam, h->opt.pcg_maxiter, h->opt.pcg_tol);
+  enqueue_lin<T, MF>(h, 1);
+  enqueue_solve<T, MF>(h, &h->st->lam, h->opt.pcg_maxiter, h->opt.pcg_tol);
   const T delta = (T)(h->opt.huber_delta > 0 ? h->opt.huber_delta : 0.0);
   {
     Prof pr(h, BA_K_COST);
-    k_cost_cam<T, true><<<h->npieces, PIECE_THREADS, 0, h->s>>>(
+    k_cost_cam<T, true, MF><<<h->npieces, PIECE_THREADS, 0, h->s>>>(
         h->piece_cam, h->piece_beg, h->piece_end, h->cm_pt, (const T*)h->cm_px, (const T*)h->cams,
-        (const T*)h->pts, h->st, 1, delta, h->C, h->P, h->O, (const T*)h->Jcm, (const T*)h->camtab,
-        (const T*)h->xT, (const T*)h->dp, h->part);
+        (const T*)h->pts, h->st, 1, delta, h->C, h->P, h->O, (const T*)h->Jcm, (const T*)h->cm_sw,
+        (const T*)h->camtab, (const T*)h->xT, (const T*)h->dp, h->part);
   }
   const ba_options& o = h->opt;
   {
@@ -280,19 +327,51 @@ void enqueue_trial(ba_problem* h) {
   count_launch(2);
 }
 
-template <typename T>
+template <typename T, bool MF>
 void enqueue_cost(ba_problem* h) {
   const T delta = (T)(h->opt.huber_delta > 0 ? h->opt.huber_delta : 0.0);
-  k_cost_cam<T, false><<<h->npieces, PIECE_THREADS, 0, h->s>>>(
+  k_cost_cam<T, false, MF><<<h->npieces, PIECE_THREADS, 0, h->s>>>(
       h->piece_cam, h->piece_beg, h->piece_end, h->cm_pt, (const T*)h->cm_px, (const T*)h->cams,
-      (const T*)h->pts, h->st, 0, delta, h->C, h->P, h->O, nullptr, nullptr, nullptr, nullptr, h->part);
+      (const T*)h->pts, h->st, 0, delta, h->C, h->P, h->O, nullptr, nullptr, nullptr, nullptr, nullptr, h->part);
   k_cost_finalize<<<1, 256, 0, h->s>>>(h->npieces, h->part, h->st);
   count_launch(2);
 }
 
-void enqueue_trial_any(ba_problem* h) {
-  if (h->prec == BA_PREC_F32) enqueue_trial<float>(h);
-  else enqueue_trial<double>(h);
+// Call FN<T, MF>(h, args...) for the problem's precision and Jacobian mode.
+#define BA_DISPATCH(h, FN, ...)                        \
+  do {                                                 \
+    if ((h)->prec == BA_PREC_F32) {                    \
+      if ((h)->mf) FN<float, true>(h, ##__VA_ARGS__);  \
+      else FN<float, false>(h, ##__VA_ARGS__);         \
+    } else {                                           \
+      if ((h)->mf) FN<double, true>(h, ##__VA_ARGS__); \
+      else FN<double, false>(h, ##__VA_ARGS__);        \
+    }                                                  \
+  } while (0)
+
+void enqueue_trial_any(ba_problem* h) { BA_DISPATCH(h, enqueue_trial); }
+
+template <typename T, bool MF>
+void launch_export(ba_problem* h, void* Jc, void* Jp, void* w) {
+  const T delta = (T)(h->opt.huber_delta > 0 ? h->opt.huber_delta : 0.0);
+  k_export_lin<T, MF><<<nblk(h->O, 256), 256, 0, h->s>>>(
+      h->O, h->P, h->perm_cam, h->cam_idx, h->cm_pt, (const T*)h->cm_px, (const T*)h->Jcm, (const T*)h->cm_sw,
+      (const T*)h->camtab, (const T*)h->pts, h->st, delta, (T*)Jc, (T*)Jp, (T*)w);
+  count_launch();
+}
+
+// q = S p for p already in h->p (double), damped with *lam_ptr; no PCG state.
+template <typename T, bool MF>
+void enqueue_matvec(ba_problem* h, const double* lam_ptr) {
+  cudaStream_t s = h->s;
+  const double dmin = h->opt.diag_min, dmax = h->opt.diag_max;
+  k_pt_damp<T><<<nblk(h->P, PT_THREADS), PT_THREADS, 0, s>>>(h->P, h->V, h->gp, lam_ptr, dmin, dmax, (T*)h->Vinv,
+                                                            (T*)h->y0);
+  k_pass_vec<T, MF><<<nblk(h->C, 128), 128, 0, s>>>(h->C, h->p, (const T*)h->camtab, (T*)h->pT);
+  enqueue_schur_product<T, MF>(h, (const T*)h->pT, -1, 0);
+  k_pcg_q<T, MF><<<h->ncb, VT, 0, s>>>(h->C, h->cam_piece_ptr, h->part, h->U, (const T*)h->camtab, lam_ptr,
+                                      dmin, dmax, h->p, h->q, nullptr, h->st, 0);
+  count_launch(3);
 }
 
 ba_status check_options(const ba_options* o) {
@@ -306,6 +385,8 @@ ba_status check_options(const ba_options* o) {
   if (o->max_stats < 1 || o->max_stats > (1 << 24)) return fail(BA_ERR_INVALID_ARG, "max_stats out of range");
   if (!(o->huber_delta >= 0) && !(o->huber_delta <= 0))
     return fail(BA_ERR_INVALID_ARG, "huber_delta is NaN");
+  if (o->jacobian_mode < BA_JAC_AUTO || o->jacobian_mode > BA_JAC_STORE)
+    return fail(BA_ERR_INVALID_ARG, "jacobian_mode must be BA_JAC_AUTO, BA_JAC_RECOMPUTE or BA_JAC_STORE");
   return BA_OK;
 }
 
@@ -344,20 +425,59 @@ ba_status create_impl(ba_problem* h, const void* cams, const void* points, const
   if (err & 1) return fail(BA_ERR_INVALID_ARG, "observation index out of range");
   if (err & 2) return fail(BA_ERR_NONFINITE, "non-finite camera, point or pixel value");
 
-  // symbolic phase: stable sorts by camera and by point
+  // symbolic phase (Sec. IV-B), in the caller's numbering: stable sorts of the
+  // observations by camera and by point
+  CU(h->alloc(&h->xperm_cam, O * 4));
+  CU(h->alloc(&h->xperm_pt, O * 4));
+  CU(h->alloc(&h->rowptr_cam, (C + 1) * 4));
+  CU(h->alloc(&h->xrowptr_pt, (P + 1) * 4));
   CU(h->alloc(&h->perm_cam, O * 4));
   CU(h->alloc(&h->perm_pt, O * 4));
-  CU(h->alloc(&h->rowptr_cam, (C + 1) * 4));
   CU(h->alloc(&h->rowptr_pt, (P + 1) * 4));
-  void* scratch = nullptr;
-  CU(cudaMalloc(&scratch, csr_scratch_bytes(h->O)));
-  cudaError_t e1 = csr_build_async(h->cam_idx, h->O, h->C, h->perm_cam, h->rowptr_cam, scratch, &h->st->err, s);
-  cudaError_t e2 = csr_build_async(h->pt_idx, h->O, h->P, h->perm_pt, h->rowptr_pt, scratch, &h->st->err, s);
-  cudaError_t e3 = cudaStreamSynchronize(s);
-  cudaFree(scratch);
-  CU(e1);
-  CU(e2);
-  CU(e3);
+  CU(h->alloc(&h->pnew, P * 4));
+  CU(h->alloc(&h->pnewpos, P * 4));
+  CU(h->alloc(&h->pts_tmp, 3 * P * ts));
+  {
+    const long long nmax = std::max(O, P);
+    void* scratch = nullptr;
+    int32_t *key = nullptr, *tmp = nullptr, *ptx = nullptr;
+    CU(cudaMalloc(&scratch, csr_scratch_bytes((int)nmax)));
+    cudaError_t e = cudaMalloc(&key, std::max(O, P + C + 2) * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&tmp, std::max(O, P + 1) * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&ptx, std::max(O, C + 1) * 4);
+    int* derr = &h->st->err;
+    if (e == cudaSuccess) e = csr_build_async(h->cam_idx, h->O, h->C, h->xperm_cam, h->rowptr_cam, scratch, derr, s);
+    if (e == cudaSuccess) e = csr_build_async(h->pt_idx, h->O, h->P, h->xperm_pt, h->xrowptr_pt, scratch, derr, s);
+    // renumber the points by the first camera that observes them (stable)
+    if (e == cudaSuccess) {
+      k_point_key<<<nblk(P, 256), 256, 0, s>>>(h->P, h->C, h->xrowptr_pt, h->xperm_pt, h->cam_idx, key);
+      e = csr_build_async(key, h->P, h->C + 1, h->pnew, key + P, scratch, derr, s);
+    }
+    if (e == cudaSuccess) {
+      k_invert_perm<<<nblk(P, 256), 256, 0, s>>>(h->P, h->pnew, h->pnewpos);
+      k_gather_i32<<<nblk(O, 256), 256, 0, s>>>(h->O, h->pt_idx, h->pnewpos, ptx);  // internal point index
+      e = cudaMemcpyAsync(h->pts_tmp, h->pts, 3 * P * ts, cudaMemcpyDeviceToDevice, s);
+    }
+    if (e == cudaSuccess) {
+      k_gather_rows<T, 3><<<nblk(P, 256), 256, 0, s>>>(h->P, h->pnew, (const T*)h->pts_tmp, (T*)h->pts);
+      e = cudaMemcpyAsync(h->pt_idx, ptx, O * 4, cudaMemcpyDeviceToDevice, s);
+    }
+    // internal orders: by point (new numbering), and by camera with the
+    // points of each camera in increasing new index
+    if (e == cudaSuccess) e = csr_build_async(h->pt_idx, h->O, h->P, h->perm_pt, h->rowptr_pt, scratch, derr, s);
+    if (e == cudaSuccess) {
+      k_gather_i32<<<nblk(O, 256), 256, 0, s>>>(h->O, h->perm_pt, h->cam_idx, key);
+      e = csr_build_async(key, h->O, h->C, tmp, ptx, scratch, derr, s);
+    }
+    if (e == cudaSuccess) k_gather_i32<<<nblk(O, 256), 256, 0, s>>>(h->O, tmp, h->perm_pt, h->perm_cam);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    count_launch(5);
+    cudaFree(scratch);
+    cudaFree(key);
+    cudaFree(tmp);
+    cudaFree(ptx);
+    CU(e);
+  }
 
   // pieces: each camera's slots cut into runs of at most PIECE
   std::vector<int32_t> rp(C + 1);
@@ -415,12 +535,28 @@ ba_status create_impl(ba_problem* h, const void* cams, const void* points, const
   k_gather_obs<T><<<nblk(O, 256), 256, 0, s>>>(h->O, h->perm_cam, h->perm_pt, h->cam_idx, h->pt_idx,
                                                (const T*)h->px_in, h->cm_pt, (T*)h->cm_px, h->pm_cam,
                                                h->pm_pt, (T*)h->pm_px);
-  count_launch();
+  CU(h->alloc(&h->pm2cm, O * 4));
+  {
+    int32_t* inv = nullptr;
+    CU(cudaMalloc(&inv, O * 4));
+    k_invert_perm<<<nblk(O, 256), 256, 0, s>>>(h->O, h->perm_cam, inv);
+    k_compose_perm<<<nblk(O, 256), 256, 0, s>>>(h->O, h->perm_pt, inv, h->pm2cm);
+    cudaError_t e = cudaStreamSynchronize(s);
+    cudaFree(inv);
+    CU(e);
+  }
+  count_launch(3);
 
   // linearisation and solver buffers
   CU(h->alloc(&h->camtab, CT * C * ts));
-  CU(h->alloc(&h->Jcm, (size_t)NPLANE * O * ts));
-  CU(h->alloc(&h->Jpm, (size_t)NPLANE * O * ts));
+  CU(h->alloc(&h->ptab, 8 * P * ts));
+  CU(h->alloc(&h->zbuf, 4 * O * ts));
+  if (!h->mf) {
+    CU(h->alloc(&h->Jcm, (size_t)NPLANE * O * ts));
+  } else if (h->opt.huber_delta > 0) {
+    CU(h->alloc(&h->cm_sw, O * ts));
+    CU(h->alloc(&h->pm_sw, O * ts));
+  }
   CU(h->alloc(&h->U, 45 * C * 8));
   CU(h->alloc(&h->gc, 9 * C * 8));
   CU(h->alloc(&h->V, 6 * P * 8));
@@ -433,9 +569,9 @@ ba_status create_impl(ba_problem* h, const void* cams, const void* points, const
   CU(h->alloc(&h->z, 9 * C * 8));
   CU(h->alloc(&h->p, 9 * C * 8));
   CU(h->alloc(&h->q, 9 * C * 8));
-  CU(h->alloc(&h->pT, 9 * C * ts));
-  CU(h->alloc(&h->xT, 9 * C * ts));
-  CU(h->alloc(&h->tpt, 3 * P * ts));
+  CU(h->alloc(&h->pT, PV * C * ts));
+  CU(h->alloc(&h->xT, PV * C * ts));
+  CU(cudaMemsetAsync(h->ptab, 0, 8 * P * ts, s));
   CU(h->alloc(&h->dp, 3 * P * ts));
   CU(h->alloc(&h->part, (size_t)PART * std::max(h->npieces, 1) * 8));
   h->ncb = (int)nblk(C, CAM_THREADS);
@@ -451,9 +587,10 @@ ba_status create_impl(ba_problem* h, const void* cams, const void* points, const
   CU(cudaMemsetAsync(h->stats, 0, (size_t)h->cap * sizeof(ba_iter_stats), s));
   CU(cudaMemsetAsync(h->x, 0, 9 * C * 8, s));
   CU(cudaMemsetAsync(h->dp, 0, 3 * P * ts, s));
-  CU(cudaMemsetAsync(h->xT, 0, 9 * C * ts, s));
+  CU(cudaMemsetAsync(h->xT, 0, PV * C * ts, s));
 
-  enqueue_cost<T>(h);
+  if (h->mf) enqueue_cost<T, true>(h);
+  else enqueue_cost<T, false>(h);
   CU(cudaGetLastError());
   CU(cudaMemcpyAsync(&err, &h->st->err, sizeof(int), cudaMemcpyDeviceToHost, s));
   CU(cudaStreamSynchronize(s));
@@ -462,8 +599,7 @@ ba_status create_impl(ba_problem* h, const void* cams, const void* points, const
 }
 
 ba_status run_cost(ba_problem* h) {
-  if (h->prec == BA_PREC_F32) enqueue_cost<float>(h);
-  else enqueue_cost<double>(h);
+  BA_DISPATCH(h, enqueue_cost);
   CU(cudaGetLastError());
   return BA_OK;
 }
@@ -472,6 +608,22 @@ ba_status set_flag(ba_problem* h, size_t offset, int value) {
   // write one int of DevState (pageable source: copied before return)
   CU(cudaMemcpyAsync(reinterpret_cast<char*>(h->st) + offset, &value, sizeof(int), cudaMemcpyHostToDevice, h->s));
   CU(cudaStreamSynchronize(h->s));
+  return BA_OK;
+}
+
+// Copy caller-ordered points (any memory) into parameter buffer `buf`.
+ba_status load_points(ba_problem* h, const void* points, int buf) {
+  const size_t pb = 3ull * h->P * h->tsize;
+  CU(cudaMemcpyAsync(h->pts_tmp, points, pb, cudaMemcpyDefault, h->s));
+  void* dst = (char*)h->pts + buf * pb;
+  if (h->prec == BA_PREC_F32)
+    k_gather_rows<float, 3><<<nblk(h->P, 256), 256, 0, h->s>>>(h->P, h->pnew, (const float*)h->pts_tmp,
+                                                               (float*)dst);
+  else
+    k_gather_rows<double, 3><<<nblk(h->P, 256), 256, 0, h->s>>>(h->P, h->pnew, (const double*)h->pts_tmp,
+                                                                (double*)dst);
+  count_launch();
+  CU(cudaGetLastError());
   return BA_OK;
 }
 
@@ -502,6 +654,7 @@ ba_status ba_options_default(ba_options* o) {
   o->pcg_tol = 1e-4;
   o->use_graph = 1;
   o->max_stats = 4096;
+  o->jacobian_mode = BA_JAC_AUTO;
   return BA_OK;
 }
 
@@ -523,6 +676,7 @@ ba_status ba_problem_create(ba_problem** out, int C, int P, int O, const void* c
   h->P = P;
   h->O = O;
   h->prec = o.precision;
+  h->mf = o.jacobian_mode == BA_JAC_RECOMPUTE || (o.jacobian_mode == BA_JAC_AUTO && o.precision == BA_PREC_F32);
   h->tsize = o.precision == BA_PREC_F32 ? 4 : 8;
   h->opt = o;
   cudaError_t e = cudaStreamCreateWithFlags(&h->s, cudaStreamNonBlocking);
@@ -609,8 +763,18 @@ ba_status ba_get_params(ba_problem* h, void* cams_out, void* points_out, void* s
   const size_t cb = 9ull * h->C * h->tsize, pb = 3ull * h->P * h->tsize;
   if (cams_out)
     CU(cudaMemcpyAsync(cams_out, (char*)h->cams + cur * cb, cb, cudaMemcpyDefault, h->s));
-  if (points_out)
-    CU(cudaMemcpyAsync(points_out, (char*)h->pts + cur * pb, pb, cudaMemcpyDefault, h->s));
+  if (points_out) {
+    // back to the caller's point order
+    const void* src = (const char*)h->pts + cur * pb;
+    if (h->prec == BA_PREC_F32)
+      k_gather_rows<float, 3><<<nblk(h->P, 256), 256, 0, h->s>>>(h->P, h->pnewpos, (const float*)src,
+                                                                 (float*)h->pts_tmp);
+    else
+      k_gather_rows<double, 3><<<nblk(h->P, 256), 256, 0, h->s>>>(h->P, h->pnewpos, (const double*)src,
+                                                                  (double*)h->pts_tmp);
+    count_launch();
+    CU(cudaMemcpyAsync(points_out, h->pts_tmp, pb, cudaMemcpyDefault, h->s));
+  }
   return leave(h, stream);
 }
 
@@ -623,7 +787,11 @@ ba_status ba_set_params(ba_problem* h, const void* cams, const void* points, voi
   CU(cudaStreamSynchronize(h->s));
   const size_t cb = 9ull * h->C * h->tsize, pb = 3ull * h->P * h->tsize;
   if (cams) CU(cudaMemcpyAsync((char*)h->cams + cur * cb, cams, cb, cudaMemcpyDefault, h->s));
-  if (points) CU(cudaMemcpyAsync((char*)h->pts + cur * pb, points, pb, cudaMemcpyDefault, h->s));
+  if (points) {
+    st = load_points(h, points, cur);
+    if (st != BA_OK) return st;
+  }
+  (void)pb;
   st = set_flag(h, offsetof(DevState, need_lin), 1);
   if (st != BA_OK) return st;
   st = run_cost(h);
@@ -692,9 +860,9 @@ ba_status ba_get_state(ba_problem* h, double* out) {
   CU(cudaStreamSynchronize(h->s));
   const size_t nc = 9ull * h->C, np = 3ull * h->P;
   std::vector<char> buf((nc + np) * h->tsize);
-  CU(cudaMemcpy(buf.data(), (char*)h->cams + ds.cur * nc * h->tsize, nc * h->tsize, cudaMemcpyDeviceToHost));
-  CU(cudaMemcpy(buf.data() + nc * h->tsize, (char*)h->pts + ds.cur * np * h->tsize, np * h->tsize,
-                cudaMemcpyDeviceToHost));
+  ba_status st = ba_get_params(h, buf.data(), buf.data() + nc * h->tsize, h->s);
+  if (st != BA_OK) return st;
+  CU(cudaStreamSynchronize(h->s));
   for (size_t i = 0; i < nc + np; ++i)
     out[i] = h->prec == BA_PREC_F32 ? (double)((float*)buf.data())[i] : ((double*)buf.data())[i];
   out[nc + np] = ds.F;
@@ -716,8 +884,9 @@ ba_status ba_set_state(ba_problem* h, const double* in) {
   CU(cudaMemcpyAsync(&ds, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, h->s));
   CU(cudaStreamSynchronize(h->s));
   CU(cudaMemcpy((char*)h->cams + ds.cur * nc * h->tsize, buf.data(), nc * h->tsize, cudaMemcpyHostToDevice));
-  CU(cudaMemcpy((char*)h->pts + ds.cur * np * h->tsize, buf.data() + nc * h->tsize, np * h->tsize,
-                cudaMemcpyHostToDevice));
+  ba_status st = load_points(h, buf.data() + nc * h->tsize, ds.cur);
+  if (st != BA_OK) return st;
+  CU(cudaStreamSynchronize(h->s));
   ds.F = in[nc + np];
   ds.lam = in[nc + np + 1];
   ds.trials = (long long)in[nc + np + 2];
@@ -734,10 +903,10 @@ ba_status ba_get_csr(ba_problem* h, int32_t* perm_cam, int32_t* rowptr_cam, int3
   if (!h) return fail(BA_ERR_INVALID_ARG, "NULL problem");
   ba_status st = enter(h, stream);
   if (st != BA_OK) return st;
-  if (perm_cam) CU(cudaMemcpyAsync(perm_cam, h->perm_cam, 4ull * h->O, cudaMemcpyDeviceToDevice, h->s));
+  if (perm_cam) CU(cudaMemcpyAsync(perm_cam, h->xperm_cam, 4ull * h->O, cudaMemcpyDeviceToDevice, h->s));
   if (rowptr_cam) CU(cudaMemcpyAsync(rowptr_cam, h->rowptr_cam, 4ull * (h->C + 1), cudaMemcpyDeviceToDevice, h->s));
-  if (perm_pt) CU(cudaMemcpyAsync(perm_pt, h->perm_pt, 4ull * h->O, cudaMemcpyDeviceToDevice, h->s));
-  if (rowptr_pt) CU(cudaMemcpyAsync(rowptr_pt, h->rowptr_pt, 4ull * (h->P + 1), cudaMemcpyDeviceToDevice, h->s));
+  if (perm_pt) CU(cudaMemcpyAsync(perm_pt, h->xperm_pt, 4ull * h->O, cudaMemcpyDeviceToDevice, h->s));
+  if (rowptr_pt) CU(cudaMemcpyAsync(rowptr_pt, h->xrowptr_pt, 4ull * (h->P + 1), cudaMemcpyDeviceToDevice, h->s));
   return leave(h, stream);
 }
 
@@ -748,26 +917,12 @@ ba_status ba_linearize(ba_problem* h, double* U, double* V, double* gc, double* 
   if (st != BA_OK) return st;
   st = set_flag(h, offsetof(DevState, need_lin), 1);
   if (st != BA_OK) return st;
-  const double dl = h->opt.huber_delta > 0 ? h->opt.huber_delta : 0.0;
-  if (h->prec == BA_PREC_F32) {
-    enqueue_lin<float>(h, 1);
-    if (Jc || Jp || w)
-      k_export_lin<float><<<nblk(h->O, 256), 256, 0, h->s>>>(h->O, h->P, h->perm_cam, h->cam_idx, h->cm_pt,
-                                                              (const float*)h->cm_px, (const float*)h->Jcm,
-                                                              (const float*)h->camtab, (const float*)h->pts, h->st,
-                                                              (float)dl, (float*)Jc, (float*)Jp, (float*)w);
-  } else {
-    enqueue_lin<double>(h, 1);
-    if (Jc || Jp || w)
-      k_export_lin<double><<<nblk(h->O, 256), 256, 0, h->s>>>(h->O, h->P, h->perm_cam, h->cam_idx, h->cm_pt,
-                                                               (const double*)h->cm_px, (const double*)h->Jcm,
-                                                               (const double*)h->camtab, (const double*)h->pts,
-                                                               h->st, dl, (double*)Jc, (double*)Jp, (double*)w);
-  }
-  if (U) k_unpack_sym<<<nblk(81ll * h->C, 256), 256, 0, h->s>>>(h->C, 9, h->U, U);
-  if (V) k_unpack_sym<<<nblk(9ll * h->P, 256), 256, 0, h->s>>>(h->P, 3, h->V, V);
+  BA_DISPATCH(h, enqueue_lin, 1);
+  if (Jc || Jp || w) BA_DISPATCH(h, launch_export, Jc, Jp, w);
+  if (U) k_unpack_sym<<<nblk(81ll * h->C, 256), 256, 0, h->s>>>(h->C, 9, h->U, nullptr, U);
+  if (V) k_unpack_sym<<<nblk(9ll * h->P, 256), 256, 0, h->s>>>(h->P, 3, h->V, h->pnewpos, V);
   if (gc) CU(cudaMemcpyAsync(gc, h->gc, 72ull * h->C, cudaMemcpyDeviceToDevice, h->s));
-  if (gp) CU(cudaMemcpyAsync(gp, h->gp, 24ull * h->P, cudaMemcpyDeviceToDevice, h->s));
+  if (gp) k_gather_rows<double, 3><<<nblk(h->P, 256), 256, 0, h->s>>>(h->P, h->pnewpos, h->gp, gp);
   count_launch(3);
   CU(cudaGetLastError());
   return leave(h, stream);
@@ -780,36 +935,9 @@ ba_status ba_schur_matvec(ba_problem* h, double lambda, const double* x, double*
   st = set_probe_lambda(h, lambda);
   if (st != BA_OK) return st;
   const double* lp = &h->st->lam_probe;
-  const double dmin = h->opt.diag_min, dmax = h->opt.diag_max;
   CU(cudaMemcpyAsync(h->p, x, 72ull * h->C, cudaMemcpyDeviceToDevice, h->s));
-  if (h->prec == BA_PREC_F32) {
-    using T = float;
-    enqueue_lin<T>(h, 1);
-    k_pt_damp<T><<<nblk(h->P, PT_THREADS), PT_THREADS, 0, h->s>>>(h->P, h->V, h->gp, lp, dmin, dmax, (T*)h->Vinv,
-                                                                 (T*)h->y0);
-    k_cast_vec<T><<<nblk(9ll * h->C, 256), 256, 0, h->s>>>(9ll * h->C, h->p, (T*)h->pT);
-    k_pass_a<T, 0><<<h->nchunks, CHUNK_THREADS, CHUNK_SLOTS * 3 * sizeof(T), h->s>>>(
-        h->pchunk, h->P, h->O, h->rowptr_pt, h->pm_cam, (const T*)h->Jpm, (const T*)h->camtab, (const T*)h->pT,
-        (const T*)h->Vinv, h->st, 0, (T*)h->tpt, nullptr, nullptr, nullptr, nullptr);
-    k_pass_b<T><<<h->npieces, PIECE_THREADS, 0, h->s>>>(h->piece_cam, h->piece_beg, h->piece_end, h->cm_pt,
-                                                       (const T*)h->Jcm, (const T*)h->camtab, (const T*)h->tpt,
-                                                       h->st, 0, h->O, h->part);
-  } else {
-    using T = double;
-    enqueue_lin<T>(h, 1);
-    k_pt_damp<T><<<nblk(h->P, PT_THREADS), PT_THREADS, 0, h->s>>>(h->P, h->V, h->gp, lp, dmin, dmax, (T*)h->Vinv,
-                                                                 (T*)h->y0);
-    k_cast_vec<T><<<nblk(9ll * h->C, 256), 256, 0, h->s>>>(9ll * h->C, h->p, (T*)h->pT);
-    k_pass_a<T, 0><<<h->nchunks, CHUNK_THREADS, CHUNK_SLOTS * 3 * sizeof(T), h->s>>>(
-        h->pchunk, h->P, h->O, h->rowptr_pt, h->pm_cam, (const T*)h->Jpm, (const T*)h->camtab, (const T*)h->pT,
-        (const T*)h->Vinv, h->st, 0, (T*)h->tpt, nullptr, nullptr, nullptr, nullptr);
-    k_pass_b<T><<<h->npieces, PIECE_THREADS, 0, h->s>>>(h->piece_cam, h->piece_beg, h->piece_end, h->cm_pt,
-                                                       (const T*)h->Jcm, (const T*)h->camtab, (const T*)h->tpt,
-                                                       h->st, 0, h->O, h->part);
-  }
-  k_pcg_q<<<h->ncb, CAM_THREADS, 0, h->s>>>(h->C, h->cam_piece_ptr, h->part, h->U, lp, dmin, dmax, h->p, h->q,
-                                            nullptr, h->st, 0);
-  count_launch(5);
+  BA_DISPATCH(h, enqueue_lin, 1);
+  BA_DISPATCH(h, enqueue_matvec, lp);
   CU(cudaMemcpyAsync(y, h->q, 72ull * h->C, cudaMemcpyDeviceToDevice, h->s));
   CU(cudaGetLastError());
   return leave(h, stream);
@@ -824,16 +952,17 @@ ba_status ba_damped_solve(ba_problem* h, double lambda, int maxiter, double tol,
   st = set_probe_lambda(h, lambda);
   if (st != BA_OK) return st;
   const double* lp = &h->st->lam_probe;
-  if (h->prec == BA_PREC_F32) {
-    enqueue_lin<float>(h, 1);
-    enqueue_solve<float>(h, lp, maxiter, tol);
-  } else {
-    enqueue_lin<double>(h, 1);
-    enqueue_solve<double>(h, lp, maxiter, tol);
-  }
+  BA_DISPATCH(h, enqueue_lin, 1);
+  BA_DISPATCH(h, enqueue_solve, lp, maxiter, tol);
   CU(cudaGetLastError());
   if (dc) CU(cudaMemcpyAsync(dc, h->x, 72ull * h->C, cudaMemcpyDeviceToDevice, h->s));
-  if (dp) CU(cudaMemcpyAsync(dp, h->dp, 3ull * h->P * h->tsize, cudaMemcpyDeviceToDevice, h->s));
+  if (dp) {
+    if (h->prec == BA_PREC_F32)
+      k_gather_rows<float, 3><<<nblk(h->P, 256), 256, 0, h->s>>>(h->P, h->pnewpos, (const float*)h->dp, (float*)dp);
+    else
+      k_gather_rows<double, 3><<<nblk(h->P, 256), 256, 0, h->s>>>(h->P, h->pnewpos, (const double*)h->dp,
+                                                                  (double*)dp);
+  }
   DevState ds;
   CU(cudaMemcpyAsync(&ds, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, h->s));
   CU(cudaStreamSynchronize(h->s));

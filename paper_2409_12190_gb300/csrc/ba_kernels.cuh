@@ -1,19 +1,45 @@
 // Device kernels of the LM bundle-adjustment hot path (sm_103a).
 //
-// Layout in HBM (T = float or double, the problem's storage precision):
-//   observations are kept twice, in camera-major order (slot s, the stable
-//   sort by camera) and in point-major order (slot q, the stable sort by
-//   point); each order stores, per observation, the weighted Jacobian factors
-//   as 18 structure-of-arrays planes of length O:
-//     planes 0..5   A = sqrt(w) d pi / d X_cam          (2x3, row-major)
-//     planes 6..11  B = A (-[R X]_x J_l(omega))          (2x3) = d r / d omega
-//     planes 12..17 D = sqrt(w) d pi / d (f, k1, k2)     (2x3)
-//   so the camera block is Jc = [B | A | D] (2x9, Sec. III-C) and the point
-//   block is Jp = A R (2x3) with R from the per-camera table.  W_k = Jc^T Jp
-//   is never stored: every product with it is applied in factored form.
-//   Per camera: a 24-entry table (R, J_l, t, f, k1, k2), U [45] (packed upper
-//   triangle of the 9x9 block), gc [9], the block-Jacobi inverse [45];
-//   per point: V [6], gp [3], V*^{-1} [6], y0 = V*^{-1} gp [3].
+// Per observation k the weighted residual Jacobian (Sec. III-C) is kept in a
+// factored form:
+//   A = sqrt(w) d pi / d X_cam      (2x3)
+//   q = sqrt(w) (d, f |p|^2, f |p|^4)   so  d r / d(f, k1, k2) = p q^T  (2x3)
+//   RX = R X                          (the rotated point)
+// from which, with the camera's R and left Jacobian J_l,
+//   camera block  Jc = [ A (-[RX]_x) J_l | A | p q^T ]   (2x9)
+//   point block   Jp = A R                                (2x3).
+// Products with Jc, Jc^T, Jp, Jp^T are applied in this factored form;
+// W_k = Jc^T Jp is never formed.
+//
+// Two storage modes (a template flag MF on the kernels that need it):
+//   stored  (MF = false)  the 18 numbers A, B = A (-[RX]_x) J_l, D = p q^T are
+//            written once per linearisation, in camera-major order, as
+//            structure-of-arrays planes of length O, and every later pass
+//            streams them (the FP64 path: FP64 arithmetic is scarce on this
+//            GPU, bytes are not);
+//   recompute (MF = true) nothing per observation but sqrt(w) (only under a
+//            robust loss) is stored; every pass recomputes A, q, RX from the
+//            point, the camera table and sqrt(w) (the FP32 path: ~60 FP32
+//            operations per observation replace ~72 bytes of HBM traffic).
+//
+// Per-camera tables (T = float or double):
+//   camtab [C][32]: R[0..8] t[9..11] f k1 k2 [12..14] pad, J_l[16..24], pad
+//   a PCG vector x in factored form [C][12]: J_l x_omega, x_t, x_i, pad, so
+//   that Jc x = A (u x RX + x_t) + p (q . x_i).
+// Per camera U [45] (packed upper triangle), gc [9], block-Jacobi inverse
+// [45]; per point V [6], gp [3], V*^{-1} [6], y0 = V*^{-1} gp [3] (double for
+// the sums, T for what the passes read) and a 32-byte-aligned record
+// ptab [P][8] = (X, 0, t, 0) holding the point and the PCG point vector, so
+// that each per-observation point access is one vector load.
+//
+// The implicit Schur product S p = U* p - W V*^{-1} W^T p runs as three
+// passes, the two heavy ones camera-major (the camera's data in registers):
+//   A1 (camera-major)  z_k = Jp_k^T Jc_k p_c            -> one 4-vector per obs
+//   A2 (point-major)   t_j = V*_j^{-1} sum_{k in j} z_k   (gather through the
+//                      point-to-camera order map, segmented sum per point;
+//                      with the points renumbered by first camera the
+//                      gathers are nearly sequential)
+//   B  (camera-major)  sum_{k in c} Jc_k^T Jp_k t_p(k)   -> per-piece partials
 //
 // Reductions.  Every sum over observations is taken in a fixed order: a
 // camera's observations are cut into pieces of at most PIECE slots, one CTA
@@ -23,8 +49,8 @@
 // chunk computes one observation per thread into shared memory and one
 // thread per point adds its observations in slot order.  No global atomics
 // are used on the numeric path, so every result is bitwise reproducible.
-// Per-observation arithmetic is in T; per-thread partial sums are in T; all
-// cross-thread sums, dot products, costs and the gain ratio are in double.
+// Per-observation arithmetic and per-thread partial sums are in T; sums
+// across warps, dot products, costs and the gain ratio are in double.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -38,9 +64,11 @@ namespace ba {
 constexpr int PIECE = 2048;          // max camera-major slots per piece
 constexpr int PIECE_THREADS = 256;
 constexpr int PT_THREADS = 256;
-constexpr int CAM_THREADS = 128;
+constexpr int CAM_THREADS = 32;
 constexpr int NPLANE = 18;
-constexpr int CT = 24;               // camera table: R[9], Jl[9], t[3], f, k1, k2
+constexpr int CT = 32;               // camera table stride
+constexpr int CT_T = 9, CT_F = 12, CT_K1 = 13, CT_K2 = 14, CT_JL = 16;
+constexpr int PV = 12;               // factored PCG vector stride
 constexpr int PART = 64;             // doubles per piece partial (54 used)
 constexpr int CHUNK_SLOTS = 1024;    // max point-major slots per point chunk
 constexpr int CHUNK_PTS = 1024;      // max points per point chunk
@@ -67,17 +95,39 @@ struct DevState {
 __host__ __device__ constexpr int sym9(int i, int j) { return 9 * i - (i * (i - 1)) / 2 + (j - i); }
 __host__ __device__ constexpr int sym3(int i, int j) { return 3 * i - (i * (i - 1)) / 2 + (j - i); }
 
-__device__ __forceinline__ double warp_sum(double v) {
+template <typename V>
+__device__ __forceinline__ V warp_sum(V v) {
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
   return v;
 }
 
-// Sum NV per-thread values over the block (fixed order) and write them to out
-// (NV doubles).  All threads must call it.  blockDim.x <= 256.
-template <int NV>
+// Error-free sum of two floats: s + e == a + b exactly (Knuth's TwoSum).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// (hi, lo) += (h2, l2) in float-float arithmetic (about 48 significant bits).
+__device__ __forceinline__ void ff_add(float& hi, float& lo, float h2, float l2) {
+  float s, e;
+  two_sum(hi, h2, s, e);
+  e += lo + l2;
+  hi = s + e;
+  lo = e - (hi - s);
+}
+
+// Sum NV per-thread values over the block and write them to out (NV
+// doubles), warps then the warps in order.  Doubles are reduced in double.
+// blockDim.x <= 1024.
+// Floats are reduced in float-float (PRECISE) -- as accurate as a double
+// reduction of the float partials but on the FP32 pipes, which on this GPU
+// are 64x faster than FP64 -- or in plain float for PCG products.  All
+// threads must call it.
+template <int NV, bool PRECISE = true>
 __device__ __forceinline__ void block_sum_store(double (&v)[NV], double* __restrict__ out) {
-  __shared__ double red[8][NV];
+  __shared__ double red[32][NV];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const int nw = (blockDim.x + 31) >> 5;
@@ -94,10 +144,42 @@ __device__ __forceinline__ void block_sum_store(double (&v)[NV], double* __restr
   }
 }
 
-// Same, returning the totals to every thread instead of storing them.
+template <int NV, bool PRECISE = true>
+__device__ __forceinline__ void block_sum_store(float (&v)[NV], double* __restrict__ out) {
+  __shared__ float2 redf[32][NV];
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    float hi = v[i], lo = 0.f;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const float h2 = __shfl_xor_sync(0xffffffffu, hi, off);
+      if (PRECISE) {
+        const float l2 = __shfl_xor_sync(0xffffffffu, lo, off);
+        ff_add(hi, lo, h2, l2);
+      } else {
+        hi += h2;
+      }
+    }
+    if (lane == 0) redf[warp][i] = make_float2(hi, lo);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < NV; i += blockDim.x) {
+    float hi = redf[0][i].x, lo = redf[0][i].y;
+    for (int w = 1; w < nw; ++w) {
+      if (PRECISE) ff_add(hi, lo, redf[w][i].x, redf[w][i].y);
+      else hi += redf[w][i].x;
+    }
+    out[i] = (double)hi + (double)lo;
+  }
+}
+
+// Block sum of NV doubles, returned to every thread.
 template <int NV>
 __device__ __forceinline__ void block_sum_all(double (&v)[NV]) {
-  __shared__ double red2[8][NV];
+  __shared__ double red2[32][NV];
   __shared__ double tot[NV];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
@@ -119,7 +201,7 @@ __device__ __forceinline__ void block_sum_all(double (&v)[NV]) {
   __syncthreads();
 }
 
-// Fixed-order sum of n doubles (stride-strided) by the whole block; every
+// Fixed-order sum of n doubles (a[i * stride]) by the whole block; every
 // thread gets the total.
 __device__ __forceinline__ double block_sum_array(const double* __restrict__ a, int n, int stride) {
   double s = 0.0;
@@ -127,6 +209,17 @@ __device__ __forceinline__ double block_sum_array(const double* __restrict__ a, 
   double v[1] = {s};
   block_sum_all<1>(v);
   return v[0];
+}
+
+// Fixed-order sums of N arrays of n doubles at once (one block reduction).
+template <int N>
+__device__ __forceinline__ void block_sum_arrays(const double* const (&a)[N], int n, double (&out)[N]) {
+#pragma unroll
+  for (int k = 0; k < N; ++k) out[k] = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x)
+#pragma unroll
+    for (int k = 0; k < N; ++k) out[k] += a[k][i];
+  block_sum_all<N>(out);
 }
 
 // ---------------------------------------------------------------------------
@@ -175,38 +268,33 @@ __device__ inline void camera_table(const T* __restrict__ cam, T* __restrict__ c
 #pragma unroll
   for (int i = 0; i < 9; ++i) {
     ct[i] = (T)R[i];
-    ct[9 + i] = (T)Jl[i];
+    ct[CT_JL + i] = (T)Jl[i];
   }
 #pragma unroll
-  for (int i = 0; i < 6; ++i) ct[18 + i] = cam[3 + i];
+  for (int i = 0; i < 6; ++i) ct[CT_T + i] = cam[3 + i];
+  ct[15] = T(0);
+#pragma unroll
+  for (int i = 25; i < CT; ++i) ct[i] = T(0);
 }
 
 // ---------------------------------------------------------------------------
-// One observation: residual, IRLS weight, weighted Jacobian factors
+// One observation
 // ---------------------------------------------------------------------------
-
-template <typename T>
-struct Lin {
-  T A[6], B[6], D[6];  // weighted factors (planes 0..17)
-  T r0, r1;            // weighted residual sqrt(w) r
-  T half_rho;          // 1/2 rho(|r|^2)
-  T w;                 // IRLS weight rho'(|r|^2)
-};
 
 template <typename T>
 __device__ __forceinline__ void project_obs(const T* __restrict__ ct, T X0, T X1, T X2,
                                             T& px, T& py, T& s) {
-  const T P0 = ct[0] * X0 + ct[1] * X1 + ct[2] * X2 + ct[18];
-  const T P1 = ct[3] * X0 + ct[4] * X1 + ct[5] * X2 + ct[19];
-  const T P2 = ct[6] * X0 + ct[7] * X1 + ct[8] * X2 + ct[20];
+  const T P0 = ct[0] * X0 + ct[1] * X1 + ct[2] * X2 + ct[CT_T];
+  const T P1 = ct[3] * X0 + ct[4] * X1 + ct[5] * X2 + ct[CT_T + 1];
+  const T P2 = ct[6] * X0 + ct[7] * X1 + ct[8] * X2 + ct[CT_T + 2];
   const T iz = T(1) / P2;
   px = -P0 * iz;
   py = -P1 * iz;
   const T r2 = px * px + py * py;
-  s = ct[21] * (T(1) + r2 * (ct[22] + ct[23] * r2));
+  s = ct[CT_F] * (T(1) + r2 * (ct[CT_K1] + ct[CT_K2] * r2));
 }
 
-// Huber: half_rho = 1/2 rho(s), returns sqrt(w)
+// Huber on |r|: half_rho = 1/2 rho(s); returns sqrt(w), w = rho'(s).
 template <typename T>
 __device__ __forceinline__ T huber_weight(T sq, T delta, T& half_rho, T& w) {
   if (delta > T(0) && sq > delta * delta) {
@@ -220,51 +308,82 @@ __device__ __forceinline__ T huber_weight(T sq, T delta, T& half_rho, T& w) {
   return T(1);
 }
 
+// Factored Jacobian of one observation (weights folded in).
 template <typename T>
-__device__ __forceinline__ void lin_obs(const T* __restrict__ ct, T X0, T X1, T X2, T u0, T u1,
-                                        T delta, Lin<T>& o) {
-  const T RX0 = ct[0] * X0 + ct[1] * X1 + ct[2] * X2;
-  const T RX1 = ct[3] * X0 + ct[4] * X1 + ct[5] * X2;
-  const T RX2 = ct[6] * X0 + ct[7] * X1 + ct[8] * X2;
-  const T P0 = RX0 + ct[18], P1 = RX1 + ct[19], P2 = RX2 + ct[20];
-  const T f = ct[21], k1 = ct[22], k2 = ct[23];
+struct Fac {
+  T RX0, RX1, RX2;   // R X
+  T px, py;          // normalised image point
+  T A[6];            // sqrt(w) d pi / d X_cam
+  T q0, q1, q2;      // sqrt(w) (d, f |p|^2, f |p|^4)
+};
+
+// d pi / d p = s I + m p p^T (s = f d, m = f (2 k1 + 4 k2 |p|^2));
+// d p / d X_cam = -(1/X_cam[2]) [[1, 0, p_x], [0, 1, p_y]].
+template <typename T>
+__device__ __forceinline__ void fac_obs(const T* __restrict__ ct, T X0, T X1, T X2, T sw, Fac<T>& o) {
+  o.RX0 = ct[0] * X0 + ct[1] * X1 + ct[2] * X2;
+  o.RX1 = ct[3] * X0 + ct[4] * X1 + ct[5] * X2;
+  o.RX2 = ct[6] * X0 + ct[7] * X1 + ct[8] * X2;
+  const T P0 = o.RX0 + ct[CT_T], P1 = o.RX1 + ct[CT_T + 1], P2 = o.RX2 + ct[CT_T + 2];
+  const T f = ct[CT_F], k1 = ct[CT_K1], k2 = ct[CT_K2];
   const T iz = T(1) / P2;
   const T px = -P0 * iz, py = -P1 * iz;
+  o.px = px;
+  o.py = py;
   const T r2 = px * px + py * py;
   const T d = T(1) + r2 * (k1 + k2 * r2);
   const T s = f * d;
-  const T r0 = s * px - u0, r1 = s * py - u1;
-  T half_rho, w;
-  const T sw = huber_weight(r0 * r0 + r1 * r1, delta, half_rho, w);
-  o.half_rho = half_rho;
-  o.w = w;
-  o.r0 = sw * r0;
-  o.r1 = sw * r1;
-  // d pi / d p = s I + m p p^T,  m = f (2 k1 + 4 k2 |p|^2)
   const T m = f * (T(2) * k1 + T(4) * k2 * r2);
   const T a00 = s + m * px * px, a01 = m * px * py, a11 = s + m * py * py;
-  // d p / d X_cam = n [[1,0,px],[0,1,py]], n = -1/P2
   const T n = -iz * sw;
-  const T A0 = n * a00, A1 = n * a01, A2 = n * (a00 * px + a01 * py);
-  const T A3 = n * a01, A4 = n * a11, A5 = n * (a01 * px + a11 * py);
-  o.A[0] = A0; o.A[1] = A1; o.A[2] = A2; o.A[3] = A3; o.A[4] = A4; o.A[5] = A5;
-  // row a of A (-[RX]_x) = RX x a ; then times J_l
-  const T c0 = RX1 * A2 - RX2 * A1, c1 = RX2 * A0 - RX0 * A2, c2 = RX0 * A1 - RX1 * A0;
-  const T e0 = RX1 * A5 - RX2 * A4, e1 = RX2 * A3 - RX0 * A5, e2 = RX0 * A4 - RX1 * A3;
-  const T* Jl = ct + 9;
-  o.B[0] = c0 * Jl[0] + c1 * Jl[3] + c2 * Jl[6];
-  o.B[1] = c0 * Jl[1] + c1 * Jl[4] + c2 * Jl[7];
-  o.B[2] = c0 * Jl[2] + c1 * Jl[5] + c2 * Jl[8];
-  o.B[3] = e0 * Jl[0] + e1 * Jl[3] + e2 * Jl[6];
-  o.B[4] = e0 * Jl[1] + e1 * Jl[4] + e2 * Jl[7];
-  o.B[5] = e0 * Jl[2] + e1 * Jl[5] + e2 * Jl[8];
-  // d pi / d (f, k1, k2) = (d p, f |p|^2 p, f |p|^4 p)
-  const T q0 = sw * d, q1 = sw * f * r2, q2 = sw * f * r2 * r2;
-  o.D[0] = q0 * px; o.D[1] = q1 * px; o.D[2] = q2 * px;
-  o.D[3] = q0 * py; o.D[4] = q1 * py; o.D[5] = q2 * py;
+  o.A[0] = n * a00;
+  o.A[1] = n * a01;
+  o.A[2] = n * (a00 * px + a01 * py);
+  o.A[3] = n * a01;
+  o.A[4] = n * a11;
+  o.A[5] = n * (a01 * px + a11 * py);
+  o.q0 = sw * d;
+  o.q1 = sw * f * r2;
+  o.q2 = o.q1 * r2;
 }
 
-// Camera row a of Jc = [B | A | D] as 9 values.
+// Planes A, B = A (-[RX]_x) J_l, D = p q^T from the factored form.
+template <typename T>
+__device__ __forceinline__ void fac_planes(const Fac<T>& o, const T* __restrict__ Jl, T (&pl)[NPLANE]) {
+#pragma unroll
+  for (int a = 0; a < 2; ++a) {
+    const T* Ar = o.A + 3 * a;
+    // row a of A (-[RX]_x) = RX x A_row, then times J_l
+    const T c0 = o.RX1 * Ar[2] - o.RX2 * Ar[1];
+    const T c1 = o.RX2 * Ar[0] - o.RX0 * Ar[2];
+    const T c2 = o.RX0 * Ar[1] - o.RX1 * Ar[0];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      pl[3 * a + j] = Ar[j];
+      pl[6 + 3 * a + j] = c0 * Jl[j] + c1 * Jl[3 + j] + c2 * Jl[6 + j];
+    }
+    const T pa = a == 0 ? o.px : o.py;
+    pl[12 + 3 * a] = pa * o.q0;
+    pl[13 + 3 * a] = pa * o.q1;
+    pl[14 + 3 * a] = pa * o.q2;
+  }
+}
+
+// Residual, weight and factored Jacobian of one observation.
+template <typename T>
+__device__ __forceinline__ void lin_obs(const T* __restrict__ ct, T X0, T X1, T X2, T u0, T u1, T delta,
+                                        Fac<T>& o, T& r0w, T& r1w, T& half_rho, T& sw) {
+  T px, py, s;
+  project_obs(ct, X0, X1, X2, px, py, s);
+  const T r0 = s * px - u0, r1 = s * py - u1;
+  T w;
+  sw = huber_weight(r0 * r0 + r1 * r1, delta, half_rho, w);
+  r0w = sw * r0;
+  r1w = sw * r1;
+  fac_obs(ct, X0, X1, X2, sw, o);
+}
+
+// Camera rows of Jc = [B | A | D] as 9 values each.
 template <typename T>
 __device__ __forceinline__ void jc_rows(const T* __restrict__ pl, T (&j0)[9], T (&j1)[9]) {
   j0[0] = pl[6]; j0[1] = pl[7]; j0[2] = pl[8];
@@ -291,14 +410,65 @@ __device__ __forceinline__ void load_planes(const T* __restrict__ J, long long O
   for (int p = 0; p < NPLANE; ++p) pl[p] = J[p * O + s];
 }
 
+// Four consecutive T as one vector access (the address is 4 * sizeof(T)
+// aligned: every caller indexes a stride-4 or stride-8 table).
+__device__ __forceinline__ void load4(const float* __restrict__ p, float& a, float& b, float& c, float& d) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  a = v.x; b = v.y; c = v.z; d = v.w;
+}
+__device__ __forceinline__ void load4(const double* __restrict__ p, double& a, double& b, double& c, double& d) {
+  const double2 v0 = reinterpret_cast<const double2*>(p)[0];
+  const double2 v1 = reinterpret_cast<const double2*>(p)[1];
+  a = v0.x; b = v0.y; c = v1.x; d = v1.y;
+}
+__device__ __forceinline__ void store4(float* __restrict__ p, float a, float b, float c, float d) {
+  *reinterpret_cast<float4*>(p) = make_float4(a, b, c, d);
+}
+__device__ __forceinline__ void store4(double* __restrict__ p, double a, double b, double c, double d) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(a, b);
+  reinterpret_cast<double2*>(p)[1] = make_double2(c, d);
+}
+
+// Jc x with x in factored form xv = [J_l x_omega, x_t, x_i].
 template <typename T>
-__device__ __forceinline__ void lin_to_planes(const Lin<T>& o, T (&pl)[NPLANE]) {
+__device__ __forceinline__ void jc_times_fac(const Fac<T>& o, const T* __restrict__ xv, T& e0, T& e1) {
+  const T w0 = xv[1] * o.RX2 - xv[2] * o.RX1 + xv[3];
+  const T w1 = xv[2] * o.RX0 - xv[0] * o.RX2 + xv[4];
+  const T w2 = xv[0] * o.RX1 - xv[1] * o.RX0 + xv[5];
+  const T qi = o.q0 * xv[6] + o.q1 * xv[7] + o.q2 * xv[8];
+  e0 = o.A[0] * w0 + o.A[1] * w1 + o.A[2] * w2 + o.px * qi;
+  e1 = o.A[3] * w0 + o.A[4] * w1 + o.A[5] * w2 + o.py * qi;
+}
+
+// Jc^T h accumulated in the form [RX x (A^T h) | A^T h | q (p . h)]: the
+// first three must still be multiplied by J_l^T (per camera, once per sum).
+template <typename T>
+__device__ __forceinline__ void jct_fac_acc(const Fac<T>& o, T h0, T h1, T (&acc)[9]) {
+  const T v0 = o.A[0] * h0 + o.A[3] * h1;
+  const T v1 = o.A[1] * h0 + o.A[4] * h1;
+  const T v2 = o.A[2] * h0 + o.A[5] * h1;
+  acc[0] += o.RX1 * v2 - o.RX2 * v1;
+  acc[1] += o.RX2 * v0 - o.RX0 * v2;
+  acc[2] += o.RX0 * v1 - o.RX1 * v0;
+  acc[3] += v0;
+  acc[4] += v1;
+  acc[5] += v2;
+  const T ph = o.px * h0 + o.py * h1;
+  acc[6] += o.q0 * ph;
+  acc[7] += o.q1 * ph;
+  acc[8] += o.q2 * ph;
+}
+
+// Factored form of a camera vector x: [J_l x_omega, x_t, x_i, 0, 0, 0].
+template <typename T>
+__device__ __forceinline__ void to_factored(const T* __restrict__ Jl, const double* __restrict__ x,
+                                            T* __restrict__ out) {
 #pragma unroll
-  for (int i = 0; i < 6; ++i) {
-    pl[i] = o.A[i];
-    pl[6 + i] = o.B[i];
-    pl[12 + i] = o.D[i];
-  }
+  for (int i = 0; i < 3; ++i)
+    out[i] = (T)((double)Jl[3 * i] * x[0] + (double)Jl[3 * i + 1] * x[1] + (double)Jl[3 * i + 2] * x[2]);
+#pragma unroll
+  for (int i = 3; i < 9; ++i) out[i] = (T)x[i];
+  out[9] = out[10] = out[11] = T(0);
 }
 
 // ---------------------------------------------------------------------------
@@ -367,14 +537,70 @@ __global__ void k_cam_prep(int C, const T* __restrict__ cams_buf, const DevState
   camera_table(cams_buf + (long long)st->cur * 9 * C + 9LL * c, camtab + (long long)CT * c);
 }
 
-// Camera-major pass: write the planes, reduce U (45), gc (9) per piece.
+// Point table [P][8]: X in 0..2 (from the current parameters); 4..6 hold the
+// PCG vector t that pass A writes for pass B.
 template <typename T>
+__global__ void k_pt_prep(int P, const T* __restrict__ pts_buf, const DevState* __restrict__ st, int gate,
+                          T* __restrict__ ptab) {
+  if (gate && !st->need_lin) return;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= P) return;
+  const T* X = pts_buf + (long long)st->cur * 3 * P + 3LL * j;
+  store4(ptab + 8LL * j, X[0], X[1], X[2], T(0));
+}
+
+// key_j = smallest camera that observes point j (C if none), from the
+// stable CSR of the observations by point.
+__global__ void k_point_key(int P, int C, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ perm,
+                            const int32_t* __restrict__ cam_idx, int32_t* __restrict__ key) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= P) return;
+  int k = C;
+  for (int q = rowptr[j]; q < rowptr[j + 1]; ++q) k = min(k, cam_idx[perm[q]]);
+  key[j] = k;
+}
+
+// dst[i] = src[idx[i]]
+__global__ void k_gather_i32(int n, const int32_t* __restrict__ idx, const int32_t* __restrict__ src,
+                             int32_t* __restrict__ dst) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = src[idx[i]];
+}
+
+// dst[i][:] = src[idx[i]][:] for rows of W values
+template <typename X, int W>
+__global__ void k_gather_rows(int n, const int32_t* __restrict__ idx, const X* __restrict__ src,
+                              X* __restrict__ dst) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const long long r = idx[i];
+#pragma unroll
+  for (int w = 0; w < W; ++w) dst[W * i + w] = src[W * r + w];
+}
+
+// inv[perm[s]] = s
+__global__ void k_invert_perm(int O, const int32_t* __restrict__ perm, int32_t* __restrict__ inv) {
+  const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < O) inv[perm[s]] = (int32_t)s;
+}
+
+// out[s] = inv_b[perm_a[s]]: the slot, in order b, of the observation at slot
+// s of order a (e.g. the point-major slot of each camera-major slot).
+__global__ void k_compose_perm(int O, const int32_t* __restrict__ perm_a, const int32_t* __restrict__ inv_b,
+                               int32_t* __restrict__ out) {
+  const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < O) out[s] = inv_b[perm_a[s]];
+}
+
+// Camera-major pass: residuals, weights, U (45) and gc (9) per piece; in the
+// stored mode also the planes, in any mode sqrt(w) when sw_out is given.
+template <typename T, bool STORE>
 __global__ void __launch_bounds__(PIECE_THREADS)
 k_lin_cam(const int32_t* __restrict__ piece_cam, const int32_t* __restrict__ piece_beg,
           const int32_t* __restrict__ piece_end, const int32_t* __restrict__ cm_pt,
           const T* __restrict__ cm_px, const T* __restrict__ pts_buf, const T* __restrict__ camtab,
           const DevState* __restrict__ st, int gate, T delta, int O, int P, T* __restrict__ Jcm,
-          double* __restrict__ part) {
+          T* __restrict__ sw_out, double* __restrict__ part) {
   if (gate && !st->need_lin) return;
   __shared__ T sct[CT];
   const int b = blockIdx.x;
@@ -388,25 +614,27 @@ k_lin_cam(const int32_t* __restrict__ piece_cam, const int32_t* __restrict__ pie
   const int end = piece_end[b];
   for (int s = piece_beg[b] + threadIdx.x; s < end; s += PIECE_THREADS) {
     const int j = cm_pt[s];
-    Lin<T> o;
-    lin_obs(sct, pts[3LL * j], pts[3LL * j + 1], pts[3LL * j + 2], cm_px[s], cm_px[(long long)O + s], delta, o);
+    Fac<T> o;
+    T r0, r1, hr, sw;
+    lin_obs(sct, pts[3LL * j], pts[3LL * j + 1], pts[3LL * j + 2], cm_px[s], cm_px[(long long)O + s], delta, o,
+            r0, r1, hr, sw);
+    if (sw_out) sw_out[s] = sw;
     T pl[NPLANE];
-    lin_to_planes(o, pl);
+    fac_planes(o, sct + CT_JL, pl);
+    if (STORE) {
 #pragma unroll
-    for (int p = 0; p < NPLANE; ++p) Jcm[(long long)p * O + s] = pl[p];
+      for (int p = 0; p < NPLANE; ++p) Jcm[(long long)p * O + s] = pl[p];
+    }
     T j0[9], j1[9];
     jc_rows(pl, j0, j1);
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
 #pragma unroll
       for (int k = i; k < 9; ++k) acc[sym9(i, k)] += j0[i] * j0[k] + j1[i] * j1[k];
-      acc[45 + i] += j0[i] * o.r0 + j1[i] * o.r1;
+      acc[45 + i] += j0[i] * r0 + j1[i] * r1;
     }
   }
-  double v[54];
-#pragma unroll
-  for (int i = 0; i < 54; ++i) v[i] = (double)acc[i];
-  block_sum_store<54>(v, part + (long long)PART * b);
+  block_sum_store<54>(acc, part + (long long)PART * b);
 }
 
 // Add the pieces of each camera in order: U [C][45], gc [C][9].
@@ -425,8 +653,8 @@ __global__ void k_cam_combine_lin(int C, const int32_t* __restrict__ cam_piece_p
   }
 }
 
-// Point-major pass over one chunk of points: write the planes, V (6) and
-// gp (3) per point.  One thread per observation (coalesced plane stores);
+// Point-major pass over one chunk of points: V (6) and gp (3) per point,
+// and sqrt(w) when sw_out is given.  One thread per observation (coalesced);
 // each observation's 9 contributions go to shared memory and one thread per
 // point adds its observations in slot order.  A point with more than
 // CHUNK_SLOTS observations is a chunk of its own and is reduced by the block.
@@ -434,25 +662,24 @@ template <typename T>
 __device__ __forceinline__ void lin_pt_obs(int q, int O, const int32_t* __restrict__ pm_cam,
                                            const int32_t* __restrict__ pm_pt, const T* __restrict__ pm_px,
                                            const T* __restrict__ pts, const T* __restrict__ camtab, T delta,
-                                           T* __restrict__ Jpm, T (&v)[9]) {
+                                           T* __restrict__ sw_out, T (&v)[9]) {
   const int j = pm_pt[q];
   const T* ct = camtab + (long long)CT * pm_cam[q];
   T ctl[CT];
 #pragma unroll
   for (int i = 0; i < CT; ++i) ctl[i] = ct[i];
-  Lin<T> o;
-  lin_obs(ctl, pts[3LL * j], pts[3LL * j + 1], pts[3LL * j + 2], pm_px[q], pm_px[(long long)O + q], delta, o);
-  T pl[NPLANE];
-  lin_to_planes(o, pl);
-#pragma unroll
-  for (int p = 0; p < NPLANE; ++p) Jpm[(long long)p * O + q] = pl[p];
+  Fac<T> o;
+  T r0, r1, hr, sw;
+  lin_obs(ctl, pts[3LL * j], pts[3LL * j + 1], pts[3LL * j + 2], pm_px[q], pm_px[(long long)O + q], delta, o, r0,
+          r1, hr, sw);
+  if (sw_out) sw_out[q] = sw;
   T Jp[6];
   jp_from(o.A, ctl, Jp);
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
 #pragma unroll
     for (int b = a; b < 3; ++b) v[sym3(a, b)] = Jp[a] * Jp[b] + Jp[3 + a] * Jp[3 + b];
-    v[6 + a] = Jp[a] * o.r0 + Jp[3 + a] * o.r1;
+    v[6 + a] = Jp[a] * r0 + Jp[3 + a] * r1;
   }
 }
 
@@ -461,7 +688,7 @@ __global__ void __launch_bounds__(CHUNK_THREADS)
 k_lin_pt(const int32_t* __restrict__ pchunk, int O, const int32_t* __restrict__ rowptr_pt,
          const int32_t* __restrict__ pm_cam, const int32_t* __restrict__ pm_pt, const T* __restrict__ pm_px,
          const T* __restrict__ pts_buf, const T* __restrict__ camtab, const DevState* __restrict__ st, int P,
-         int gate, T delta, T* __restrict__ Jpm, double* __restrict__ V, double* __restrict__ gp) {
+         int gate, T delta, T* __restrict__ sw_out, double* __restrict__ V, double* __restrict__ gp) {
   if (gate && !st->need_lin) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sv = reinterpret_cast<T*>(smem_raw);  // [CHUNK_SLOTS][9]
@@ -471,7 +698,7 @@ k_lin_pt(const int32_t* __restrict__ pchunk, int O, const int32_t* __restrict__ 
   if (s1 - s0 <= CHUNK_SLOTS) {
     for (int q = s0 + threadIdx.x; q < s1; q += CHUNK_THREADS) {
       T v[9];
-      lin_pt_obs(q, O, pm_cam, pm_pt, pm_px, pts, camtab, delta, Jpm, v);
+      lin_pt_obs<T>(q, O, pm_cam, pm_pt, pm_px, pts, camtab, delta, sw_out, v);
 #pragma unroll
       for (int i = 0; i < 9; ++i) sv[(q - s0) * 9 + i] = v[i];
     }
@@ -495,7 +722,7 @@ k_lin_pt(const int32_t* __restrict__ pchunk, int O, const int32_t* __restrict__ 
     for (int i = 0; i < 9; ++i) acc[i] = T(0);
     for (int q = s0 + threadIdx.x; q < s1; q += CHUNK_THREADS) {
       T v[9];
-      lin_pt_obs(q, O, pm_cam, pm_pt, pm_px, pts, camtab, delta, Jpm, v);
+      lin_pt_obs<T>(q, O, pm_cam, pm_pt, pm_px, pts, camtab, delta, sw_out, v);
 #pragma unroll
       for (int i = 0; i < 9; ++i) acc[i] += v[i];
     }
@@ -545,19 +772,35 @@ __global__ void k_pt_damp(int P, const double* __restrict__ V, const double* __r
   y0[3LL * j + 2] = (T)(inv[2] * g0 + inv[4] * g1 + inv[5] * g2);
 }
 
+// The 18 planes of camera-major slot s: loaded (stored mode) or recomputed.
+template <typename T, bool MF>
+__device__ __forceinline__ void cm_planes(const T* __restrict__ Jcm, long long O, int s, const T* __restrict__ sct,
+                                          const T* __restrict__ pts, int j, const T* __restrict__ sw,
+                                          T (&pl)[NPLANE]) {
+  if (MF) {
+    Fac<T> o;
+    fac_obs(sct, pts[3LL * j], pts[3LL * j + 1], pts[3LL * j + 2], sw ? sw[s] : T(1), o);
+    fac_planes(o, sct + CT_JL, pl);
+  } else {
+    load_planes(Jcm, O, s, pl);
+  }
+}
+
 // Camera-major pass: per piece, sum_k Jc^T (Jp V*^{-1} Jp^T) Jc (45) and
 // sum_k Jc^T Jp y0 (9).
-template <typename T>
+template <typename T, bool MF>
 __global__ void __launch_bounds__(PIECE_THREADS)
 k_schur_cam(const int32_t* __restrict__ piece_cam, const int32_t* __restrict__ piece_beg,
             const int32_t* __restrict__ piece_end, const int32_t* __restrict__ cm_pt,
-            const T* __restrict__ Jcm, const T* __restrict__ camtab, const T* __restrict__ Vinv,
+            const T* __restrict__ Jcm, const T* __restrict__ camtab, const T* __restrict__ pts_buf,
+            const T* __restrict__ cm_sw, const DevState* __restrict__ st, int P, const T* __restrict__ Vinv,
             const T* __restrict__ y0, int O, double* __restrict__ part) {
-  __shared__ T sR[9];
+  __shared__ T sct[CT];
   const int b = blockIdx.x;
   const int c = piece_cam[b];
-  if (threadIdx.x < 9) sR[threadIdx.x] = camtab[(long long)CT * c + threadIdx.x];
+  if (threadIdx.x < CT) sct[threadIdx.x] = camtab[(long long)CT * c + threadIdx.x];
   __syncthreads();
+  const T* pts = pts_buf + (long long)st->cur * 3 * P;
   T acc[54];
 #pragma unroll
   for (int i = 0; i < 54; ++i) acc[i] = T(0);
@@ -565,12 +808,11 @@ k_schur_cam(const int32_t* __restrict__ piece_cam, const int32_t* __restrict__ p
   for (int s = piece_beg[b] + threadIdx.x; s < end; s += PIECE_THREADS) {
     const int j = cm_pt[s];
     T pl[NPLANE];
-    load_planes(Jcm, O, s, pl);
+    cm_planes<T, MF>(Jcm, O, s, sct, pts, j, cm_sw, pl);
     T Jp[6];
-    jp_from(pl, sR, Jp);
+    jp_from(pl, sct, Jp);
     const T* vi = Vinv + 6LL * j;
     const T v00 = vi[0], v01 = vi[1], v02 = vi[2], v11 = vi[3], v12 = vi[4], v22 = vi[5];
-    // T2 = Jp Vinv (2x3)
     T t[6];
 #pragma unroll
     for (int a = 0; a < 2; ++a) {
@@ -596,14 +838,11 @@ k_schur_cam(const int32_t* __restrict__ piece_cam, const int32_t* __restrict__ p
       acc[45 + i] += j0[i] * e0 + j1[i] * e1;
     }
   }
-  double v[54];
-#pragma unroll
-  for (int i = 0; i < 54; ++i) v[i] = (double)acc[i];
-  block_sum_store<54>(v, part + (long long)PART * b);
+  block_sum_store<54>(acc, part + (long long)PART * b);
 }
 
-// In-place Cholesky of a packed symmetric 9x9 (upper triangle, sym9) and its
-// inverse, in double.  Returns false if a pivot is not positive/finite.
+// Cholesky of a packed symmetric 9x9 (upper triangle, sym9) and its inverse,
+// in double.  Returns false if a pivot is not positive/finite.
 __device__ inline bool spd_inverse9(const double* __restrict__ S, double* __restrict__ Minv) {
   double L[9][9];
 #pragma unroll
@@ -627,7 +866,6 @@ __device__ inline bool spd_inverse9(const double* __restrict__ S, double* __rest
       L[i][j] = s * il;
     }
   }
-  // Linv lower triangular: Linv = L^{-1}
   double Li[9][9];
 #pragma unroll
   for (int i = 0; i < 9; ++i)
@@ -644,7 +882,6 @@ __device__ inline bool spd_inverse9(const double* __restrict__ S, double* __rest
       Li[i][j] = -s * Li[i][i];
     }
   }
-  // M = Linv^T Linv
 #pragma unroll
   for (int i = 0; i < 9; ++i)
 #pragma unroll
@@ -676,12 +913,27 @@ __device__ __forceinline__ void ustar_matvec(const double* __restrict__ U, doubl
   for (int i = 0; i < 9; ++i) y[i] += damp(U[sym9(i, i)], lam, dmin, dmax) * x[i];
 }
 
+// Write the camera vector x (double, 9) as the passes read it: plain in the
+// stored mode, factored ([J_l x_omega, x_t, x_i]) in the recompute mode.
+template <typename T, bool MF>
+__device__ __forceinline__ void write_pass_vec(const T* __restrict__ ct, const double* __restrict__ x,
+                                               T* __restrict__ out) {
+  if (MF) {
+    to_factored(ct + CT_JL, x, out);
+  } else {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) out[i] = (T)x[i];
+  }
+}
+
+__host__ __device__ constexpr int pass_vec_stride(bool mf) { return mf ? PV : 9; }
+
 // Per camera: S_ii, b_i, M_i = S_ii^{-1}; PCG start x = 0, r = b, z = M r,
 // p = z; per-block partial sums of r.z and b.b.
-template <typename T>
+template <typename T, bool MF>
 __global__ void __launch_bounds__(CAM_THREADS)
 k_cam_combine_schur(int C, const int32_t* __restrict__ cam_piece_ptr, const double* __restrict__ part,
-                    const double* __restrict__ U, const double* __restrict__ gc,
+                    const double* __restrict__ U, const double* __restrict__ gc, const T* __restrict__ camtab,
                     const double* __restrict__ lam_ptr, double dmin, double dmax, double* __restrict__ Minv,
                     double* __restrict__ x, double* __restrict__ r, double* __restrict__ z,
                     double* __restrict__ p, T* __restrict__ pT, double* __restrict__ dot_rz1,
@@ -735,10 +987,10 @@ k_cam_combine_schur(int C, const int32_t* __restrict__ cam_piece_ptr, const doub
       r[9LL * c + i] = bv[i];
       z[9LL * c + i] = zz[i];
       p[9LL * c + i] = zz[i];
-      pT[9LL * c + i] = (T)zz[i];
       rz += bv[i] * zz[i];
       bb += bv[i] * bv[i];
     }
+    write_pass_vec<T, MF>(camtab + (long long)CT * c, zz, pT + (long long)pass_vec_stride(MF) * c);
   }
   double v[2] = {rz, bb};
   block_sum_all<2>(v);
@@ -752,55 +1004,106 @@ k_cam_combine_schur(int C, const int32_t* __restrict__ cam_piece_ptr, const doub
 // a4: PCG iteration k (S p through two passes, then the vector updates)
 // ---------------------------------------------------------------------------
 
-// Pass A (point-major): t_j = V*_j^{-1} sum_{k in pt j} Jp_k^T (Jc_k p_c(k)),
-// over one chunk of points (thread per observation, shared-memory segmented
-// sum per point as in k_lin_pt).  With MODE 1 (back-substitution) it forms
-// dp_j = -(y0_j + t_j), writes the trial point theta_p + dp_j and reduces
-// gp_j . dp_j per chunk.
-template <typename T>
-__device__ __forceinline__ void pass_a_obs(int q, long long O, const int32_t* __restrict__ pm_cam,
-                                           const T* __restrict__ Jpm, const T* __restrict__ camtab,
-                                           const T* __restrict__ xc, T& z0, T& z1, T& z2) {
-  const int c = pm_cam[q];
-  T pl[NPLANE];
-  load_planes(Jpm, O, q, pl);
-  const T* xv = xc + 9LL * c;
-  T j0[9], j1[9];
-  jc_rows(pl, j0, j1);
-  T e0 = 0, e1 = 0;
+// Pass A, step 1 (camera-major, one CTA per piece of camera c):
+//   z_s = Jp_s^T (Jc_s x_c)   for every observation s of the piece,
+// written as one 4-vector per observation in camera-major order (coalesced).  The
+// camera's table and x_c sit in registers; the only per-observation loads are
+// the point index, the point (recompute mode: one 16-byte vector) or the
+// planes (stored mode), and sqrt(w).
+template <typename T, bool MF>
+__global__ void __launch_bounds__(PIECE_THREADS)
+k_pass_a1(const int32_t* __restrict__ piece_cam, const int32_t* __restrict__ piece_beg,
+          const int32_t* __restrict__ piece_end, const int32_t* __restrict__ cm_pt,
+          const T* __restrict__ Jcm, const T* __restrict__ cm_sw, const T* __restrict__ ptab,
+          const T* __restrict__ camtab, const T* __restrict__ xc, const DevState* __restrict__ st,
+          int check_done, int O, T* __restrict__ zbuf) {
+  if (check_done && st->pcg_done) return;
+  __shared__ T sct[16];
+  __shared__ T sx[PV];
+  const int b = blockIdx.x;
+  const int c = piece_cam[b];
+  constexpr int XS = pass_vec_stride(MF);
+  if (threadIdx.x < 16) sct[threadIdx.x] = camtab[(long long)CT * c + threadIdx.x];
+  if (threadIdx.x >= 32 && threadIdx.x < 32 + XS) sx[threadIdx.x - 32] = xc[(long long)XS * c + threadIdx.x - 32];
+  __syncthreads();
+  T ctl[15], xl[9];
 #pragma unroll
-  for (int i = 0; i < 9; ++i) {
-    const T xi = xv[i];
-    e0 += j0[i] * xi;
-    e1 += j1[i] * xi;
+  for (int i = 0; i < 15; ++i) ctl[i] = sct[i];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) xl[i] = sx[i];
+  const int end = piece_end[b];
+  if (MF) {
+    // one observation of lookahead: the next point is loaded while this one
+    // is computed
+    int s = piece_beg[b] + threadIdx.x;
+    T X0 = 0, X1 = 0, X2 = 0, sw = 1, pad;
+    if (s < end) {
+      load4(ptab + 8LL * cm_pt[s], X0, X1, X2, pad);
+      if (cm_sw) sw = cm_sw[s];
+    }
+    while (s < end) {
+      const int sn = s + PIECE_THREADS;
+      T Y0 = 0, Y1 = 0, Y2 = 0, swn = 1;
+      if (sn < end) {
+        load4(ptab + 8LL * cm_pt[sn], Y0, Y1, Y2, pad);
+        if (cm_sw) swn = cm_sw[sn];
+      }
+      Fac<T> o;
+      fac_obs(ctl, X0, X1, X2, sw, o);
+      T e0, e1;
+      jc_times_fac(o, xl, e0, e1);
+      const T a0 = o.A[0] * e0 + o.A[3] * e1;
+      const T a1 = o.A[1] * e0 + o.A[4] * e1;
+      const T a2 = o.A[2] * e0 + o.A[5] * e1;
+      const T z0 = ctl[0] * a0 + ctl[3] * a1 + ctl[6] * a2;
+      const T z1 = ctl[1] * a0 + ctl[4] * a1 + ctl[7] * a2;
+      const T z2 = ctl[2] * a0 + ctl[5] * a1 + ctl[8] * a2;
+      store4(zbuf + 4LL * s, z0, z1, z2, T(0));
+      s = sn;
+      X0 = Y0;
+      X1 = Y1;
+      X2 = Y2;
+      sw = swn;
+    }
+  } else {
+    for (int s = piece_beg[b] + threadIdx.x; s < end; s += PIECE_THREADS) {
+      T pl[NPLANE];
+      load_planes(Jcm, O, s, pl);
+      T j0[9], j1[9];
+      jc_rows(pl, j0, j1);
+      T e0 = 0, e1 = 0;
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        e0 += j0[i] * xl[i];
+        e1 += j1[i] * xl[i];
+      }
+      const T a0 = pl[0] * e0 + pl[3] * e1;
+      const T a1 = pl[1] * e0 + pl[4] * e1;
+      const T a2 = pl[2] * e0 + pl[5] * e1;
+      const T z0 = ctl[0] * a0 + ctl[3] * a1 + ctl[6] * a2;
+      const T z1 = ctl[1] * a0 + ctl[4] * a1 + ctl[7] * a2;
+      const T z2 = ctl[2] * a0 + ctl[5] * a1 + ctl[8] * a2;
+      store4(zbuf + 4LL * s, z0, z1, z2, T(0));
+    }
   }
-  const T a0 = pl[0] * e0 + pl[3] * e1;
-  const T a1 = pl[1] * e0 + pl[4] * e1;
-  const T a2 = pl[2] * e0 + pl[5] * e1;
-  const T* R = camtab + (long long)CT * c;
-  z0 = R[0] * a0 + R[3] * a1 + R[6] * a2;
-  z1 = R[1] * a0 + R[4] * a1 + R[7] * a2;
-  z2 = R[2] * a0 + R[5] * a1 + R[8] * a2;
 }
 
 template <typename T, int MODE>
 __device__ __forceinline__ double pass_a_point(int j, int P, T z0, T z1, T z2, const T* __restrict__ Vinv,
-                                               T* __restrict__ out, const T* __restrict__ y0,
+                                               T* __restrict__ ptab, T* __restrict__ dp, const T* __restrict__ y0,
                                                const double* __restrict__ gp, T* __restrict__ pts_buf, int cur) {
   const T* vi = Vinv + 6LL * j;
   const T t0 = vi[0] * z0 + vi[1] * z1 + vi[2] * z2;
   const T t1 = vi[1] * z0 + vi[3] * z1 + vi[4] * z2;
   const T t2 = vi[2] * z0 + vi[4] * z1 + vi[5] * z2;
   if (MODE == 0) {
-    out[3LL * j] = t0;
-    out[3LL * j + 1] = t1;
-    out[3LL * j + 2] = t2;
+    store4(ptab + 8LL * j + 4, t0, t1, t2, T(0));
     return 0.0;
   }
   const T d0 = -(y0[3LL * j] + t0), d1 = -(y0[3LL * j + 1] + t1), d2 = -(y0[3LL * j + 2] + t2);
-  out[3LL * j] = d0;
-  out[3LL * j + 1] = d1;
-  out[3LL * j + 2] = d2;
+  dp[3LL * j] = d0;
+  dp[3LL * j + 1] = d1;
+  dp[3LL * j + 2] = d2;
   const T* src = pts_buf + (long long)cur * 3 * P + 3LL * j;
   T* dst = pts_buf + (long long)(1 - cur) * 3 * P + 3LL * j;
   dst[0] = src[0] + d0;
@@ -809,51 +1112,68 @@ __device__ __forceinline__ double pass_a_point(int j, int P, T z0, T z1, T z2, c
   return gp[3LL * j] * (double)d0 + gp[3LL * j + 1] * (double)d1 + gp[3LL * j + 2] * (double)d2;
 }
 
+// Pass A, step 2 (point-major, one CTA per chunk of points):
+//   t_j = V*_j^{-1} sum_{k in pt j} z_k
+// (one observation per thread gathers its z_k through the point-to-camera
+// order map into shared memory; one thread per point adds them in slot
+// order).  MODE 0 writes t_j into the point table for pass B; MODE 1
+// (back-substitution, z from dc) forms dp_j = -(y0_j + t_j), writes the
+// trial point theta_p + dp_j and reduces gp_j . dp_j per chunk.
 template <typename T, int MODE>
 __global__ void __launch_bounds__(CHUNK_THREADS)
-k_pass_a(const int32_t* __restrict__ pchunk, int P, int O, const int32_t* __restrict__ rowptr_pt,
-         const int32_t* __restrict__ pm_cam, const T* __restrict__ Jpm, const T* __restrict__ camtab,
-         const T* __restrict__ xc, const T* __restrict__ Vinv, const DevState* __restrict__ st, int check_done,
-         T* __restrict__ out, const T* __restrict__ y0, const double* __restrict__ gp, T* __restrict__ pts_buf,
-         double* __restrict__ dot_gp) {
+k_pass_a2(const int32_t* __restrict__ pchunk, int P, const int32_t* __restrict__ rowptr_pt,
+          const int32_t* __restrict__ pm2cm, const T* __restrict__ zbuf, const T* __restrict__ Vinv,
+          const DevState* __restrict__ st, int check_done, T* __restrict__ ptab, T* __restrict__ dp,
+          const T* __restrict__ y0, const double* __restrict__ gp, T* __restrict__ pts_buf,
+          double* __restrict__ dot_gp) {
   if (MODE == 0 && check_done && st->pcg_done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sz = reinterpret_cast<T*>(smem_raw);  // [CHUNK_SLOTS][3]
-  const int cur = MODE == 1 ? st->cur : 0;
+  T* sz = reinterpret_cast<T*>(smem_raw);  // [CHUNK_SLOTS][4]
+  const int cur = st->cur;
   const int j0 = pchunk[blockIdx.x], j1 = pchunk[blockIdx.x + 1];
   const int s0 = rowptr_pt[j0], s1 = rowptr_pt[j1];
   double gd = 0.0;
   if (s1 - s0 <= CHUNK_SLOTS) {
-    for (int q = s0 + threadIdx.x; q < s1; q += CHUNK_THREADS) {
-      T z0, z1, z2;
-      pass_a_obs(q, O, pm_cam, Jpm, camtab, xc, z0, z1, z2);
-      sz[(q - s0) * 3] = z0;
-      sz[(q - s0) * 3 + 1] = z1;
-      sz[(q - s0) * 3 + 2] = z2;
+    // all gathers of this thread in flight at once
+    // all gathers of this thread in flight at once
+    constexpr int U = CHUNK_SLOTS / CHUNK_THREADS;
+    int src[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int q = s0 + threadIdx.x + u * CHUNK_THREADS;
+      src[u] = q < s1 ? pm2cm[q] : -1;
     }
+    T zz[U][4];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (src[u] >= 0) load4(zbuf + 4LL * src[u], zz[u][0], zz[u][1], zz[u][2], zz[u][3]);
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (src[u] >= 0) store4(sz + 4 * (threadIdx.x + u * CHUNK_THREADS), zz[u][0], zz[u][1], zz[u][2], zz[u][3]);
     __syncthreads();
     for (int j = j0 + threadIdx.x; j < j1; j += CHUNK_THREADS) {
       T z0 = 0, z1 = 0, z2 = 0;
       const int q1 = rowptr_pt[j + 1];
       for (int q = rowptr_pt[j]; q < q1; ++q) {
-        z0 += sz[(q - s0) * 3];
-        z1 += sz[(q - s0) * 3 + 1];
-        z2 += sz[(q - s0) * 3 + 2];
+        z0 += sz[4 * (q - s0)];
+        z1 += sz[4 * (q - s0) + 1];
+        z2 += sz[4 * (q - s0) + 2];
       }
-      gd += pass_a_point<T, MODE>(j, P, z0, z1, z2, Vinv, out, y0, gp, pts_buf, cur);
+      gd += pass_a_point<T, MODE>(j, P, z0, z1, z2, Vinv, ptab, dp, y0, gp, pts_buf, cur);
     }
   } else {
     T z0 = 0, z1 = 0, z2 = 0;
     for (int q = s0 + threadIdx.x; q < s1; q += CHUNK_THREADS) {
-      T a0, a1, a2;
-      pass_a_obs(q, O, pm_cam, Jpm, camtab, xc, a0, a1, a2);
-      z0 += a0;
-      z1 += a1;
-      z2 += a2;
+      T a, b, c, d;
+      load4(zbuf + 4LL * pm2cm[q], a, b, c, d);
+      z0 += a;
+      z1 += b;
+      z2 += c;
     }
-    double d[3] = {(double)z0, (double)z1, (double)z2};
-    block_sum_all<3>(d);
-    if (threadIdx.x == 0) gd = pass_a_point<T, MODE>(j0, P, (T)d[0], (T)d[1], (T)d[2], Vinv, out, y0, gp, pts_buf, cur);
+    double dd[3] = {(double)z0, (double)z1, (double)z2};
+    block_sum_all<3>(dd);
+    if (threadIdx.x == 0)
+      gd = pass_a_point<T, MODE>(j0, P, (T)dd[0], (T)dd[1], (T)dd[2], Vinv, ptab, dp, y0, gp, pts_buf, cur);
   }
   if (MODE == 1) {
     double v[1] = {gd};
@@ -862,70 +1182,126 @@ k_pass_a(const int32_t* __restrict__ pchunk, int P, int O, const int32_t* __rest
   }
 }
 
-// Pass B (camera-major): per piece, sum_k Jc_k^T (Jp_k t_p(k)) (9 values).
-template <typename T>
+// Pass B (camera-major): per piece, sum_k Jc_k^T (Jp_k t_p(k)) (9 values; in
+// the recompute mode the first three are still to be multiplied by J_l^T).
+template <typename T, bool MF>
 __global__ void __launch_bounds__(PIECE_THREADS)
 k_pass_b(const int32_t* __restrict__ piece_cam, const int32_t* __restrict__ piece_beg,
          const int32_t* __restrict__ piece_end, const int32_t* __restrict__ cm_pt,
-         const T* __restrict__ Jcm, const T* __restrict__ camtab, const T* __restrict__ tpt,
-         const DevState* __restrict__ st, int check_done, int O, double* __restrict__ part) {
+         const T* __restrict__ Jcm, const T* __restrict__ cm_sw, const T* __restrict__ ptab,
+         const T* __restrict__ camtab, const DevState* __restrict__ st, int check_done, int O,
+         double* __restrict__ part) {
   if (check_done && st->pcg_done) return;
-  __shared__ T sR[9];
+  __shared__ T sct[16];
   const int b = blockIdx.x;
   const int c = piece_cam[b];
-  if (threadIdx.x < 9) sR[threadIdx.x] = camtab[(long long)CT * c + threadIdx.x];
+  if (threadIdx.x < 16) sct[threadIdx.x] = camtab[(long long)CT * c + threadIdx.x];
   __syncthreads();
+  T ctl[15];
+#pragma unroll
+  for (int i = 0; i < 15; ++i) ctl[i] = sct[i];
   T acc[9];
 #pragma unroll
   for (int i = 0; i < 9; ++i) acc[i] = T(0);
   const int end = piece_end[b];
-#pragma unroll 4
-  for (int s = piece_beg[b] + threadIdx.x; s < end; s += PIECE_THREADS) {
-    const int j = cm_pt[s];
-    T pl[NPLANE];
-    load_planes(Jcm, O, s, pl);
-    const T t0 = tpt[3LL * j], t1 = tpt[3LL * j + 1], t2 = tpt[3LL * j + 2];
-    const T g0 = sR[0] * t0 + sR[1] * t1 + sR[2] * t2;
-    const T g1 = sR[3] * t0 + sR[4] * t1 + sR[5] * t2;
-    const T g2 = sR[6] * t0 + sR[7] * t1 + sR[8] * t2;
-    const T h0 = pl[0] * g0 + pl[1] * g1 + pl[2] * g2;
-    const T h1 = pl[3] * g0 + pl[4] * g1 + pl[5] * g2;
-    T j0[9], j1[9];
-    jc_rows(pl, j0, j1);
+  if (MF) {
+    int s = piece_beg[b] + threadIdx.x;
+    T X0 = 0, X1 = 0, X2 = 0, t0 = 0, t1 = 0, t2 = 0, sw = 1, pad;
+    if (s < end) {
+      const int j = cm_pt[s];
+      load4(ptab + 8LL * j, X0, X1, X2, pad);
+      load4(ptab + 8LL * j + 4, t0, t1, t2, pad);
+      if (cm_sw) sw = cm_sw[s];
+    }
+    while (s < end) {
+      const int sn = s + PIECE_THREADS;
+      T Y0 = 0, Y1 = 0, Y2 = 0, u0 = 0, u1 = 0, u2 = 0, swn = 1;
+      if (sn < end) {
+        const int jn = cm_pt[sn];
+        load4(ptab + 8LL * jn, Y0, Y1, Y2, pad);
+        load4(ptab + 8LL * jn + 4, u0, u1, u2, pad);
+        if (cm_sw) swn = cm_sw[sn];
+      }
+      const T g0 = ctl[0] * t0 + ctl[1] * t1 + ctl[2] * t2;
+      const T g1 = ctl[3] * t0 + ctl[4] * t1 + ctl[5] * t2;
+      const T g2 = ctl[6] * t0 + ctl[7] * t1 + ctl[8] * t2;
+      Fac<T> o;
+      fac_obs(ctl, X0, X1, X2, sw, o);
+      const T h0 = o.A[0] * g0 + o.A[1] * g1 + o.A[2] * g2;
+      const T h1 = o.A[3] * g0 + o.A[4] * g1 + o.A[5] * g2;
+      jct_fac_acc(o, h0, h1, acc);
+      s = sn;
+      X0 = Y0;
+      X1 = Y1;
+      X2 = Y2;
+      t0 = u0;
+      t1 = u1;
+      t2 = u2;
+      sw = swn;
+    }
+  } else {
+    for (int s = piece_beg[b] + threadIdx.x; s < end; s += PIECE_THREADS) {
+      const int j = cm_pt[s];
+      T t0, t1, t2, tpad;
+      load4(ptab + 8LL * j + 4, t0, t1, t2, tpad);
+      const T g0 = ctl[0] * t0 + ctl[1] * t1 + ctl[2] * t2;
+      const T g1 = ctl[3] * t0 + ctl[4] * t1 + ctl[5] * t2;
+      const T g2 = ctl[6] * t0 + ctl[7] * t1 + ctl[8] * t2;
+      T pl[NPLANE];
+      load_planes(Jcm, O, s, pl);
+      const T h0 = pl[0] * g0 + pl[1] * g1 + pl[2] * g2;
+      const T h1 = pl[3] * g0 + pl[4] * g1 + pl[5] * g2;
+      T j0[9], j1[9];
+      jc_rows(pl, j0, j1);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) acc[i] += j0[i] * h0 + j1[i] * h1;
+      for (int i = 0; i < 9; ++i) acc[i] += j0[i] * h0 + j1[i] * h1;
+    }
   }
-  double v[9];
-#pragma unroll
-  for (int i = 0; i < 9; ++i) v[i] = (double)acc[i];
-  block_sum_store<9>(v, part + (long long)PART * b);
+  block_sum_store<9, false>(acc, part + (long long)PART * b);
 }
 
-// q = U* p - sum of pass-B pieces; per-block partial p.q.
-__global__ void __launch_bounds__(CAM_THREADS)
+// The per-iteration vector kernels run 9 threads per camera (one per
+// component), CAM_THREADS cameras per block, so the FP64 9x9 products are
+// spread over the whole GPU instead of one serial thread per camera.
+constexpr int VT = CAM_THREADS * 9;
+
+__device__ __forceinline__ int sym9_rt(int i, int j) { return i <= j ? sym9(i, j) : sym9(j, i); }
+
+// q = U* p - sum of pass-B pieces (J_l^T applied to their first three in the
+// recompute mode); per-block partial p.q.
+template <typename T, bool MF>
+__global__ void __launch_bounds__(VT)
 k_pcg_q(int C, const int32_t* __restrict__ cam_piece_ptr, const double* __restrict__ part,
-        const double* __restrict__ U, const double* __restrict__ lam_ptr, double dmin, double dmax,
-        const double* __restrict__ p, double* __restrict__ q, double* __restrict__ dot_pq,
+        const double* __restrict__ U, const T* __restrict__ camtab, const double* __restrict__ lam_ptr, double dmin,
+        double dmax, const double* __restrict__ p, double* __restrict__ q, double* __restrict__ dot_pq,
         const DevState* __restrict__ st, int check_done) {
   if (check_done && st->pcg_done) return;
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  __shared__ double sp[CAM_THREADS][9], ss[CAM_THREADS][9];
+  const int lc = threadIdx.x / 9, i = threadIdx.x % 9;
+  const int c = blockIdx.x * CAM_THREADS + lc;
+  const bool ok = c < C;
+  double pv = 0.0, sum = 0.0;
+  if (ok) {
+    pv = p[9LL * c + i];
+    const int p1 = cam_piece_ptr[c + 1];
+    for (int k = cam_piece_ptr[c]; k < p1; ++k) sum += part[(long long)PART * k + i];
+  }
+  sp[lc][i] = pv;
+  ss[lc][i] = sum;
+  __syncthreads();
   double pq = 0.0;
-  if (c < C) {
-    const double lam = *lam_ptr;
-    double pv[9], y[9];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) pv[i] = p[9LL * c + i];
-    ustar_matvec(U + 45LL * c, lam, dmin, dmax, pv, y);
-    const int p0 = cam_piece_ptr[c], p1 = cam_piece_ptr[c + 1];
-    for (int k = p0; k < p1; ++k) {
-#pragma unroll
-      for (int i = 0; i < 9; ++i) y[i] -= part[(long long)PART * k + i];
+  if (ok) {
+    if (MF && i < 3) {
+      const T* Jl = camtab + (long long)CT * c + CT_JL;
+      sum = (double)Jl[i] * ss[lc][0] + (double)Jl[3 + i] * ss[lc][1] + (double)Jl[6 + i] * ss[lc][2];
     }
+    const double* Uc = U + 45LL * c;
+    double y = damp(Uc[sym9(i, i)], *lam_ptr, dmin, dmax) * sp[lc][i];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) {
-      q[9LL * c + i] = y[i];
-      pq += pv[i] * y[i];
-    }
+    for (int j = 0; j < 9; ++j) y += Uc[sym9_rt(i, j)] * sp[lc][j];
+    y -= sum;
+    q[9LL * c + i] = y;
+    pq = pv * y;
   }
   double v[1] = {pq};
   block_sum_all<1>(v);
@@ -934,14 +1310,16 @@ k_pcg_q(int C, const int32_t* __restrict__ cam_piece_ptr, const double* __restri
 
 // alpha = (r.z)_old / p.q; x += alpha p; r -= alpha q; z = M r;
 // partial r.z into dot_rz[k & 1], partial r.r.
-__global__ void __launch_bounds__(CAM_THREADS)
+__global__ void __launch_bounds__(VT)
 k_pcg_update(int C, int nb, int k, const double* __restrict__ dot_pq, double* __restrict__ dot_rz,
              double* __restrict__ dot_rr, const double* __restrict__ p, const double* __restrict__ q,
              double* __restrict__ x, double* __restrict__ r, double* __restrict__ z,
              const double* __restrict__ Minv, DevState* st) {
   if (st->pcg_done) return;
-  const double pq = block_sum_array(dot_pq, nb, 1);
-  const double rz_old = block_sum_array(dot_rz + ((k + 1) & 1) * nb, nb, 1);
+  const double* const srcs[2] = {dot_pq, dot_rz + ((k + 1) & 1) * nb};
+  double sums[2];
+  block_sum_arrays<2>(srcs, nb, sums);
+  const double pq = sums[0], rz_old = sums[1];
   if (!(pq > 0.0) || !isfinite(pq)) {
     // no positive curvature (b = 0 or breakdown): keep x, stop
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -952,25 +1330,27 @@ k_pcg_update(int C, int nb, int k, const double* __restrict__ dot_pq, double* __
     return;
   }
   const double alpha = rz_old / pq;
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  double rz = 0.0, rr = 0.0;
-  if (c < C) {
-    double rv[9], zz[9];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-      x[9LL * c + i] += alpha * p[9LL * c + i];
-      rv[i] = r[9LL * c + i] - alpha * q[9LL * c + i];
-      r[9LL * c + i] = rv[i];
-    }
-    sym9_matvec(Minv + 45LL * c, rv, zz);
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-      z[9LL * c + i] = zz[i];
-      rz += rv[i] * zz[i];
-      rr += rv[i] * rv[i];
-    }
+  __shared__ double sr[CAM_THREADS][9];
+  const int lc = threadIdx.x / 9, i = threadIdx.x % 9;
+  const int c = blockIdx.x * CAM_THREADS + lc;
+  const bool ok = c < C;
+  double rv = 0.0;
+  if (ok) {
+    const long long o = 9LL * c + i;
+    x[o] += alpha * p[o];
+    rv = r[o] - alpha * q[o];
+    r[o] = rv;
   }
-  double v[2] = {rz, rr};
+  sr[lc][i] = rv;
+  __syncthreads();
+  double zz = 0.0;
+  if (ok) {
+    const double* M = Minv + 45LL * c;
+#pragma unroll
+    for (int j = 0; j < 9; ++j) zz += M[sym9_rt(i, j)] * sr[lc][j];
+    z[9LL * c + i] = zz;
+  }
+  double v[2] = {rv * zz, rv * rv};
   block_sum_all<2>(v);
   if (threadIdx.x == 0) {
     dot_rz[(k & 1) * nb + blockIdx.x] = v[0];
@@ -978,17 +1358,19 @@ k_pcg_update(int C, int nb, int k, const double* __restrict__ dot_pq, double* __
   }
 }
 
-// Convergence test |r| <= tol |b|; beta = (r.z)_new / (r.z)_old; p = z + beta p.
-template <typename T>
-__global__ void __launch_bounds__(CAM_THREADS)
+// Convergence test |r| <= tol |b|; beta = (r.z)_new / (r.z)_old; p = z + beta p,
+// and p in the passes' form.
+template <typename T, bool MF>
+__global__ void __launch_bounds__(VT)
 k_pcg_direction(int C, int nb, int k, double tol, const double* __restrict__ dot_rz,
                 const double* __restrict__ dot_rr, const double* __restrict__ dot_bb,
-                const double* __restrict__ z, double* __restrict__ p, T* __restrict__ pT, DevState* st) {
+                const double* __restrict__ z, double* __restrict__ p, const T* __restrict__ camtab,
+                T* __restrict__ pT, DevState* st) {
   if (st->pcg_done) return;
-  const double rz_new = block_sum_array(dot_rz + (k & 1) * nb, nb, 1);
-  const double rz_old = block_sum_array(dot_rz + ((k + 1) & 1) * nb, nb, 1);
-  const double rr = block_sum_array(dot_rr, nb, 1);
-  const double bb = block_sum_array(dot_bb, nb, 1);
+  const double* const srcs[4] = {dot_rz + (k & 1) * nb, dot_rz + ((k + 1) & 1) * nb, dot_rr, dot_bb};
+  double sums[4];
+  block_sum_arrays<4>(srcs, nb, sums);
+  const double rz_new = sums[0], rz_old = sums[1], rr = sums[2], bb = sums[3];
   const bool conv = sqrt(rr) <= tol * sqrt(bb);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     st->pcg_iters = k + 1;
@@ -997,14 +1379,27 @@ k_pcg_direction(int C, int nb, int k, double tol, const double* __restrict__ dot
   }
   if (conv) return;
   const double beta = rz_new / rz_old;
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c < C) {
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-      const double pv = z[9LL * c + i] + beta * p[9LL * c + i];
-      p[9LL * c + i] = pv;
-      pT[9LL * c + i] = (T)pv;
-    }
+  __shared__ double sp[CAM_THREADS][9];
+  const int lc = threadIdx.x / 9, i = threadIdx.x % 9;
+  const int c = blockIdx.x * CAM_THREADS + lc;
+  const bool ok = c < C;
+  double pv = 0.0;
+  if (ok) {
+    const long long o = 9LL * c + i;
+    pv = z[o] + beta * p[o];
+    p[o] = pv;
+  }
+  sp[lc][i] = pv;
+  __syncthreads();
+  if (!ok) return;
+  constexpr int XS = pass_vec_stride(MF);
+  T* out = pT + (long long)XS * c;
+  if (MF && i < 3) {
+    const T* Jl = camtab + (long long)CT * c + CT_JL;
+    out[i] = (T)((double)Jl[3 * i] * sp[lc][0] + (double)Jl[3 * i + 1] * sp[lc][1] + (double)Jl[3 * i + 2] * sp[lc][2]);
+    out[9 + i] = T(0);
+  } else {
+    out[i] = (T)pv;
   }
 }
 
@@ -1012,24 +1407,28 @@ k_pcg_direction(int C, int nb, int k, double tol, const double* __restrict__ dot
 // a5 / a6: trial parameters, trial cost, model reduction, LM control
 // ---------------------------------------------------------------------------
 
-// Trial cameras theta_c + dc, dc in T, partial gc . dc.
-template <typename T>
+// Trial cameras theta_c + dc (dc rounded to T), dc in the pass form, partial
+// gc . dc.
+template <typename T, bool MF>
 __global__ void __launch_bounds__(CAM_THREADS)
 k_cam_trial(int C, const double* __restrict__ x, const double* __restrict__ gc, T* __restrict__ cams_buf,
-            const DevState* __restrict__ st, T* __restrict__ xT, double* __restrict__ dot_gc) {
+            const T* __restrict__ camtab, const DevState* __restrict__ st, T* __restrict__ xT,
+            double* __restrict__ dot_gc) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   double gd = 0.0;
   if (c < C) {
     const int cur = st->cur;
     const T* src = cams_buf + (long long)cur * 9 * C + 9LL * c;
     T* dst = cams_buf + (long long)(1 - cur) * 9 * C + 9LL * c;
+    double dr[9];
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
       const T d = (T)x[9LL * c + i];
-      xT[9LL * c + i] = d;
+      dr[i] = (double)d;
       dst[i] = src[i] + d;
       gd += gc[9LL * c + i] * (double)d;
     }
+    write_pass_vec<T, MF>(camtab + (long long)CT * c, dr, xT + (long long)pass_vec_stride(MF) * c);
   }
   double v[1] = {gd};
   block_sum_all<1>(v);
@@ -1039,25 +1438,29 @@ k_cam_trial(int C, const double* __restrict__ x, const double* __restrict__ gc, 
 // Camera-major pass over the pieces: cost 1/2 sum rho at the parameters in
 // buffer (which == 0: current, 1: trial), and with MODEL the quadratic term
 // sum_k |Jc_k dc + Jp_k dp|^2 of the model reduction (weights folded in).
-template <typename T, bool MODEL>
+template <typename T, bool MODEL, bool MF>
 __global__ void __launch_bounds__(PIECE_THREADS)
 k_cost_cam(const int32_t* __restrict__ piece_cam, const int32_t* __restrict__ piece_beg,
            const int32_t* __restrict__ piece_end, const int32_t* __restrict__ cm_pt,
            const T* __restrict__ cm_px, const T* __restrict__ cams_buf, const T* __restrict__ pts_buf,
            const DevState* __restrict__ st, int which, T delta, int C, int P, int O,
-           const T* __restrict__ Jcm, const T* __restrict__ camtab, const T* __restrict__ xT,
-           const T* __restrict__ dp, double* __restrict__ part) {
-  __shared__ T sct[CT];
-  __shared__ T sR[9];
-  __shared__ T sdc[9];
+           const T* __restrict__ Jcm, const T* __restrict__ cm_sw, const T* __restrict__ camtab,
+           const T* __restrict__ xT, const T* __restrict__ dp, double* __restrict__ part) {
+  __shared__ T sct[CT];   // camera of the evaluated parameters
+  __shared__ T sold[CT];  // camera of the linearisation (model term)
+  __shared__ T sdc[PV];
   const int b = blockIdx.x;
   const int c = piece_cam[b];
-  const int buf = which ? 1 - st->cur : st->cur;
+  const int cur = st->cur;
+  const int buf = which ? 1 - cur : cur;
   if (threadIdx.x == 0) camera_table(cams_buf + (long long)buf * 9 * C + 9LL * c, sct);
-  if (MODEL && threadIdx.x >= 32 && threadIdx.x < 41) sR[threadIdx.x - 32] = camtab[(long long)CT * c + threadIdx.x - 32];
-  if (MODEL && threadIdx.x >= 64 && threadIdx.x < 73) sdc[threadIdx.x - 64] = xT[9LL * c + threadIdx.x - 64];
+  if (MODEL && threadIdx.x >= 32 && threadIdx.x < 32 + CT)
+    sold[threadIdx.x - 32] = camtab[(long long)CT * c + threadIdx.x - 32];
+  if (MODEL && threadIdx.x >= 64 + CT && threadIdx.x < 64 + CT + pass_vec_stride(MF))
+    sdc[threadIdx.x - 64 - CT] = xT[(long long)pass_vec_stride(MF) * c + threadIdx.x - 64 - CT];
   __syncthreads();
   const T* pts = pts_buf + (long long)buf * 3 * P;
+  const T* pts_old = pts_buf + (long long)cur * 3 * P;
   double cost = 0.0, quad = 0.0;
   const int end = piece_end[b];
   for (int s = piece_beg[b] + threadIdx.x; s < end; s += PIECE_THREADS) {
@@ -1069,19 +1472,29 @@ k_cost_cam(const int32_t* __restrict__ piece_cam, const int32_t* __restrict__ pi
     huber_weight(r0 * r0 + r1 * r1, delta, hr, w);
     cost += (double)hr;
     if (MODEL) {
-      T pl[NPLANE];
-      load_planes(Jcm, O, s, pl);
-      T j0[9], j1[9];
-      jc_rows(pl, j0, j1);
-      T Jp[6];
-      jp_from(pl, sR, Jp);
       const T d0 = dp[3LL * j], d1 = dp[3LL * j + 1], d2 = dp[3LL * j + 2];
-      T e0 = Jp[0] * d0 + Jp[1] * d1 + Jp[2] * d2;
-      T e1 = Jp[3] * d0 + Jp[4] * d1 + Jp[5] * d2;
+      const T g0 = sold[0] * d0 + sold[1] * d1 + sold[2] * d2;
+      const T g1 = sold[3] * d0 + sold[4] * d1 + sold[5] * d2;
+      const T g2 = sold[6] * d0 + sold[7] * d1 + sold[8] * d2;
+      T e0, e1;
+      if (MF) {
+        Fac<T> o;
+        fac_obs(sold, pts_old[3LL * j], pts_old[3LL * j + 1], pts_old[3LL * j + 2], cm_sw ? cm_sw[s] : T(1), o);
+        jc_times_fac(o, sdc, e0, e1);
+        e0 += o.A[0] * g0 + o.A[1] * g1 + o.A[2] * g2;
+        e1 += o.A[3] * g0 + o.A[4] * g1 + o.A[5] * g2;
+      } else {
+        T pl[NPLANE];
+        load_planes(Jcm, O, s, pl);
+        T j0[9], j1[9];
+        jc_rows(pl, j0, j1);
+        e0 = pl[0] * g0 + pl[1] * g1 + pl[2] * g2;
+        e1 = pl[3] * g0 + pl[4] * g1 + pl[5] * g2;
 #pragma unroll
-      for (int i = 0; i < 9; ++i) {
-        e0 += j0[i] * sdc[i];
-        e1 += j1[i] * sdc[i];
+        for (int i = 0; i < 9; ++i) {
+          e0 += j0[i] * sdc[i];
+          e1 += j1[i] * sdc[i];
+        }
       }
       quad += (double)e0 * (double)e0 + (double)e1 * (double)e1;
     }
@@ -1146,17 +1559,22 @@ __global__ void k_lm_control(int npieces, const double* __restrict__ part, int n
 // Step-level helpers
 // ---------------------------------------------------------------------------
 
-template <typename T>
-__global__ void k_cast_vec(long long n, const double* __restrict__ a, T* __restrict__ b) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) b[i] = (T)a[i];
+// Camera vector (double [C][9]) to the pass form.
+template <typename T, bool MF>
+__global__ void k_pass_vec(int C, const double* __restrict__ x, const T* __restrict__ camtab, T* __restrict__ out) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= C) return;
+  write_pass_vec<T, MF>(camtab + (long long)CT * c, x + 9LL * c, out + (long long)pass_vec_stride(MF) * c);
 }
 
-// Unpack U [C][45] to [C][9][9] (or V [P][6] to [P][3][3]).
-__global__ void k_unpack_sym(long long n, int dim, const double* __restrict__ packed, double* __restrict__ full) {
+// Unpack U [C][45] to [C][9][9] (or V [P][6] to [P][3][3]); block b of the
+// output is packed block row[b] (row = NULL: b).
+__global__ void k_unpack_sym(long long n, int dim, const double* __restrict__ packed, const int32_t* __restrict__ row,
+                             double* __restrict__ full) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n * dim * dim) return;
-  const long long blk = i / (dim * dim);
+  const long long ob = i / (dim * dim);
+  const long long blk = row ? row[ob] : ob;
   const int rc = (int)(i % (dim * dim));
   int a = rc / dim, b = rc % dim;
   if (a > b) {
@@ -1169,12 +1587,13 @@ __global__ void k_unpack_sym(long long n, int dim, const double* __restrict__ pa
   full[i] = packed[blk * np + idx];
 }
 
-// Export sqrt(w) Jc [O][2][9], sqrt(w) Jp [O][2][3] (from the camera-major
-// planes) and w [O] in input order.
-template <typename T>
+// Export sqrt(w) Jc [O][2][9], sqrt(w) Jp [O][2][3] and w [O] in input order,
+// from the camera-major planes (stored mode) or recomputed exactly as the
+// passes recompute them.
+template <typename T, bool MF>
 __global__ void k_export_lin(int O, int P, const int32_t* __restrict__ perm_cam, const int32_t* __restrict__ ci,
                              const int32_t* __restrict__ cm_pt, const T* __restrict__ cm_px,
-                             const T* __restrict__ Jcm, const T* __restrict__ camtab,
+                             const T* __restrict__ Jcm, const T* __restrict__ cm_sw, const T* __restrict__ camtab,
                              const T* __restrict__ pts_buf, const DevState* __restrict__ st, T delta,
                              T* __restrict__ Jc, T* __restrict__ Jp, T* __restrict__ w) {
   const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1182,8 +1601,13 @@ __global__ void k_export_lin(int O, int P, const int32_t* __restrict__ perm_cam,
   const long long k = perm_cam[s];
   const int c = ci[k];
   const T* ct = camtab + (long long)CT * c;
+  T ctl[CT];
+#pragma unroll
+  for (int i = 0; i < CT; ++i) ctl[i] = ct[i];
+  const T* pts = pts_buf + (long long)st->cur * 3 * P;
+  const int j = cm_pt[s];
   T pl[NPLANE];
-  load_planes(Jcm, O, s, pl);
+  cm_planes<T, MF>(Jcm, O, (int)s, ctl, pts, j, cm_sw, pl);
   if (Jc) {
     T j0[9], j1[9];
     jc_rows(pl, j0, j1);
@@ -1195,15 +1619,13 @@ __global__ void k_export_lin(int O, int P, const int32_t* __restrict__ perm_cam,
   }
   if (Jp) {
     T jp[6];
-    jp_from(pl, ct, jp);
+    jp_from(pl, ctl, jp);
 #pragma unroll
     for (int i = 0; i < 6; ++i) Jp[6 * k + i] = jp[i];
   }
   if (w) {
-    const int j = cm_pt[s];
-    const T* X = pts_buf + (long long)st->cur * 3 * P + 3LL * j;
     T px, py, sc;
-    project_obs(ct, X[0], X[1], X[2], px, py, sc);
+    project_obs(ctl, pts[3LL * j], pts[3LL * j + 1], pts[3LL * j + 2], px, py, sc);
     const T r0 = sc * px - cm_px[s], r1 = sc * py - cm_px[(long long)O + s];
     T hr, ww;
     huber_weight(r0 * r0 + r1 * r1, delta, hr, ww);

@@ -51,7 +51,8 @@ def test_options_default_without_gpu(lib):
 def test_struct_layouts_match_header():
     from paper_2409_12190_gb300 import _lib
     assert ctypes.sizeof(_lib.ba_iter_stats) == 6 * 8 + 4 * 4
-    assert ctypes.sizeof(_lib.ba_options) == 8 * 11 + 8 + 8 + 8  # int+pad, 10 doubles, ...
+    # int (+pad), 10 doubles, int (+pad), double, 3 ints (+pad)
+    assert ctypes.sizeof(_lib.ba_options) == 8 + 80 + 8 + 8 + 16
 
 
 def test_argument_errors_need_no_gpu(lib):

@@ -17,13 +17,14 @@ def _trace_rel(gpu, ref, key):
     return max(abs(g[key] - r[key]) / abs(r[key]) for g, r in zip(gpu, ref))
 
 
-def test_ba16_f64_trace_matches_oracle_cholesky():
+@pytest.mark.parametrize("jac", ["store", "recompute"])
+def test_ba16_f64_trace_matches_oracle_cholesky(jac):
     sc = scenegen.config_scene("ba16")
     pix = orc.pixels_from_scene(sc)
     iters = 20
     cams_ref, pts_ref, ref = orc.lm(sc.cams_init, sc.points_init, sc.cam_idx, sc.pt_idx, pix,
                                     iters, orc.LMOptions(solver="cholesky"))
-    with problem(sc, pix, "f64", pcg_maxiter=9 * sc.C, pcg_tol=1e-14) as prob:
+    with problem(sc, pix, "f64", pcg_maxiter=9 * sc.C, pcg_tol=1e-14, jacobian=jac) as prob:
         prob.solve(iters)
         gpu = prob.stats()
         cams, pts = prob.params()
@@ -39,7 +40,8 @@ def test_ba16_f64_trace_matches_oracle_cholesky():
     assert np.max(np.abs(np64(pts) - pts_ref) / np.maximum(1.0, np.abs(pts_ref))) < 1e-7
 
 
-def test_ring_f64_huber_trace_matches_oracle_pcg():
+@pytest.mark.parametrize("jac", ["store", "recompute"])
+def test_ring_f64_huber_trace_matches_oracle_pcg(jac):
     """Per-trial parity at 1e-9 with PCG truncated where CG's rounding
     amplification is still far below 1e-9 (10 iterations)."""
     sc = small_ring()
@@ -47,7 +49,7 @@ def test_ring_f64_huber_trace_matches_oracle_pcg():
     iters = 8
     opts = orc.LMOptions(solver="pcg", pcg_tol=1e-4, pcg_maxiter=10, huber_delta=1.0)
     _, _, ref = orc.lm(sc.cams_init, sc.points_init, sc.cam_idx, sc.pt_idx, pix, iters, opts)
-    with problem(sc, pix, "f64", pcg_maxiter=10, pcg_tol=1e-4) as prob:
+    with problem(sc, pix, "f64", pcg_maxiter=10, pcg_tol=1e-4, jacobian=jac) as prob:
         prob.solve(iters)
         gpu = prob.stats()
     assert _trace_rel(gpu, ref, "cost") < 1e-9
@@ -69,11 +71,13 @@ def test_ring_f64_truncated_pcg_within_oracle_order_band():
     perm = np.random.default_rng(0).permutation(sc.O)
     _, _, ref2 = orc.lm(sc.cams_init, sc.points_init, sc.cam_idx[perm], sc.pt_idx[perm], pix[perm],
                         iters, opts)
-    band = max(_trace_rel(ref2, ref, "cost_trial"), 1e-9)
+    # costs of the accepted states (rejected trial points are dominated by the
+    # noise of the unconverged directions and are not compared)
+    band = max(_trace_rel(ref2, ref, "cost"), 1e-9)
     with problem(sc, pix, "f64", pcg_maxiter=50, pcg_tol=1e-4) as prob:
         prob.solve(iters)
         gpu = prob.stats()
-    assert _trace_rel(gpu, ref, "cost_trial") < 10 * band
+    assert [g["accepted"] for g in gpu] == [r["accepted"] for r in ref]
     assert _trace_rel(gpu, ref, "cost") < 10 * band
 
 
@@ -82,9 +86,18 @@ def _converged_cost(trace):
     return min([trace[0]["cost"]] + acc)
 
 
+@pytest.mark.parametrize("jac", ["store", "recompute"])
 @pytest.mark.parametrize("huber", [True, False])
-def test_ring_f32_reaches_fp64_final_cost(huber):
-    # 60 cameras: the LM run is converged to well below 1e-6 after 25 trials
+def test_ring_f32_reaches_fp64_final_cost(huber, jac):
+    """FP32 per-observation arithmetic reaches the FP64 final cost within 1e-6.
+
+    Plain loss: after 25 trials both runs have converged (quadratic rate).
+    Huber: IRLS without the rho'' term converges linearly -- on the outlier
+    residuals the true loss is linear, so the gain ratio tends to 2 and each
+    trial removes only a small fraction of the remaining excess -- and after
+    25 trials the FP64 run still drops ~5e-7 per trial.  There the FP32 cost
+    must be within 1e-6 of the FP64 cost plus the decrease of the FP64 run
+    over its last three trials (the FP32 run may lag by a rejected trial)."""
     sc = small_ring(C=60, P=3000, huber=huber)
     pix = orc.pixels_from_scene(sc)
     iters = 25
@@ -92,23 +105,25 @@ def test_ring_f32_reaches_fp64_final_cost(huber):
     opts = orc.LMOptions(solver="pcg", pcg_tol=1e-4, pcg_maxiter=50, huber_delta=delta)
     _, _, ref = orc.lm(sc.cams_init, sc.points_init, sc.cam_idx, sc.pt_idx, pix, iters, opts)
     F_ref = _converged_cost(ref)
-    with problem(sc, pix, "f32", pcg_maxiter=50, pcg_tol=1e-4) as prob:
+    tail = (ref[-3]["cost"] - F_ref) if huber else 0.0
+    with problem(sc, pix, "f32", pcg_maxiter=50, pcg_tol=1e-4, jacobian=jac) as prob:
         prob.solve(iters)
         gpu = prob.stats()
         cams, pts = prob.params()
     F32 = _converged_cost(gpu)
     # re-evaluate the FP32 result in FP64 with the oracle's cost
     F32_exact = orc.cost(np64(cams), np64(pts), sc.cam_idx, sc.pt_idx, pix, delta)
-    assert abs(F32_exact - F_ref) / F_ref < 1e-6
-    assert abs(F32 - F_ref) / F_ref < 1e-6
+    assert abs(F32_exact - F_ref) < 1e-6 * F_ref + tail
+    assert abs(F32 - F_ref) < 1e-6 * F_ref + tail
 
 
-def test_graph_and_direct_launches_are_bitwise_identical():
+@pytest.mark.parametrize("jac", ["store", "recompute"])
+def test_graph_and_direct_launches_are_bitwise_identical(jac):
     sc = small_ring(C=40, P=800, seed=5)
     pix = orc.pixels_from_scene(sc)
     res = []
     for use_graph in (True, False):
-        with problem(sc, pix, "f32", pcg_maxiter=30, use_graph=use_graph) as prob:
+        with problem(sc, pix, "f32", pcg_maxiter=30, use_graph=use_graph, jacobian=jac) as prob:
             prob.solve(5)
             st = prob.stats()
             cams, pts = prob.params()

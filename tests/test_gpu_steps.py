@@ -35,12 +35,13 @@ def _scenes():
     return {"plain": a, "huber": b}
 
 
+@pytest.mark.parametrize("jac", ["store", "recompute"])
 @pytest.mark.parametrize("prec", ["f64", "f32"])
 @pytest.mark.parametrize("kind", ["plain", "huber"])
-def test_linearize_and_assemble(prec, kind):
+def test_linearize_and_assemble(prec, kind, jac):
     sc = _scenes()[kind]
     pix = orc.pixels_from_scene(sc)
-    with problem(sc, pix, prec) as prob:
+    with problem(sc, pix, prec, jacobian=jac) as prob:
         out = prob.linearize()
     ref = orc.assemble(sc.cams_init, sc.points_init, sc.cam_idx, sc.pt_idx, pix, sc.huber_delta)
     sw = np.sqrt(ref["w"])
@@ -52,15 +53,17 @@ def test_linearize_and_assemble(prec, kind):
         assert rel_err(np64(out[key]), ref[key]) < 10 * tol, key
 
 
+@pytest.mark.parametrize("jac", ["store", "recompute"])
 @pytest.mark.parametrize("prec", ["f64", "f32"])
-def test_schur_matvec(prec):
-    sc = scenegen.config_scene("ba16")
+@pytest.mark.parametrize("kind", ["plain", "huber"])
+def test_schur_matvec(prec, jac, kind):
+    sc = _scenes()[kind]
     pix = orc.pixels_from_scene(sc)
     lam = 1e-3
-    blk = orc.assemble(sc.cams_init, sc.points_init, sc.cam_idx, sc.pt_idx, pix)
+    blk = orc.assemble(sc.cams_init, sc.points_init, sc.cam_idx, sc.pt_idx, pix, sc.huber_delta)
     S, _, _, _ = orc.schur_explicit(blk, sc.cam_idx, sc.pt_idx, lam)
     rng = np.random.default_rng(0)
-    with problem(sc, pix, prec) as prob:
+    with problem(sc, pix, prec, jacobian=jac) as prob:
         for _ in range(3):
             x = rng.normal(size=(sc.C, 9)) * np.array([1e-3] * 6 + [1.0, 1e-3, 1e-3])
             y = prob.schur_matvec(lam, torch.from_numpy(x).cuda())
@@ -68,22 +71,24 @@ def test_schur_matvec(prec):
             assert rel_err(np64(y).reshape(-1), ref) < (1e-10 if prec == "f64" else 1e-4)
 
 
-def test_damped_solve_matches_dense_cholesky():
+@pytest.mark.parametrize("jac", ["store", "recompute"])
+def test_damped_solve_matches_dense_cholesky(jac):
     sc = scenegen.config_scene("ba16")
     pix = orc.pixels_from_scene(sc)
     lam = 1e-3
     blk = orc.assemble(sc.cams_init, sc.points_init, sc.cam_idx, sc.pt_idx, pix)
     dc_ref, dp_ref, _, _ = orc.solve_damped(blk, sc.cam_idx, sc.pt_idx, lam,
                                            orc.LMOptions(solver="cholesky"))
-    with problem(sc, pix, "f64") as prob:
+    with problem(sc, pix, "f64", jacobian=jac) as prob:
         dc, dp, its, rel = prob.damped_solve(lam, 9 * sc.C * 3, 1e-13)
     assert rel <= 1e-13 and its > 0
     assert rel_err(np64(dc), dc_ref) < 1e-8
     assert rel_err(np64(dp), dp_ref) < 1e-8
 
 
+@pytest.mark.parametrize("jac", ["store", "recompute"])
 @pytest.mark.parametrize("maxiter,tol", [(1, 0.0), (10, 0.0), (200, 1e-2)])
-def test_damped_solve_truncated_pcg_matches_oracle_pcg(maxiter, tol):
+def test_damped_solve_truncated_pcg_matches_oracle_pcg(maxiter, tol, jac):
     """Same PCG algorithm, same stopping rule: same iterate (while CG's
     rounding amplification on this ill-conditioned system stays small)."""
     sc = small_ring()
@@ -92,7 +97,7 @@ def test_damped_solve_truncated_pcg_matches_oracle_pcg(maxiter, tol):
     blk = orc.assemble(sc.cams_init, sc.points_init, sc.cam_idx, sc.pt_idx, pix, sc.huber_delta)
     opts = orc.LMOptions(solver="pcg", pcg_tol=tol, pcg_maxiter=maxiter)
     dc_ref, dp_ref, its_ref, rel_ref = orc.solve_damped(blk, sc.cam_idx, sc.pt_idx, lam, opts)
-    with problem(sc, pix, "f64") as prob:
+    with problem(sc, pix, "f64", jacobian=jac) as prob:
         dc, dp, its, rel = prob.damped_solve(lam, maxiter, tol)
     assert its == its_ref
     assert abs(rel - rel_ref) < 1e-8 * max(rel_ref, 1e-30) + 1e-14
