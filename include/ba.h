@@ -155,6 +155,10 @@ ba_status ba_get_stats(ba_problem* h, ba_iter_stats* host_out, int cap,
  * Synchronises. */
 ba_status ba_get_scalars(ba_problem* h, double* cost, double* lambda);
 
+/* Set the damping of the next trial (lambda > 0, e.g. to restart a solve
+ * after new observations).  Synchronises. */
+ba_status ba_set_lambda(ba_problem* h, double lambda);
+
 /* Checkpoint: the number of doubles ba_get_state writes (9C + 3P + 4). */
 size_t ba_state_size(const ba_problem* h);
 /* Write theta, cost, lambda and the trial counter to host_state (host,
@@ -163,6 +167,35 @@ ba_status ba_get_state(ba_problem* h, double* host_state);
 /* Restore a state written by ba_get_state on a problem with the same
  * C, P, O and precision.  Synchronises. */
 ba_status ba_set_state(ba_problem* h, const double* host_state);
+
+/* Freeze camera parameters: mask (any, uint8 [C][9], nonzero = frozen) or
+ * NULL to free them all.  Frozen parameters never move; each LM step solves
+ * the system restricted to the free ones (S -> m S m + (I - m), b -> m b).
+ * Freezing all nine parameters of one camera and one translation component
+ * of another removes the 7-dimensional similarity gauge of BA, which the
+ * adjoint needs for a well-defined derivative.  Not in the paper. */
+ba_status ba_set_fixed(ba_problem* h, const uint8_t* mask, void* stream);
+
+/* Implicit-function adjoint at the current parameters theta* (meant to be a
+ * converged solution, where the gradient vanishes).  With the Gauss-Newton
+ * H* = J^T W J + lambda clamp(diag), restricted to the free parameters,
+ * v = H*^{-1} dL/dtheta is solved by the same Schur / block-Jacobi PCG as the
+ * forward step (maxiter, tol), then
+ *   dL/dx_k      = w_k J_k v                      (r_k = pi_k - x_k)
+ *   dL/dtheta0   = dL/dtheta - (H* v) on frozen camera parameters, 0 on free
+ *                  ones and on points (theta* does not depend on where the
+ *                  free parameters start).
+ * Not in the paper (its bilevel use of BA, Sec. VI, motivates it).  Inputs
+ * dL_dcams [C][9], dL_dpoints [P][3] (dev, precision type, either may be
+ * NULL = zero); outputs dL_dpixels_out [O][2] (required),
+ * dL_dcams0_out [C][9], dL_dpoints0_out [P][3] (dev, may be NULL); iters /
+ * rel_res (host, may be NULL: then no synchronisation).  The next LM trial
+ * re-linearises. */
+ba_status ba_backward(ba_problem* h, double lambda, int maxiter, double tol,
+                      const void* dL_dcams, const void* dL_dpoints,
+                      void* dL_dpixels_out, void* dL_dcams0_out,
+                      void* dL_dpoints0_out, int* iters, double* rel_res,
+                      void* stream);
 
 /* Thread-local message of the last failing call ("" if none). */
 const char* ba_last_error(void);

@@ -48,7 +48,8 @@ __all__ = [
     "dense_jacobian", "damp_diag", "point_damped_inverse", "schur_explicit",
     "schur_matvec", "block_jacobi", "pcg", "cholesky_solve", "back_substitute",
     "model_reduction", "solve_damped", "LMOptions", "lm", "dense_lm_delta",
-    "gauge_transform", "pixels_from_scene",
+    "gauge_transform", "pixels_from_scene", "gauge_mask", "adjoint_dense",
+    "adjoint_schur",
 ]
 
 
@@ -407,22 +408,36 @@ def model_reduction(blk, dc, dp, cam_idx, pt_idx):
     return -lin - 0.5 * quad
 
 
-def solve_damped(blk, cam_idx, pt_idx, lam, opts):
-    """One damped solve (Eq. 2) through the reduced camera system."""
+def _mask_blocks(A, m):
+    """Restrict 9x9 blocks to the free parameters: m A m + (I - m)."""
+    mm = m[:, :, None] * m[:, None, :]
+    return A * mm + np.eye(9)[None] * (1.0 - m)[:, :, None]
+
+
+def solve_damped(blk, cam_idx, pt_idx, lam, opts, fixed=None):
+    """One damped solve (Eq. 2) through the reduced camera system.
+
+    fixed: optional [C, 9] boolean mask of frozen camera parameters.  The
+    solve is then the one of the system restricted to the free parameters
+    (frozen steps are exactly zero): S -> m S m + (I - m), b -> m b."""
     Us = _ustar(blk["U"], lam, opts.diag_min, opts.diag_max)
     Vinv = point_damped_inverse(blk["V"], lam, opts.diag_min, opts.diag_max)
     C = Us.shape[0]
+    m = np.ones((C, 9)) if fixed is None else 1.0 - np.asarray(fixed, dtype=np.float64)
     if opts.solver == "cholesky":
         S, b, _, _ = schur_explicit(blk, cam_idx, pt_idx, lam, opts.diag_min, opts.diag_max)
-        dc = cholesky_solve(S, b).reshape(C, 9)
+        mv = m.reshape(-1)
+        S = S * mv[:, None] * mv[None, :] + np.diag(1.0 - mv)
+        dc = cholesky_solve(S, b * mv).reshape(C, 9)
         its, rel = 0, 0.0
     else:
-        b = -blk["gc"] + segment_sum(
+        b = m * (-blk["gc"] + segment_sum(
             cam_idx, np.einsum("oij,oj->oi", blk["W"],
-                               np.einsum("pij,pj->pi", Vinv, blk["gp"])[pt_idx]), C)
-        M = block_jacobi(Us, Vinv, blk["W"], cam_idx, pt_idx)
+                               np.einsum("pij,pj->pi", Vinv, blk["gp"])[pt_idx]), C))
+        Sii = Us - segment_sum(cam_idx, blk["W"] @ Vinv[pt_idx] @ np.transpose(blk["W"], (0, 2, 1)), C)
+        M = np.linalg.inv(_mask_blocks(Sii, m))
         dc, its, rel = pcg(
-            lambda x: schur_matvec(x, Us, Vinv, blk["W"], cam_idx, pt_idx),
+            lambda x: m * schur_matvec(x, Us, Vinv, blk["W"], cam_idx, pt_idx),
             lambda r: np.einsum("cij,cj->ci", M, r), b, opts.pcg_tol, opts.pcg_maxiter)
     dp = back_substitute(dc, blk, Vinv, cam_idx, pt_idx)
     return dc, dp, its, rel
@@ -466,7 +481,7 @@ class LMOptions:
     huber_delta: float = 0.0
 
 
-def lm(cams0, points0, cam_idx, pt_idx, pixels, iters, opts=None):
+def lm(cams0, points0, cam_idx, pt_idx, pixels, iters, opts=None, fixed=None):
     """Run ``iters`` LM trials (a rejected trial counts as one).
 
     Per trial: linearise at theta (skipped after a rejection: theta and J are
@@ -475,6 +490,7 @@ def lm(cams0, points0, cam_idx, pt_idx, pixels, iters, opts=None):
     Delta L > 0 and F' < F.  lambda <- max(lambda/up, lambda_min) when
     accepted with rho > rho_good; lambda <- min(lambda/down, lambda_max) when
     rejected or rho < rho_bad; unchanged otherwise.
+    fixed: optional [C, 9] mask of camera parameters that never move.
     Returns (cams, points, trace) with one dict per trial."""
     opts = opts or LMOptions()
     cams = np.array(cams0, dtype=np.float64, copy=True)
@@ -487,7 +503,7 @@ def lm(cams0, points0, cam_idx, pt_idx, pixels, iters, opts=None):
     for _ in range(iters):
         if blk is None:
             blk = assemble(cams, points, cam_idx, pt_idx, pixels, delta)
-        dc, dp, its, rel = solve_damped(blk, cam_idx, pt_idx, lam, opts)
+        dc, dp, its, rel = solve_damped(blk, cam_idx, pt_idx, lam, opts, fixed)
         cams_t = cams + dc
         points_t = points + dp
         Ft = cost(cams_t, points_t, cam_idx, pt_idx, pixels, delta)
@@ -527,6 +543,69 @@ def gauge_transform(cams, points, s, Q, tau):
     out[:, 3:6] = s * cams[:, 3:6] - np.einsum("cij,j->ci", Rn, tau)
     pts = s * (np.asarray(points, np.float64) @ Q.T) + tau
     return out, pts
+
+
+def gauge_mask(C):
+    """Frozen parameters that remove the 7-dim similarity gauge: all nine of
+    camera 0 and the x-translation of camera 1 (scale)."""
+    m = np.zeros((C, 9), dtype=bool)
+    m[0, :] = True
+    if C > 1:
+        m[1, 3] = True
+    return m
+
+
+def adjoint_dense(cams, points, cam_idx, pt_idx, pixels, dL_dcams, dL_dpoints, fixed,
+                  delta=0.0, lam=0.0, diag_min=1e-6, diag_max=1e32):
+    """Implicit-function adjoint at a converged solution, written out densely.
+
+    At the minimiser g(theta*, x) = 0, with the Gauss-Newton H = J^T W J
+    restricted to the free parameters f:  v_f = H_ff^{-1} dL/dtheta_f,
+    v_fixed = 0;  dL/dx_k = w_k J_k v  (r_k = pi_k - x_k);  for a frozen
+    parameter dL/dtheta0 = dL/dtheta - (H v), and 0 for a free one.  lam adds
+    lam * clamp(diag H) to H (0: the undamped adjoint).
+    Returns (dL/dpixels [O, 2], dL/dcams0 [C, 9], dL/dpoints0 [P, 3], v)."""
+    C = np.asarray(cams).shape[0]
+    J, _ = dense_jacobian(cams, points, cam_idx, pt_idx, pixels, delta)
+    r = residuals(cams, points, cam_idx, pt_idx, pixels)
+    _, w = huber(np.sum(r * r, axis=1), delta)
+    H = J.T @ J
+    H = H + np.diag(damp_diag(np.diag(H), lam, diag_min, diag_max))
+    a = np.concatenate([np.asarray(dL_dcams, np.float64).reshape(-1),
+                        np.asarray(dL_dpoints, np.float64).reshape(-1)])
+    free = np.concatenate([~np.asarray(fixed).reshape(-1), np.ones(a.shape[0] - 9 * C, bool)])
+    v = np.zeros_like(a)
+    v[free] = np.linalg.solve(H[np.ix_(free, free)], a[free])
+    Jv = (J @ v).reshape(-1, 2)                      # sqrt(w) J_k v
+    dpix = np.sqrt(w)[:, None] * Jv
+    d0 = np.where(free, 0.0, a - H @ v)
+    return dpix, d0[:9 * C].reshape(C, 9), d0[9 * C:].reshape(-1, 3), v
+
+
+def adjoint_schur(cams, points, cam_idx, pt_idx, pixels, dL_dcams, dL_dpoints, fixed,
+                  delta=0.0, lam=0.0, diag_min=1e-6, diag_max=1e32):
+    """The same adjoint through the Schur complement of the point blocks
+    (explicit S, dense Cholesky), for scenes too large for the dense H:
+    S v_c = a_c - W V^{-1} a_p,  v_p = V^{-1} (a_p - W^T v_c)."""
+    C = np.asarray(cams).shape[0]
+    blk = assemble(cams, points, cam_idx, pt_idx, pixels, delta)
+    a_c = np.asarray(dL_dcams, np.float64)
+    a_p = np.asarray(dL_dpoints, np.float64)
+    adj = dict(blk)
+    adj["gc"] = -a_c
+    adj["gp"] = -a_p
+    opts = LMOptions(solver="cholesky", diag_min=diag_min, diag_max=diag_max)
+    v_c, v_p, _, _ = solve_damped(adj, cam_idx, pt_idx, lam, opts, fixed)
+    sw = np.sqrt(blk["w"])
+    Jv = np.einsum("oai,oi->oa", blk["Jc"], v_c[cam_idx]) + \
+        np.einsum("oai,oi->oa", blk["Jp"], v_p[pt_idx])
+    dpix = (sw * sw)[:, None] * Jv
+    Hv_c = segment_sum(cam_idx, blk["w"][:, None] * np.einsum("oai,oa->oi", blk["Jc"], Jv), C)
+    if lam > 0.0:
+        idx = np.arange(9)
+        Hv_c = Hv_c + damp_diag(blk["U"][:, idx, idx], lam, diag_min, diag_max) * v_c
+    d0c = np.where(np.asarray(fixed), a_c - Hv_c, 0.0)
+    return dpix, d0c, np.zeros_like(a_p), (v_c, v_p)
 
 
 def pixels_from_scene(scene):

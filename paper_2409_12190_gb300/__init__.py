@@ -22,7 +22,7 @@ from . import _lib
 from ._lib import BAError, BA_PREC_F32, BA_PREC_F64
 
 __all__ = ["Options", "Problem", "project", "csr_build", "kernel_launch_count",
-           "BAError", "library_path"]
+           "BAError", "library_path", "bundle_adjust"]
 
 library_path = _lib.LIB_PATH
 
@@ -178,6 +178,9 @@ class Problem:
         _lib.check(_L().ba_get_scalars(self._h, ct.byref(c), ct.byref(l)))
         return c.value, l.value
 
+    def set_lambda(self, lam: float):
+        _lib.check(_L().ba_set_lambda(self._h, float(lam)))
+
     def get_state(self):
         n = _L().ba_state_size(self._h)
         out = torch.empty(n, dtype=torch.float64)
@@ -189,6 +192,39 @@ class Problem:
         if s.numel() != _L().ba_state_size(self._h):
             raise ValueError("state size mismatch")
         _lib.check(_L().ba_set_state(self._h, _ptr(s)))
+
+    def set_fixed(self, mask=None, stream=None):
+        """Freeze camera parameters: bool/uint8 [C, 9] (True = frozen) or None."""
+        if mask is None:
+            _lib.check(_L().ba_set_fixed(self._h, None, _stream(stream)))
+            return
+        m = torch.as_tensor(mask).to(device=self.device, dtype=torch.uint8).contiguous()
+        if tuple(m.shape) != (self.C, 9):
+            raise ValueError("mask must have shape [C, 9]")
+        _lib.check(_L().ba_set_fixed(self._h, _ptr(m), _stream(stream)))
+        torch.cuda.current_stream(self.device).synchronize()
+
+    def backward(self, dL_dcams=None, dL_dpoints=None, lam: float = 0.0, maxiter: int = 1000,
+                 tol: float = 1e-12, stream=None):
+        """Implicit-function adjoint at the current (converged) parameters.
+
+        Returns (dL/dpixels [O, 2], dL/dcams0 [C, 9], dL/dpoints0 [P, 3],
+        pcg iterations, relative residual)."""
+        def prep(t, shape):
+            if t is None:
+                return None
+            return t.to(device=self.device, dtype=self.dtype).contiguous().reshape(shape)
+        gc = prep(dL_dcams, (self.C, 9))
+        gp = prep(dL_dpoints, (self.P, 3))
+        dpix = torch.empty((self.O, 2), dtype=self.dtype, device=self.device)
+        dc0 = torch.empty((self.C, 9), dtype=self.dtype, device=self.device)
+        dp0 = torch.empty((self.P, 3), dtype=self.dtype, device=self.device)
+        it = ct.c_int()
+        rel = ct.c_double()
+        _lib.check(_L().ba_backward(self._h, float(lam), int(maxiter), float(tol), _ptr(gc), _ptr(gp),
+                                    _ptr(dpix), _ptr(dc0), _ptr(dp0), ct.byref(it), ct.byref(rel),
+                                    _stream(stream)))
+        return dpix, dc0, dp0, it.value, rel.value
 
     def profile_trials(self, iters: int):
         """Run iters LM trials with a CUDA event pair around every launch;
@@ -241,6 +277,40 @@ class Problem:
         _lib.check(_L().ba_damped_solve(self._h, float(lam), int(maxiter), float(tol), _ptr(dc),
                                         _ptr(dp), ct.byref(it), ct.byref(rel), _stream(stream)))
         return dc, dp, it.value, rel.value
+
+
+class _BundleAdjust(torch.autograd.Function):
+    """theta* = LM(pixels, theta0) with the implicit-function adjoint as its
+    backward (gradients w.r.t. the observed pixels and the initial
+    parameters)."""
+
+    @staticmethod
+    def forward(ctx, pixels, cams0, points0, problem, iters, adjoint):
+        problem.set_params(cams0.detach().to(problem.dtype).contiguous(),
+                           points0.detach().to(problem.dtype).contiguous())
+        problem.set_pixels(pixels.detach().to(problem.dtype).contiguous())
+        problem.set_lambda(problem.options.lambda0)
+        problem.solve(iters)
+        cams, points = problem.params()
+        ctx.problem = problem
+        ctx.adjoint = adjoint
+        ctx.dtypes = (pixels.dtype, cams0.dtype, points0.dtype)
+        return cams, points
+
+    @staticmethod
+    def backward(ctx, g_cams, g_points):
+        dpix, dc0, dp0, _, _ = ctx.problem.backward(g_cams, g_points, **ctx.adjoint)
+        tp, tc, tq = ctx.dtypes
+        return dpix.to(tp), dc0.to(tc), dp0.to(tq), None, None, None
+
+
+def bundle_adjust(pixels, cams0, points0, problem: "Problem", iters: int, lam: float = 0.0,
+                  maxiter: int = 1000, tol: float = 1e-12):
+    """Differentiable LM solve on an existing problem (its structure and
+    frozen-parameter mask are reused): returns (cams*, points*); gradients
+    flow to pixels, cams0 and points0 through the implicit-function adjoint."""
+    return _BundleAdjust.apply(pixels, cams0, points0, problem, int(iters),
+                               dict(lam=lam, maxiter=maxiter, tol=tol))
 
 
 def project(cams, points, cam_idx, pt_idx, stream=None):

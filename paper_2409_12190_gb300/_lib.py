@@ -89,6 +89,9 @@ SIGNATURES = {
     "ba_csr_build_noalloc": (_S, [_VP, _I, _I, _VP, _VP, _VP]),
     "ba_kernel_launch_count": (ct.c_uint64, []),
     "ba_profile_trials": (_S, [_VP, _I, ct.POINTER(ba_kernel_times)]),
+    "ba_set_fixed": (_S, [_VP, _VP, _VP]),
+    "ba_set_lambda": (_S, [_VP, _D]),
+    "ba_backward": (_S, [_VP, _D, _I, _D, _VP, _VP, _VP, _VP, _VP, ct.POINTER(_I), ct.POINTER(_D), _VP]),
 }
 
 _lib = None

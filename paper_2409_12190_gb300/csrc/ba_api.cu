@@ -87,6 +87,8 @@ struct ba_problem {
   // the symbolic phase in the caller's numbering (ba_get_csr)
   int32_t *xperm_cam = nullptr, *xperm_pt = nullptr, *xrowptr_pt = nullptr;
   void* pts_tmp = nullptr;  // [P][3] staging for reordering parameters
+  uint8_t* fixed = nullptr;  // [C][9] frozen camera parameters, or NULL
+  uint8_t* fixed_buf = nullptr;
   int32_t *cm_pt = nullptr, *pm_cam = nullptr, *pm_pt = nullptr;
   int32_t* pm2cm = nullptr;  // camera-major slot of each point-major slot
   int nchunks = 0;
@@ -246,7 +248,7 @@ void enqueue_pcg_iter(ba_problem* h, const double* lam_ptr, int k, double tol) {
   {
     Prof pr(h, BA_K_OTHER, k);
     k_pcg_q<T, MF><<<h->ncb, VT, 0, s>>>(h->C, h->cam_piece_ptr, h->part, h->U, (const T*)h->camtab, lam_ptr,
-                                        dmin, dmax, h->p, h->q, h->dot_pq, h->st, 1);
+                                        dmin, dmax, h->p, h->q, h->dot_pq, h->fixed, h->st, 1);
   }
   count_launch(3);
   {
@@ -282,7 +284,7 @@ void enqueue_solve(ba_problem* h, const double* lam_ptr, int maxiter, double tol
     Prof pr(h, BA_K_OTHER);
     k_cam_combine_schur<T, MF><<<h->ncb, CAM_THREADS, 0, s>>>(
         h->C, h->cam_piece_ptr, h->part, h->U, h->gc, (const T*)h->camtab, lam_ptr, dmin, dmax, h->Minv, h->x,
-        h->r, h->z, h->p, (T*)h->pT, h->dot_rz + h->ncb, h->dot_bb, h->st);
+        h->r, h->z, h->p, (T*)h->pT, h->dot_rz + h->ncb, h->dot_bb, h->fixed, h->st);
   }
   count_launch(3);
   for (int k = 0; k < maxiter; ++k) enqueue_pcg_iter<T, MF>(h, lam_ptr, k, tol);
@@ -351,6 +353,32 @@ void enqueue_cost(ba_problem* h) {
 
 void enqueue_trial_any(ba_problem* h) { BA_DISPATCH(h, enqueue_trial); }
 
+// Implicit-function adjoint at the current parameters: v = H*^{-1} dL/dtheta
+// through the forward Schur/PCG solver (its gradient slots hold -dL/dtheta),
+// then dL/dx_k = w_k J_k v and dL/dtheta0 on frozen parameters.
+template <typename T, bool MF>
+void enqueue_backward(ba_problem* h, const double* lam_ptr, int maxiter, double tol, const void* dLc,
+                      const void* dLp, void* dpix, void* dc0, void* dp0) {
+  cudaStream_t s = h->s;
+  enqueue_lin<T, MF>(h, 1);
+  const long long n = std::max(9LL * h->C, 3LL * h->P);
+  k_adj_rhs<T><<<nblk(n, 256), 256, 0, s>>>(h->C, h->P, (const T*)dLc, (const T*)dLp, h->pnew, h->gc, h->gp);
+  count_launch();
+  enqueue_solve<T, MF>(h, lam_ptr, maxiter, tol);
+  const T delta = (T)(h->opt.huber_delta > 0 ? h->opt.huber_delta : 0.0);
+  k_adjoint_cam<T, MF><<<h->npieces, PIECE_THREADS, 0, s>>>(
+      h->piece_cam, h->piece_beg, h->piece_end, h->cm_pt, h->perm_cam, (const T*)h->cm_px, (const T*)h->Jcm,
+      (const T*)h->cm_sw, (const T*)h->ptab, (const T*)h->camtab, (const T*)h->xT, (const T*)h->dp, delta, h->O,
+      (T*)dpix, h->part);
+  count_launch();
+  if (dc0) {
+    k_adjoint_combine<T, MF><<<nblk(h->C, 128), 128, 0, s>>>(h->C, h->cam_piece_ptr, h->part, h->U,
+                                                            (const T*)h->camtab, lam_ptr, h->opt.diag_min,
+                                                            h->opt.diag_max, h->x, (const T*)dLc, h->fixed, (T*)dc0);
+    count_launch();
+  }
+}
+
 template <typename T, bool MF>
 void launch_export(ba_problem* h, void* Jc, void* Jp, void* w) {
   const T delta = (T)(h->opt.huber_delta > 0 ? h->opt.huber_delta : 0.0);
@@ -370,7 +398,7 @@ void enqueue_matvec(ba_problem* h, const double* lam_ptr) {
   k_pass_vec<T, MF><<<nblk(h->C, 128), 128, 0, s>>>(h->C, h->p, (const T*)h->camtab, (T*)h->pT);
   enqueue_schur_product<T, MF>(h, (const T*)h->pT, -1, 0);
   k_pcg_q<T, MF><<<h->ncb, VT, 0, s>>>(h->C, h->cam_piece_ptr, h->part, h->U, (const T*)h->camtab, lam_ptr,
-                                      dmin, dmax, h->p, h->q, nullptr, h->st, 0);
+                                      dmin, dmax, h->p, h->q, nullptr, h->fixed, h->st, 0);
   count_launch(3);
 }
 
@@ -851,6 +879,13 @@ ba_status ba_get_scalars(ba_problem* h, double* cost, double* lambda) {
   return BA_OK;
 }
 
+ba_status ba_set_lambda(ba_problem* h, double lambda) {
+  if (!h || !(lambda > 0)) return fail(BA_ERR_INVALID_ARG, "lambda must be > 0");
+  CU(cudaMemcpyAsync(&h->st->lam, &lambda, sizeof(double), cudaMemcpyHostToDevice, h->s));
+  CU(cudaStreamSynchronize(h->s));
+  return BA_OK;
+}
+
 size_t ba_state_size(const ba_problem* h) { return h ? 9ull * h->C + 3ull * h->P + 4 : 0; }
 
 ba_status ba_get_state(ba_problem* h, double* out) {
@@ -1007,6 +1042,56 @@ ba_status ba_csr_build(const int32_t* keys, int n, int n_keys, int32_t* perm_out
   if (e != cudaSuccess) return fail(BA_ERR_CUDA, "csr build failed: %s", cudaGetErrorString(e));
   if (err) return fail(BA_ERR_INVALID_ARG, "key out of range [0, %d)", n_keys);
   return BA_OK;
+}
+
+ba_status ba_set_fixed(ba_problem* h, const uint8_t* mask, void* stream) {
+  if (!h) return fail(BA_ERR_INVALID_ARG, "NULL problem");
+  ba_status st = enter(h, stream);
+  if (st != BA_OK) return st;
+  if (!mask) {
+    h->fixed = nullptr;  // the allocation (if any) stays owned by the problem
+  } else {
+    if (!h->fixed_buf) CU(h->alloc(&h->fixed_buf, 9ull * h->C));
+    CU(cudaMemcpyAsync(h->fixed_buf, mask, 9ull * h->C, cudaMemcpyDefault, h->s));
+    h->fixed = h->fixed_buf;
+  }
+  if (h->gexec) {
+    // the captured trial bakes in the mask pointer: capture again on next use
+    cudaGraphExecDestroy(h->gexec);
+    h->gexec = nullptr;
+  }
+  return leave(h, stream);
+}
+
+ba_status ba_backward(ba_problem* h, double lambda, int maxiter, double tol, const void* dL_dcams,
+                      const void* dL_dpoints, void* dL_dpixels_out, void* dL_dcams0_out, void* dL_dpoints0_out,
+                      int* iters, double* rel_res, void* stream) {
+  if (!h || !dL_dpixels_out) return fail(BA_ERR_INVALID_ARG, "NULL argument");
+  if (maxiter < 0 || maxiter > 100000 || !(tol >= 0) || !(lambda >= 0))
+    return fail(BA_ERR_INVALID_ARG, "bad lambda/maxiter/tol");
+  ba_status st = enter(h, stream);
+  if (st != BA_OK) return st;
+  st = set_probe_lambda(h, lambda);
+  if (st != BA_OK) return st;
+  st = set_flag(h, offsetof(DevState, need_lin), 1);
+  if (st != BA_OK) return st;
+  const double* lp = &h->st->lam_probe;
+  BA_DISPATCH(h, enqueue_backward, lp, maxiter, tol, dL_dcams, dL_dpoints, dL_dpixels_out, dL_dcams0_out,
+              dL_dpoints0_out);
+  if (dL_dpoints0_out) CU(cudaMemsetAsync(dL_dpoints0_out, 0, 3ull * h->P * h->tsize, h->s));
+  CU(cudaGetLastError());
+  // the gradient slots now hold the adjoint right-hand side: linearise again
+  // before the next trial
+  st = set_flag(h, offsetof(DevState, need_lin), 1);
+  if (st != BA_OK) return st;
+  if (iters || rel_res) {
+    DevState ds;
+    CU(cudaMemcpyAsync(&ds, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, h->s));
+    CU(cudaStreamSynchronize(h->s));
+    if (iters) *iters = ds.pcg_iters;
+    if (rel_res) *rel_res = ds.pcg_rel;
+  }
+  return leave(h, stream);
 }
 
 uint64_t ba_kernel_launch_count(void) { return ba::g_launches.load(); }

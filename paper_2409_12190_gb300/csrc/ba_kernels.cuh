@@ -937,7 +937,7 @@ k_cam_combine_schur(int C, const int32_t* __restrict__ cam_piece_ptr, const doub
                     const double* __restrict__ lam_ptr, double dmin, double dmax, double* __restrict__ Minv,
                     double* __restrict__ x, double* __restrict__ r, double* __restrict__ z,
                     double* __restrict__ p, T* __restrict__ pT, double* __restrict__ dot_rz1,
-                    double* __restrict__ dot_bb, DevState* st) {
+                    double* __restrict__ dot_bb, const uint8_t* __restrict__ fixed, DevState* st) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   double rz = 0.0, bb = 0.0;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -964,6 +964,21 @@ k_cam_combine_schur(int C, const int32_t* __restrict__ cam_piece_ptr, const doub
       for (int i = 0; i < 45; ++i) S[i] -= pp[i];
 #pragma unroll
       for (int i = 0; i < 9; ++i) bv[i] += pp[45 + i];
+    }
+    if (fixed) {
+      // frozen parameters: the system restricted to the free ones,
+      // S -> m S m + (I - m), b -> m b
+      bool fz[9];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        fz[i] = fixed[9LL * c + i] != 0;
+        if (fz[i]) bv[i] = 0.0;
+      }
+#pragma unroll
+      for (int i = 0; i < 9; ++i)
+#pragma unroll
+        for (int j = i; j < 9; ++j)
+          if (fz[i] || fz[j]) S[sym9(i, j)] = i == j ? 1.0 : 0.0;
     }
     double M[45];
     if (!spd_inverse9(S, M)) {
@@ -1274,7 +1289,7 @@ __global__ void __launch_bounds__(VT)
 k_pcg_q(int C, const int32_t* __restrict__ cam_piece_ptr, const double* __restrict__ part,
         const double* __restrict__ U, const T* __restrict__ camtab, const double* __restrict__ lam_ptr, double dmin,
         double dmax, const double* __restrict__ p, double* __restrict__ q, double* __restrict__ dot_pq,
-        const DevState* __restrict__ st, int check_done) {
+        const uint8_t* __restrict__ fixed, const DevState* __restrict__ st, int check_done) {
   if (check_done && st->pcg_done) return;
   __shared__ double sp[CAM_THREADS][9], ss[CAM_THREADS][9];
   const int lc = threadIdx.x / 9, i = threadIdx.x % 9;
@@ -1300,6 +1315,7 @@ k_pcg_q(int C, const int32_t* __restrict__ cam_piece_ptr, const double* __restri
 #pragma unroll
     for (int j = 0; j < 9; ++j) y += Uc[sym9_rt(i, j)] * sp[lc][j];
     y -= sum;
+    if (fixed && fixed[9LL * c + i]) y = 0.0;
     q[9LL * c + i] = y;
     pq = pv * y;
   }
@@ -1553,6 +1569,122 @@ __global__ void k_lm_control(int npieces, const double* __restrict__ part, int n
   }
   st->lam = nl;
   st->trials = t + 1;
+}
+
+// ---------------------------------------------------------------------------
+// Implicit-function adjoint (ba_backward)
+// ---------------------------------------------------------------------------
+
+// Right-hand side of H v = dL/dtheta in the forward solver's slots:
+// gc = -dL/dcams, gp = -dL/dpoints (points to the internal numbering).
+template <typename T>
+__global__ void k_adj_rhs(int C, int P, const T* __restrict__ dLc, const T* __restrict__ dLp,
+                          const int32_t* __restrict__ pnew, double* __restrict__ gc, double* __restrict__ gp) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < 9LL * C) gc[i] = dLc ? -(double)dLc[i] : 0.0;
+  if (i < 3LL * P) {
+    const long long j = i / 3, a = i % 3;
+    gp[i] = dLp ? -(double)dLp[3LL * pnew[j] + a] : 0.0;
+  }
+}
+
+// Camera-major pass over the pieces: e_k = sqrt(w) J_k v (v = (v_c, v_p)),
+// dL/dx_k = sqrt(w) e_k written in input order, and per piece
+// sum_k (sqrt(w) Jc_k)^T e_k = (H v)_c (J_l^T still to apply to the first
+// three in the recompute mode).
+template <typename T, bool MF>
+__global__ void __launch_bounds__(PIECE_THREADS)
+k_adjoint_cam(const int32_t* __restrict__ piece_cam, const int32_t* __restrict__ piece_beg,
+              const int32_t* __restrict__ piece_end, const int32_t* __restrict__ cm_pt,
+              const int32_t* __restrict__ perm_cam, const T* __restrict__ cm_px, const T* __restrict__ Jcm,
+              const T* __restrict__ cm_sw, const T* __restrict__ ptab, const T* __restrict__ camtab,
+              const T* __restrict__ xv, const T* __restrict__ vp, T delta, int O, T* __restrict__ dpix,
+              double* __restrict__ part) {
+  __shared__ T sct[CT];
+  __shared__ T sx[PV];
+  const int b = blockIdx.x;
+  const int c = piece_cam[b];
+  constexpr int XS = pass_vec_stride(MF);
+  if (threadIdx.x < CT) sct[threadIdx.x] = camtab[(long long)CT * c + threadIdx.x];
+  if (threadIdx.x >= 32 && threadIdx.x < 32 + XS) sx[threadIdx.x - 32] = xv[(long long)XS * c + threadIdx.x - 32];
+  __syncthreads();
+  T acc[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) acc[i] = T(0);
+  const int end = piece_end[b];
+  for (int s = piece_beg[b] + threadIdx.x; s < end; s += PIECE_THREADS) {
+    const int j = cm_pt[s];
+    T X0, X1, X2, pad;
+    load4(ptab + 8LL * j, X0, X1, X2, pad);
+    // sqrt(w) from the residual at the current parameters
+    T px, py, sc;
+    project_obs(sct, X0, X1, X2, px, py, sc);
+    const T r0 = sc * px - cm_px[s], r1 = sc * py - cm_px[(long long)O + s];
+    T hr, w;
+    const T sw = huber_weight(r0 * r0 + r1 * r1, delta, hr, w);
+    const T d0 = vp[3LL * j], d1 = vp[3LL * j + 1], d2 = vp[3LL * j + 2];
+    const T g0 = sct[0] * d0 + sct[1] * d1 + sct[2] * d2;
+    const T g1 = sct[3] * d0 + sct[4] * d1 + sct[5] * d2;
+    const T g2 = sct[6] * d0 + sct[7] * d1 + sct[8] * d2;
+    T e0, e1;
+    if (MF) {
+      Fac<T> o;
+      fac_obs(sct, X0, X1, X2, cm_sw ? cm_sw[s] : T(1), o);
+      jc_times_fac(o, sx, e0, e1);
+      e0 += o.A[0] * g0 + o.A[1] * g1 + o.A[2] * g2;
+      e1 += o.A[3] * g0 + o.A[4] * g1 + o.A[5] * g2;
+      jct_fac_acc(o, e0, e1, acc);
+    } else {
+      T pl[NPLANE];
+      load_planes(Jcm, O, s, pl);
+      T j0[9], j1[9];
+      jc_rows(pl, j0, j1);
+      e0 = pl[0] * g0 + pl[1] * g1 + pl[2] * g2;
+      e1 = pl[3] * g0 + pl[4] * g1 + pl[5] * g2;
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        e0 += j0[i] * sx[i];
+        e1 += j1[i] * sx[i];
+      }
+#pragma unroll
+      for (int i = 0; i < 9; ++i) acc[i] += j0[i] * e0 + j1[i] * e1;
+    }
+    const long long k = perm_cam[s];
+    dpix[2 * k] = sw * e0;
+    dpix[2 * k + 1] = sw * e1;
+  }
+  block_sum_store<9>(acc, part + (long long)PART * b);
+}
+
+// dL/dtheta0 for the cameras: a_c - (H* v)_c on frozen parameters, 0 on free
+// ones (theta* does not depend on the start of the free parameters).
+template <typename T, bool MF>
+__global__ void k_adjoint_combine(int C, const int32_t* __restrict__ cam_piece_ptr, const double* __restrict__ part,
+                                  const double* __restrict__ U, const T* __restrict__ camtab,
+                                  const double* __restrict__ lam_ptr, double dmin, double dmax,
+                                  const double* __restrict__ vc, const T* __restrict__ dLc,
+                                  const uint8_t* __restrict__ fixed, T* __restrict__ out) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= C) return;
+  double sum[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) sum[i] = 0.0;
+  for (int k = cam_piece_ptr[c]; k < cam_piece_ptr[c + 1]; ++k)
+#pragma unroll
+    for (int i = 0; i < 9; ++i) sum[i] += part[(long long)PART * k + i];
+  if (MF) {
+    const T* Jl = camtab + (long long)CT * c + CT_JL;
+    const double s0 = sum[0], s1 = sum[1], s2 = sum[2];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) sum[i] = (double)Jl[i] * s0 + (double)Jl[3 + i] * s1 + (double)Jl[6 + i] * s2;
+  }
+  const double lam = *lam_ptr;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const double hv = sum[i] + damp(U[45LL * c + sym9(i, i)], lam, dmin, dmax) * vc[9LL * c + i];
+    const bool fz = fixed && fixed[9LL * c + i];
+    out[9LL * c + i] = fz ? (T)((dLc ? (double)dLc[9LL * c + i] : 0.0) - hv) : T(0);
+  }
 }
 
 // ---------------------------------------------------------------------------

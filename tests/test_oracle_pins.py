@@ -356,3 +356,79 @@ def test_csr_build_is_stable_counting_sort(n, O):
     p2, r2 = _counting_sort(keys.tolist(), n)
     assert perm.tolist() == p2
     assert rowptr.tolist() == r2
+
+
+# --------------------------------------------------------------------------
+# implicit-function adjoint
+# --------------------------------------------------------------------------
+
+def _converge(cams, pts, ci, pi, pix, fixed, iters=40):
+    opts = orc.LMOptions(solver="cholesky", lambda0=1e-6)
+    c, p, tr = orc.lm(cams, pts, ci, pi, pix, iters, opts, fixed=fixed)
+    return c, p, tr
+
+
+def test_gauge_fixed_lm_keeps_frozen_parameters():
+    sc = scenegen.ring_scene(6, 60, seed=21, view_p=0.4, noise_px=1.0)
+    pix = orc.pixels_from_scene(sc)
+    fixed = orc.gauge_mask(sc.C)
+    c, _, tr = _converge(sc.cams_init, sc.points_init, sc.cam_idx, sc.pt_idx, pix, fixed, 15)
+    assert np.array_equal(c[fixed], sc.cams_init[fixed])
+    assert tr[-1]["cost"] < 0.05 * tr[0]["cost"]
+
+
+def test_adjoint_matches_central_differences():
+    """dL/dx from the implicit-function adjoint equals central differences of
+    L(theta*(x)) with warm-started re-solves (noise 1e-3 px, where the
+    Gauss-Newton Hessian is the exact one up to O(residual))."""
+    sc = scenegen.ring_scene(5, 40, seed=22, view_p=0.4, noise_px=1e-3)
+    pix = orc.pixels_from_scene(sc)
+    fixed = orc.gauge_mask(sc.C)
+    ci, pi = sc.cam_idx, sc.pt_idx
+    c, p, _ = _converge(sc.cams_init, sc.points_init, ci, pi, pix, fixed, 40)
+    tgt = sc.cams_gt[:, 3:6]
+
+    def L(cams):
+        return float(np.sum((cams[:, 3:6] - tgt) ** 2))
+
+    dLc = np.zeros_like(c)
+    dLc[:, 3:6] = 2.0 * (c[:, 3:6] - tgt)
+    dpix, d0c, d0p, _ = orc.adjoint_dense(c, p, ci, pi, pix, dLc, np.zeros_like(p), fixed)
+    rng = np.random.default_rng(0)
+    h = 1e-5
+    for k in rng.choice(sc.O, size=6, replace=False):
+        for a in range(2):
+            vals = []
+            for sgn in (1.0, -1.0):
+                px2 = pix.copy()
+                px2[k, a] += sgn * h
+                c2, _, _ = _converge(c, p, ci, pi, px2, fixed, 8)
+                vals.append(L(c2))
+            fd = (vals[0] - vals[1]) / (2 * h)
+            assert abs(fd - dpix[k, a]) < 1e-3 * np.max(np.abs(dpix)) + 1e-9, (k, a, fd, dpix[k, a])
+    # initial values: free parameters do not influence theta*, frozen ones do
+    assert np.all(d0c[~fixed] == 0.0) and np.all(d0p == 0.0)
+    j = 1  # camera 1's frozen t_x
+    e = np.zeros_like(c)
+    e[j, 3] = h
+    cp, _, _ = _converge(c + e, p, ci, pi, pix, fixed, 8)
+    cm, _, _ = _converge(c - e, p, ci, pi, pix, fixed, 8)
+    fd0 = (L(cp) - L(cm)) / (2 * h)
+    assert abs(fd0 - d0c[j, 3]) < 1e-3 * abs(d0c[j, 3]) + 1e-9
+
+
+def test_adjoint_schur_equals_dense():
+    sc = scenegen.ring_scene(6, 50, seed=23, view_p=0.4, noise_px=1.0, outlier_frac=0.1,
+                             huber_delta=1.0)
+    pix = orc.pixels_from_scene(sc)
+    fixed = orc.gauge_mask(sc.C)
+    rng = np.random.default_rng(1)
+    a_c = rng.normal(size=(sc.C, 9))
+    a_p = rng.normal(size=(sc.P, 3))
+    for lam in (0.0, 1e-3):
+        d1 = orc.adjoint_dense(sc.cams_init, sc.points_init, sc.cam_idx, sc.pt_idx, pix, a_c, a_p,
+                               fixed, 1.0, lam)
+        d2 = orc.adjoint_schur(sc.cams_init, sc.points_init, sc.cam_idx, sc.pt_idx, pix, a_c, a_p,
+                               fixed, 1.0, lam)
+        for x, y in zip(d1[:3], d2[:3]):
+            assert np.max(np.abs(x - y)) <= 1e-8 * max(np.max(np.abs(x)), 1e-30)
