@@ -60,6 +60,10 @@ def parse():
     ap.add_argument("--jacobian", choices=["auto", "recompute", "store"], default="auto")
     ap.add_argument("--points", type=int, default=0,
                     help="profiling only: same recipe with fewer points")
+    ap.add_argument("--workload", choices=["ba4000", "batch512"], default="ba4000",
+                    help="batch512: 512 sliding-window problems solved by one persistent launch")
+    ap.add_argument("--no-sequential", action="store_true",
+                    help="batch512: skip the 512 sequential single-problem solves")
     return ap.parse_args()
 
 
@@ -382,10 +386,178 @@ def run_ours(args):
     prob.close()
 
 
+# --------------------------------------------------------------------------
+# batch512: many small problems, one persistent launch per solve
+# --------------------------------------------------------------------------
+
+BATCH_N = 512
+BATCH_ITERS = 10
+# FP32 operations per observation and PCG iteration of the batched kernel's
+# passes A1 and B (recompute mode, as for the single-problem kernels)
+BATCH_FLOPS_PER_OBS_PCG = FLOPS_PER_OBS["pass_a1"] + FLOPS_PER_OBS["pass_b"]
+
+
+def run_batch(args):
+    import torch
+    import paper_2409_12190_gb300 as ba
+    from paper_2409_12190_gb300 import build as bbuild
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    bbuild.build()
+    scenes = scenegen.batch_scenes(BATCH_N, seed=4)
+    O = sum(s.O for s in scenes)
+    inputs = []
+    for s in scenes:
+        ci = torch.from_numpy(s.cam_idx).to(dev)
+        pi = torch.from_numpy(s.pt_idx).to(dev)
+        px = ba.project(torch.tensor(s.cams_gt, dtype=torch.float32, device=dev),
+                        torch.tensor(s.points_gt, dtype=torch.float32, device=dev), ci, pi)
+        px = px + torch.tensor(s.noise, dtype=torch.float32, device=dev)
+        inputs.append((s.cams_init, s.points_init, ci, pi, px))
+    opts = ba.Options(precision="f32", pcg_maxiter=PCG_MAXITER, pcg_tol=PCG_TOL)
+    bt = ba.Batch(inputs, opts, device=dev)
+    cache = os.path.join(ROOT, "paper_2409_12190_gb300", ".autotune.jsonl")
+    cfg, tune_ms = bt.autotune(BATCH_ITERS, cache)
+    for _ in range(args.warmup):
+        bt.reset()
+        bt.solve(BATCH_ITERS)
+    torch.cuda.synchronize()
+
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local) if rank == 0 else None
+    time.sleep(0.3 if clocks else 0)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    n0 = ba.kernel_launch_count()
+    e0.record(stream)
+    for _ in range(args.steps):
+        bt.reset()
+        bt.solve(BATCH_ITERS)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    launches = ba.kernel_launch_count() - n0
+    clk = clocks.stop() if clocks else None
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    stats = bt.stats()
+    pcg_total = sum(t["pcg_iters"] for st in stats for t in st)
+    costs, _ = bt.scalars()
+    # problem-iterations per second over all ranks
+    value = world * BATCH_N * BATCH_ITERS * args.steps / (ms / 1000.0)
+
+    # the solve alone (one persistent launch, no reset) for the roofline
+    bt.reset()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    bt.solve(BATCH_ITERS)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    solve_ms = e0.elapsed_time(e1)
+    st2 = bt.stats()
+    pcg_obs = sum(t["pcg_iters"] * s.O for st, s in zip(st2, scenes) for t in st)
+    flops = BATCH_FLOPS_PER_OBS_PCG * pcg_obs
+    sm_mhz = (clk or {}).get("sm_max_mhz") or 2070.0
+    alu_peak = fp32_peak_tflops(sm_mhz)
+    ach = flops / (solve_ms / 1000.0) / 1e12
+    roofline = {"bound": "alu", "kernel": "k_batch_lm", "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": ach / alu_peak, "flops_per_launch": flops,
+                "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz",
+                "note": "PCG passes A1+B only (113+119 FP32 flops per observation and PCG iteration); "
+                        "each problem's arrays stay in L2 across its trials", "traffic": None}
+
+    # end to end: pinned host parameters in, solve, parameters out
+    C, P = bt.C, bt.P
+    hc = torch.from_numpy(np.concatenate([s.cams_init for s in scenes]).astype(np.float32)).pin_memory()
+    hp = torch.from_numpy(np.concatenate([s.points_init for s in scenes]).astype(np.float32)).pin_memory()
+    oc = torch.empty((C, 9), dtype=torch.float32).pin_memory()
+    op = torch.empty((P, 3), dtype=torch.float32).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        bt.reset(hc, hp)
+        bt.solve(BATCH_ITERS)
+        cams_d, pts_d = bt.params(split=False)
+        oc.copy_(cams_d, non_blocking=True)
+        op.copy_(pts_d, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": world * BATCH_N * BATCH_ITERS * args.e2e_steps / e2e_s, "unit": "problem LM iters/s",
+           "h2d_bytes_per_step": (9 * C + 3 * P) * 4, "d2h_bytes_per_step": (9 * C + 3 * P) * 4,
+           "steps": args.e2e_steps}
+
+    if rank != 0:
+        return
+    seq = None
+    if world == 1 and not args.no_sequential:
+        # the same problems solved one after another by the single-problem path
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        tot = 0.0
+        worst = 0.0
+        for b, inp in enumerate(inputs):
+            pr = ba.Problem(*inp, options=opts, device=dev)
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            pr.solve(BATCH_ITERS)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            tot += ev0.elapsed_time(ev1)
+            F, _ = pr.scalars()
+            worst = max(worst, abs(costs[b] - F) / F)
+            pr.close()
+        seq = {"ms": tot, "problem_iters_per_s": BATCH_N * BATCH_ITERS / (tot / 1000.0),
+               "speedup_of_batch": tot / solve_ms, "max_rel_final_cost_diff": worst}
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        import oracle as orc
+        t0 = time.perf_counter()
+        n_done, obs_done = 0, 0
+        for s in scenes[:3]:
+            pix = orc.pixels_from_scene(s)
+            orc.lm(s.cams_init, s.points_init, s.cam_idx, s.pt_idx, pix, BATCH_ITERS,
+                   orc.LMOptions(solver="pcg", pcg_tol=PCG_TOL, pcg_maxiter=PCG_MAXITER))
+            n_done += 1
+            obs_done += s.O
+        dt = time.perf_counter() - t0
+        rate = n_done * BATCH_ITERS / dt * (obs_done / n_done) / (O / BATCH_N)
+        cpu = {"value": rate, "unit": "problem LM iters/s", "cores": 1, "kind": "oracle",
+               "sample": f"{n_done} of {BATCH_N} problems ({obs_done} observations), {BATCH_ITERS} LM trials "
+                         f"each, {dt:.1f} s; rate scaled to the mean problem size"}
+    line = {"metric": METRIC, "value": value, "unit": "problem LM iters/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "batch512", "problems": BATCH_N, "lm_iters_per_problem": BATCH_ITERS,
+                       "cameras": bt.C, "points": bt.P, "observations": O,
+                       "pcg": f"block-Jacobi, maxiter {PCG_MAXITER}, tol {PCG_TOL}",
+                       "pcg_iters_mean": pcg_total / max(1, BATCH_N * BATCH_ITERS),
+                       "step": "reset + one persistent launch solving every problem for 10 LM trials",
+                       "launch": cfg, "l2": "per-problem arrays L2-resident by design; no flush"},
+            "gpu_launches": launches, "clocks": clk, "roofline": roofline, "solve_ms": solve_ms,
+            "sequential_single_problem": seq, "cpu_baseline": cpu, "e2e": e2e}
+    print(json.dumps(line), flush=True)
+    bt.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch512":
+        run_batch(args)
     else:
         run_ours(args)
 

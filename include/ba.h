@@ -301,6 +301,92 @@ typedef struct {
  * Synchronises. */
 ba_status ba_profile_trials(ba_problem* h, int iters, ba_kernel_times* out);
 
+/* ------------------------------------------------------------------------
+ * Batched form: many independent small problems (sliding windows of
+ * uneven size) solved by one persistent launch.  Each problem runs the LM
+ * iteration of Alg. 1 with the Schur / block-Jacobi PCG solve as a
+ * ba_problem of its own would: same options, same device code, same
+ * reduction order.  The compiler forms fused multiply-adds per kernel, so
+ * the trials agree with ba_solve's to rounding (not bit for bit).  The
+ * paper solves one problem at a time; batching is an interface of this
+ * library.
+ * ------------------------------------------------------------------------ */
+
+typedef struct ba_batch ba_batch; /* opaque, owned by the library */
+
+/* Cameras per problem accepted by the batched form. */
+#define BA_BATCH_MAX_CAMS 28
+
+/* Create a batch of nprob problems.  cam_counts, pt_counts, obs_counts
+ * (host, [nprob]) give problem b's C_b in [1, BA_BATCH_MAX_CAMS], P_b >= 1
+ * and O_b >= 1; the totals must fit in int32.  cams [sum C_b][9], points
+ * [sum P_b][3], pixels [sum O_b][2] (any) and cam_idx, pt_idx [sum O_b]
+ * (dev) are the problems' arrays concatenated in problem order, with
+ * cam_idx / pt_idx LOCAL to the problem (camera in [0, C_b), point in
+ * [0, P_b)).  Every point must be observed at least once.  opt as for
+ * ba_problem_create (pcg_maxiter, pcg_tol, the loss and the damping
+ * constants apply to every problem; use_graph is ignored: a solve is
+ * always one graph launch).  Out-of-range indices give BA_ERR_INVALID_ARG,
+ * non-finite inputs BA_ERR_NONFINITE.  Synchronises. */
+ba_status ba_batch_create(ba_batch** out, int nprob, const int32_t* cam_counts,
+                          const int32_t* pt_counts, const int32_t* obs_counts,
+                          const void* cams, const void* points,
+                          const int32_t* cam_idx, const int32_t* pt_idx,
+                          const void* pixels, const ba_options* opt,
+                          void* stream);
+ba_status ba_batch_destroy(ba_batch* h);
+
+/* Run iters LM trials of every problem: ONE persistent kernel launch
+ * (replayed from a CUDA graph) in which each CTA takes whole problems
+ * from a work list.  Stream-ordered. */
+ba_status ba_batch_solve(ba_batch* h, int iters, void* stream);
+
+/* Current parameters of every problem, concatenated in the caller's order
+ * (cams_out [sum C_b][9], points_out [sum P_b][3], dev; either may be
+ * NULL).  Stream-ordered. */
+ba_status ba_batch_get_params(ba_batch* h, void* cams_out, void* points_out,
+                              void* stream);
+
+/* Restart every problem from the given parameters (any; NULL: the
+ * parameters given at creation): damping lambda0, trial count and
+ * statistics cleared, cost re-evaluated on the next solve.
+ * Stream-ordered. */
+ba_status ba_batch_reset(ba_batch* h, const void* cams, const void* points,
+                         void* stream);
+
+/* Per-problem statistics: host_out [nprob][cap] (host) receives, for each
+ * problem, its last min(trials, cap, max_stats) trials oldest first in row
+ * b; n_out [nprob] (host) their counts.  Synchronises.  Returns
+ * BA_ERR_NONFINITE (after filling the outputs) if a trial of some problem
+ * had a non-finite cost since the last call. */
+ba_status ba_batch_get_stats(ba_batch* h, ba_iter_stats* host_out, int cap,
+                             int* n_out);
+
+/* Cost at the current parameters and next damping of every problem
+ * (host [nprob] each; either may be NULL).  Synchronises. */
+ba_status ba_batch_get_scalars(ba_batch* h, double* cost, double* lambda);
+
+/* Launch configuration of ba_batch_solve (results do not depend on it):
+ * ctas_per_sm in [1, 64] CTAs per SM in the persistent grid (capped at
+ * the number of problems), variant 0 or 1 (register budget for 1 or 2
+ * resident CTAs per SM), order 0 (largest problems first) or 1 (the
+ * caller's order).  Synchronises. */
+ba_status ba_batch_set_launch(ba_batch* h, int ctas_per_sm, int variant, int order);
+ba_status ba_batch_get_launch(ba_batch* h, int* ctas_per_sm, int* variant, int* order,
+                              int* grid);
+
+/* Autotuner: time `iters` trials of the batch under every launch
+ * configuration (variant x CTAs per SM up to the occupancy limit x
+ * order), from the batch's current state each time, and keep the fastest;
+ * the batch's state is restored afterwards.  With cache_path (host
+ * string, may be NULL) the choice is looked up first in, and then appended
+ * to, a JSON-lines file keyed by the GPU name, precision, Jacobian mode and
+ * a histogram of the problem sizes.  best_ms (host, may be NULL) receives
+ * the chosen configuration's time (0 when taken from the cache).
+ * Synchronises. */
+ba_status ba_batch_autotune(ba_batch* h, int iters, const char* cache_path,
+                            double* best_ms);
+
 #ifdef __cplusplus
 }
 #endif

@@ -21,7 +21,7 @@ import torch
 from . import _lib
 from ._lib import BAError, BA_PREC_F32, BA_PREC_F64
 
-__all__ = ["Options", "Problem", "project", "csr_build", "kernel_launch_count",
+__all__ = ["Options", "Problem", "Batch", "project", "csr_build", "kernel_launch_count",
            "BAError", "library_path", "bundle_adjust"]
 
 library_path = _lib.LIB_PATH
@@ -277,6 +277,120 @@ class Problem:
         _lib.check(_L().ba_damped_solve(self._h, float(lam), int(maxiter), float(tol), _ptr(dc),
                                         _ptr(dp), ct.byref(it), ct.byref(rel), _stream(stream)))
         return dc, dp, it.value, rel.value
+
+
+def _stats_dict(s):
+    return dict(cost=s.cost, cost_trial=s.cost_trial, model=s.model, rho=s.rho, lam=s.lambda_,
+                pcg_rel_res=s.pcg_rel_res, accepted=bool(s.accepted), pcg_iters=s.pcg_iters,
+                precond_fallbacks=s.precond_fallbacks)
+
+
+class Batch:
+    """Many independent small problems solved by one persistent launch.
+
+    problems: a sequence of (cams [C_b, 9], points [P_b, 3], cam_idx [O_b],
+    pt_idx [O_b], pixels [O_b, 2]) with indices local to the problem;
+    C_b <= 28 and every point observed.  Each problem runs exactly the trials
+    a Problem of its own would run with the same options."""
+
+    MAX_CAMS = _lib.BA_BATCH_MAX_CAMS
+
+    def __init__(self, problems, options: Options | None = None, device="cuda", stream=None):
+        self.options = options or Options()
+        self.dtype = self.options.dtype
+        self.device = torch.device(device)
+        problems = list(problems)
+        if not problems:
+            raise ValueError("empty batch")
+        cams = [torch.as_tensor(p[0]) for p in problems]
+        pts = [torch.as_tensor(p[1]) for p in problems]
+        ci = [torch.as_tensor(p[2]) for p in problems]
+        pi = [torch.as_tensor(p[3]) for p in problems]
+        px = [torch.as_tensor(p[4]) for p in problems]
+        self.n = len(problems)
+        self.cam_counts = [int(c.shape[0]) for c in cams]
+        self.pt_counts = [int(p.shape[0]) for p in pts]
+        self.obs_counts = [int(c.shape[0]) for c in ci]
+        cat = lambda xs, dt: _dev(torch.cat([x.reshape(x.shape[0], -1) if x.dim() > 1 else x for x in xs]), dt,
+                                  self.device)
+        c_all = cat(cams, self.dtype)
+        p_all = cat(pts, self.dtype)
+        ci_all = cat(ci, torch.int32)
+        pi_all = cat(pi, torch.int32)
+        px_all = cat(px, self.dtype)
+        self.C, self.P, self.O = int(c_all.shape[0]), int(p_all.shape[0]), int(ci_all.shape[0])
+        counts = [(ct.c_int32 * self.n)(*v) for v in (self.cam_counts, self.pt_counts, self.obs_counts)]
+        h = ct.c_void_p()
+        o = self.options.to_c()
+        _lib.check(_L().ba_batch_create(ct.byref(h), self.n, ct.cast(counts[0], ct.c_void_p),
+                                        ct.cast(counts[1], ct.c_void_p), ct.cast(counts[2], ct.c_void_p),
+                                        _ptr(c_all), _ptr(p_all), _ptr(ci_all), _ptr(pi_all), _ptr(px_all),
+                                        ct.byref(o), _stream(stream)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _L().ba_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def solve(self, iters: int, stream=None):
+        _lib.check(_L().ba_batch_solve(self._h, int(iters), _stream(stream)))
+
+    def params(self, stream=None, split: bool = True):
+        cams = torch.empty((self.C, 9), dtype=self.dtype, device=self.device)
+        pts = torch.empty((self.P, 3), dtype=self.dtype, device=self.device)
+        _lib.check(_L().ba_batch_get_params(self._h, _ptr(cams), _ptr(pts), _stream(stream)))
+        if not split:
+            return cams, pts
+        return list(zip(torch.split(cams, self.cam_counts), torch.split(pts, self.pt_counts)))
+
+    def reset(self, cams=None, points=None, stream=None):
+        c = None if cams is None else _dev(cams, self.dtype, self.device)
+        p = None if points is None else _dev(points, self.dtype, self.device)
+        _lib.check(_L().ba_batch_reset(self._h, _ptr(c), _ptr(p), _stream(stream)))
+
+    def stats(self, cap: int = 256, raise_nonfinite: bool = True):
+        buf = (_lib.ba_iter_stats * (cap * self.n))()
+        n = (ct.c_int * self.n)()
+        st = _L().ba_batch_get_stats(self._h, buf, cap, ct.cast(n, ct.c_void_p))
+        out = [[_stats_dict(buf[b * cap + k]) for k in range(n[b])] for b in range(self.n)]
+        if st != _lib.BA_OK and (raise_nonfinite or st != 3):
+            _lib.check(st)
+        return out
+
+    def scalars(self):
+        cost = (ct.c_double * self.n)()
+        lam = (ct.c_double * self.n)()
+        _lib.check(_L().ba_batch_get_scalars(self._h, ct.cast(cost, ct.c_void_p), ct.cast(lam, ct.c_void_p)))
+        return list(cost), list(lam)
+
+    def set_launch(self, ctas_per_sm: int, variant: int = 0, order: int = 0):
+        _lib.check(_L().ba_batch_set_launch(self._h, int(ctas_per_sm), int(variant), int(order)))
+
+    def launch(self):
+        c, v, o, g = ct.c_int(), ct.c_int(), ct.c_int(), ct.c_int()
+        _lib.check(_L().ba_batch_get_launch(self._h, ct.byref(c), ct.byref(v), ct.byref(o), ct.byref(g)))
+        return dict(ctas_per_sm=c.value, variant=v.value, order=o.value, grid=g.value)
+
+    def autotune(self, iters: int, cache_path: str | None = None):
+        """Pick the fastest launch configuration (results do not depend on
+        it); returns the chosen configuration and its time (0 if cached)."""
+        ms = ct.c_double()
+        path = None if cache_path is None else str(cache_path).encode()
+        _lib.check(_L().ba_batch_autotune(self._h, int(iters), path, ct.byref(ms)))
+        return self.launch(), ms.value
 
 
 class _BundleAdjust(torch.autograd.Function):

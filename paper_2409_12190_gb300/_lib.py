@@ -92,7 +92,20 @@ SIGNATURES = {
     "ba_set_fixed": (_S, [_VP, _VP, _VP]),
     "ba_set_lambda": (_S, [_VP, _D]),
     "ba_backward": (_S, [_VP, _D, _I, _D, _VP, _VP, _VP, _VP, _VP, ct.POINTER(_I), ct.POINTER(_D), _VP]),
+    "ba_batch_create": (_S, [ct.POINTER(_VP), _I, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP,
+                             ct.POINTER(ba_options), _VP]),
+    "ba_batch_destroy": (_S, [_VP]),
+    "ba_batch_solve": (_S, [_VP, _I, _VP]),
+    "ba_batch_get_params": (_S, [_VP, _VP, _VP, _VP]),
+    "ba_batch_reset": (_S, [_VP, _VP, _VP, _VP]),
+    "ba_batch_get_stats": (_S, [_VP, ct.POINTER(ba_iter_stats), _I, _VP]),
+    "ba_batch_get_scalars": (_S, [_VP, _VP, _VP]),
+    "ba_batch_set_launch": (_S, [_VP, _I, _I, _I]),
+    "ba_batch_get_launch": (_S, [_VP, ct.POINTER(_I), ct.POINTER(_I), ct.POINTER(_I), ct.POINTER(_I)]),
+    "ba_batch_autotune": (_S, [_VP, _I, ct.c_char_p, ct.POINTER(_D)]),
 }
+
+BA_BATCH_MAX_CAMS = 28
 
 _lib = None
 

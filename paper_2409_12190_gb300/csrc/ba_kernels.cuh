@@ -476,7 +476,7 @@ __device__ __forceinline__ void to_factored(const T* __restrict__ Jl, const doub
 // ---------------------------------------------------------------------------
 
 template <typename T>
-__global__ void k_validate(int C, int P, int O, const T* __restrict__ cams, const T* __restrict__ pts,
+static __global__ void k_validate(int C, int P, int O, const T* __restrict__ cams, const T* __restrict__ pts,
                            const int32_t* __restrict__ ci, const int32_t* __restrict__ pi,
                            const T* __restrict__ px, DevState* st) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -493,7 +493,7 @@ __global__ void k_validate(int C, int P, int O, const T* __restrict__ cams, cons
 
 // Gather the observation arrays into camera-major and point-major order.
 template <typename T>
-__global__ void k_gather_obs(int O, const int32_t* __restrict__ perm_cam, const int32_t* __restrict__ perm_pt,
+static __global__ void k_gather_obs(int O, const int32_t* __restrict__ perm_cam, const int32_t* __restrict__ perm_pt,
                              const int32_t* __restrict__ ci, const int32_t* __restrict__ pi,
                              const T* __restrict__ px, int32_t* __restrict__ cm_pt, T* __restrict__ cm_px,
                              int32_t* __restrict__ pm_cam, int32_t* __restrict__ pm_pt, T* __restrict__ pm_px) {
@@ -511,7 +511,7 @@ __global__ void k_gather_obs(int O, const int32_t* __restrict__ perm_cam, const 
 }
 
 template <typename T>
-__global__ void k_project(int O, const T* __restrict__ cams, const T* __restrict__ pts,
+static __global__ void k_project(int O, const T* __restrict__ cams, const T* __restrict__ pts,
                           const int32_t* __restrict__ ci, const int32_t* __restrict__ pi, T* __restrict__ out) {
   const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= O) return;
@@ -529,7 +529,7 @@ __global__ void k_project(int O, const T* __restrict__ cams, const T* __restrict
 // ---------------------------------------------------------------------------
 
 template <typename T>
-__global__ void k_cam_prep(int C, const T* __restrict__ cams_buf, const DevState* __restrict__ st,
+static __global__ void k_cam_prep(int C, const T* __restrict__ cams_buf, const DevState* __restrict__ st,
                            int gate, T* __restrict__ camtab) {
   if (gate && !st->need_lin) return;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -540,7 +540,7 @@ __global__ void k_cam_prep(int C, const T* __restrict__ cams_buf, const DevState
 // Point table [P][8]: X in 0..2 (from the current parameters); 4..6 hold the
 // PCG vector t that pass A writes for pass B.
 template <typename T>
-__global__ void k_pt_prep(int P, const T* __restrict__ pts_buf, const DevState* __restrict__ st, int gate,
+static __global__ void k_pt_prep(int P, const T* __restrict__ pts_buf, const DevState* __restrict__ st, int gate,
                           T* __restrict__ ptab) {
   if (gate && !st->need_lin) return;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -551,7 +551,7 @@ __global__ void k_pt_prep(int P, const T* __restrict__ pts_buf, const DevState* 
 
 // key_j = smallest camera that observes point j (C if none), from the
 // stable CSR of the observations by point.
-__global__ void k_point_key(int P, int C, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ perm,
+static __global__ void k_point_key(int P, int C, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ perm,
                             const int32_t* __restrict__ cam_idx, int32_t* __restrict__ key) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= P) return;
@@ -561,7 +561,7 @@ __global__ void k_point_key(int P, int C, const int32_t* __restrict__ rowptr, co
 }
 
 // dst[i] = src[idx[i]]
-__global__ void k_gather_i32(int n, const int32_t* __restrict__ idx, const int32_t* __restrict__ src,
+static __global__ void k_gather_i32(int n, const int32_t* __restrict__ idx, const int32_t* __restrict__ src,
                              int32_t* __restrict__ dst) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) dst[i] = src[idx[i]];
@@ -569,7 +569,7 @@ __global__ void k_gather_i32(int n, const int32_t* __restrict__ idx, const int32
 
 // dst[i][:] = src[idx[i]][:] for rows of W values
 template <typename X, int W>
-__global__ void k_gather_rows(int n, const int32_t* __restrict__ idx, const X* __restrict__ src,
+static __global__ void k_gather_rows(int n, const int32_t* __restrict__ idx, const X* __restrict__ src,
                               X* __restrict__ dst) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -579,40 +579,28 @@ __global__ void k_gather_rows(int n, const int32_t* __restrict__ idx, const X* _
 }
 
 // inv[perm[s]] = s
-__global__ void k_invert_perm(int O, const int32_t* __restrict__ perm, int32_t* __restrict__ inv) {
+static __global__ void k_invert_perm(int O, const int32_t* __restrict__ perm, int32_t* __restrict__ inv) {
   const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (s < O) inv[perm[s]] = (int32_t)s;
 }
 
 // out[s] = inv_b[perm_a[s]]: the slot, in order b, of the observation at slot
 // s of order a (e.g. the point-major slot of each camera-major slot).
-__global__ void k_compose_perm(int O, const int32_t* __restrict__ perm_a, const int32_t* __restrict__ inv_b,
+static __global__ void k_compose_perm(int O, const int32_t* __restrict__ perm_a, const int32_t* __restrict__ inv_b,
                                int32_t* __restrict__ out) {
   const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (s < O) out[s] = inv_b[perm_a[s]];
 }
 
-// Camera-major pass: residuals, weights, U (45) and gc (9) per piece; in the
-// stored mode also the planes, in any mode sqrt(w) when sw_out is given.
-template <typename T, bool STORE>
-__global__ void __launch_bounds__(PIECE_THREADS)
-k_lin_cam(const int32_t* __restrict__ piece_cam, const int32_t* __restrict__ piece_beg,
-          const int32_t* __restrict__ piece_end, const int32_t* __restrict__ cm_pt,
-          const T* __restrict__ cm_px, const T* __restrict__ pts_buf, const T* __restrict__ camtab,
-          const DevState* __restrict__ st, int gate, T delta, int O, int P, T* __restrict__ Jcm,
-          T* __restrict__ sw_out, double* __restrict__ part) {
-  if (gate && !st->need_lin) return;
-  __shared__ T sct[CT];
-  const int b = blockIdx.x;
-  const int c = piece_cam[b];
-  if (threadIdx.x < CT) sct[threadIdx.x] = camtab[(long long)CT * c + threadIdx.x];
-  __syncthreads();
-  const T* pts = pts_buf + (long long)st->cur * 3 * P;
-  T acc[54];
-#pragma unroll
-  for (int i = 0; i < 54; ++i) acc[i] = T(0);
-  const int end = piece_end[b];
-  for (int s = piece_beg[b] + threadIdx.x; s < end; s += PIECE_THREADS) {
+// Camera-major slots [beg, end) of one camera, NT threads striding: residuals,
+// weights and the per-thread partial U (45) and gc (9); in the stored mode
+// also the planes, in any mode sqrt(w) when sw_out is given.
+template <typename T, bool STORE, int NT>
+__device__ __forceinline__ void lin_cam_range(int beg, int end, const int32_t* __restrict__ cm_pt,
+                                              const T* __restrict__ cm_px, const T* __restrict__ pts,
+                                              const T* __restrict__ sct, T delta, int O, T* __restrict__ Jcm,
+                                              T* __restrict__ sw_out, T (&acc)[54]) {
+  for (int s = beg + threadIdx.x; s < end; s += NT) {
     const int j = cm_pt[s];
     Fac<T> o;
     T r0, r1, hr, sw;
@@ -634,23 +622,51 @@ k_lin_cam(const int32_t* __restrict__ piece_cam, const int32_t* __restrict__ pie
       acc[45 + i] += j0[i] * r0 + j1[i] * r1;
     }
   }
+}
+
+// Camera-major pass: residuals, weights, U (45) and gc (9) per piece; in the
+// stored mode also the planes, in any mode sqrt(w) when sw_out is given.
+template <typename T, bool STORE>
+static __global__ void __launch_bounds__(PIECE_THREADS)
+k_lin_cam(const int32_t* __restrict__ piece_cam, const int32_t* __restrict__ piece_beg,
+          const int32_t* __restrict__ piece_end, const int32_t* __restrict__ cm_pt,
+          const T* __restrict__ cm_px, const T* __restrict__ pts_buf, const T* __restrict__ camtab,
+          const DevState* __restrict__ st, int gate, T delta, int O, int P, T* __restrict__ Jcm,
+          T* __restrict__ sw_out, double* __restrict__ part) {
+  if (gate && !st->need_lin) return;
+  __shared__ T sct[CT];
+  const int b = blockIdx.x;
+  const int c = piece_cam[b];
+  if (threadIdx.x < CT) sct[threadIdx.x] = camtab[(long long)CT * c + threadIdx.x];
+  __syncthreads();
+  const T* pts = pts_buf + (long long)st->cur * 3 * P;
+  T acc[54];
+#pragma unroll
+  for (int i = 0; i < 54; ++i) acc[i] = T(0);
+  lin_cam_range<T, STORE, PIECE_THREADS>(piece_beg[b], piece_end[b], cm_pt, cm_px, pts, sct, delta, O, Jcm, sw_out,
+                                         acc);
   block_sum_store<54>(acc, part + (long long)PART * b);
 }
 
+// Add pieces [p0, p1) of one camera in order: U (45), gc (9).
+__device__ __forceinline__ void cam_combine_lin_one(int p0, int p1, const double* __restrict__ part,
+                                                    double* __restrict__ U, double* __restrict__ gc) {
+  for (int i = 0; i < 54; ++i) {
+    double s = 0.0;
+    for (int p = p0; p < p1; ++p) s += part[(long long)PART * p + i];
+    if (i < 45) U[i] = s;
+    else gc[i - 45] = s;
+  }
+}
+
 // Add the pieces of each camera in order: U [C][45], gc [C][9].
-__global__ void k_cam_combine_lin(int C, const int32_t* __restrict__ cam_piece_ptr,
+static __global__ void k_cam_combine_lin(int C, const int32_t* __restrict__ cam_piece_ptr,
                                   const double* __restrict__ part, const DevState* __restrict__ st,
                                   int gate, double* __restrict__ U, double* __restrict__ gc) {
   if (gate && !st->need_lin) return;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= C) return;
-  const int p0 = cam_piece_ptr[c], p1 = cam_piece_ptr[c + 1];
-  for (int i = 0; i < 54; ++i) {
-    double s = 0.0;
-    for (int p = p0; p < p1; ++p) s += part[(long long)PART * p + i];
-    if (i < 45) U[45LL * c + i] = s;
-    else gc[9LL * c + i - 45] = s;
-  }
+  cam_combine_lin_one(cam_piece_ptr[c], cam_piece_ptr[c + 1], part, U + 45LL * c, gc + 9LL * c);
 }
 
 // Point-major pass over one chunk of points: V (6) and gp (3) per point,
@@ -684,7 +700,7 @@ __device__ __forceinline__ void lin_pt_obs(int q, int O, const int32_t* __restri
 }
 
 template <typename T>
-__global__ void __launch_bounds__(CHUNK_THREADS)
+static __global__ void __launch_bounds__(CHUNK_THREADS)
 k_lin_pt(const int32_t* __restrict__ pchunk, int O, const int32_t* __restrict__ rowptr_pt,
          const int32_t* __restrict__ pm_cam, const int32_t* __restrict__ pm_pt, const T* __restrict__ pm_px,
          const T* __restrict__ pts_buf, const T* __restrict__ camtab, const DevState* __restrict__ st, int P,
@@ -749,12 +765,9 @@ __device__ __forceinline__ double damp(double d, double lam, double dmin, double
 
 // V*_j = V_j + lam clamp(diag V_j);  Vinv = V*^{-1};  y0 = Vinv gp.
 template <typename T>
-__global__ void k_pt_damp(int P, const double* __restrict__ V, const double* __restrict__ gp,
-                          const double* __restrict__ lam_ptr, double dmin, double dmax,
-                          T* __restrict__ Vinv, T* __restrict__ y0) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= P) return;
-  const double lam = *lam_ptr;
+__device__ __forceinline__ void pt_damp_one(int j, const double* __restrict__ V, const double* __restrict__ gp,
+                                            double lam, double dmin, double dmax, T* __restrict__ Vinv,
+                                            T* __restrict__ y0) {
   const double* v = V + 6LL * j;
   const double a = v[0] + damp(v[0], lam, dmin, dmax), b = v[1], c = v[2];
   const double d = v[3] + damp(v[3], lam, dmin, dmax), e = v[4];
@@ -772,6 +785,15 @@ __global__ void k_pt_damp(int P, const double* __restrict__ V, const double* __r
   y0[3LL * j + 2] = (T)(inv[2] * g0 + inv[4] * g1 + inv[5] * g2);
 }
 
+template <typename T>
+static __global__ void k_pt_damp(int P, const double* __restrict__ V, const double* __restrict__ gp,
+                          const double* __restrict__ lam_ptr, double dmin, double dmax,
+                          T* __restrict__ Vinv, T* __restrict__ y0) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= P) return;
+  pt_damp_one<T>(j, V, gp, *lam_ptr, dmin, dmax, Vinv, y0);
+}
+
 // The 18 planes of camera-major slot s: loaded (stored mode) or recomputed.
 template <typename T, bool MF>
 __device__ __forceinline__ void cm_planes(const T* __restrict__ Jcm, long long O, int s, const T* __restrict__ sct,
@@ -786,26 +808,15 @@ __device__ __forceinline__ void cm_planes(const T* __restrict__ Jcm, long long O
   }
 }
 
-// Camera-major pass: per piece, sum_k Jc^T (Jp V*^{-1} Jp^T) Jc (45) and
-// sum_k Jc^T Jp y0 (9).
-template <typename T, bool MF>
-__global__ void __launch_bounds__(PIECE_THREADS)
-k_schur_cam(const int32_t* __restrict__ piece_cam, const int32_t* __restrict__ piece_beg,
-            const int32_t* __restrict__ piece_end, const int32_t* __restrict__ cm_pt,
-            const T* __restrict__ Jcm, const T* __restrict__ camtab, const T* __restrict__ pts_buf,
-            const T* __restrict__ cm_sw, const DevState* __restrict__ st, int P, const T* __restrict__ Vinv,
-            const T* __restrict__ y0, int O, double* __restrict__ part) {
-  __shared__ T sct[CT];
-  const int b = blockIdx.x;
-  const int c = piece_cam[b];
-  if (threadIdx.x < CT) sct[threadIdx.x] = camtab[(long long)CT * c + threadIdx.x];
-  __syncthreads();
-  const T* pts = pts_buf + (long long)st->cur * 3 * P;
-  T acc[54];
-#pragma unroll
-  for (int i = 0; i < 54; ++i) acc[i] = T(0);
-  const int end = piece_end[b];
-  for (int s = piece_beg[b] + threadIdx.x; s < end; s += PIECE_THREADS) {
+// Camera-major slots [beg, end), NT threads striding: per-thread partial
+// sum_k Jc^T (Jp V*^{-1} Jp^T) Jc (45) and sum_k Jc^T Jp y0 (9).
+template <typename T, bool MF, int NT>
+__device__ __forceinline__ void schur_cam_range(int beg, int end, const int32_t* __restrict__ cm_pt,
+                                                const T* __restrict__ Jcm, const T* __restrict__ sct,
+                                                const T* __restrict__ pts, const T* __restrict__ cm_sw,
+                                                const T* __restrict__ Vinv, const T* __restrict__ y0, int O,
+                                                T (&acc)[54]) {
+  for (int s = beg + threadIdx.x; s < end; s += NT) {
     const int j = cm_pt[s];
     T pl[NPLANE];
     cm_planes<T, MF>(Jcm, O, s, sct, pts, j, cm_sw, pl);
@@ -838,6 +849,27 @@ k_schur_cam(const int32_t* __restrict__ piece_cam, const int32_t* __restrict__ p
       acc[45 + i] += j0[i] * e0 + j1[i] * e1;
     }
   }
+}
+
+// Camera-major pass: per piece, sum_k Jc^T (Jp V*^{-1} Jp^T) Jc (45) and
+// sum_k Jc^T Jp y0 (9).
+template <typename T, bool MF>
+static __global__ void __launch_bounds__(PIECE_THREADS)
+k_schur_cam(const int32_t* __restrict__ piece_cam, const int32_t* __restrict__ piece_beg,
+            const int32_t* __restrict__ piece_end, const int32_t* __restrict__ cm_pt,
+            const T* __restrict__ Jcm, const T* __restrict__ camtab, const T* __restrict__ pts_buf,
+            const T* __restrict__ cm_sw, const DevState* __restrict__ st, int P, const T* __restrict__ Vinv,
+            const T* __restrict__ y0, int O, double* __restrict__ part) {
+  __shared__ T sct[CT];
+  const int b = blockIdx.x;
+  const int c = piece_cam[b];
+  if (threadIdx.x < CT) sct[threadIdx.x] = camtab[(long long)CT * c + threadIdx.x];
+  __syncthreads();
+  const T* pts = pts_buf + (long long)st->cur * 3 * P;
+  T acc[54];
+#pragma unroll
+  for (int i = 0; i < 54; ++i) acc[i] = T(0);
+  schur_cam_range<T, MF, PIECE_THREADS>(piece_beg[b], piece_end[b], cm_pt, Jcm, sct, pts, cm_sw, Vinv, y0, O, acc);
   block_sum_store<54>(acc, part + (long long)PART * b);
 }
 
@@ -894,6 +926,56 @@ __device__ inline bool spd_inverse9(const double* __restrict__ S, double* __rest
   return true;
 }
 
+// The same inverse with one 81-double work array W (for kernels that must
+// keep few registers): the strict
+// lower triangle holds L, the diagonal L_ii and then 1 / L_ii, the strict
+// upper triangle the strict lower triangle of L^{-1} transposed.  Loops are
+// kept rolled (few registers; the same operation order wherever it is
+// inlined).  Returns false if a pivot is not positive/finite.
+__device__ inline bool spd_inverse9_w(const double* __restrict__ S, double* __restrict__ Minv, double* __restrict__ W) {
+#pragma unroll 1
+  for (int j = 0; j < 9; ++j) {
+    double d = S[sym9(j, j)];
+#pragma unroll 1
+    for (int k = 0; k < j; ++k) d -= W[9 * j + k] * W[9 * j + k];
+    if (!(d > 0.0) || !isfinite(d)) return false;
+    const double ljj = sqrt(d);
+    W[9 * j + j] = ljj;
+    const double il = 1.0 / ljj;
+#pragma unroll 1
+    for (int i = j + 1; i < 9; ++i) {
+      double s = S[sym9(j, i)];
+#pragma unroll 1
+      for (int k = 0; k < j; ++k) s -= W[9 * i + k] * W[9 * j + k];
+      W[9 * i + j] = s * il;
+    }
+  }
+  // L^{-1} row by row: Li_ii = 1 / L_ii, Li_ij = -(sum_{k=j}^{i-1} L_ik Li_kj) Li_ii
+#pragma unroll 1
+  for (int i = 0; i < 9; ++i) {
+    const double dii = 1.0 / W[9 * i + i];
+    W[9 * i + i] = dii;
+#pragma unroll 1
+    for (int j = 0; j < i; ++j) {
+      double s = 0.0;
+#pragma unroll 1
+      for (int k = j; k < i; ++k) s += W[9 * i + k] * W[9 * j + k];  // Li_kj: diagonal (k = j) or transposed
+      W[9 * j + i] = -s * dii;
+    }
+  }
+  // M_ij = sum_{k >= max(i, j)} Li_ki Li_kj
+#pragma unroll 1
+  for (int i = 0; i < 9; ++i)
+#pragma unroll 1
+    for (int j = i; j < 9; ++j) {
+      double s = 0.0;
+#pragma unroll 1
+      for (int k = j; k < 9; ++k) s += W[9 * i + k] * W[9 * j + k];
+      Minv[sym9(i, j)] = s;
+    }
+  return true;
+}
+
 __device__ __forceinline__ void sym9_matvec(const double* __restrict__ M, const double* __restrict__ x,
                                             double* __restrict__ y) {
 #pragma unroll
@@ -928,10 +1010,90 @@ __device__ __forceinline__ void write_pass_vec(const T* __restrict__ ct, const d
 
 __host__ __device__ constexpr int pass_vec_stride(bool mf) { return mf ? PV : 9; }
 
+// One camera: S_ii = U*_i - (sum of its Schur pieces [p0, p1)), b_i = -gc_i +
+// (their right-hand-side part), M_i = S_ii^{-1} (or the inverse diagonal of
+// U* when S_ii is not SPD in this precision: *fallback = 1); PCG start x = 0,
+// r = b, z = p = M r, p also in the passes' form; returns r.z and b.b.
+template <typename T, bool MF, bool ROLLED = false>
+__device__ __forceinline__ void cam_schur_one(int p0, int p1, const double* __restrict__ part,
+                                              const double* __restrict__ Uc, const double* __restrict__ gcc,
+                                              const T* __restrict__ ct, double lam, double dmin, double dmax,
+                                              const uint8_t* __restrict__ fixed_c, double* __restrict__ Mc,
+                                              double* __restrict__ xc, double* __restrict__ rc,
+                                              double* __restrict__ zc, double* __restrict__ pc,
+                                              T* __restrict__ pTc, double& rz, double& bb, int& fallback) {
+  double S[45], bv[9];
+#pragma unroll
+  for (int i = 0; i < 45; ++i) S[i] = Uc[i];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    S[sym9(i, i)] += damp(Uc[sym9(i, i)], lam, dmin, dmax);
+    bv[i] = -gcc[i];
+  }
+  for (int q = p0; q < p1; ++q) {
+    const double* pp = part + (long long)PART * q;
+#pragma unroll
+    for (int i = 0; i < 45; ++i) S[i] -= pp[i];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) bv[i] += pp[45 + i];
+  }
+  if (fixed_c) {
+    // frozen parameters: the system restricted to the free ones,
+    // S -> m S m + (I - m), b -> m b
+    bool fz[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      fz[i] = fixed_c[i] != 0;
+      if (fz[i]) bv[i] = 0.0;
+    }
+#pragma unroll
+    for (int i = 0; i < 9; ++i)
+#pragma unroll
+      for (int j = i; j < 9; ++j)
+        if (fz[i] || fz[j]) S[sym9(i, j)] = i == j ? 1.0 : 0.0;
+  }
+  double M[45];
+  fallback = 0;
+  bool spd;
+  if (ROLLED) {
+    double W[81];
+    spd = spd_inverse9_w(S, M, W);
+  } else {
+    spd = spd_inverse9(S, M);
+  }
+  if (!spd) {
+    // not SPD in this precision: fall back to the inverse diagonal of U*
+#pragma unroll
+    for (int i = 0; i < 45; ++i) M[i] = 0.0;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      const double d = Uc[sym9(i, i)] + damp(Uc[sym9(i, i)], lam, dmin, dmax);
+      M[sym9(i, i)] = 1.0 / d;
+    }
+    fallback = 1;
+  }
+#pragma unroll
+  for (int i = 0; i < 45; ++i) Mc[i] = M[i];
+  double zz[9];
+  sym9_matvec(M, bv, zz);
+  rz = 0.0;
+  bb = 0.0;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    xc[i] = 0.0;
+    rc[i] = bv[i];
+    zc[i] = zz[i];
+    pc[i] = zz[i];
+    rz += bv[i] * zz[i];
+    bb += bv[i] * bv[i];
+  }
+  write_pass_vec<T, MF>(ct, zz, pTc);
+}
+
 // Per camera: S_ii, b_i, M_i = S_ii^{-1}; PCG start x = 0, r = b, z = M r,
 // p = z; per-block partial sums of r.z and b.b.
 template <typename T, bool MF>
-__global__ void __launch_bounds__(CAM_THREADS)
+static __global__ void __launch_bounds__(CAM_THREADS)
 k_cam_combine_schur(int C, const int32_t* __restrict__ cam_piece_ptr, const double* __restrict__ part,
                     const double* __restrict__ U, const double* __restrict__ gc, const T* __restrict__ camtab,
                     const double* __restrict__ lam_ptr, double dmin, double dmax, double* __restrict__ Minv,
@@ -947,65 +1109,12 @@ k_cam_combine_schur(int C, const int32_t* __restrict__ cam_piece_ptr, const doub
     st->fallbacks = 0;
   }
   if (c < C) {
-    const double lam = *lam_ptr;
-    const int p0 = cam_piece_ptr[c], p1 = cam_piece_ptr[c + 1];
-    double S[45], bv[9];
-    const double* Uc = U + 45LL * c;
-#pragma unroll
-    for (int i = 0; i < 45; ++i) S[i] = Uc[i];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-      S[sym9(i, i)] += damp(Uc[sym9(i, i)], lam, dmin, dmax);
-      bv[i] = -gc[9LL * c + i];
-    }
-    for (int q = p0; q < p1; ++q) {
-      const double* pp = part + (long long)PART * q;
-#pragma unroll
-      for (int i = 0; i < 45; ++i) S[i] -= pp[i];
-#pragma unroll
-      for (int i = 0; i < 9; ++i) bv[i] += pp[45 + i];
-    }
-    if (fixed) {
-      // frozen parameters: the system restricted to the free ones,
-      // S -> m S m + (I - m), b -> m b
-      bool fz[9];
-#pragma unroll
-      for (int i = 0; i < 9; ++i) {
-        fz[i] = fixed[9LL * c + i] != 0;
-        if (fz[i]) bv[i] = 0.0;
-      }
-#pragma unroll
-      for (int i = 0; i < 9; ++i)
-#pragma unroll
-        for (int j = i; j < 9; ++j)
-          if (fz[i] || fz[j]) S[sym9(i, j)] = i == j ? 1.0 : 0.0;
-    }
-    double M[45];
-    if (!spd_inverse9(S, M)) {
-      // not SPD in this precision: fall back to the inverse diagonal of U*
-#pragma unroll
-      for (int i = 0; i < 45; ++i) M[i] = 0.0;
-#pragma unroll
-      for (int i = 0; i < 9; ++i) {
-        const double d = Uc[sym9(i, i)] + damp(Uc[sym9(i, i)], lam, dmin, dmax);
-        M[sym9(i, i)] = 1.0 / d;
-      }
-      atomicAdd(&st->fallbacks, 1);
-    }
-#pragma unroll
-    for (int i = 0; i < 45; ++i) Minv[45LL * c + i] = M[i];
-    double zz[9];
-    sym9_matvec(M, bv, zz);
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-      x[9LL * c + i] = 0.0;
-      r[9LL * c + i] = bv[i];
-      z[9LL * c + i] = zz[i];
-      p[9LL * c + i] = zz[i];
-      rz += bv[i] * zz[i];
-      bb += bv[i] * bv[i];
-    }
-    write_pass_vec<T, MF>(camtab + (long long)CT * c, zz, pT + (long long)pass_vec_stride(MF) * c);
+    int fb;
+    cam_schur_one<T, MF>(cam_piece_ptr[c], cam_piece_ptr[c + 1], part, U + 45LL * c, gc + 9LL * c,
+                         camtab + (long long)CT * c, *lam_ptr, dmin, dmax, fixed ? fixed + 9LL * c : nullptr,
+                         Minv + 45LL * c, x + 9LL * c, r + 9LL * c, z + 9LL * c, p + 9LL * c,
+                         pT + (long long)pass_vec_stride(MF) * c, rz, bb, fb);
+    if (fb) atomicAdd(&st->fallbacks, 1);
   }
   double v[2] = {rz, bb};
   block_sum_all<2>(v);
@@ -1025,39 +1134,22 @@ k_cam_combine_schur(int C, const int32_t* __restrict__ cam_piece_ptr, const doub
 // camera's table and x_c sit in registers; the only per-observation loads are
 // the point index, the point (recompute mode: one 16-byte vector) or the
 // planes (stored mode), and sqrt(w).
-template <typename T, bool MF>
-__global__ void __launch_bounds__(PIECE_THREADS)
-k_pass_a1(const int32_t* __restrict__ piece_cam, const int32_t* __restrict__ piece_beg,
-          const int32_t* __restrict__ piece_end, const int32_t* __restrict__ cm_pt,
-          const T* __restrict__ Jcm, const T* __restrict__ cm_sw, const T* __restrict__ ptab,
-          const T* __restrict__ camtab, const T* __restrict__ xc, const DevState* __restrict__ st,
-          int check_done, int O, T* __restrict__ zbuf) {
-  if (check_done && st->pcg_done) return;
-  __shared__ T sct[16];
-  __shared__ T sx[PV];
-  const int b = blockIdx.x;
-  const int c = piece_cam[b];
-  constexpr int XS = pass_vec_stride(MF);
-  if (threadIdx.x < 16) sct[threadIdx.x] = camtab[(long long)CT * c + threadIdx.x];
-  if (threadIdx.x >= 32 && threadIdx.x < 32 + XS) sx[threadIdx.x - 32] = xc[(long long)XS * c + threadIdx.x - 32];
-  __syncthreads();
-  T ctl[15], xl[9];
-#pragma unroll
-  for (int i = 0; i < 15; ++i) ctl[i] = sct[i];
-#pragma unroll
-  for (int i = 0; i < 9; ++i) xl[i] = sx[i];
-  const int end = piece_end[b];
+template <typename T, bool MF, int NT>
+__device__ __forceinline__ void pass_a1_range(int beg, int end, const int32_t* __restrict__ cm_pt,
+                                              const T* __restrict__ Jcm, const T* __restrict__ cm_sw,
+                                              const T* __restrict__ ptab, const T (&ctl)[15], const T (&xl)[9],
+                                              int O, T* __restrict__ zbuf) {
   if (MF) {
     // one observation of lookahead: the next point is loaded while this one
     // is computed
-    int s = piece_beg[b] + threadIdx.x;
+    int s = beg + threadIdx.x;
     T X0 = 0, X1 = 0, X2 = 0, sw = 1, pad;
     if (s < end) {
       load4(ptab + 8LL * cm_pt[s], X0, X1, X2, pad);
       if (cm_sw) sw = cm_sw[s];
     }
     while (s < end) {
-      const int sn = s + PIECE_THREADS;
+      const int sn = s + NT;
       T Y0 = 0, Y1 = 0, Y2 = 0, swn = 1;
       if (sn < end) {
         load4(ptab + 8LL * cm_pt[sn], Y0, Y1, Y2, pad);
@@ -1081,7 +1173,7 @@ k_pass_a1(const int32_t* __restrict__ piece_cam, const int32_t* __restrict__ pie
       sw = swn;
     }
   } else {
-    for (int s = piece_beg[b] + threadIdx.x; s < end; s += PIECE_THREADS) {
+    for (int s = beg + threadIdx.x; s < end; s += NT) {
       T pl[NPLANE];
       load_planes(Jcm, O, s, pl);
       T j0[9], j1[9];
@@ -1101,6 +1193,30 @@ k_pass_a1(const int32_t* __restrict__ piece_cam, const int32_t* __restrict__ pie
       store4(zbuf + 4LL * s, z0, z1, z2, T(0));
     }
   }
+}
+
+template <typename T, bool MF>
+static __global__ void __launch_bounds__(PIECE_THREADS)
+k_pass_a1(const int32_t* __restrict__ piece_cam, const int32_t* __restrict__ piece_beg,
+          const int32_t* __restrict__ piece_end, const int32_t* __restrict__ cm_pt,
+          const T* __restrict__ Jcm, const T* __restrict__ cm_sw, const T* __restrict__ ptab,
+          const T* __restrict__ camtab, const T* __restrict__ xc, const DevState* __restrict__ st,
+          int check_done, int O, T* __restrict__ zbuf) {
+  if (check_done && st->pcg_done) return;
+  __shared__ T sct[16];
+  __shared__ T sx[PV];
+  const int b = blockIdx.x;
+  const int c = piece_cam[b];
+  constexpr int XS = pass_vec_stride(MF);
+  if (threadIdx.x < 16) sct[threadIdx.x] = camtab[(long long)CT * c + threadIdx.x];
+  if (threadIdx.x >= 32 && threadIdx.x < 32 + XS) sx[threadIdx.x - 32] = xc[(long long)XS * c + threadIdx.x - 32];
+  __syncthreads();
+  T ctl[15], xl[9];
+#pragma unroll
+  for (int i = 0; i < 15; ++i) ctl[i] = sct[i];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) xl[i] = sx[i];
+  pass_a1_range<T, MF, PIECE_THREADS>(piece_beg[b], piece_end[b], cm_pt, Jcm, cm_sw, ptab, ctl, xl, O, zbuf);
 }
 
 template <typename T, int MODE>
@@ -1135,7 +1251,7 @@ __device__ __forceinline__ double pass_a_point(int j, int P, T z0, T z1, T z2, c
 // (back-substitution, z from dc) forms dp_j = -(y0_j + t_j), writes the
 // trial point theta_p + dp_j and reduces gp_j . dp_j per chunk.
 template <typename T, int MODE>
-__global__ void __launch_bounds__(CHUNK_THREADS)
+static __global__ void __launch_bounds__(CHUNK_THREADS)
 k_pass_a2(const int32_t* __restrict__ pchunk, int P, const int32_t* __restrict__ rowptr_pt,
           const int32_t* __restrict__ pm2cm, const T* __restrict__ zbuf, const T* __restrict__ Vinv,
           const DevState* __restrict__ st, int check_done, T* __restrict__ ptab, T* __restrict__ dp,
@@ -1197,30 +1313,15 @@ k_pass_a2(const int32_t* __restrict__ pchunk, int P, const int32_t* __restrict__
   }
 }
 
-// Pass B (camera-major): per piece, sum_k Jc_k^T (Jp_k t_p(k)) (9 values; in
-// the recompute mode the first three are still to be multiplied by J_l^T).
-template <typename T, bool MF>
-__global__ void __launch_bounds__(PIECE_THREADS)
-k_pass_b(const int32_t* __restrict__ piece_cam, const int32_t* __restrict__ piece_beg,
-         const int32_t* __restrict__ piece_end, const int32_t* __restrict__ cm_pt,
-         const T* __restrict__ Jcm, const T* __restrict__ cm_sw, const T* __restrict__ ptab,
-         const T* __restrict__ camtab, const DevState* __restrict__ st, int check_done, int O,
-         double* __restrict__ part) {
-  if (check_done && st->pcg_done) return;
-  __shared__ T sct[16];
-  const int b = blockIdx.x;
-  const int c = piece_cam[b];
-  if (threadIdx.x < 16) sct[threadIdx.x] = camtab[(long long)CT * c + threadIdx.x];
-  __syncthreads();
-  T ctl[15];
-#pragma unroll
-  for (int i = 0; i < 15; ++i) ctl[i] = sct[i];
-  T acc[9];
-#pragma unroll
-  for (int i = 0; i < 9; ++i) acc[i] = T(0);
-  const int end = piece_end[b];
+// Pass B over camera-major slots [beg, end), NT threads striding: per-thread
+// partial sum_k Jc_k^T (Jp_k t_p(k)) (9 values; in the recompute mode the
+// first three are still to be multiplied by J_l^T).
+template <typename T, bool MF, int NT>
+__device__ __forceinline__ void pass_b_range(int beg, int end, const int32_t* __restrict__ cm_pt,
+                                             const T* __restrict__ Jcm, const T* __restrict__ cm_sw,
+                                             const T* __restrict__ ptab, const T (&ctl)[15], int O, T (&acc)[9]) {
   if (MF) {
-    int s = piece_beg[b] + threadIdx.x;
+    int s = beg + threadIdx.x;
     T X0 = 0, X1 = 0, X2 = 0, t0 = 0, t1 = 0, t2 = 0, sw = 1, pad;
     if (s < end) {
       const int j = cm_pt[s];
@@ -1229,7 +1330,7 @@ k_pass_b(const int32_t* __restrict__ piece_cam, const int32_t* __restrict__ piec
       if (cm_sw) sw = cm_sw[s];
     }
     while (s < end) {
-      const int sn = s + PIECE_THREADS;
+      const int sn = s + NT;
       T Y0 = 0, Y1 = 0, Y2 = 0, u0 = 0, u1 = 0, u2 = 0, swn = 1;
       if (sn < end) {
         const int jn = cm_pt[sn];
@@ -1255,7 +1356,7 @@ k_pass_b(const int32_t* __restrict__ piece_cam, const int32_t* __restrict__ piec
       sw = swn;
     }
   } else {
-    for (int s = piece_beg[b] + threadIdx.x; s < end; s += PIECE_THREADS) {
+    for (int s = beg + threadIdx.x; s < end; s += NT) {
       const int j = cm_pt[s];
       T t0, t1, t2, tpad;
       load4(ptab + 8LL * j + 4, t0, t1, t2, tpad);
@@ -1272,6 +1373,29 @@ k_pass_b(const int32_t* __restrict__ piece_cam, const int32_t* __restrict__ piec
       for (int i = 0; i < 9; ++i) acc[i] += j0[i] * h0 + j1[i] * h1;
     }
   }
+}
+
+// Pass B (camera-major): per piece, sum_k Jc_k^T (Jp_k t_p(k)).
+template <typename T, bool MF>
+static __global__ void __launch_bounds__(PIECE_THREADS)
+k_pass_b(const int32_t* __restrict__ piece_cam, const int32_t* __restrict__ piece_beg,
+         const int32_t* __restrict__ piece_end, const int32_t* __restrict__ cm_pt,
+         const T* __restrict__ Jcm, const T* __restrict__ cm_sw, const T* __restrict__ ptab,
+         const T* __restrict__ camtab, const DevState* __restrict__ st, int check_done, int O,
+         double* __restrict__ part) {
+  if (check_done && st->pcg_done) return;
+  __shared__ T sct[16];
+  const int b = blockIdx.x;
+  const int c = piece_cam[b];
+  if (threadIdx.x < 16) sct[threadIdx.x] = camtab[(long long)CT * c + threadIdx.x];
+  __syncthreads();
+  T ctl[15];
+#pragma unroll
+  for (int i = 0; i < 15; ++i) ctl[i] = sct[i];
+  T acc[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) acc[i] = T(0);
+  pass_b_range<T, MF, PIECE_THREADS>(piece_beg[b], piece_end[b], cm_pt, Jcm, cm_sw, ptab, ctl, O, acc);
   block_sum_store<9, false>(acc, part + (long long)PART * b);
 }
 
@@ -1285,7 +1409,7 @@ __device__ __forceinline__ int sym9_rt(int i, int j) { return i <= j ? sym9(i, j
 // q = U* p - sum of pass-B pieces (J_l^T applied to their first three in the
 // recompute mode); per-block partial p.q.
 template <typename T, bool MF>
-__global__ void __launch_bounds__(VT)
+static __global__ void __launch_bounds__(VT)
 k_pcg_q(int C, const int32_t* __restrict__ cam_piece_ptr, const double* __restrict__ part,
         const double* __restrict__ U, const T* __restrict__ camtab, const double* __restrict__ lam_ptr, double dmin,
         double dmax, const double* __restrict__ p, double* __restrict__ q, double* __restrict__ dot_pq,
@@ -1326,7 +1450,7 @@ k_pcg_q(int C, const int32_t* __restrict__ cam_piece_ptr, const double* __restri
 
 // alpha = (r.z)_old / p.q; x += alpha p; r -= alpha q; z = M r;
 // partial r.z into dot_rz[k & 1], partial r.r.
-__global__ void __launch_bounds__(VT)
+static __global__ void __launch_bounds__(VT)
 k_pcg_update(int C, int nb, int k, const double* __restrict__ dot_pq, double* __restrict__ dot_rz,
              double* __restrict__ dot_rr, const double* __restrict__ p, const double* __restrict__ q,
              double* __restrict__ x, double* __restrict__ r, double* __restrict__ z,
@@ -1377,7 +1501,7 @@ k_pcg_update(int C, int nb, int k, const double* __restrict__ dot_pq, double* __
 // Convergence test |r| <= tol |b|; beta = (r.z)_new / (r.z)_old; p = z + beta p,
 // and p in the passes' form.
 template <typename T, bool MF>
-__global__ void __launch_bounds__(VT)
+static __global__ void __launch_bounds__(VT)
 k_pcg_direction(int C, int nb, int k, double tol, const double* __restrict__ dot_rz,
                 const double* __restrict__ dot_rr, const double* __restrict__ dot_bb,
                 const double* __restrict__ z, double* __restrict__ p, const T* __restrict__ camtab,
@@ -1423,10 +1547,29 @@ k_pcg_direction(int C, int nb, int k, double tol, const double* __restrict__ dot
 // a5 / a6: trial parameters, trial cost, model reduction, LM control
 // ---------------------------------------------------------------------------
 
+// One trial camera dst = src + dc (dc rounded to T), dc in the pass form;
+// returns gc . dc.
+template <typename T, bool MF>
+__device__ __forceinline__ double cam_trial_one(const double* __restrict__ xc, const double* __restrict__ gcc,
+                                                const T* __restrict__ src, T* __restrict__ dst,
+                                                const T* __restrict__ ct, T* __restrict__ xTc) {
+  double gd = 0.0;
+  double dr[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const T d = (T)xc[i];
+    dr[i] = (double)d;
+    dst[i] = src[i] + d;
+    gd += gcc[i] * (double)d;
+  }
+  write_pass_vec<T, MF>(ct, dr, xTc);
+  return gd;
+}
+
 // Trial cameras theta_c + dc (dc rounded to T), dc in the pass form, partial
 // gc . dc.
 template <typename T, bool MF>
-__global__ void __launch_bounds__(CAM_THREADS)
+static __global__ void __launch_bounds__(CAM_THREADS)
 k_cam_trial(int C, const double* __restrict__ x, const double* __restrict__ gc, T* __restrict__ cams_buf,
             const T* __restrict__ camtab, const DevState* __restrict__ st, T* __restrict__ xT,
             double* __restrict__ dot_gc) {
@@ -1434,52 +1577,27 @@ k_cam_trial(int C, const double* __restrict__ x, const double* __restrict__ gc, 
   double gd = 0.0;
   if (c < C) {
     const int cur = st->cur;
-    const T* src = cams_buf + (long long)cur * 9 * C + 9LL * c;
-    T* dst = cams_buf + (long long)(1 - cur) * 9 * C + 9LL * c;
-    double dr[9];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-      const T d = (T)x[9LL * c + i];
-      dr[i] = (double)d;
-      dst[i] = src[i] + d;
-      gd += gc[9LL * c + i] * (double)d;
-    }
-    write_pass_vec<T, MF>(camtab + (long long)CT * c, dr, xT + (long long)pass_vec_stride(MF) * c);
+    gd = cam_trial_one<T, MF>(x + 9LL * c, gc + 9LL * c, cams_buf + (long long)cur * 9 * C + 9LL * c,
+                              cams_buf + (long long)(1 - cur) * 9 * C + 9LL * c, camtab + (long long)CT * c,
+                              xT + (long long)pass_vec_stride(MF) * c);
   }
   double v[1] = {gd};
   block_sum_all<1>(v);
   if (threadIdx.x == 0) dot_gc[blockIdx.x] = v[0];
 }
 
-// Camera-major pass over the pieces: cost 1/2 sum rho at the parameters in
-// buffer (which == 0: current, 1: trial), and with MODEL the quadratic term
-// sum_k |Jc_k dc + Jp_k dp|^2 of the model reduction (weights folded in).
-template <typename T, bool MODEL, bool MF>
-__global__ void __launch_bounds__(PIECE_THREADS)
-k_cost_cam(const int32_t* __restrict__ piece_cam, const int32_t* __restrict__ piece_beg,
-           const int32_t* __restrict__ piece_end, const int32_t* __restrict__ cm_pt,
-           const T* __restrict__ cm_px, const T* __restrict__ cams_buf, const T* __restrict__ pts_buf,
-           const DevState* __restrict__ st, int which, T delta, int C, int P, int O,
-           const T* __restrict__ Jcm, const T* __restrict__ cm_sw, const T* __restrict__ camtab,
-           const T* __restrict__ xT, const T* __restrict__ dp, double* __restrict__ part) {
-  __shared__ T sct[CT];   // camera of the evaluated parameters
-  __shared__ T sold[CT];  // camera of the linearisation (model term)
-  __shared__ T sdc[PV];
-  const int b = blockIdx.x;
-  const int c = piece_cam[b];
-  const int cur = st->cur;
-  const int buf = which ? 1 - cur : cur;
-  if (threadIdx.x == 0) camera_table(cams_buf + (long long)buf * 9 * C + 9LL * c, sct);
-  if (MODEL && threadIdx.x >= 32 && threadIdx.x < 32 + CT)
-    sold[threadIdx.x - 32] = camtab[(long long)CT * c + threadIdx.x - 32];
-  if (MODEL && threadIdx.x >= 64 + CT && threadIdx.x < 64 + CT + pass_vec_stride(MF))
-    sdc[threadIdx.x - 64 - CT] = xT[(long long)pass_vec_stride(MF) * c + threadIdx.x - 64 - CT];
-  __syncthreads();
-  const T* pts = pts_buf + (long long)buf * 3 * P;
-  const T* pts_old = pts_buf + (long long)cur * 3 * P;
-  double cost = 0.0, quad = 0.0;
-  const int end = piece_end[b];
-  for (int s = piece_beg[b] + threadIdx.x; s < end; s += PIECE_THREADS) {
+// Cost terms over camera-major slots [beg, end), NT threads striding:
+// 1/2 rho at the camera table sct and points pts, and with MODEL the
+// quadratic model term |Jc dc + Jp dp|^2 at the linearisation (camera table
+// sold, points pts_old, dc in the pass form sdc).
+template <typename T, bool MODEL, bool MF, int NT>
+__device__ __forceinline__ void cost_cam_range(int beg, int end, const int32_t* __restrict__ cm_pt,
+                                               const T* __restrict__ cm_px, const T* __restrict__ pts,
+                                               const T* __restrict__ pts_old, const T* __restrict__ sct,
+                                               const T* __restrict__ sold, const T* __restrict__ sdc, T delta, int O,
+                                               const T* __restrict__ Jcm, const T* __restrict__ cm_sw,
+                                               const T* __restrict__ dp, double& cost, double& quad) {
+  for (int s = beg + threadIdx.x; s < end; s += NT) {
     const int j = cm_pt[s];
     T px, py, sc;
     project_obs(sct, pts[3LL * j], pts[3LL * j + 1], pts[3LL * j + 2], px, py, sc);
@@ -1515,12 +1633,43 @@ k_cost_cam(const int32_t* __restrict__ piece_cam, const int32_t* __restrict__ pi
       quad += (double)e0 * (double)e0 + (double)e1 * (double)e1;
     }
   }
+}
+
+// Camera-major pass over the pieces: cost 1/2 sum rho at the parameters in
+// buffer (which == 0: current, 1: trial), and with MODEL the quadratic term
+// sum_k |Jc_k dc + Jp_k dp|^2 of the model reduction (weights folded in).
+template <typename T, bool MODEL, bool MF>
+static __global__ void __launch_bounds__(PIECE_THREADS)
+k_cost_cam(const int32_t* __restrict__ piece_cam, const int32_t* __restrict__ piece_beg,
+           const int32_t* __restrict__ piece_end, const int32_t* __restrict__ cm_pt,
+           const T* __restrict__ cm_px, const T* __restrict__ cams_buf, const T* __restrict__ pts_buf,
+           const DevState* __restrict__ st, int which, T delta, int C, int P, int O,
+           const T* __restrict__ Jcm, const T* __restrict__ cm_sw, const T* __restrict__ camtab,
+           const T* __restrict__ xT, const T* __restrict__ dp, double* __restrict__ part) {
+  __shared__ T sct[CT];   // camera of the evaluated parameters
+  __shared__ T sold[CT];  // camera of the linearisation (model term)
+  __shared__ T sdc[PV];
+  const int b = blockIdx.x;
+  const int c = piece_cam[b];
+  const int cur = st->cur;
+  const int buf = which ? 1 - cur : cur;
+  if (threadIdx.x == 0) camera_table(cams_buf + (long long)buf * 9 * C + 9LL * c, sct);
+  if (MODEL && threadIdx.x >= 32 && threadIdx.x < 32 + CT)
+    sold[threadIdx.x - 32] = camtab[(long long)CT * c + threadIdx.x - 32];
+  if (MODEL && threadIdx.x >= 64 + CT && threadIdx.x < 64 + CT + pass_vec_stride(MF))
+    sdc[threadIdx.x - 64 - CT] = xT[(long long)pass_vec_stride(MF) * c + threadIdx.x - 64 - CT];
+  __syncthreads();
+  const T* pts = pts_buf + (long long)buf * 3 * P;
+  const T* pts_old = pts_buf + (long long)cur * 3 * P;
+  double cost = 0.0, quad = 0.0;
+  cost_cam_range<T, MODEL, MF, PIECE_THREADS>(piece_beg[b], piece_end[b], cm_pt, cm_px, pts, pts_old, sct, sold,
+                                              sdc, delta, O, Jcm, cm_sw, dp, cost, quad);
   double v[2] = {cost, quad};
   block_sum_store<2>(v, part + (long long)PART * b);
 }
 
 // Sum the cost pieces into st->F (initial cost / after set_params).
-__global__ void k_cost_finalize(int npieces, const double* __restrict__ part, DevState* st) {
+static __global__ void k_cost_finalize(int npieces, const double* __restrict__ part, DevState* st) {
   const double F = block_sum_array(part, npieces, PART);
   if (threadIdx.x == 0) {
     st->F = F;
@@ -1528,8 +1677,39 @@ __global__ void k_cost_finalize(int npieces, const double* __restrict__ part, De
   }
 }
 
+// One LM decision: gain ratio rho = (F - Ft) / model with the model
+// reduction -lin - quad / 2, accept iff Ft is finite, model > 0 and Ft < F,
+// damping update; fills the stats record and returns the next damping.
+__device__ __forceinline__ bool lm_decide(double F, double Ft, double quad, double lin, double lam, double pcg_rel,
+                                          int pcg_iters, int fallbacks, double up, double down, double rho_good,
+                                          double rho_bad, double lam_min, double lam_max, ba_iter_stats& sr,
+                                          double& nl) {
+  const double model = -lin - 0.5 * quad;
+  const double rho = model != 0.0 ? (F - Ft) / model : nan("");
+  const bool finite = isfinite(Ft);
+  const bool accept = finite && model > 0.0 && Ft < F;
+  sr.cost = F;
+  sr.cost_trial = Ft;
+  sr.model = model;
+  sr.rho = rho;
+  sr.lambda = lam;
+  sr.pcg_rel_res = pcg_rel;
+  sr.accepted = accept ? 1 : 0;
+  sr.pcg_iters = pcg_iters;
+  sr.precond_fallbacks = fallbacks;
+  sr.reserved = 0;
+  nl = lam;
+  if (accept) {
+    if (rho > rho_good) nl = fmax(lam / up, lam_min);
+    else if (rho < rho_bad) nl = fmin(lam / down, lam_max);
+  } else {
+    nl = fmin(lam / down, lam_max);
+  }
+  return accept;
+}
+
 // Gain ratio, accept / reject and the damping update (one block).
-__global__ void k_lm_control(int npieces, const double* __restrict__ part, int ncb,
+static __global__ void k_lm_control(int npieces, const double* __restrict__ part, int ncb,
                              const double* __restrict__ dot_gc, int npb, const double* __restrict__ dot_gp,
                              double up, double down, double rho_good, double rho_bad, double lam_min,
                              double lam_max, DevState* st, ba_iter_stats* __restrict__ stats, int cap) {
@@ -1538,34 +1718,17 @@ __global__ void k_lm_control(int npieces, const double* __restrict__ part, int n
   const double lin = block_sum_array(dot_gc, ncb, 1) + block_sum_array(dot_gp, npb, 1);
   if (threadIdx.x != 0) return;
   const double F = st->F;
-  const double lam = st->lam;
-  const double model = -lin - 0.5 * quad;
-  const double rho = model != 0.0 ? (F - Ft) / model : nan("");
-  const bool finite = isfinite(Ft);
-  const bool accept = finite && model > 0.0 && Ft < F;
   const long long t = st->trials;
-  ba_iter_stats& sr = stats[t % cap];
-  sr.cost = F;
-  sr.cost_trial = Ft;
-  sr.model = model;
-  sr.rho = rho;
-  sr.lambda = lam;
-  sr.pcg_rel_res = st->pcg_rel;
-  sr.accepted = accept ? 1 : 0;
-  sr.pcg_iters = st->pcg_iters;
-  sr.precond_fallbacks = st->fallbacks;
-  sr.reserved = 0;
-  if (!finite) st->nonfinite += 1;
-  double nl = lam;
+  double nl;
+  const bool accept = lm_decide(F, Ft, quad, lin, st->lam, st->pcg_rel, st->pcg_iters, st->fallbacks, up, down,
+                                rho_good, rho_bad, lam_min, lam_max, stats[t % cap], nl);
+  if (!isfinite(Ft)) st->nonfinite += 1;
   if (accept) {
     st->cur = 1 - st->cur;
     st->F = Ft;
     st->need_lin = 1;
-    if (rho > rho_good) nl = fmax(lam / up, lam_min);
-    else if (rho < rho_bad) nl = fmin(lam / down, lam_max);
   } else {
     st->need_lin = 0;
-    nl = fmin(lam / down, lam_max);
   }
   st->lam = nl;
   st->trials = t + 1;
@@ -1578,7 +1741,7 @@ __global__ void k_lm_control(int npieces, const double* __restrict__ part, int n
 // Right-hand side of H v = dL/dtheta in the forward solver's slots:
 // gc = -dL/dcams, gp = -dL/dpoints (points to the internal numbering).
 template <typename T>
-__global__ void k_adj_rhs(int C, int P, const T* __restrict__ dLc, const T* __restrict__ dLp,
+static __global__ void k_adj_rhs(int C, int P, const T* __restrict__ dLc, const T* __restrict__ dLp,
                           const int32_t* __restrict__ pnew, double* __restrict__ gc, double* __restrict__ gp) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < 9LL * C) gc[i] = dLc ? -(double)dLc[i] : 0.0;
@@ -1593,7 +1756,7 @@ __global__ void k_adj_rhs(int C, int P, const T* __restrict__ dLc, const T* __re
 // sum_k (sqrt(w) Jc_k)^T e_k = (H v)_c (J_l^T still to apply to the first
 // three in the recompute mode).
 template <typename T, bool MF>
-__global__ void __launch_bounds__(PIECE_THREADS)
+static __global__ void __launch_bounds__(PIECE_THREADS)
 k_adjoint_cam(const int32_t* __restrict__ piece_cam, const int32_t* __restrict__ piece_beg,
               const int32_t* __restrict__ piece_end, const int32_t* __restrict__ cm_pt,
               const int32_t* __restrict__ perm_cam, const T* __restrict__ cm_px, const T* __restrict__ Jcm,
@@ -1659,7 +1822,7 @@ k_adjoint_cam(const int32_t* __restrict__ piece_cam, const int32_t* __restrict__
 // dL/dtheta0 for the cameras: a_c - (H* v)_c on frozen parameters, 0 on free
 // ones (theta* does not depend on the start of the free parameters).
 template <typename T, bool MF>
-__global__ void k_adjoint_combine(int C, const int32_t* __restrict__ cam_piece_ptr, const double* __restrict__ part,
+static __global__ void k_adjoint_combine(int C, const int32_t* __restrict__ cam_piece_ptr, const double* __restrict__ part,
                                   const double* __restrict__ U, const T* __restrict__ camtab,
                                   const double* __restrict__ lam_ptr, double dmin, double dmax,
                                   const double* __restrict__ vc, const T* __restrict__ dLc,
@@ -1693,7 +1856,7 @@ __global__ void k_adjoint_combine(int C, const int32_t* __restrict__ cam_piece_p
 
 // Camera vector (double [C][9]) to the pass form.
 template <typename T, bool MF>
-__global__ void k_pass_vec(int C, const double* __restrict__ x, const T* __restrict__ camtab, T* __restrict__ out) {
+static __global__ void k_pass_vec(int C, const double* __restrict__ x, const T* __restrict__ camtab, T* __restrict__ out) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= C) return;
   write_pass_vec<T, MF>(camtab + (long long)CT * c, x + 9LL * c, out + (long long)pass_vec_stride(MF) * c);
@@ -1701,7 +1864,7 @@ __global__ void k_pass_vec(int C, const double* __restrict__ x, const T* __restr
 
 // Unpack U [C][45] to [C][9][9] (or V [P][6] to [P][3][3]); block b of the
 // output is packed block row[b] (row = NULL: b).
-__global__ void k_unpack_sym(long long n, int dim, const double* __restrict__ packed, const int32_t* __restrict__ row,
+static __global__ void k_unpack_sym(long long n, int dim, const double* __restrict__ packed, const int32_t* __restrict__ row,
                              double* __restrict__ full) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n * dim * dim) return;
@@ -1723,7 +1886,7 @@ __global__ void k_unpack_sym(long long n, int dim, const double* __restrict__ pa
 // from the camera-major planes (stored mode) or recomputed exactly as the
 // passes recompute them.
 template <typename T, bool MF>
-__global__ void k_export_lin(int O, int P, const int32_t* __restrict__ perm_cam, const int32_t* __restrict__ ci,
+static __global__ void k_export_lin(int O, int P, const int32_t* __restrict__ perm_cam, const int32_t* __restrict__ ci,
                              const int32_t* __restrict__ cm_pt, const T* __restrict__ cm_px,
                              const T* __restrict__ Jcm, const T* __restrict__ cm_sw, const T* __restrict__ camtab,
                              const T* __restrict__ pts_buf, const DevState* __restrict__ st, T delta,

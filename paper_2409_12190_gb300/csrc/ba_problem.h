@@ -1,0 +1,90 @@
+// The problem object behind the C ABI (shared by the library's translation
+// units; not part of the public interface).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "ba.h"
+#include "ba_kernels.cuh"
+
+struct ba_problem {
+  int C = 0, P = 0, O = 0, prec = 0;
+  bool mf = false;  // recompute the Jacobian factors in every pass
+  size_t tsize = 8;
+  ba_options opt{};
+  cudaStream_t s = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  std::vector<void*> allocs;
+  // structure (symbolic phase)
+  // Points are renumbered internally (sorted by the first camera that sees
+  // them) so that the points of one camera are close together in memory.
+  // pt_idx, perm_*, rowptr_pt and every per-point array use the internal
+  // numbering; pnew[new] = caller's index, pnewpos[caller's] = new.
+  int32_t *cam_idx = nullptr, *pt_idx = nullptr;
+  int32_t *perm_cam = nullptr, *rowptr_cam = nullptr, *perm_pt = nullptr, *rowptr_pt = nullptr;
+  int32_t *pnew = nullptr, *pnewpos = nullptr;
+  // the symbolic phase in the caller's numbering (ba_get_csr)
+  int32_t *xperm_cam = nullptr, *xperm_pt = nullptr, *xrowptr_pt = nullptr;
+  void* pts_tmp = nullptr;  // [P][3] staging for reordering parameters
+  uint8_t* fixed = nullptr;  // [C][9] frozen camera parameters, or NULL
+  uint8_t* fixed_buf = nullptr;
+  int32_t *cm_pt = nullptr, *pm_cam = nullptr, *pm_pt = nullptr;
+  int32_t* pm2cm = nullptr;  // camera-major slot of each point-major slot
+  int nchunks = 0;
+  int32_t* pchunk = nullptr;  // [nchunks + 1] first point of each point chunk
+  void *cm_px = nullptr, *pm_px = nullptr, *px_in = nullptr;
+  int npieces = 0;
+  int32_t *piece_cam = nullptr, *piece_beg = nullptr, *piece_end = nullptr, *cam_piece_ptr = nullptr;
+  // parameters, double-buffered (current / trial)
+  void *cams = nullptr, *pts = nullptr;
+  // linearisation
+  void *camtab = nullptr, *Jcm = nullptr;
+  void *ptab = nullptr;  // [P][8]: X, 0, t, 0
+  void *zbuf = nullptr;  // [O][4]: pass A1 output, camera-major
+  void *cm_sw = nullptr, *pm_sw = nullptr;  // sqrt(w) per observation (recompute mode, robust loss)
+  double *U = nullptr, *gc = nullptr, *V = nullptr, *gp = nullptr;
+  void *Vinv = nullptr, *y0 = nullptr;
+  // PCG
+  double *Minv = nullptr, *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
+  void *pT = nullptr, *xT = nullptr, *dp = nullptr;
+  double* part = nullptr;
+  int ncb = 0, npb = 0;
+  double *dot_pq = nullptr, *dot_rz = nullptr, *dot_rr = nullptr, *dot_bb = nullptr;
+  double *dot_gc = nullptr, *dot_gp = nullptr;
+  ba::DevState* st = nullptr;
+  ba_iter_stats* stats = nullptr;
+  int cap = 0;
+  // graph of one trial
+  cudaGraphExec_t gexec = nullptr;
+  size_t gnodes = 0;
+  // per-launch CUDA events (ba_profile_trials only)
+  struct ProfRec {
+    int kind, trial, k;
+    cudaEvent_t a, b;
+  };
+  std::vector<ProfRec>* prof = nullptr;
+  int prof_trial = 0;
+
+  template <typename X>
+  cudaError_t alloc(X** ptr, size_t bytes) {
+    void* v = nullptr;
+    cudaError_t e = cudaMalloc(&v, bytes > 0 ? bytes : 16);
+    if (e == cudaSuccess) {
+      allocs.push_back(v);
+      *ptr = static_cast<X*>(v);
+    }
+    return e;
+  }
+  ~ba_problem() {
+    if (gexec) cudaGraphExecDestroy(gexec);
+    for (void* v : allocs) cudaFree(v);
+    if (ev_in) cudaEventDestroy(ev_in);
+    if (ev_out) cudaEventDestroy(ev_out);
+    if (s) cudaStreamDestroy(s);
+  }
+};
+

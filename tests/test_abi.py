@@ -63,3 +63,27 @@ def test_argument_errors_need_no_gpu(lib):
     assert b"must be >= 1" in L.ba_last_error()
     assert L.ba_csr_build(None, -1, 3, None, None, None) == 1
     assert L.ba_lm_step(None, None) == 1
+
+
+def test_batch_argument_errors_need_no_gpu(lib):
+    from paper_2409_12190_gb300 import _lib
+    L = _lib.load()
+    h = ctypes.c_void_p()
+    dummy = ctypes.c_void_p(256)  # never dereferenced: the counts are checked first
+    one = (ctypes.c_int32 * 1)(1)
+    too_many = (ctypes.c_int32 * 1)(_lib.BA_BATCH_MAX_CAMS + 1)
+    assert L.ba_batch_create(ctypes.byref(h), 0, one, one, one, dummy, dummy, dummy, dummy, dummy, None,
+                             None) == 1
+    assert b"nprob" in L.ba_last_error()
+    assert L.ba_batch_create(ctypes.byref(h), 1, too_many, one, one, dummy, dummy, dummy, dummy, dummy, None,
+                             None) == 1
+    assert b"C_b" in L.ba_last_error()
+    assert L.ba_batch_solve(None, 1, None) == 1
+    assert L.ba_batch_set_launch(None, 1, 0, 0) == 1
+
+
+def test_batch_max_cams_matches_header():
+    from paper_2409_12190_gb300 import _lib
+    src = open(os.path.join(ROOT, "include", "ba.h")).read()
+    m = re.search(r"#define BA_BATCH_MAX_CAMS (\d+)", src)
+    assert m and int(m.group(1)) == _lib.BA_BATCH_MAX_CAMS
