@@ -387,6 +387,86 @@ ba_status ba_batch_get_launch(ba_batch* h, int* ctas_per_sm, int* variant, int* 
 ba_status ba_batch_autotune(ba_batch* h, int iters, const char* cache_path,
                             double* best_ms);
 
+/* ------------------------------------------------------------------------
+ * Learned block-Jacobi correction (not in the paper: its PCG uses a
+ * diagonal preconditioner, Sec. IV-C).  A 96-64-64-45 ReLU network maps
+ * per-camera quantities of the reduced camera system S to a lower-triangular
+ * G (off-diagonal: the outputs; diagonal: exp of the outputs) and the PCG
+ * uses M_i = L_i^{-T} G G^T L_i^{-1}, L_i = chol(S_ii), in place of the
+ * block-Jacobi inverse S_ii^{-1} (SPD for any output; output 0 gives
+ * block-Jacobi).  Features x_i (96, FP32), in the scaled coordinates
+ * D = diag(S_ii), S^ = D^{-1/2} S D^{-1/2}: the 36 off-diagonal entries of
+ * S^_ii (row-major upper triangle); the 45 entries (row-major upper
+ * triangle with diagonal) of R^ = D^{-1/2} (U*_i - S_ii) D^{-1/2} divided by
+ * sqrt((1 + R^_aa)(1 + R^_bb)); (ln D_a - mean_a ln D_a) / 10;
+ * log10(lambda) / 8; log10(1 + observations of camera i) / 4; 1; three
+ * zeros.  Parameters: FP32 [BA_MLP_NPARAM] laid out W1 [64][96], b1 [64],
+ * W2 [64][64], b2 [64], W3 [45][64], b3 [45]; the kernels feed the tensor
+ * cores BF16 copies of the weights, inputs and activations and accumulate
+ * in FP32.  Training loss (per camera, K Rademacher probes z^_k, y^_k =
+ * S^ z^_k, A = chol(S^_ii)^{-1}): 1/(9K) sum_k |A^T G G^T A y^_k - z^_k|^2,
+ * averaged over the cameras (E_z |M S z - z|^2 in the scaled coordinates).
+ * ------------------------------------------------------------------------ */
+
+#define BA_MLP_FIN 96
+#define BA_MLP_FOUT 45
+#define BA_MLP_NPARAM 13293
+#define BA_MLP_KMAX 16
+
+/* Use the network with parameters params (any, FP32 [BA_MLP_NPARAM],
+ * copied) for the preconditioner of every later ba_lm_step / ba_solve /
+ * ba_damped_solve of h; NULL returns to block-Jacobi.  Cameras whose S_ii is
+ * not positive definite, whose block is not finite or that have a frozen
+ * parameter keep the block-Jacobi inverse (counted in precond_fallbacks).
+ * ba_backward always uses block-Jacobi. */
+ba_status ba_set_preconditioner(ba_problem* h, const float* params, void* stream);
+
+/* Training data at the current parameters and damping lambda (> 0):
+ * X_out [C][96] features, Ahat_out [C][45] A = chol(S^_ii)^{-1} (packed
+ * lower triangle, row-major), and for the K (0..BA_MLP_KMAX) probes zhat
+ * [C][K][9] (+-1, FP32) the products Yhat_out [C][K][9] = S^ z^ (one
+ * implicit Schur product per probe), and, if D_out is not NULL, the scales
+ * D_out [C][9] = diag(S_ii) (FP64).  All dev.  Any +-1 or real probe
+ * vectors may be given (e.g. D^{1/2} times slow error components of a
+ * truncated PCG).  A camera whose S_ii is not positive definite gets zero
+ * features, A = 0, D = 0 and y^ = 0.  The next trial re-linearises.
+ * Stream-ordered. */
+ba_status ba_learn_collect(ba_problem* h, double lambda, int K, const float* zhat, float* X_out,
+                           float* Ahat_out, float* Yhat_out, double* D_out, void* stream);
+
+/* Probe vectors along the slow modes of the block-Jacobi PCG at the current
+ * parameters and damping lambda: x_ref = the PCG solution after maxiter_ref
+ * iterations / relative tolerance tol_ref, x_k = the PCG iterate after
+ * k = iters[j] iterations (iters host [n], n <= BA_MLP_KMAX), and
+ * zhat_out [C][n][9] (dev, FP32) = D^{1/2} (x_ref - x_k) scaled to unit
+ * root-mean-square per j (D = diag(S_ii)).  The error of a truncated PCG is
+ * dominated by the slow modes of the preconditioned system, which Rademacher
+ * probes barely weight.  Synchronises. */
+ba_status ba_learn_slow_probes(ba_problem* h, double lambda, int n, const int* iters, int maxiter_ref,
+                               double tol_ref, float* zhat_out, void* stream);
+
+/* Network output E_out [n][45] for features X [n][96] (dev, FP32).
+ * Stream-ordered. */
+ba_status ba_mlp_forward(const float* params, int n, const float* X, float* E_out, void* stream);
+
+/* Mean training loss over n samples (X [n][96], Ahat [n][45], Yhat, Zhat
+ * [n][K][9], dev, FP32) into *loss_out (host, may be NULL) and its gradient
+ * grad_out [BA_MLP_NPARAM] (dev, FP64; summed over fixed tiles of 64 samples
+ * in a fixed order).  Synchronises. */
+ba_status ba_mlp_loss_grad(const float* params, int n, int K, const float* X, const float* Ahat,
+                           const float* Yhat, const float* Zhat, double* grad_out, double* loss_out,
+                           void* stream);
+
+/* Adam (beta1 0.9, beta2 0.999, eps 1e-8, learning rate lr) on params with
+ * moments adam_m, adam_v (dev, FP32 [BA_MLP_NPARAM], in/out; zero them for a
+ * fresh start), over `epochs` passes of the n samples in minibatches of
+ * `batch` consecutive samples (a shorter tail is skipped; shuffle the samples
+ * beforehand).  loss_hist (host [epochs], may be NULL) receives each epoch's
+ * mean minibatch loss.  Synchronises. */
+ba_status ba_mlp_train(float* params, float* adam_m, float* adam_v, int n, int K, const float* X,
+                       const float* Ahat, const float* Yhat, const float* Zhat, int epochs, int batch,
+                       double lr, double* loss_hist, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

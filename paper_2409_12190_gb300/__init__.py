@@ -22,7 +22,12 @@ from . import _lib
 from ._lib import BAError, BA_PREC_F32, BA_PREC_F64
 
 __all__ = ["Options", "Problem", "Batch", "project", "csr_build", "kernel_launch_count",
-           "BAError", "library_path", "bundle_adjust"]
+           "BAError", "library_path", "bundle_adjust", "MLP_NPARAM", "MLP_FIN", "mlp_init",
+           "mlp_forward", "mlp_loss_grad", "mlp_train"]
+
+MLP_NPARAM = _lib.BA_MLP_NPARAM
+MLP_FIN = _lib.BA_MLP_FIN
+MLP_FOUT = _lib.BA_MLP_FOUT
 
 library_path = _lib.LIB_PATH
 
@@ -233,6 +238,39 @@ class Problem:
         _lib.check(_L().ba_profile_trials(self._h, int(iters), ct.byref(t)))
         per = {name: (t.ms[i], int(t.launches[i])) for i, name in enumerate(_lib.BA_K_NAMES)}
         return per, t.trial_ms
+
+    # -- learned block-Jacobi correction ---------------------------------------
+    def set_preconditioner(self, params=None, stream=None):
+        """Use the network with these parameters (FP32 [MLP_NPARAM]) for the
+        PCG's block preconditioner; None returns to block-Jacobi."""
+        p = None if params is None else _dev(params, torch.float32, self.device)
+        _lib.check(_L().ba_set_preconditioner(self._h, _ptr(p), _stream(stream)))
+        torch.cuda.current_stream(self.device).synchronize()
+
+    def learn_collect(self, lam: float, zhat, stream=None, scales=False):
+        """Training data at the current parameters and damping lam: features
+        X [C, 96], A = chol(S^_ii)^{-1} [C, 45] and y^ = S^ z^ [C, K, 9] for the
+        probes zhat [C, K, 9]; with scales=True also D = diag(S_ii) [C, 9]."""
+        z = _dev(zhat, torch.float32, self.device)
+        K = int(z.shape[1]) if z.dim() == 3 else 0
+        X = torch.empty((self.C, MLP_FIN), dtype=torch.float32, device=self.device)
+        A = torch.empty((self.C, 45), dtype=torch.float32, device=self.device)
+        Y = torch.empty((self.C, K, 9), dtype=torch.float32, device=self.device)
+        D = torch.empty((self.C, 9), dtype=torch.float64, device=self.device) if scales else None
+        _lib.check(_L().ba_learn_collect(self._h, float(lam), K, _ptr(z), _ptr(X), _ptr(A), _ptr(Y), _ptr(D),
+                                         _stream(stream)))
+        return (X, A, Y, D) if scales else (X, A, Y)
+
+    def learn_slow_probes(self, lam: float, iters=(20, 50), maxiter_ref: int = 600, tol_ref: float = 1e-10,
+                          stream=None):
+        """Probe vectors [C, len(iters), 9] along the slow modes of the
+        block-Jacobi PCG (scaled truncated-PCG errors, unit RMS)."""
+        n = len(iters)
+        z = torch.empty((self.C, n, 9), dtype=torch.float32, device=self.device)
+        its = (ct.c_int * max(1, n))(*iters)
+        _lib.check(_L().ba_learn_slow_probes(self._h, float(lam), n, ct.cast(its, ct.c_void_p), int(maxiter_ref),
+                                             float(tol_ref), _ptr(z), _stream(stream)))
+        return z
 
     # -- step-level -----------------------------------------------------------
     def csr(self, stream=None):
@@ -449,6 +487,54 @@ def csr_build(keys, n_keys: int, stream=None):
     _lib.check(_L().ba_csr_build(_ptr(k) if k.numel() else None, k.shape[0], int(n_keys),
                                  _ptr(perm) if k.numel() else None, _ptr(rowptr), _stream(stream)))
     return perm, rowptr
+
+
+def mlp_init(seed: int = 0, device="cuda"):
+    """Initial network parameters (FP32 [MLP_NPARAM]): uniform +-1/sqrt(fan_in)
+    weights and biases in the hidden layers, a zero output layer (so the
+    preconditioner starts as block-Jacobi)."""
+    g = torch.Generator().manual_seed(int(seed))
+    parts = []
+    for fan_out, fan_in, zero in ((64, MLP_FIN, False), (64, 64, False), (MLP_FOUT, 64, True)):
+        bound = 1.0 / fan_in ** 0.5
+        w = torch.zeros(fan_out * fan_in) if zero else (torch.rand(fan_out * fan_in, generator=g) * 2 - 1) * bound
+        b = torch.zeros(fan_out) if zero else (torch.rand(fan_out, generator=g) * 2 - 1) * bound
+        parts += [w, b]
+    return torch.cat(parts).to(device=device, dtype=torch.float32)
+
+
+def mlp_forward(params, X, stream=None):
+    """Network output [n, 45] for features X [n, 96] (tensor-core kernel)."""
+    X = X.to(torch.float32).contiguous()
+    E = torch.empty((X.shape[0], MLP_FOUT), dtype=torch.float32, device=X.device)
+    _lib.check(_L().ba_mlp_forward(_ptr(params.contiguous()), int(X.shape[0]), _ptr(X), _ptr(E), _stream(stream)))
+    return E
+
+
+def mlp_loss_grad(params, X, A, Y, Z, stream=None):
+    """(mean probe loss, gradient [MLP_NPARAM] float64)."""
+    n, K = int(X.shape[0]), int(Y.shape[1])
+    grad = torch.empty(MLP_NPARAM, dtype=torch.float64, device=X.device)
+    loss = ct.c_double()
+    args = [t.to(torch.float32).contiguous() for t in (X, A, Y, Z)]
+    _lib.check(_L().ba_mlp_loss_grad(_ptr(params.contiguous()), n, K, *(_ptr(t) for t in args), _ptr(grad),
+                                     ct.byref(loss), _stream(stream)))
+    return loss.value, grad
+
+
+def mlp_train(params, adam_m, adam_v, X, A, Y, Z, epochs: int, batch: int, lr: float, stream=None):
+    """Adam on params (in place, FP32 device tensors) over minibatches of
+    consecutive samples; returns the per-epoch mean minibatch losses."""
+    n, K = int(X.shape[0]), int(Y.shape[1])
+    hist = (ct.c_double * max(1, int(epochs)))()
+    args = [t.to(torch.float32).contiguous() for t in (X, A, Y, Z)]
+    for t in (params, adam_m, adam_v):
+        if not (t.is_contiguous() and t.dtype == torch.float32 and t.numel() == MLP_NPARAM):
+            raise ValueError("params / moments must be contiguous float32 [MLP_NPARAM]")
+    _lib.check(_L().ba_mlp_train(_ptr(params), _ptr(adam_m), _ptr(adam_v), n, K, *(_ptr(t) for t in args),
+                                 int(epochs), int(batch), float(lr), ct.cast(hist, ct.c_void_p),
+                                 _stream(stream)))
+    return list(hist)[:int(epochs)]
 
 
 def kernel_launch_count() -> int:

@@ -103,7 +103,18 @@ SIGNATURES = {
     "ba_batch_set_launch": (_S, [_VP, _I, _I, _I]),
     "ba_batch_get_launch": (_S, [_VP, ct.POINTER(_I), ct.POINTER(_I), ct.POINTER(_I), ct.POINTER(_I)]),
     "ba_batch_autotune": (_S, [_VP, _I, ct.c_char_p, ct.POINTER(_D)]),
+    "ba_set_preconditioner": (_S, [_VP, _VP, _VP]),
+    "ba_learn_collect": (_S, [_VP, _D, _I, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "ba_learn_slow_probes": (_S, [_VP, _D, _I, _VP, _I, _D, _VP, _VP]),
+    "ba_mlp_forward": (_S, [_VP, _I, _VP, _VP, _VP]),
+    "ba_mlp_loss_grad": (_S, [_VP, _I, _I, _VP, _VP, _VP, _VP, _VP, ct.POINTER(_D), _VP]),
+    "ba_mlp_train": (_S, [_VP, _VP, _VP, _I, _I, _VP, _VP, _VP, _VP, _I, _I, _D, _VP, _VP]),
 }
+
+BA_MLP_FIN = 96
+BA_MLP_FOUT = 45
+BA_MLP_NPARAM = 13293
+BA_MLP_KMAX = 16
 
 BA_BATCH_MAX_CAMS = 28
 

@@ -14,6 +14,7 @@
 #include "ba.h"
 #include "ba_internal.h"
 #include "ba_kernels.cuh"
+#include "ba_learn.cuh"
 #include "ba_problem.h"
 
 namespace ba {
@@ -190,7 +191,7 @@ void enqueue_pcg_iter(ba_problem* h, const double* lam_ptr, int k, double tol) {
 }
 
 template <typename T, bool MF>
-void enqueue_solve(ba_problem* h, const double* lam_ptr, int maxiter, double tol) {
+void enqueue_solve(ba_problem* h, const double* lam_ptr, int maxiter, double tol, bool learned = false) {
   cudaStream_t s = h->s;
   const double dmin = h->opt.diag_min, dmax = h->opt.diag_max;
   {
@@ -208,9 +209,21 @@ void enqueue_solve(ba_problem* h, const double* lam_ptr, int maxiter, double tol
     Prof pr(h, BA_K_OTHER);
     k_cam_combine_schur<T, MF><<<h->ncb, CAM_THREADS, 0, s>>>(
         h->C, h->cam_piece_ptr, h->part, h->U, h->gc, (const T*)h->camtab, lam_ptr, dmin, dmax, h->Minv, h->x,
-        h->r, h->z, h->p, (T*)h->pT, h->dot_rz + h->ncb, h->dot_bb, h->fixed, h->st);
+        h->r, h->z, h->p, (T*)h->pT, h->dot_rz + h->ncb, h->dot_bb, h->fixed, h->st, learned ? h->Sii : nullptr);
   }
   count_launch(3);
+  if (learned) {
+    // the learned correction of the block-Jacobi blocks: features, network
+    // (tensor cores), SPD blocks and the PCG start with them
+    Prof pr(h, BA_K_OTHER);
+    k_learn_features<<<h->ncb, CAM_THREADS, 0, s>>>(h->C, h->Sii, h->U, lam_ptr, dmin, dmax, h->rowptr_cam, h->Xf,
+                                                    nullptr, nullptr);
+    k_mlp_forward<<<nblk(h->C, MLP_ROWS), MLP_THREADS, MLP_SMEM_FWD, s>>>(h->C, h->mlp, h->Xf, h->Ef);
+    k_learn_start<T, MF><<<h->ncb, CAM_THREADS, 0, s>>>(h->C, h->Sii, h->Ef, (const T*)h->camtab, h->Minv, h->r,
+                                                         h->z, h->p, (T*)h->pT, h->dot_rz + h->ncb, h->fixed,
+                                                         h->st);
+    count_launch(3);
+  }
   for (int k = 0; k < maxiter; ++k) enqueue_pcg_iter<T, MF>(h, lam_ptr, k, tol);
   {
     Prof pr(h, BA_K_OTHER);
@@ -235,7 +248,7 @@ void enqueue_solve(ba_problem* h, const double* lam_ptr, int maxiter, double tol
 template <typename T, bool MF>
 void enqueue_trial(ba_problem* h) {
   enqueue_lin<T, MF>(h, 1);
-  enqueue_solve<T, MF>(h, &h->st->lam, h->opt.pcg_maxiter, h->opt.pcg_tol);
+  enqueue_solve<T, MF>(h, &h->st->lam, h->opt.pcg_maxiter, h->opt.pcg_tol, h->learned);
   const T delta = (T)(h->opt.huber_delta > 0 ? h->opt.huber_delta : 0.0);
   {
     Prof pr(h, BA_K_COST);
@@ -585,6 +598,65 @@ ba_status set_probe_lambda(ba_problem* h, double lam) {
   return BA_OK;
 }
 
+// Features, scaled inverse factors and probe products S^ z^ at the current
+// parameters and damping *lam_ptr (ba_learn_collect).
+template <typename T, bool MF>
+void enqueue_collect(ba_problem* h, const double* lam_ptr, int K, const float* zhat, float* X, float* Ahat,
+                     float* Yhat) {
+  cudaStream_t s = h->s;
+  const double dmin = h->opt.diag_min, dmax = h->opt.diag_max;
+  enqueue_lin<T, MF>(h, 1);
+  k_pt_damp<T><<<nblk(h->P, PT_THREADS), PT_THREADS, 0, s>>>(h->P, h->V, h->gp, lam_ptr, dmin, dmax, (T*)h->Vinv,
+                                                            (T*)h->y0);
+  k_schur_cam<T, MF><<<h->npieces, PIECE_THREADS, 0, s>>>(
+      h->piece_cam, h->piece_beg, h->piece_end, h->cm_pt, (const T*)h->Jcm, (const T*)h->camtab, (const T*)h->pts,
+      (const T*)h->cm_sw, h->st, h->P, (const T*)h->Vinv, (const T*)h->y0, h->O, h->part);
+  k_cam_combine_schur<T, MF><<<h->ncb, CAM_THREADS, 0, s>>>(
+      h->C, h->cam_piece_ptr, h->part, h->U, h->gc, (const T*)h->camtab, lam_ptr, dmin, dmax, h->Minv, h->x, h->r,
+      h->z, h->p, (T*)h->pT, h->dot_rz + h->ncb, h->dot_bb, h->fixed, h->st, h->Sii);
+  k_learn_features<<<h->ncb, CAM_THREADS, 0, s>>>(h->C, h->Sii, h->U, lam_ptr, dmin, dmax, h->rowptr_cam, X, Ahat,
+                                                  h->Dsc);
+  count_launch(4);
+  for (int k = 0; k < K; ++k) {
+    k_probe_in<T, MF><<<nblk(h->C, 128), 128, 0, s>>>(h->C, K, k, zhat, h->Dsc, (const T*)h->camtab, h->p,
+                                                      (T*)h->pT);
+    enqueue_schur_product<T, MF>(h, (const T*)h->pT, -1, 0);
+    k_pcg_q<T, MF><<<h->ncb, VT, 0, s>>>(h->C, h->cam_piece_ptr, h->part, h->U, (const T*)h->camtab, lam_ptr, dmin,
+                                        dmax, h->p, h->q, nullptr, h->fixed, h->st, 0);
+    k_probe_out<<<nblk(h->C, 128), 128, 0, s>>>(h->C, K, k, h->q, h->Dsc, Yhat);
+    count_launch(3);
+  }
+}
+
+// Slow-mode probes: z^_j = D^{1/2} (x_ref - x_its[j]) / rms, x_ref from a
+// PCG run of maxiter_ref iterations / tol_ref, x_k after k iterations.
+template <typename T, bool MF>
+void enqueue_slow_probes(ba_problem* h, const double* lam_ptr, int n, const int* its, int maxiter_ref, double tol_ref,
+                         float* zhat, double* xref) {
+  cudaStream_t s = h->s;
+  enqueue_collect<T, MF>(h, lam_ptr, 0, nullptr, h->Xf, nullptr, nullptr);  // scales D
+  enqueue_solve<T, MF>(h, lam_ptr, maxiter_ref, tol_ref, false);
+  cudaMemcpyAsync(xref, h->x, 72ull * h->C, cudaMemcpyDeviceToDevice, s);
+  for (int j = 0; j < n; ++j) {
+    enqueue_solve<T, MF>(h, lam_ptr, its[j], 0.0, false);
+    k_slow_diff<<<nblk(9LL * h->C, 256), 256, 0, s>>>(h->C, n, j, xref, h->x, h->Dsc, zhat);
+    count_launch();
+  }
+  k_slow_normalize<<<1, 256, 0, s>>>(h->C, n, zhat);
+  count_launch();
+}
+
+ba_status ensure_learn_buffers(ba_problem* h) {
+  if (h->Sii) return BA_OK;
+  CU(h->alloc(&h->mlp, (size_t)MLP_NPARAM * 4));
+  CU(h->alloc(&h->Sii, 45ull * h->C * 8));
+  CU(h->alloc(&h->Xf, (size_t)MLP_FIN * h->C * 4));
+  CU(h->alloc(&h->Ef, (size_t)MLP_FOUT * h->C * 4));
+  CU(h->alloc(&h->Dsc, 9ull * h->C * 8));
+  CU(cudaFuncSetAttribute(k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MLP_SMEM_FWD));
+  return BA_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -912,7 +984,7 @@ ba_status ba_damped_solve(ba_problem* h, double lambda, int maxiter, double tol,
   if (st != BA_OK) return st;
   const double* lp = &h->st->lam_probe;
   BA_DISPATCH(h, enqueue_lin, 1);
-  BA_DISPATCH(h, enqueue_solve, lp, maxiter, tol);
+  BA_DISPATCH(h, enqueue_solve, lp, maxiter, tol, h->learned);
   CU(cudaGetLastError());
   if (dc) CU(cudaMemcpyAsync(dc, h->x, 72ull * h->C, cudaMemcpyDeviceToDevice, h->s));
   if (dp) {
@@ -1015,6 +1087,70 @@ ba_status ba_backward(ba_problem* h, double lambda, int maxiter, double tol, con
     if (iters) *iters = ds.pcg_iters;
     if (rel_res) *rel_res = ds.pcg_rel;
   }
+  return leave(h, stream);
+}
+
+ba_status ba_set_preconditioner(ba_problem* h, const float* params, void* stream) {
+  if (!h) return fail(BA_ERR_INVALID_ARG, "NULL problem");
+  ba_status st = enter(h, stream);
+  if (st != BA_OK) return st;
+  if (params) {
+    st = ensure_learn_buffers(h);
+    if (st != BA_OK) return st;
+    CU(cudaMemcpyAsync(h->mlp, params, (size_t)MLP_NPARAM * 4, cudaMemcpyDefault, h->s));
+  }
+  if (h->learned != (params != nullptr) && h->gexec) {
+    // the captured trial has the other preconditioner: capture again
+    cudaGraphExecDestroy(h->gexec);
+    h->gexec = nullptr;
+  }
+  h->learned = params != nullptr;
+  return leave(h, stream);
+}
+
+ba_status ba_learn_collect(ba_problem* h, double lambda, int K, const float* zhat, float* X_out, float* Ahat_out,
+                           float* Yhat_out, double* D_out, void* stream) {
+  if (!h || !X_out || !Ahat_out || (K > 0 && (!zhat || !Yhat_out)))
+    return fail(BA_ERR_INVALID_ARG, "NULL argument");
+  if (K < 0 || K > MLP_KMAX || !(lambda > 0)) return fail(BA_ERR_INVALID_ARG, "need 0 <= K <= %d, lambda > 0", MLP_KMAX);
+  ba_status st = enter(h, stream);
+  if (st != BA_OK) return st;
+  st = ensure_learn_buffers(h);
+  if (st != BA_OK) return st;
+  st = set_probe_lambda(h, lambda);
+  if (st != BA_OK) return st;
+  st = set_flag(h, offsetof(DevState, need_lin), 1);
+  if (st != BA_OK) return st;
+  BA_DISPATCH(h, enqueue_collect, &h->st->lam_probe, K, zhat, X_out, Ahat_out, Yhat_out);
+  CU(cudaGetLastError());
+  if (D_out) CU(cudaMemcpyAsync(D_out, h->Dsc, 72ull * h->C, cudaMemcpyDeviceToDevice, h->s));
+  return leave(h, stream);
+}
+
+ba_status ba_learn_slow_probes(ba_problem* h, double lambda, int n, const int* iters, int maxiter_ref,
+                               double tol_ref, float* zhat_out, void* stream) {
+  if (!h || (n > 0 && (!iters || !zhat_out))) return fail(BA_ERR_INVALID_ARG, "NULL argument");
+  if (n < 0 || n > MLP_KMAX || !(lambda > 0) || maxiter_ref < 1 || maxiter_ref > 100000 || !(tol_ref >= 0))
+    return fail(BA_ERR_INVALID_ARG, "need 0 <= n <= %d, lambda > 0, 1 <= maxiter_ref <= 100000", MLP_KMAX);
+  for (int j = 0; j < n; ++j)
+    if (iters[j] < 0 || iters[j] > 100000) return fail(BA_ERR_INVALID_ARG, "iters out of range");
+  if (n == 0) return BA_OK;
+  ba_status st = enter(h, stream);
+  if (st != BA_OK) return st;
+  st = ensure_learn_buffers(h);
+  if (st != BA_OK) return st;
+  double* xref = nullptr;
+  CU(cudaMalloc(&xref, 72ull * h->C));
+  st = set_probe_lambda(h, lambda);
+  if (st == BA_OK) st = set_flag(h, offsetof(DevState, need_lin), 1);
+  if (st == BA_OK) {
+    BA_DISPATCH(h, enqueue_slow_probes, &h->st->lam_probe, n, iters, maxiter_ref, tol_ref, zhat_out, xref);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->s);
+    if (e != cudaSuccess) st = fail(BA_ERR_CUDA, "slow probes failed: %s", cudaGetErrorString(e));
+  }
+  cudaFree(xref);
+  if (st != BA_OK) return st;
   return leave(h, stream);
 }
 

@@ -1021,7 +1021,8 @@ __device__ __forceinline__ void cam_schur_one(int p0, int p1, const double* __re
                                               const uint8_t* __restrict__ fixed_c, double* __restrict__ Mc,
                                               double* __restrict__ xc, double* __restrict__ rc,
                                               double* __restrict__ zc, double* __restrict__ pc,
-                                              T* __restrict__ pTc, double& rz, double& bb, int& fallback) {
+                                              T* __restrict__ pTc, double& rz, double& bb, int& fallback,
+                                              double* __restrict__ S_out = nullptr) {
   double S[45], bv[9];
 #pragma unroll
   for (int i = 0; i < 45; ++i) S[i] = Uc[i];
@@ -1051,6 +1052,10 @@ __device__ __forceinline__ void cam_schur_one(int p0, int p1, const double* __re
 #pragma unroll
       for (int j = i; j < 9; ++j)
         if (fz[i] || fz[j]) S[sym9(i, j)] = i == j ? 1.0 : 0.0;
+  }
+  if (S_out) {
+#pragma unroll
+    for (int i = 0; i < 45; ++i) S_out[i] = S[i];
   }
   double M[45];
   fallback = 0;
@@ -1099,7 +1104,8 @@ k_cam_combine_schur(int C, const int32_t* __restrict__ cam_piece_ptr, const doub
                     const double* __restrict__ lam_ptr, double dmin, double dmax, double* __restrict__ Minv,
                     double* __restrict__ x, double* __restrict__ r, double* __restrict__ z,
                     double* __restrict__ p, T* __restrict__ pT, double* __restrict__ dot_rz1,
-                    double* __restrict__ dot_bb, const uint8_t* __restrict__ fixed, DevState* st) {
+                    double* __restrict__ dot_bb, const uint8_t* __restrict__ fixed, DevState* st,
+                    double* __restrict__ Sii_out) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   double rz = 0.0, bb = 0.0;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -1113,7 +1119,8 @@ k_cam_combine_schur(int C, const int32_t* __restrict__ cam_piece_ptr, const doub
     cam_schur_one<T, MF>(cam_piece_ptr[c], cam_piece_ptr[c + 1], part, U + 45LL * c, gc + 9LL * c,
                          camtab + (long long)CT * c, *lam_ptr, dmin, dmax, fixed ? fixed + 9LL * c : nullptr,
                          Minv + 45LL * c, x + 9LL * c, r + 9LL * c, z + 9LL * c, p + 9LL * c,
-                         pT + (long long)pass_vec_stride(MF) * c, rz, bb, fb);
+                         pT + (long long)pass_vec_stride(MF) * c, rz, bb, fb,
+                         Sii_out ? Sii_out + 45LL * c : nullptr);
     if (fb) atomicAdd(&st->fallbacks, 1);
   }
   double v[2] = {rz, bb};

@@ -55,6 +55,13 @@ struct ba_problem {
   int ncb = 0, npb = 0;
   double *dot_pq = nullptr, *dot_rz = nullptr, *dot_rr = nullptr, *dot_bb = nullptr;
   double *dot_gc = nullptr, *dot_gp = nullptr;
+  // learned block-Jacobi correction (ba_set_preconditioner, ba_learn_collect)
+  bool learned = false;
+  float* mlp = nullptr;     // [13293] network parameters
+  double* Sii = nullptr;    // [C][45] diagonal blocks of S (packed upper)
+  float* Xf = nullptr;      // [C][96] features
+  float* Ef = nullptr;      // [C][45] network output
+  double* Dsc = nullptr;    // [C][9] scales diag(S_ii)
   ba::DevState* st = nullptr;
   ba_iter_stats* stats = nullptr;
   int cap = 0;
