@@ -173,6 +173,8 @@ def algorithmic_bytes(kind, C, P, O, npieces, tsize, mf, huber=False):
         return O * (4 + ob + 4 * tsize) + (P * 4 * tsize if mf else 0) + C * (16 + 12) * tsize
     if kind == "pass_a2":  # order map + one 4-vector per obs; rowptr, V*^-1, t out per point
         return O * (4 + 4 * tsize) + P * (4 + 6 * tsize + 4 * tsize)
+    if kind == "pass_fa":  # point index + chunk camera position (+ sqrt(w)) per obs; X in, V*^-1, t out per point
+        return O * (4 + 2 + (tsize if huber else 0)) + P * (4 + 4 * tsize + 6 * tsize + 4 * tsize)
     if kind == "lin_cam":  # pixels + point index in; planes / weights out; points once; partials
         return O * (2 * tsize + 4 + ob) + P * 3 * tsize + npieces * 54 * 8
     if kind == "lin_pt":
@@ -189,7 +191,7 @@ def algorithmic_bytes(kind, C, P, O, npieces, tsize, mf, huber=False):
 
 # FP32 operations per observation of the recompute-mode passes (an FMA counts
 # two): the factored Jacobian (61) plus the pass's products.
-FLOPS_PER_OBS = {"pass_b": 119, "pass_a1": 113}
+FLOPS_PER_OBS = {"pass_b": 119, "pass_a1": 113, "pass_fa": 116}
 
 
 def fp32_peak_tflops(sm_mhz):

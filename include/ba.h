@@ -285,7 +285,8 @@ enum {
   BA_K_BACKSUB = 6,   /* a5 back-substitution passes */
   BA_K_OTHER = 7,     /* per-camera / per-point / scalar kernels */
   BA_K_PASS_A2 = 8,   /* a4 PCG pass A2 (point-major sum, V*^{-1}) */
-  BA_K_COUNT = 9
+  BA_K_PASS_FA = 9,   /* a4 fused point-major pass A (A1 + A2, recompute mode) */
+  BA_K_COUNT = 10
 };
 
 typedef struct {

@@ -51,11 +51,12 @@ class ba_iter_stats(ct.Structure):
     ]
 
 
-BA_K_NAMES = ["lin_cam", "lin_pt", "schur_cam", "pass_a1", "pass_b", "cost", "backsub", "other", "pass_a2"]
+BA_K_NAMES = ["lin_cam", "lin_pt", "schur_cam", "pass_a1", "pass_b", "cost", "backsub", "other", "pass_a2",
+              "pass_fa"]
 
 
 class ba_kernel_times(ct.Structure):
-    _fields_ = [("ms", ct.c_double * 9), ("launches", ct.c_int64 * 9), ("trial_ms", ct.c_double)]
+    _fields_ = [("ms", ct.c_double * 10), ("launches", ct.c_int64 * 10), ("trial_ms", ct.c_double)]
 
 
 _VP = ct.c_void_p

@@ -2,6 +2,7 @@
 // object, its device buffers, the stream-ordered LM trial and its CUDA graph.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstdarg>
@@ -143,6 +144,23 @@ void enqueue_lin(ba_problem* h, int gate) {
 template <typename T, bool MF>
 void enqueue_schur_product(ba_problem* h, const T* xc, int k, int check_done) {
   cudaStream_t s = h->s;
+  if (MF && h->fa) {
+    {
+      Prof pr(h, BA_K_PASS_FA, k);
+      k_pass_fa<T, 0><<<h->nchunks, CHUNK_THREADS, CHUNK_SLOTS * 4 * sizeof(T), s>>>(
+          h->pchunk, h->P, h->rowptr_pt, h->pm_pt, h->pm_lc, (const T*)h->pm_sw, h->chunk_cams, h->chunk_cam_ptr,
+          (const T*)h->camtab, xc, (const T*)h->Vinv, h->st, check_done, (T*)h->ptab, nullptr, nullptr, nullptr,
+          nullptr, nullptr);
+    }
+    {
+      Prof pr(h, BA_K_PASS_B, k);
+      k_pass_b<T, MF><<<h->npieces, PIECE_THREADS, 0, s>>>(h->piece_cam, h->piece_beg, h->piece_end, h->cm_pt,
+                                                          (const T*)h->Jcm, (const T*)h->cm_sw, (const T*)h->ptab,
+                                                          (const T*)h->camtab, h->st, check_done, h->O, h->part);
+    }
+    count_launch(2);
+    return;
+  }
   {
     Prof pr(h, BA_K_PASS_A, k);
     k_pass_a1<T, MF><<<h->npieces, PIECE_THREADS, 0, s>>>(
@@ -229,6 +247,15 @@ void enqueue_solve(ba_problem* h, const double* lam_ptr, int maxiter, double tol
     Prof pr(h, BA_K_OTHER);
     k_cam_trial<T, MF><<<h->ncb, CAM_THREADS, 0, s>>>(h->C, h->x, h->gc, (T*)h->cams, (const T*)h->camtab, h->st,
                                                      (T*)h->xT, h->dot_gc);
+  }
+  if (MF && h->fa) {
+    Prof pr(h, BA_K_BACKSUB);
+    k_pass_fa<T, 1><<<h->nchunks, CHUNK_THREADS, CHUNK_SLOTS * 4 * sizeof(T), s>>>(
+        h->pchunk, h->P, h->rowptr_pt, h->pm_pt, h->pm_lc, (const T*)h->pm_sw, h->chunk_cams, h->chunk_cam_ptr,
+        (const T*)h->camtab, (const T*)h->xT, (const T*)h->Vinv, h->st, 0, (T*)h->ptab, (T*)h->dp, (const T*)h->y0,
+        h->gp, (T*)h->pts, h->dot_gp);
+    count_launch(2);
+    return;
   }
   {
     Prof pr(h, BA_K_BACKSUB);
@@ -471,10 +498,9 @@ ba_status create_impl(ba_problem* h, const void* cams, const void* points, const
 
   // point chunks: runs of whole points with at most CHUNK_SLOTS observations
   // and CHUNK_PTS points (a point with more observations is a chunk alone)
+  std::vector<int32_t> rq(P + 1), pch;
   {
-    std::vector<int32_t> rq(P + 1);
     CU(cudaMemcpy(rq.data(), h->rowptr_pt, (P + 1) * 4, cudaMemcpyDeviceToHost));
-    std::vector<int32_t> pch;
     long long j = 0;
     while (j < P) {
       pch.push_back((int32_t)j);
@@ -490,6 +516,11 @@ ba_status create_impl(ba_problem* h, const void* cams, const void* points, const
   if (sizeof(T) * CHUNK_SLOTS * 9 > 48 * 1024)
     CU(cudaFuncSetAttribute(k_lin_pt<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                             (int)(sizeof(T) * CHUNK_SLOTS * 9)));
+  CU(cudaFuncSetAttribute(k_pass_fa<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          (int)(sizeof(T) * CHUNK_SLOTS * 4)));
+  CU(cudaFuncSetAttribute(k_pass_fa<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          (int)(sizeof(T) * CHUNK_SLOTS * 4)));
+
 
   // observation data in both orders
   CU(h->alloc(&h->cm_pt, O * 4));
@@ -511,6 +542,39 @@ ba_status create_impl(ba_problem* h, const void* cams, const void* points, const
     CU(e);
   }
   count_launch(3);
+
+  // fused point-major pass A (recompute mode): every chunk's distinct
+  // cameras, if no chunk has more than FA_CAMS of them
+  if (h->mf) {
+    std::vector<int32_t> pmc(O), list, ptr(h->nchunks + 1), tmp;
+    std::vector<int16_t> lc(O);
+    CU(cudaMemcpy(pmc.data(), h->pm_cam, O * 4, cudaMemcpyDeviceToHost));
+    bool ok = true;
+    for (int k = 0; k < h->nchunks && ok; ++k) {
+      const int s0 = rq[pch[k]], s1 = rq[pch[k + 1]];
+      tmp.assign(pmc.begin() + s0, pmc.begin() + s1);
+      std::sort(tmp.begin(), tmp.end());
+      tmp.erase(std::unique(tmp.begin(), tmp.end()), tmp.end());
+      if ((int)tmp.size() > FA_CAMS) {
+        ok = false;
+        break;
+      }
+      ptr[k] = (int32_t)list.size();
+      list.insert(list.end(), tmp.begin(), tmp.end());
+      for (int q = s0; q < s1; ++q)
+        lc[q] = (int16_t)(std::lower_bound(tmp.begin(), tmp.end(), pmc[q]) - tmp.begin());
+    }
+    if (ok) {
+      ptr[h->nchunks] = (int32_t)list.size();
+      CU(h->alloc(&h->chunk_cams, std::max<size_t>(list.size(), 1) * 4));
+      CU(h->alloc(&h->chunk_cam_ptr, ptr.size() * 4));
+      CU(h->alloc(&h->pm_lc, O * 2));
+      CU(cudaMemcpy(h->chunk_cams, list.data(), list.size() * 4, cudaMemcpyHostToDevice));
+      CU(cudaMemcpy(h->chunk_cam_ptr, ptr.data(), ptr.size() * 4, cudaMemcpyHostToDevice));
+      CU(cudaMemcpy(h->pm_lc, lc.data(), O * 2, cudaMemcpyHostToDevice));
+      h->fa = true;
+    }
+  }
 
   // linearisation and solver buffers
   CU(h->alloc(&h->camtab, CT * C * ts));

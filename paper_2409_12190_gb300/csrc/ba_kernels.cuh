@@ -1141,6 +1141,23 @@ k_cam_combine_schur(int C, const int32_t* __restrict__ cam_piece_ptr, const doub
 // camera's table and x_c sit in registers; the only per-observation loads are
 // the point index, the point (recompute mode: one 16-byte vector) or the
 // planes (stored mode), and sqrt(w).
+// z = Jp^T (Jc x) of one observation in the recompute mode: the camera
+// table's first 15 entries in ct, the camera vector in the passes' form in xv.
+template <typename T, typename CT15, typename XV9>
+__device__ __forceinline__ void a1_obs(const CT15& ct, const XV9& xv, T X0, T X1, T X2, T sw, T& z0, T& z1,
+                                       T& z2) {
+  Fac<T> o;
+  fac_obs(ct, X0, X1, X2, sw, o);
+  T e0, e1;
+  jc_times_fac(o, xv, e0, e1);
+  const T a0 = o.A[0] * e0 + o.A[3] * e1;
+  const T a1 = o.A[1] * e0 + o.A[4] * e1;
+  const T a2 = o.A[2] * e0 + o.A[5] * e1;
+  z0 = ct[0] * a0 + ct[3] * a1 + ct[6] * a2;
+  z1 = ct[1] * a0 + ct[4] * a1 + ct[7] * a2;
+  z2 = ct[2] * a0 + ct[5] * a1 + ct[8] * a2;
+}
+
 template <typename T, bool MF, int NT>
 __device__ __forceinline__ void pass_a1_range(int beg, int end, const int32_t* __restrict__ cm_pt,
                                               const T* __restrict__ Jcm, const T* __restrict__ cm_sw,
@@ -1162,16 +1179,8 @@ __device__ __forceinline__ void pass_a1_range(int beg, int end, const int32_t* _
         load4(ptab + 8LL * cm_pt[sn], Y0, Y1, Y2, pad);
         if (cm_sw) swn = cm_sw[sn];
       }
-      Fac<T> o;
-      fac_obs(ctl, X0, X1, X2, sw, o);
-      T e0, e1;
-      jc_times_fac(o, xl, e0, e1);
-      const T a0 = o.A[0] * e0 + o.A[3] * e1;
-      const T a1 = o.A[1] * e0 + o.A[4] * e1;
-      const T a2 = o.A[2] * e0 + o.A[5] * e1;
-      const T z0 = ctl[0] * a0 + ctl[3] * a1 + ctl[6] * a2;
-      const T z1 = ctl[1] * a0 + ctl[4] * a1 + ctl[7] * a2;
-      const T z2 = ctl[2] * a0 + ctl[5] * a1 + ctl[8] * a2;
+      T z0, z1, z2;
+      a1_obs(ctl, xl, X0, X1, X2, sw, z0, z1, z2);
       store4(zbuf + 4LL * s, z0, z1, z2, T(0));
       s = sn;
       X0 = Y0;
@@ -1304,6 +1313,132 @@ k_pass_a2(const int32_t* __restrict__ pchunk, int P, const int32_t* __restrict__
     for (int q = s0 + threadIdx.x; q < s1; q += CHUNK_THREADS) {
       T a, b, c, d;
       load4(zbuf + 4LL * pm2cm[q], a, b, c, d);
+      z0 += a;
+      z1 += b;
+      z2 += c;
+    }
+    double dd[3] = {(double)z0, (double)z1, (double)z2};
+    block_sum_all<3>(dd);
+    if (threadIdx.x == 0)
+      gd = pass_a_point<T, MODE>(j0, P, (T)dd[0], (T)dd[1], (T)dd[2], Vinv, ptab, dp, y0, gp, pts_buf, cur);
+  }
+  if (MODE == 1) {
+    double v[1] = {gd};
+    block_sum_all<1>(v);
+    if (threadIdx.x == 0) dot_gp[blockIdx.x] = v[0];
+  }
+}
+
+// Fused pass A (recompute mode, point-major, one CTA per chunk of points):
+//   t_j = V*_j^{-1} sum_{k in pt j} Jp_k^T (Jc_k x_c(k))
+// in one kernel.  The points of a chunk are seen by few cameras (points are
+// numbered by their first camera): the chunk's cameras -- their tables and
+// vectors x_c -- are staged in shared memory (at most FA_CAMS of them, the
+// list built in the symbolic phase, pm_lc the position of each slot's camera
+// in it), so no per-observation camera data and no per-observation
+// intermediate leave the SM.  Each thread issues all loads of its slots and
+// of its point before the first barrier.  The per-observation products and
+// the per-point sums are those of passes A1 and A2 (same order).  MODE as in
+// k_pass_a2.
+constexpr int FA_CAMS = 128;
+constexpr int FA_CT = 17;  // padded strides: different cameras in different banks
+constexpr int FA_XV = 13;
+
+template <typename T, int MODE>
+static __global__ void __launch_bounds__(CHUNK_THREADS)
+k_pass_fa(const int32_t* __restrict__ pchunk, int P, const int32_t* __restrict__ rowptr_pt,
+          const int32_t* __restrict__ pm_pt, const int16_t* __restrict__ pm_lc, const T* __restrict__ pm_sw,
+          const int32_t* __restrict__ chunk_cams, const int32_t* __restrict__ chunk_cam_ptr,
+          const T* __restrict__ camtab, const T* __restrict__ xc, const T* __restrict__ Vinv,
+          const DevState* __restrict__ st, int check_done, T* __restrict__ ptab, T* __restrict__ dp,
+          const T* __restrict__ y0, const double* __restrict__ gp, T* __restrict__ pts_buf,
+          double* __restrict__ dot_gp) {
+  if (MODE == 0 && check_done && st->pcg_done) return;
+  __shared__ T sct[FA_CAMS * FA_CT];
+  __shared__ T sxv[FA_CAMS * FA_XV];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sz = reinterpret_cast<T*>(smem_raw);  // [CHUNK_SLOTS][4]
+  constexpr int U = CHUNK_SLOTS / CHUNK_THREADS;
+  const int k = blockIdx.x;
+  const int j0 = pchunk[k], j1 = pchunk[k + 1];
+  const int s0 = rowptr_pt[j0], s1 = rowptr_pt[j1];
+  const int c0 = chunk_cam_ptr[k], nc = chunk_cam_ptr[k + 1] - c0;
+  const bool small = s1 - s0 <= CHUNK_SLOTS;
+  // this thread's slots: index loads first, then the point gathers
+  int jj[U], ll[U];
+  T sw[U], X[U][3];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int q = s0 + threadIdx.x + u * CHUNK_THREADS;
+    const bool v = small && q < s1;
+    jj[u] = v ? pm_pt[q] : -1;
+    ll[u] = v ? pm_lc[q] : 0;
+    sw[u] = (v && pm_sw) ? pm_sw[q] : T(1);
+  }
+  // this thread's first point: its slot range and V*^{-1}
+  const int jp = j0 + threadIdx.x;
+  int p0 = 0, p1 = 0;
+  T vi[6] = {};
+  if (small && jp < j1) {
+    p0 = rowptr_pt[jp];
+    p1 = rowptr_pt[jp + 1];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) vi[i] = Vinv[6LL * jp + i];
+  }
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    T pad;
+    if (jj[u] >= 0) load4(ptab + 8LL * jj[u], X[u][0], X[u][1], X[u][2], pad);
+  }
+  for (int i = threadIdx.x; i < nc * 16; i += CHUNK_THREADS) {
+    const int l = i >> 4, e = i & 15;
+    if (e < 15) sct[l * FA_CT + e] = camtab[(long long)CT * chunk_cams[c0 + l] + e];
+  }
+  for (int i = threadIdx.x; i < nc * 9; i += CHUNK_THREADS) {
+    const int l = i / 9, e = i % 9;
+    sxv[l * FA_XV + e] = xc[(long long)PV * chunk_cams[c0 + l] + e];
+  }
+  __syncthreads();
+  const int cur = st->cur;
+  double gd = 0.0;
+  if (small) {
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (jj[u] < 0) continue;
+      T z0, z1, z2;
+      a1_obs(sct + ll[u] * FA_CT, sxv + ll[u] * FA_XV, X[u][0], X[u][1], X[u][2], sw[u], z0, z1, z2);
+      store4(sz + 4 * (threadIdx.x + u * CHUNK_THREADS), z0, z1, z2, T(0));
+    }
+    __syncthreads();
+    for (int j = jp; j < j1; j += CHUNK_THREADS) {
+      if (j != jp) {
+        p0 = rowptr_pt[j];
+        p1 = rowptr_pt[j + 1];
+      }
+      T z0 = 0, z1 = 0, z2 = 0;
+      for (int q = p0; q < p1; ++q) {
+        z0 += sz[4 * (q - s0)];
+        z1 += sz[4 * (q - s0) + 1];
+        z2 += sz[4 * (q - s0) + 2];
+      }
+      if (j == jp && MODE == 0) {
+        // V*^{-1} already in registers: t_j as in pass_a_point
+        const T t0 = vi[0] * z0 + vi[1] * z1 + vi[2] * z2;
+        const T t1 = vi[1] * z0 + vi[3] * z1 + vi[4] * z2;
+        const T t2 = vi[2] * z0 + vi[4] * z1 + vi[5] * z2;
+        store4(ptab + 8LL * j + 4, t0, t1, t2, T(0));
+      } else {
+        gd += pass_a_point<T, MODE>(j, P, z0, z1, z2, Vinv, ptab, dp, y0, gp, pts_buf, cur);
+      }
+    }
+  } else {
+    T z0 = 0, z1 = 0, z2 = 0;
+    for (int q = s0 + threadIdx.x; q < s1; q += CHUNK_THREADS) {
+      const int l = pm_lc[q];
+      T X0, X1, X2, pad;
+      load4(ptab + 8LL * pm_pt[q], X0, X1, X2, pad);
+      T a, b, c;
+      a1_obs(sct + l * FA_CT, sxv + l * FA_XV, X0, X1, X2, pm_sw ? pm_sw[q] : T(1), a, b, c);
       z0 += a;
       z1 += b;
       z2 += c;

@@ -36,6 +36,12 @@ struct ba_problem {
   int32_t* pm2cm = nullptr;  // camera-major slot of each point-major slot
   int nchunks = 0;
   int32_t* pchunk = nullptr;  // [nchunks + 1] first point of each point chunk
+  // fused point-major pass A (recompute mode): the distinct cameras of each
+  // point chunk (chunk_cams[chunk_cam_ptr[k] ..]) and each point-major slot's
+  // position in its chunk's list
+  bool fa = false;
+  int32_t *chunk_cams = nullptr, *chunk_cam_ptr = nullptr;
+  int16_t* pm_lc = nullptr;
   void *cm_px = nullptr, *pm_px = nullptr, *px_in = nullptr;
   int npieces = 0;
   int32_t *piece_cam = nullptr, *piece_beg = nullptr, *piece_end = nullptr, *cam_piece_ptr = nullptr;

@@ -123,3 +123,31 @@ def test_pcg_rounding_sensitivity_is_the_systems_not_the_kernels():
     with problem(sc, pix, "f64") as prob:
         dc, _, _, _ = prob.damped_solve(lam, 50, 0.0)
     assert rel_err(np64(dc), dc_ref) < 10 * band
+
+
+@pytest.mark.parametrize("scene", ["banded", "scattered"])
+def test_recompute_pass_a_variants_match_oracle_pcg(scene):
+    """The recompute mode runs the fused point-major pass A when every point
+    chunk is seen by at most 128 cameras (banded visibility, the ring) and
+    passes A1 + A2 otherwise (300 cameras, each point seen by a uniformly
+    random subset); both give the oracle's truncated PCG iterate."""
+    if scene == "banded":
+        sc = small_ring(huber=True)
+    else:
+        sc = scenegen.arc_scene(300, 1500, seed=21, views_lo=4, views_hi=12)
+    pix = orc.pixels_from_scene(sc)
+    lam = 1e-4
+    blk = orc.assemble(sc.cams_init, sc.points_init, sc.cam_idx, sc.pt_idx, pix, sc.huber_delta)
+    opts = orc.LMOptions(solver="pcg", pcg_tol=0.0, pcg_maxiter=10)
+    dc_ref, dp_ref, _, _ = orc.solve_damped(blk, sc.cam_idx, sc.pt_idx, lam, opts)
+    with problem(sc, pix, "f64", jacobian="recompute") as prob:
+        dc, dp, its, _ = prob.damped_solve(lam, 10, 0.0)
+        per, _ = prob.profile_trials(1)
+    assert its == 10
+    assert rel_err(np64(dc), dc_ref) < 1e-9
+    assert rel_err(np64(dp), dp_ref) < 1e-9
+    fused, split = per["pass_fa"][1], per["pass_a1"][1]
+    if scene == "banded":
+        assert fused > 0 and split == 0
+    else:
+        assert fused == 0 and split > 0
