@@ -60,8 +60,10 @@ def parse():
     ap.add_argument("--jacobian", choices=["auto", "recompute", "store"], default="auto")
     ap.add_argument("--points", type=int, default=0,
                     help="profiling only: same recipe with fewer points")
-    ap.add_argument("--workload", choices=["ba4000", "batch512"], default="ba4000",
-                    help="batch512: 512 sliding-window problems solved by one persistent launch")
+    ap.add_argument("--workload", choices=["ba4000", "batch512", "learned"], default="ba4000",
+                    help="batch512: 512 sliding-window problems solved by one persistent launch; "
+                         "learned: time to 1e-6 relative cost with the learned block-Jacobi correction")
+    ap.add_argument("--train-scenes", type=int, default=24, help="learned: training scenes")
     ap.add_argument("--no-sequential", action="store_true",
                     help="batch512: skip the 512 sequential single-problem solves")
     return ap.parse_args()
@@ -554,12 +556,113 @@ def run_batch(args):
     bt.close()
 
 
+# --------------------------------------------------------------------------
+# learned: the learned block-Jacobi correction against block-Jacobi
+# --------------------------------------------------------------------------
+
+LEARN_PCG_TOL = 1e-5
+LEARN_PCG_MAXITER = 500
+LEARN_TRIALS = 20
+
+
+def _timed_trials(prob, trials, stream):
+    """Run `trials` LM trials one by one with an event after each; returns
+    (seconds after each trial, cost after each trial, PCG iterations)."""
+    import torch
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(trials + 1)]
+    evs[0].record(stream)
+    for i in range(trials):
+        prob.solve(1)
+        evs[i + 1].record(stream)
+    torch.cuda.synchronize()
+    st = prob.stats(cap=trials, raise_nonfinite=False)
+    t = [evs[0].elapsed_time(e) / 1000.0 for e in evs[1:]]
+    cost = [s["cost_trial"] if s["accepted"] else s["cost"] for s in st]
+    bad = sum(1 for s in st if not math.isfinite(s["cost_trial"]))
+    return t, cost, [s["pcg_iters"] for s in st], bad
+
+
+def run_learned(args):
+    import torch
+    import paper_2409_12190_gb300 as ba
+    from paper_2409_12190_gb300 import build as bbuild, learned
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    bbuild.build()
+
+    def make(scene, prec="f32", tol=1e-4, maxiter=50):
+        ci = torch.from_numpy(scene.cam_idx).to(dev)
+        pi = torch.from_numpy(scene.pt_idx).to(dev)
+        dt = torch.float32 if prec == "f32" else torch.float64
+        px = ba.project(torch.tensor(scene.cams_gt, dtype=dt, device=dev), torch.tensor(scene.points_gt, dtype=dt, device=dev),
+                        ci, pi) + torch.tensor(scene.noise, dtype=dt, device=dev)
+        return ba.Problem(scene.cams_init, scene.points_init, ci, pi, px,
+                          ba.Options(precision=prec, pcg_maxiter=maxiter, pcg_tol=tol), device=dev)
+
+    # training set: ring scenes of 500-2,000 cameras (seeds 1000..)
+    t0 = time.perf_counter()
+    rng = np.random.default_rng(1000)
+    samples = []
+    for i in range(args.train_scenes):
+        C = int(rng.integers(500, 2001))
+        sc = scenegen.ring_scene(C, 30 * C, seed=1000 + i, view_p=1.0 / 5.7, name=f"train{i}")
+        with make(sc) as pr:
+            samples.append(learned.collect(pr, seed=i))
+    t_collect = time.perf_counter() - t0
+    n_samples = sum(s[0].shape[0] for s in samples)
+    t0 = time.perf_counter()
+    params, hist = learned.train(samples, epochs=100, lr=2e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    del samples
+
+    # evaluation on the bench scene: block-Jacobi, then the learned blocks
+    scene = scenegen.config_scene(WORKLOAD)
+    stream = torch.cuda.current_stream()
+    runs = {}
+    for name, par in (("block_jacobi", None), ("learned", params)):
+        with make(scene, tol=LEARN_PCG_TOL, maxiter=LEARN_PCG_MAXITER) as pr:
+            pr.set_preconditioner(par)
+            pr.solve(1)  # warm-up: captures the trial graph
+            pr.set_params(torch.tensor(scene.cams_init, dtype=torch.float32, device=dev),
+                          torch.tensor(scene.points_init, dtype=torch.float32, device=dev))
+            pr.set_lambda(1e-4)
+            pr.stats()
+            runs[name] = _timed_trials(pr, LEARN_TRIALS, stream)
+    f_ref = min(min(r[1]) for r in runs.values())
+    out = {}
+    for name, (t, cost, pcg, bad) in runs.items():
+        hit = next((i for i, c in enumerate(cost) if c <= (1 + 1e-6) * f_ref), None)
+        out[name] = {"time_to_cost_s": t[hit] if hit is not None else None, "trials_to_cost": None if hit is None else hit + 1,
+                     "pcg_iters_to_cost": None if hit is None else sum(pcg[:hit + 1]), "final_cost": cost[-1],
+                     "ms_per_pcg_iter": 1000.0 * t[-1] / max(1, sum(pcg)), "pcg_iters_per_trial": pcg,
+                     "nonfinite_trials": bad}
+    value = out["learned"]["time_to_cost_s"]
+    line = {"metric": METRIC, "value": value, "unit": "s to 1e-6 relative cost", "n_gpus": 1,
+            "steps": LEARN_TRIALS, "warmup": 1, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": scene.name, "cameras": scene.C, "points": scene.P, "observations": scene.O,
+                       "pcg": f"tol {LEARN_PCG_TOL}, maxiter {LEARN_PCG_MAXITER}",
+                       "f_ref": f_ref, "f_ref_rule": "lowest cost either run reaches in the trials",
+                       "training": {"scenes": args.train_scenes, "cameras": "500-2000", "points_per_camera": 30,
+                                    "samples": n_samples, "epochs": 100, "collect_s": t_collect, "train_s": t_train,
+                                    "loss_first_last": [hist[0], hist[-1]]}},
+            "block_jacobi": out["block_jacobi"], "learned": out["learned"],
+            "speedup_time_to_cost": (out["block_jacobi"]["time_to_cost_s"] / value) if value and out["block_jacobi"]["time_to_cost_s"] else None}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batch512":
         run_batch(args)
+    elif args.workload == "learned":
+        run_learned(args)
     else:
         run_ours(args)
 
