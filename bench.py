@@ -60,7 +60,7 @@ def parse():
     ap.add_argument("--jacobian", choices=["auto", "recompute", "store"], default="auto")
     ap.add_argument("--points", type=int, default=0,
                     help="profiling only: same recipe with fewer points")
-    ap.add_argument("--workload", choices=["ba4000", "batch512", "learned"], default="ba4000",
+    ap.add_argument("--workload", choices=["ba4000", "batch512", "learned", "adjoint"], default="ba4000",
                     help="batch512: 512 sliding-window problems solved by one persistent launch; "
                          "learned: time to 1e-6 relative cost with the learned block-Jacobi correction")
     ap.add_argument("--train-scenes", type=int, default=24, help="learned: training scenes")
@@ -655,6 +655,74 @@ def run_learned(args):
     print(json.dumps(line), flush=True)
 
 
+# --------------------------------------------------------------------------
+# adjoint: the implicit-function adjoint (ba_backward) on the ba64 scene
+# --------------------------------------------------------------------------
+
+def run_adjoint(args):
+    import torch
+    import paper_2409_12190_gb300 as ba
+    from paper_2409_12190_gb300 import build as bbuild
+    import oracle as orc
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    bbuild.build()
+    scene = scenegen.config_scene("ba64")
+    ci = torch.from_numpy(scene.cam_idx).to(dev)
+    pi = torch.from_numpy(scene.pt_idx).to(dev)
+    px = ba.project(torch.tensor(scene.cams_gt, device=dev), torch.tensor(scene.points_gt, device=dev), ci, pi) + \
+        torch.tensor(scene.noise, device=dev)
+    fixed = np.zeros((scene.C, 9), dtype=bool)
+    fixed[0, :] = True
+    fixed[1, 3] = True
+    prob = ba.Problem(scene.cams_init, scene.points_init, ci, pi, px,
+                      ba.Options(precision="f64", pcg_maxiter=600, pcg_tol=1e-12, lambda0=1e-6), device=dev)
+    prob.set_fixed(torch.from_numpy(fixed))
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    prob.solve(30)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    fwd_ms = e0.elapsed_time(e1)
+    cams, pts = prob.params()
+    tgt = torch.tensor(scene.cams_gt[:, 3:6], device=dev)
+    g = torch.zeros_like(cams)
+    g[:, 3:6] = 2.0 * (cams[:, 3:6] - tgt)
+    lam, maxiter, tol = 1e-8, 2000, 1e-12
+    for _ in range(args.warmup):
+        prob.backward(g, None, lam=lam, maxiter=maxiter, tol=tol)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        dpix, dc0, _, its, rel = prob.backward(g, None, lam=lam, maxiter=maxiter, tol=tol)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    # the oracle's adjoint at the GPU's converged parameters, timed on the host
+    t0 = time.perf_counter()
+    ref_pix, ref_c0, _, _ = orc.adjoint_schur(cams.cpu().numpy(), pts.cpu().numpy(), scene.cam_idx, scene.pt_idx,
+                                              px.cpu().numpy(), g.cpu().numpy(), np.zeros((scene.P, 3)), fixed,
+                                              0.0, lam)
+    t_orc = time.perf_counter() - t0
+    err = float(np.max(np.abs(dpix.cpu().numpy() - ref_pix)) / np.max(np.abs(ref_pix)))
+    line = {"metric": METRIC, "value": 1000.0 / ms, "unit": "adjoint solves/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "ba64", "cameras": scene.C, "points": scene.P, "observations": scene.O,
+                       "loss": "sum over cameras of |t - t_gt|^2", "gauge": "camera 0 and t_x of camera 1 frozen",
+                       "forward": "30 LM trials, FP64, PCG tol 1e-12", "adjoint_pcg": f"tol {tol}, maxiter {maxiter}",
+                       "step": "one ba_backward: linearisation, Schur/PCG solve of H v = dL/dtheta, dL/dpixels"},
+            "forward_ms_30_trials": fwd_ms, "adjoint_pcg_iters": its, "adjoint_rel_res": rel,
+            "max_rel_err_vs_oracle_dense_adjoint": err,
+            "cpu_baseline": {"value": 1.0 / t_orc, "unit": "adjoint solves/s", "cores": 1, "kind": "oracle",
+                             "sample": f"the whole ba64 adjoint (explicit Schur, dense Cholesky), {t_orc:.1f} s"}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -663,6 +731,8 @@ def main():
         run_batch(args)
     elif args.workload == "learned":
         run_learned(args)
+    elif args.workload == "adjoint":
+        run_adjoint(args)
     else:
         run_ours(args)
 

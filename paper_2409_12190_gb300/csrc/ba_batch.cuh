@@ -22,6 +22,8 @@
 // atomic is the work-list counter.
 #pragma once
 
+#include <stddef.h>
+
 #include "ba_kernels.cuh"
 
 namespace ba {
@@ -99,10 +101,19 @@ struct BShared {
   T pT[BMAXC][PV];  // PCG direction in the passes' form
   T xT[BMAXC][PV];  // camera step in the passes' form
   T sce[CT];        // camera table of the evaluated parameters (cost)
+  // recompute mode: padded copies of the camera tables and of the vector a
+  // point-major pass reads (neighbouring slots use different cameras), and
+  // the per-observation products of one point chunk
+  T fct[BMAXC][17];
+  T fxv[BMAXC][13];
+  alignas(16) T sz[CHUNK_SLOTS * 4];  // read and written as 4-vectors
   double lam, F, rz_old, bb, pcg_rel, dot_gc;
   long long trials;
   int cur, need_lin, pcg_iters, fallbacks, widx;
 };
+
+static_assert(offsetof(BShared<float>, sz) % 16 == 0 && offsetof(BShared<double>, sz) % 16 == 0,
+              "4-vector accesses to the chunk buffer need 16-byte alignment");
 
 // ---------------------------------------------------------------------------
 // Block reductions with the single-problem kernels' order (BT threads, 8
@@ -265,6 +276,77 @@ __device__ __forceinline__ void batch_pass_a1(const BatchArgs<T>& a, const BRang
   }
 }
 
+// Point-major pass A of the recompute mode over the problem's point chunks
+// (the cameras' padded tables and vectors in shared memory, the vector in
+// S.fxv): z per observation into shared memory, then per point t_j
+// (MODE 0, into the point table) or the back-substitution (MODE 1, with
+// per-chunk partials of g_p . dp).  The same per-observation products and
+// per-point sums as passes A1 + A2.
+template <typename T, int MODE>
+__device__ __forceinline__ void batch_pass_fa(const BatchArgs<T>& a, const BRange<T>& R, BShared<T>& S, int cur) {
+  constexpr int U = CHUNK_SLOTS / BT;
+  for (int kk = 0; kk < R.nk; ++kk) {
+    const int js = a.bchunk[R.k0 + kk], je = a.bchunk[R.k0 + kk + 1];
+    const int s0 = a.rowptr_pt[js], s1 = a.rowptr_pt[je];
+    double gd = 0.0;
+    if (s1 - s0 <= CHUNK_SLOTS) {
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int q = s0 + threadIdx.x + u * BT;
+        if (q >= s1) continue;
+        const int j = a.pm_pt[q];
+        const int l = a.pm_cam[q] - R.c0;
+        T X0, X1, X2, pad;
+        load4(a.ptab + 8LL * j, X0, X1, X2, pad);
+        T z0, z1, z2;
+        a1_obs(&S.fct[l][0], &S.fxv[l][0], X0, X1, X2, a.pm_sw ? a.pm_sw[q] : T(1), z0, z1, z2);
+        store4(S.sz + 4 * (q - s0), z0, z1, z2, T(0));
+      }
+      __syncthreads();
+      for (int j = js + threadIdx.x; j < je; j += BT) {
+        T z0 = 0, z1 = 0, z2 = 0;
+        const int q1 = a.rowptr_pt[j + 1];
+        for (int q = a.rowptr_pt[j]; q < q1; ++q) {
+          z0 += S.sz[4 * (q - s0)];
+          z1 += S.sz[4 * (q - s0) + 1];
+          z2 += S.sz[4 * (q - s0) + 2];
+        }
+        gd += pass_a_point<T, MODE>(j, a.P, z0, z1, z2, a.Vinv, a.ptab, a.dp, a.y0, a.gp, a.pts, cur);
+      }
+      __syncthreads();
+    } else {
+      T z0 = 0, z1 = 0, z2 = 0;
+      for (int q = s0 + threadIdx.x; q < s1; q += BT) {
+        const int l = a.pm_cam[q] - R.c0;
+        T X0, X1, X2, pad;
+        load4(a.ptab + 8LL * a.pm_pt[q], X0, X1, X2, pad);
+        T u0, u1, u2;
+        a1_obs(&S.fct[l][0], &S.fxv[l][0], X0, X1, X2, a.pm_sw ? a.pm_sw[q] : T(1), u0, u1, u2);
+        z0 += u0;
+        z1 += u1;
+        z2 += u2;
+      }
+      double dd[3] = {(double)z0, (double)z1, (double)z2};
+      bred_all<3>(S, dd);
+      if (threadIdx.x == 0)
+        gd = pass_a_point<T, MODE>(js, a.P, (T)dd[0], (T)dd[1], (T)dd[2], a.Vinv, a.ptab, a.dp, a.y0, a.gp, a.pts,
+                                   cur);
+    }
+    if (MODE == 1) {
+      double v[1] = {gd};
+      bred_all<1>(S, v);
+      if (threadIdx.x == 0) a.dot_gp[R.k0 + kk] = v[0];
+    }
+  }
+}
+
+// Padded copy of camera vectors (the passes' form) for batch_pass_fa.
+template <typename T>
+__device__ __forceinline__ void batch_stage_fxv(BShared<T>& S, const BRange<T>& R, T (*xv)[PV]) {
+  for (int i = threadIdx.x; i < R.nc * 9; i += BT) S.fxv[i / 9][i % 9] = xv[i / 9][i % 9];
+  __syncthreads();
+}
+
 // The linearisation (a1 + a2) at the current parameters.
 template <typename T, bool MF>
 __device__ void batch_linearise(const BatchArgs<T>& a, const BRange<T>& R, BShared<T>& S, int cur) {
@@ -274,6 +356,8 @@ __device__ void batch_linearise(const BatchArgs<T>& a, const BRange<T>& R, BShar
     camera_table(a.cams + (long long)cur * 9 * a.C + 9LL * c, S.ct[threadIdx.x]);
 #pragma unroll
     for (int i = 0; i < CT; ++i) a.camtab[(long long)CT * c + i] = S.ct[threadIdx.x][i];
+#pragma unroll
+    for (int i = 0; i < 15; ++i) S.fct[threadIdx.x][i] = S.ct[threadIdx.x][i];
   }
   for (int j = R.j0 + threadIdx.x; j < R.j1; j += BT) {
     const T* X = pts + 3LL * j;
@@ -412,9 +496,14 @@ __device__ void batch_trial(const BatchArgs<T>& a, const BRange<T>& R, BShared<T
   const bool ok = lc < R.nc;
   const int o = 9 * lc + ci;
   for (int k = 0; k < a.maxiter; ++k) {
-    batch_pass_a1<T, MF>(a, R, S, S.pT);
-    __syncthreads();
-    batch_pass_a2<T, 0>(a, R, S, cur);
+    if (MF) {
+      batch_stage_fxv(S, R, S.pT);
+      batch_pass_fa<T, 0>(a, R, S, cur);
+    } else {
+      batch_pass_a1<T, MF>(a, R, S, S.pT);
+      __syncthreads();
+      batch_pass_a2<T, 0>(a, R, S, cur);
+    }
     __syncthreads();
     for (int q = R.q0; q < R.q1; ++q) {
       const int c = a.piece_cam[q] - R.c0;
@@ -522,9 +611,14 @@ __device__ void batch_trial(const BatchArgs<T>& a, const BRange<T>& R, BShared<T
     if (tid == 0) S.dot_gc = gd;
   }
   __syncthreads();
-  batch_pass_a1<T, MF>(a, R, S, S.xT);
-  __syncthreads();
-  batch_pass_a2<T, 1>(a, R, S, cur);
+  if (MF) {
+    batch_stage_fxv(S, R, S.xT);
+    batch_pass_fa<T, 1>(a, R, S, cur);
+  } else {
+    batch_pass_a1<T, MF>(a, R, S, S.xT);
+    __syncthreads();
+    batch_pass_a2<T, 1>(a, R, S, cur);
+  }
   __syncthreads();
 
   // a6: trial cost, model reduction, accept / reject
