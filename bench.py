@@ -74,6 +74,24 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
+def rank_max(value, device, world):
+    """The largest value over all ranks (the slowest rank's time); the value
+    itself on one rank.  No data-path collective: timing only."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def batch_seed(rank):
+    """Seed of a rank's own batch of problems (weak scaling: every rank
+    solves BATCH_N problems of its own, no data-path collective)."""
+    return 4 + 1000 * rank
+
+
 # --------------------------------------------------------------------------
 # the CPU oracle on a bounded sample (cpu_baseline and --impl reference)
 # --------------------------------------------------------------------------
@@ -288,11 +306,7 @@ def run_ours(args):
     launches = ba.kernel_launch_count() - n0
     clk = clocks.stop() if clocks else None
     ms = e0.elapsed_time(e1)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = rank_max(ms, dev, world)
     trials = prob.stats(cap=args.steps)
     value = world * args.steps / (ms / 1000.0)
 
@@ -352,11 +366,7 @@ def run_ours(args):
         cost, _ = prob.scalars()
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = rank_max(e2e_s, dev, world)
     e2e = {"value": world * args.e2e_steps / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": (9 * C + 3 * P + 2 * O) * 4,
            "d2h_bytes_per_step": (9 * C + 3 * P) * 4 + 8, "steps": args.e2e_steps}
@@ -413,7 +423,7 @@ def run_batch(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
     bbuild.build()
-    scenes = scenegen.batch_scenes(BATCH_N, seed=4)
+    scenes = scenegen.batch_scenes(BATCH_N, seed=batch_seed(rank))
     O = sum(s.O for s in scenes)
     inputs = []
     for s in scenes:
@@ -452,10 +462,7 @@ def run_batch(args):
     launches = ba.kernel_launch_count() - n0
     clk = clocks.stop() if clocks else None
     ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = rank_max(ms, dev, world)
     stats = bt.stats()
     pcg_total = sum(t["pcg_iters"] for st in stats for t in st)
     costs, _ = bt.scalars()
