@@ -161,7 +161,10 @@ def test_batch_f64_matches_oracle_per_trial():
                                    orc.LMOptions(solver="cholesky"))
         for g, r in zip(bstats[b], ref):
             assert abs(g["cost_trial"] - r["cost_trial"]) <= 1e-9 * r["cost"], (b, g, r)
-            assert g["accepted"] == r["accepted"]
+            # a trial that changes the cost by less than that tolerance is
+            # decided by rounding: its accept flag is compared only above it
+            if abs(r["cost_trial"] - r["cost"]) > 1e-9 * r["cost"]:
+                assert g["accepted"] == r["accepted"]
         scale = max(np.max(np.abs(c_ref)), 1.0)
         assert np.max(np.abs(np64(bparams[b][0]) - c_ref)) <= 1e-7 * scale
         assert np.max(np.abs(np64(bparams[b][1]) - p_ref)) <= 1e-7 * max(np.max(np.abs(p_ref)), 1.0)
