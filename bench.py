@@ -64,6 +64,8 @@ def parse():
                     help="batch512: 512 sliding-window problems solved by one persistent launch; "
                          "learned: time to 1e-6 relative cost with the learned block-Jacobi correction")
     ap.add_argument("--train-scenes", type=int, default=24, help="learned: training scenes")
+    ap.add_argument("--batch-problems", type=int, default=512,
+                    help="batch512: problems per rank (profiling only: a smaller batch of the same recipe)")
     ap.add_argument("--no-sequential", action="store_true",
                     help="batch512: skip the 512 sequential single-problem solves")
     return ap.parse_args()
@@ -423,7 +425,8 @@ def run_batch(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
     bbuild.build()
-    scenes = scenegen.batch_scenes(BATCH_N, seed=batch_seed(rank))
+    n_prob = args.batch_problems
+    scenes = scenegen.batch_scenes(n_prob, seed=batch_seed(rank))
     O = sum(s.O for s in scenes)
     inputs = []
     for s in scenes:
@@ -467,7 +470,7 @@ def run_batch(args):
     pcg_total = sum(t["pcg_iters"] for st in stats for t in st)
     costs, _ = bt.scalars()
     # problem-iterations per second over all ranks
-    value = world * BATCH_N * BATCH_ITERS * args.steps / (ms / 1000.0)
+    value = world * n_prob * BATCH_ITERS * args.steps / (ms / 1000.0)
 
     # the solve alone (one persistent launch, no reset) for the roofline
     bt.reset()
@@ -505,7 +508,7 @@ def run_batch(args):
         op.copy_(pts_d, non_blocking=True)
         torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    e2e = {"value": world * BATCH_N * BATCH_ITERS * args.e2e_steps / e2e_s, "unit": "problem LM iters/s",
+    e2e = {"value": world * n_prob * BATCH_ITERS * args.e2e_steps / e2e_s, "unit": "problem LM iters/s",
            "h2d_bytes_per_step": (9 * C + 3 * P) * 4, "d2h_bytes_per_step": (9 * C + 3 * P) * 4,
            "steps": args.e2e_steps}
 
@@ -529,7 +532,7 @@ def run_batch(args):
             F, _ = pr.scalars()
             worst = max(worst, abs(costs[b] - F) / F)
             pr.close()
-        seq = {"ms": tot, "problem_iters_per_s": BATCH_N * BATCH_ITERS / (tot / 1000.0),
+        seq = {"ms": tot, "problem_iters_per_s": n_prob * BATCH_ITERS / (tot / 1000.0),
                "speedup_of_batch": tot / solve_ms, "max_rel_final_cost_diff": worst}
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
@@ -543,18 +546,19 @@ def run_batch(args):
             n_done += 1
             obs_done += s.O
         dt = time.perf_counter() - t0
-        rate = n_done * BATCH_ITERS / dt * (obs_done / n_done) / (O / BATCH_N)
+        rate = n_done * BATCH_ITERS / dt * (obs_done / n_done) / (O / n_prob)
         cpu = {"value": rate, "unit": "problem LM iters/s", "cores": 1, "kind": "oracle",
-               "sample": f"{n_done} of {BATCH_N} problems ({obs_done} observations), {BATCH_ITERS} LM trials "
+               "sample": f"{n_done} of {n_prob} problems ({obs_done} observations), {BATCH_ITERS} LM trials "
                          f"each, {dt:.1f} s; rate scaled to the mean problem size"}
     line = {"metric": METRIC, "value": value, "unit": "problem LM iters/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": "batch512", "problems": BATCH_N, "lm_iters_per_problem": BATCH_ITERS,
+            "config": {"workload": "batch512" if n_prob == BATCH_N else f"batch{n_prob}", "problems": n_prob,
+                       "lm_iters_per_problem": BATCH_ITERS,
                        "cameras": bt.C, "points": bt.P, "observations": O,
                        "pcg": f"block-Jacobi, maxiter {PCG_MAXITER}, tol {PCG_TOL}",
-                       "pcg_iters_mean": pcg_total / max(1, BATCH_N * BATCH_ITERS),
+                       "pcg_iters_mean": pcg_total / max(1, n_prob * BATCH_ITERS),
                        "step": "reset + one persistent launch solving every problem for 10 LM trials",
                        "launch": cfg, "l2": "per-problem arrays L2-resident by design; no flush"},
             "gpu_launches": launches, "clocks": clk, "roofline": roofline, "solve_ms": solve_ms,
