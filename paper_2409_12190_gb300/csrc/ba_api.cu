@@ -10,6 +10,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "ba.h"
@@ -154,9 +155,11 @@ void enqueue_schur_product(ba_problem* h, const T* xc, int k, int check_done) {
     }
     {
       Prof pr(h, BA_K_PASS_B, k);
-      k_pass_b<T, MF><<<h->npieces, PIECE_THREADS, 0, s>>>(h->piece_cam, h->piece_beg, h->piece_end, h->cm_pt,
-                                                          (const T*)h->Jcm, (const T*)h->cm_sw, (const T*)h->ptab,
-                                                          (const T*)h->camtab, h->st, check_done, h->O, h->part);
+      // FP32 recompute mode: two gathers in flight per thread, next indices prefetched
+      constexpr int UB = (MF && std::is_same<T, float>::value) ? 2 : 1;
+      k_pass_b<T, MF, UB, (UB > 1)><<<h->npieces, PIECE_THREADS, 0, s>>>(
+          h->piece_cam, h->piece_beg, h->piece_end, h->cm_pt, (const T*)h->Jcm, (const T*)h->cm_sw,
+          (const T*)h->ptab, (const T*)h->camtab, h->st, check_done, h->O, h->part);
     }
     count_launch(2);
     return;
@@ -175,9 +178,10 @@ void enqueue_schur_product(ba_problem* h, const T* xc, int k, int check_done) {
   }
   {
     Prof pr(h, BA_K_PASS_B, k);
-    k_pass_b<T, MF><<<h->npieces, PIECE_THREADS, 0, s>>>(h->piece_cam, h->piece_beg, h->piece_end, h->cm_pt,
-                                                        (const T*)h->Jcm, (const T*)h->cm_sw, (const T*)h->ptab,
-                                                        (const T*)h->camtab, h->st, check_done, h->O, h->part);
+    constexpr int UB = (MF && std::is_same<T, float>::value) ? 2 : 1;
+    k_pass_b<T, MF, UB, (UB > 1)><<<h->npieces, PIECE_THREADS, 0, s>>>(
+        h->piece_cam, h->piece_beg, h->piece_end, h->cm_pt, (const T*)h->Jcm, (const T*)h->cm_sw,
+        (const T*)h->ptab, (const T*)h->camtab, h->st, check_done, h->O, h->part);
   }
   count_launch(3);
 }

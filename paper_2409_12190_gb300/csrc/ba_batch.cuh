@@ -513,7 +513,9 @@ __device__ void batch_trial(const BatchArgs<T>& a, const BRange<T>& R, BShared<T
       T acc[9];
 #pragma unroll
       for (int i = 0; i < 9; ++i) acc[i] = T(0);
-      pass_b_range<T, MF, BT>(a.piece_beg[q], a.piece_end[q], a.cm_pt, a.Jcm, a.cm_sw, a.ptab, ctl, a.O, acc);
+      // FP32 recompute mode: two gathers in flight per thread, next indices prefetched
+      pass_b_range<T, MF, BT, (MF && sizeof(T) == 4) ? 2 : 1, (MF && sizeof(T) == 4)>(
+          a.piece_beg[q], a.piece_end[q], a.cm_pt, a.Jcm, a.cm_sw, a.ptab, ctl, a.O, acc);
       bred_store<9, false>(acc, S.red, a.part + (long long)PART * q);
     }
     // q = U* p - (pass-B sums), p.q

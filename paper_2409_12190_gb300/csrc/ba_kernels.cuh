@@ -1458,11 +1458,63 @@ k_pass_fa(const int32_t* __restrict__ pchunk, int P, const int32_t* __restrict__
 // Pass B over camera-major slots [beg, end), NT threads striding: per-thread
 // partial sum_k Jc_k^T (Jp_k t_p(k)) (9 values; in the recompute mode the
 // first three are still to be multiplied by J_l^T).
-template <typename T, bool MF, int NT>
+template <typename T, bool MF, int NT, int UB = 1, bool PF = false>
 __device__ __forceinline__ void pass_b_range(int beg, int end, const int32_t* __restrict__ cm_pt,
                                              const T* __restrict__ Jcm, const T* __restrict__ cm_sw,
                                              const T* __restrict__ ptab, const T (&ctl)[15], int O, T (&acc)[9]) {
-  if (MF) {
+  if (MF && UB > 1) {
+    // UB slots per thread and round: all index loads, then all point
+    // gathers, then the products (UB gathers in flight per thread); with
+    // PF the next round's indices are loaded before this round's gathers
+    int jn[UB];
+    T swn[UB];
+    if (PF) {
+#pragma unroll
+      for (int u = 0; u < UB; ++u) {
+        const int s = beg + threadIdx.x + u * NT;
+        jn[u] = s < end ? cm_pt[s] : -1;
+        swn[u] = (s < end && cm_sw) ? cm_sw[s] : T(1);
+      }
+    }
+    for (int s0 = beg + threadIdx.x; s0 < end; s0 += UB * NT) {
+      int j[UB];
+      T sw[UB], X[UB][3], t[UB][3];
+#pragma unroll
+      for (int u = 0; u < UB; ++u) {
+        if (PF) {
+          j[u] = jn[u];
+          sw[u] = swn[u];
+          const int s = s0 + (UB + u) * NT;
+          jn[u] = s < end ? cm_pt[s] : -1;
+          swn[u] = (s < end && cm_sw) ? cm_sw[s] : T(1);
+        } else {
+          const int s = s0 + u * NT;
+          j[u] = s < end ? cm_pt[s] : -1;
+          sw[u] = (s < end && cm_sw) ? cm_sw[s] : T(1);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < UB; ++u) {
+        T pad;
+        if (j[u] >= 0) {
+          load4(ptab + 8LL * j[u], X[u][0], X[u][1], X[u][2], pad);
+          load4(ptab + 8LL * j[u] + 4, t[u][0], t[u][1], t[u][2], pad);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < UB; ++u) {
+        if (j[u] < 0) continue;
+        const T g0 = ctl[0] * t[u][0] + ctl[1] * t[u][1] + ctl[2] * t[u][2];
+        const T g1 = ctl[3] * t[u][0] + ctl[4] * t[u][1] + ctl[5] * t[u][2];
+        const T g2 = ctl[6] * t[u][0] + ctl[7] * t[u][1] + ctl[8] * t[u][2];
+        Fac<T> o;
+        fac_obs(ctl, X[u][0], X[u][1], X[u][2], sw[u], o);
+        const T h0 = o.A[0] * g0 + o.A[1] * g1 + o.A[2] * g2;
+        const T h1 = o.A[3] * g0 + o.A[4] * g1 + o.A[5] * g2;
+        jct_fac_acc(o, h0, h1, acc);
+      }
+    }
+  } else if (MF) {
     int s = beg + threadIdx.x;
     T X0 = 0, X1 = 0, X2 = 0, t0 = 0, t1 = 0, t2 = 0, sw = 1, pad;
     if (s < end) {
@@ -1517,9 +1569,10 @@ __device__ __forceinline__ void pass_b_range(int beg, int end, const int32_t* __
   }
 }
 
-// Pass B (camera-major): per piece, sum_k Jc_k^T (Jp_k t_p(k)).
-template <typename T, bool MF>
-static __global__ void __launch_bounds__(PIECE_THREADS)
+// Pass B (camera-major): per piece, sum_k Jc_k^T (Jp_k t_p(k)); UB, PF as in
+// pass_b_range.
+template <typename T, bool MF, int UB = 1, bool PF = false>
+static __global__ void __launch_bounds__(PIECE_THREADS, UB > 1 ? 4 : 1)
 k_pass_b(const int32_t* __restrict__ piece_cam, const int32_t* __restrict__ piece_beg,
          const int32_t* __restrict__ piece_end, const int32_t* __restrict__ cm_pt,
          const T* __restrict__ Jcm, const T* __restrict__ cm_sw, const T* __restrict__ ptab,
@@ -1537,7 +1590,7 @@ k_pass_b(const int32_t* __restrict__ piece_cam, const int32_t* __restrict__ piec
   T acc[9];
 #pragma unroll
   for (int i = 0; i < 9; ++i) acc[i] = T(0);
-  pass_b_range<T, MF, PIECE_THREADS>(piece_beg[b], piece_end[b], cm_pt, Jcm, cm_sw, ptab, ctl, O, acc);
+  pass_b_range<T, MF, PIECE_THREADS, UB, PF>(piece_beg[b], piece_end[b], cm_pt, Jcm, cm_sw, ptab, ctl, O, acc);
   block_sum_store<9, false>(acc, part + (long long)PART * b);
 }
 
