@@ -63,7 +63,7 @@ def parse():
     ap.add_argument("--workload", choices=["ba4000", "batch512", "learned", "adjoint"], default="ba4000",
                     help="batch512: 512 sliding-window problems solved by one persistent launch; "
                          "learned: time to 1e-6 relative cost with the learned block-Jacobi correction")
-    ap.add_argument("--train-scenes", type=int, default=24, help="learned: training scenes")
+    ap.add_argument("--train-scenes", type=int, default=200, help="learned: training scenes")
     ap.add_argument("--batch-problems", type=int, default=512,
                     help="batch512: problems per rank (profiling only: a smaller batch of the same recipe)")
     ap.add_argument("--no-sequential", action="store_true",
@@ -643,21 +643,23 @@ def run_learned(args):
             pr.set_lambda(1e-4)
             pr.stats()
             runs[name] = _timed_trials(pr, LEARN_TRIALS, stream)
-    f_ref = min(min(r[1]) for r in runs.values())
+    # target: within 1e-6 of the best cost BOTH runs reach (the higher of the
+    # two minima), so that each run has a time to it
+    f_ref = max(min(r[1]) for r in runs.values())
     out = {}
     for name, (t, cost, pcg, bad) in runs.items():
         hit = next((i for i, c in enumerate(cost) if c <= (1 + 1e-6) * f_ref), None)
         out[name] = {"time_to_cost_s": t[hit] if hit is not None else None, "trials_to_cost": None if hit is None else hit + 1,
                      "pcg_iters_to_cost": None if hit is None else sum(pcg[:hit + 1]), "final_cost": cost[-1],
-                     "ms_per_pcg_iter": 1000.0 * t[-1] / max(1, sum(pcg)), "pcg_iters_per_trial": pcg,
-                     "nonfinite_trials": bad}
+                     "lowest_cost": min(cost), "ms_per_pcg_iter": 1000.0 * t[-1] / max(1, sum(pcg)),
+                     "pcg_iters_per_trial": pcg, "cost_per_trial": cost, "nonfinite_trials": bad}
     value = out["learned"]["time_to_cost_s"]
     line = {"metric": METRIC, "value": value, "unit": "s to 1e-6 relative cost", "n_gpus": 1,
             "steps": LEARN_TRIALS, "warmup": 1, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": scene.name, "cameras": scene.C, "points": scene.P, "observations": scene.O,
                        "pcg": f"tol {LEARN_PCG_TOL}, maxiter {LEARN_PCG_MAXITER}",
-                       "f_ref": f_ref, "f_ref_rule": "lowest cost either run reaches in the trials",
+                       "f_ref": f_ref, "f_ref_rule": "the higher of the two runs' lowest costs (a cost both reach)",
                        "training": {"scenes": args.train_scenes, "cameras": "500-2000", "points_per_camera": 30,
                                     "samples": n_samples, "epochs": 100, "collect_s": t_collect, "train_s": t_train,
                                     "loss_first_last": [hist[0], hist[-1]]}},
