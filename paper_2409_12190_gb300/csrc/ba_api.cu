@@ -148,10 +148,10 @@ void enqueue_schur_product(ba_problem* h, const T* xc, int k, int check_done) {
   if (MF && h->fa) {
     {
       Prof pr(h, BA_K_PASS_FA, k);
-      k_pass_fa<T, 0><<<h->nchunks, CHUNK_THREADS, CHUNK_SLOTS * 4 * sizeof(T), s>>>(
+      k_pass_fa<T, 0><<<h->nchunks, CHUNK_THREADS, fa_smem<T>(), s>>>(
           h->pchunk, h->P, h->rowptr_pt, h->pm_pt, h->pm_lc, (const T*)h->pm_sw, h->chunk_cams, h->chunk_cam_ptr,
           (const T*)h->camtab, xc, (const T*)h->Vinv, h->st, check_done, (T*)h->ptab, nullptr, nullptr, nullptr,
-          nullptr, nullptr);
+          nullptr, nullptr, h->chunk_hdr);
     }
     {
       Prof pr(h, BA_K_PASS_B, k);
@@ -254,10 +254,10 @@ void enqueue_solve(ba_problem* h, const double* lam_ptr, int maxiter, double tol
   }
   if (MF && h->fa) {
     Prof pr(h, BA_K_BACKSUB);
-    k_pass_fa<T, 1><<<h->nchunks, CHUNK_THREADS, CHUNK_SLOTS * 4 * sizeof(T), s>>>(
+    k_pass_fa<T, 1><<<h->nchunks, CHUNK_THREADS, fa_smem<T>(), s>>>(
         h->pchunk, h->P, h->rowptr_pt, h->pm_pt, h->pm_lc, (const T*)h->pm_sw, h->chunk_cams, h->chunk_cam_ptr,
         (const T*)h->camtab, (const T*)h->xT, (const T*)h->Vinv, h->st, 0, (T*)h->ptab, (T*)h->dp, (const T*)h->y0,
-        h->gp, (T*)h->pts, h->dot_gp);
+        h->gp, (T*)h->pts, h->dot_gp, h->chunk_hdr);
     count_launch(2);
     return;
   }
@@ -520,10 +520,8 @@ ba_status create_impl(ba_problem* h, const void* cams, const void* points, const
   if (sizeof(T) * CHUNK_SLOTS * 9 > 48 * 1024)
     CU(cudaFuncSetAttribute(k_lin_pt<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                             (int)(sizeof(T) * CHUNK_SLOTS * 9)));
-  CU(cudaFuncSetAttribute(k_pass_fa<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                          (int)(sizeof(T) * CHUNK_SLOTS * 4)));
-  CU(cudaFuncSetAttribute(k_pass_fa<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                          (int)(sizeof(T) * CHUNK_SLOTS * 4)));
+  CU(cudaFuncSetAttribute(k_pass_fa<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, fa_smem<T>()));
+  CU(cudaFuncSetAttribute(k_pass_fa<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, fa_smem<T>()));
 
 
   // observation data in both orders
@@ -576,6 +574,17 @@ ba_status create_impl(ba_problem* h, const void* cams, const void* points, const
       CU(cudaMemcpy(h->chunk_cams, list.data(), list.size() * 4, cudaMemcpyHostToDevice));
       CU(cudaMemcpy(h->chunk_cam_ptr, ptr.data(), ptr.size() * 4, cudaMemcpyHostToDevice));
       CU(cudaMemcpy(h->pm_lc, lc.data(), O * 2, cudaMemcpyHostToDevice));
+      // per-chunk headers of the fused pass: j0, j1, s0, s1 | c0, nc, first
+      // camera if the list is a contiguous range (else -1), 0
+      std::vector<int4> hdr(2 * (size_t)h->nchunks);
+      for (int k = 0; k < h->nchunks; ++k) {
+        const int c0 = ptr[k], nc = ptr[k + 1] - ptr[k];
+        const bool contiguous = nc > 0 && list[c0 + nc - 1] - list[c0] == nc - 1;
+        hdr[2 * k] = make_int4(pch[k], pch[k + 1], rq[pch[k]], rq[pch[k + 1]]);
+        hdr[2 * k + 1] = make_int4(c0, nc, contiguous ? list[c0] : -1, 0);
+      }
+      CU(h->alloc(&h->chunk_hdr, hdr.size() * sizeof(int4)));
+      CU(cudaMemcpy(h->chunk_hdr, hdr.data(), hdr.size() * sizeof(int4), cudaMemcpyHostToDevice));
       h->fa = true;
     }
   }

@@ -71,7 +71,7 @@ constexpr int CT_T = 9, CT_F = 12, CT_K1 = 13, CT_K2 = 14, CT_JL = 16;
 constexpr int PV = 12;               // factored PCG vector stride
 constexpr int PART = 64;             // doubles per piece partial (54 used)
 constexpr int CHUNK_SLOTS = 1024;    // max point-major slots per point chunk
-constexpr int CHUNK_PTS = 1024;      // max points per point chunk
+constexpr int CHUNK_PTS = 512;       // max points per point chunk
 constexpr int CHUNK_THREADS = 256;
 
 // Device-resident LM / PCG state; every field is written by exactly one
@@ -1343,30 +1343,36 @@ k_pass_a2(const int32_t* __restrict__ pchunk, int P, const int32_t* __restrict__
 constexpr int FA_CAMS = 128;
 constexpr int FA_CT = 17;  // padded strides: different cameras in different banks
 constexpr int FA_XV = 13;
+// dynamic shared memory of k_pass_fa: z per slot, then the chunk's points
+template <typename T>
+constexpr int fa_smem() { return (CHUNK_SLOTS + CHUNK_PTS) * 4 * (int)sizeof(T); }
 
 template <typename T, int MODE>
-static __global__ void __launch_bounds__(CHUNK_THREADS)
+static __global__ void __launch_bounds__(CHUNK_THREADS, sizeof(T) == 4 ? 5 : 1)
 k_pass_fa(const int32_t* __restrict__ pchunk, int P, const int32_t* __restrict__ rowptr_pt,
           const int32_t* __restrict__ pm_pt, const int16_t* __restrict__ pm_lc, const T* __restrict__ pm_sw,
           const int32_t* __restrict__ chunk_cams, const int32_t* __restrict__ chunk_cam_ptr,
           const T* __restrict__ camtab, const T* __restrict__ xc, const T* __restrict__ Vinv,
           const DevState* __restrict__ st, int check_done, T* __restrict__ ptab, T* __restrict__ dp,
           const T* __restrict__ y0, const double* __restrict__ gp, T* __restrict__ pts_buf,
-          double* __restrict__ dot_gp) {
+          double* __restrict__ dot_gp, const int4* __restrict__ chunk_hdr) {
   if (MODE == 0 && check_done && st->pcg_done) return;
   __shared__ T sct[FA_CAMS * FA_CT];
   __shared__ T sxv[FA_CAMS * FA_XV];
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sz = reinterpret_cast<T*>(smem_raw);  // [CHUNK_SLOTS][4]
+  T* sX = sz + 4 * CHUNK_SLOTS;            // [CHUNK_PTS][4]: the chunk's points
   constexpr int U = CHUNK_SLOTS / CHUNK_THREADS;
   const int k = blockIdx.x;
-  const int j0 = pchunk[k], j1 = pchunk[k + 1];
-  const int s0 = rowptr_pt[j0], s1 = rowptr_pt[j1];
-  const int c0 = chunk_cam_ptr[k], nc = chunk_cam_ptr[k + 1] - c0;
+  // the chunk's header: first/last point and slot, camera list, and the
+  // first camera when the list is a contiguous range (else -1), so every
+  // other load of the kernel depends on this one only
+  const int4 h0 = chunk_hdr[2 * k], h1 = chunk_hdr[2 * k + 1];
+  const int j0 = h0.x, j1 = h0.y, s0 = h0.z, s1 = h0.w, c0 = h1.x, nc = h1.y, cmin = h1.z;
   const bool small = s1 - s0 <= CHUNK_SLOTS;
-  // this thread's slots: index loads first, then the point gathers
+  // this thread's slots: their point, camera position and sqrt(w)
   int jj[U], ll[U];
-  T sw[U], X[U][3];
+  T sw[U];
 #pragma unroll
   for (int u = 0; u < U; ++u) {
     const int q = s0 + threadIdx.x + u * CHUNK_THREADS;
@@ -1385,18 +1391,24 @@ k_pass_fa(const int32_t* __restrict__ pchunk, int P, const int32_t* __restrict__
 #pragma unroll
     for (int i = 0; i < 6; ++i) vi[i] = Vinv[6LL * jp + i];
   }
-#pragma unroll
-  for (int u = 0; u < U; ++u) {
-    T pad;
-    if (jj[u] >= 0) load4(ptab + 8LL * jj[u], X[u][0], X[u][1], X[u][2], pad);
+  // the chunk's points are contiguous: their X, one coalesced row each, not
+  // a gather behind the slot's point index
+  if (small) {
+    for (int p = threadIdx.x; p < j1 - j0; p += CHUNK_THREADS) {
+      T a, b, c, pad;
+      load4(ptab + 8LL * (j0 + p), a, b, c, pad);
+      store4(sX + 4 * p, a, b, c, T(0));
+    }
   }
   for (int i = threadIdx.x; i < nc * 16; i += CHUNK_THREADS) {
     const int l = i >> 4, e = i & 15;
-    if (e < 15) sct[l * FA_CT + e] = camtab[(long long)CT * chunk_cams[c0 + l] + e];
+    const int cam = cmin >= 0 ? cmin + l : chunk_cams[c0 + l];
+    if (e < 15) sct[l * FA_CT + e] = camtab[(long long)CT * cam + e];
   }
   for (int i = threadIdx.x; i < nc * 9; i += CHUNK_THREADS) {
     const int l = i / 9, e = i % 9;
-    sxv[l * FA_XV + e] = xc[(long long)PV * chunk_cams[c0 + l] + e];
+    const int cam = cmin >= 0 ? cmin + l : chunk_cams[c0 + l];
+    sxv[l * FA_XV + e] = xc[(long long)PV * cam + e];
   }
   __syncthreads();
   const int cur = st->cur;
@@ -1405,8 +1417,10 @@ k_pass_fa(const int32_t* __restrict__ pchunk, int P, const int32_t* __restrict__
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       if (jj[u] < 0) continue;
+      T X0, X1, X2, pad;
+      load4(sX + 4 * (jj[u] - j0), X0, X1, X2, pad);
       T z0, z1, z2;
-      a1_obs(sct + ll[u] * FA_CT, sxv + ll[u] * FA_XV, X[u][0], X[u][1], X[u][2], sw[u], z0, z1, z2);
+      a1_obs(sct + ll[u] * FA_CT, sxv + ll[u] * FA_XV, X0, X1, X2, sw[u], z0, z1, z2);
       store4(sz + 4 * (threadIdx.x + u * CHUNK_THREADS), z0, z1, z2, T(0));
     }
     __syncthreads();

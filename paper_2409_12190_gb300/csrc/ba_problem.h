@@ -42,6 +42,7 @@ struct ba_problem {
   bool fa = false;
   int32_t *chunk_cams = nullptr, *chunk_cam_ptr = nullptr;
   int16_t* pm_lc = nullptr;
+  int4* chunk_hdr = nullptr;  // [nchunks][2] headers of the fused pass
   void *cm_px = nullptr, *pm_px = nullptr, *px_in = nullptr;
   int npieces = 0;
   int32_t *piece_cam = nullptr, *piece_beg = nullptr, *piece_end = nullptr, *cam_piece_ptr = nullptr;
