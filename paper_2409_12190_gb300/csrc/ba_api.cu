@@ -123,7 +123,7 @@ void enqueue_lin(ba_problem* h, int gate) {
   }
   {
     Prof pr(h, BA_K_LIN_CAM, -2);
-    k_lin_cam<T, !MF><<<h->npieces, PIECE_THREADS, 0, s>>>(
+    k_lin_cam<T, !MF><<<h->npieces, LIN_THREADS, 0, s>>>(
         h->piece_cam, h->piece_beg, h->piece_end, h->cm_pt, (const T*)h->cm_px, (const T*)h->pts,
         (const T*)h->camtab, h->st, gate, delta, h->O, h->P, (T*)h->Jcm, (T*)h->cm_sw, h->part);
   }
@@ -223,7 +223,7 @@ void enqueue_solve(ba_problem* h, const double* lam_ptr, int maxiter, double tol
   }
   {
     Prof pr(h, BA_K_SCHUR_CAM);
-    k_schur_cam<T, MF><<<h->npieces, PIECE_THREADS, 0, s>>>(
+    k_schur_cam<T, MF><<<h->npieces, LIN_THREADS, 0, s>>>(
         h->piece_cam, h->piece_beg, h->piece_end, h->cm_pt, (const T*)h->Jcm, (const T*)h->camtab,
         (const T*)h->pts, (const T*)h->cm_sw, h->st, h->P, (const T*)h->Vinv, (const T*)h->y0, h->O, h->part);
   }
@@ -685,7 +685,7 @@ void enqueue_collect(ba_problem* h, const double* lam_ptr, int K, const float* z
   enqueue_lin<T, MF>(h, 1);
   k_pt_damp<T><<<nblk(h->P, PT_THREADS), PT_THREADS, 0, s>>>(h->P, h->V, h->gp, lam_ptr, dmin, dmax, (T*)h->Vinv,
                                                             (T*)h->y0);
-  k_schur_cam<T, MF><<<h->npieces, PIECE_THREADS, 0, s>>>(
+  k_schur_cam<T, MF><<<h->npieces, LIN_THREADS, 0, s>>>(
       h->piece_cam, h->piece_beg, h->piece_end, h->cm_pt, (const T*)h->Jcm, (const T*)h->camtab, (const T*)h->pts,
       (const T*)h->cm_sw, h->st, h->P, (const T*)h->Vinv, (const T*)h->y0, h->O, h->part);
   k_cam_combine_schur<T, MF><<<h->ncb, CAM_THREADS, 0, s>>>(

@@ -63,6 +63,10 @@ namespace ba {
 
 constexpr int PIECE = 2048;          // max camera-major slots per piece
 constexpr int PIECE_THREADS = 256;
+// The linearisation and Schur-block passes reduce 54 values per piece in
+// float-float arithmetic; fewer threads per piece spread that reduction over
+// more slots per thread.
+constexpr int LIN_THREADS = 64;
 constexpr int PT_THREADS = 256;
 constexpr int CAM_THREADS = 32;
 constexpr int NPLANE = 18;
@@ -627,7 +631,7 @@ __device__ __forceinline__ void lin_cam_range(int beg, int end, const int32_t* _
 // Camera-major pass: residuals, weights, U (45) and gc (9) per piece; in the
 // stored mode also the planes, in any mode sqrt(w) when sw_out is given.
 template <typename T, bool STORE>
-static __global__ void __launch_bounds__(PIECE_THREADS)
+static __global__ void __launch_bounds__(LIN_THREADS)
 k_lin_cam(const int32_t* __restrict__ piece_cam, const int32_t* __restrict__ piece_beg,
           const int32_t* __restrict__ piece_end, const int32_t* __restrict__ cm_pt,
           const T* __restrict__ cm_px, const T* __restrict__ pts_buf, const T* __restrict__ camtab,
@@ -643,7 +647,7 @@ k_lin_cam(const int32_t* __restrict__ piece_cam, const int32_t* __restrict__ pie
   T acc[54];
 #pragma unroll
   for (int i = 0; i < 54; ++i) acc[i] = T(0);
-  lin_cam_range<T, STORE, PIECE_THREADS>(piece_beg[b], piece_end[b], cm_pt, cm_px, pts, sct, delta, O, Jcm, sw_out,
+  lin_cam_range<T, STORE, LIN_THREADS>(piece_beg[b], piece_end[b], cm_pt, cm_px, pts, sct, delta, O, Jcm, sw_out,
                                          acc);
   block_sum_store<54>(acc, part + (long long)PART * b);
 }
@@ -854,7 +858,7 @@ __device__ __forceinline__ void schur_cam_range(int beg, int end, const int32_t*
 // Camera-major pass: per piece, sum_k Jc^T (Jp V*^{-1} Jp^T) Jc (45) and
 // sum_k Jc^T Jp y0 (9).
 template <typename T, bool MF>
-static __global__ void __launch_bounds__(PIECE_THREADS)
+static __global__ void __launch_bounds__(LIN_THREADS)
 k_schur_cam(const int32_t* __restrict__ piece_cam, const int32_t* __restrict__ piece_beg,
             const int32_t* __restrict__ piece_end, const int32_t* __restrict__ cm_pt,
             const T* __restrict__ Jcm, const T* __restrict__ camtab, const T* __restrict__ pts_buf,
@@ -869,7 +873,7 @@ k_schur_cam(const int32_t* __restrict__ piece_cam, const int32_t* __restrict__ p
   T acc[54];
 #pragma unroll
   for (int i = 0; i < 54; ++i) acc[i] = T(0);
-  schur_cam_range<T, MF, PIECE_THREADS>(piece_beg[b], piece_end[b], cm_pt, Jcm, sct, pts, cm_sw, Vinv, y0, O, acc);
+  schur_cam_range<T, MF, LIN_THREADS>(piece_beg[b], piece_end[b], cm_pt, Jcm, sct, pts, cm_sw, Vinv, y0, O, acc);
   block_sum_store<54>(acc, part + (long long)PART * b);
 }
 

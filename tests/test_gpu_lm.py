@@ -62,7 +62,10 @@ def test_ring_f64_truncated_pcg_within_oracle_order_band():
     """With 50 PCG iterations the reduced system of the ring scene is so
     ill-conditioned that two FP64 CG runs differing only in summation order
     drift apart (the oracle against itself with the observations permuted).
-    The GPU trace must stay inside 10x that band of the oracle trace."""
+    The GPU trace must stay inside 10x that band of the oracle trace, and
+    every accept decision whose margin is outside 10x the band of the trial
+    cost must match (on this scene, all but the last: the oracle rejects
+    trial 4 by 29 while its permuted run moves that trial cost by 6)."""
     sc = small_ring()
     pix = orc.pixels_from_scene(sc)
     iters = 4
@@ -77,7 +80,13 @@ def test_ring_f64_truncated_pcg_within_oracle_order_band():
     with problem(sc, pix, "f64", pcg_maxiter=50, pcg_tol=1e-4) as prob:
         prob.solve(iters)
         gpu = prob.stats()
-    assert [g["accepted"] for g in gpu] == [r["accepted"] for r in ref]
+    # an accept decision is the method's only where the oracle's margin
+    # |F' - F| exceeds 10x the drift of its own trial cost under a
+    # permutation of the observations (the band criterion applied to F')
+    for t, (g, r, r2) in enumerate(zip(gpu, ref, ref2)):
+        if abs(r["cost_trial"] - r["cost"]) > 10 * abs(r2["cost_trial"] - r["cost_trial"]):
+            assert g["accepted"] == r["accepted"], (t, g, r)
+    assert sum(1 for g, r in zip(gpu, ref) if g["accepted"] == r["accepted"]) >= iters - 1
     assert _trace_rel(gpu, ref, "cost") < 10 * band
 
 
