@@ -1810,6 +1810,9 @@ __device__ __forceinline__ void cost_cam_range(int beg, int end, const int32_t* 
                                                const T* __restrict__ sold, const T* __restrict__ sdc, T delta, int O,
                                                const T* __restrict__ Jcm, const T* __restrict__ cm_sw,
                                                const T* __restrict__ dp, double& cost, double& quad) {
+  // FP32: per-thread sums in float-float (about 48 bits, on the FP32 pipes;
+  // the products of the model term exact by fma), FP64: in double
+  float ch = 0.f, cl = 0.f, qh = 0.f, ql = 0.f;
   for (int s = beg + threadIdx.x; s < end; s += NT) {
     const int j = cm_pt[s];
     T px, py, sc;
@@ -1817,7 +1820,10 @@ __device__ __forceinline__ void cost_cam_range(int beg, int end, const int32_t* 
     const T r0 = sc * px - cm_px[s], r1 = sc * py - cm_px[(long long)O + s];
     T hr, w;
     huber_weight(r0 * r0 + r1 * r1, delta, hr, w);
-    cost += (double)hr;
+    if constexpr (sizeof(T) == 4)
+      ff_add(ch, cl, hr, 0.f);
+    else
+      cost += (double)hr;
     if (MODEL) {
       const T d0 = dp[3LL * j], d1 = dp[3LL * j + 1], d2 = dp[3LL * j + 2];
       const T g0 = sold[0] * d0 + sold[1] * d1 + sold[2] * d2;
@@ -1843,8 +1849,18 @@ __device__ __forceinline__ void cost_cam_range(int beg, int end, const int32_t* 
           e1 += j1[i] * sdc[i];
         }
       }
-      quad += (double)e0 * (double)e0 + (double)e1 * (double)e1;
+      if constexpr (sizeof(T) == 4) {
+        const float p0 = e0 * e0, p1 = e1 * e1;
+        ff_add(qh, ql, p0, fmaf(e0, e0, -p0));
+        ff_add(qh, ql, p1, fmaf(e1, e1, -p1));
+      } else {
+        quad += (double)e0 * (double)e0 + (double)e1 * (double)e1;
+      }
     }
+  }
+  if constexpr (sizeof(T) == 4) {
+    cost += (double)ch + (double)cl;
+    quad += (double)qh + (double)ql;
   }
 }
 
