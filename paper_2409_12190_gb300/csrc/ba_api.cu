@@ -133,9 +133,10 @@ void enqueue_lin(ba_problem* h, int gate) {
   }
   {
     Prof pr(h, BA_K_LIN_PT, -2);
-    k_lin_pt<T><<<h->nchunks, CHUNK_THREADS, CHUNK_SLOTS * 9 * sizeof(T), s>>>(
+    k_lin_pt<T><<<h->nchunks, CHUNK_THREADS, lin_pt_smem<T>(h->fa), s>>>(
         h->pchunk, h->O, h->rowptr_pt, h->pm_cam, h->pm_pt, (const T*)h->pm_px, (const T*)h->pts,
-        (const T*)h->camtab, h->st, h->P, gate, delta, (T*)h->pm_sw, h->V, h->gp);
+        (const T*)h->camtab, h->st, h->P, gate, delta, (T*)h->pm_sw, h->V, h->gp, h->fa ? h->chunk_hdr : nullptr,
+        h->pm_lc, h->chunk_cams);
   }
   count_launch(5);
 }
@@ -517,9 +518,8 @@ ba_status create_impl(ba_problem* h, const void* cams, const void* points, const
     CU(h->alloc(&h->pchunk, pch.size() * 4));
     CU(cudaMemcpy(h->pchunk, pch.data(), pch.size() * 4, cudaMemcpyHostToDevice));
   }
-  if (sizeof(T) * CHUNK_SLOTS * 9 > 48 * 1024)
-    CU(cudaFuncSetAttribute(k_lin_pt<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                            (int)(sizeof(T) * CHUNK_SLOTS * 9)));
+  if (lin_pt_smem<T>(true) > 48 * 1024)
+    CU(cudaFuncSetAttribute(k_lin_pt<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, lin_pt_smem<T>(true)));
   CU(cudaFuncSetAttribute(k_pass_fa<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, fa_smem<T>()));
   CU(cudaFuncSetAttribute(k_pass_fa<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, fa_smem<T>()));
 

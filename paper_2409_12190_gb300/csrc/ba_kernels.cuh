@@ -77,6 +77,20 @@ constexpr int PART = 64;             // doubles per piece partial (54 used)
 constexpr int CHUNK_SLOTS = 1024;    // max point-major slots per point chunk
 constexpr int CHUNK_PTS = 512;       // max points per point chunk
 constexpr int CHUNK_THREADS = 256;
+// fused pass A: staged cameras per chunk, padded row strides (different
+// cameras in different banks)
+constexpr int FA_CAMS = 128;
+constexpr int FA_CT = 17;  // padded strides: different cameras in different banks
+constexpr int FA_XV = 13;
+// dynamic shared memory of k_pass_fa: z per slot, then the chunk's points
+template <typename T>
+constexpr int fa_smem() { return (CHUNK_SLOTS + CHUNK_PTS) * 4 * (int)sizeof(T); }
+// dynamic shared memory of k_lin_pt: its per-slot sums, and with the chunk
+// headers the chunk's camera tables and points
+template <typename T>
+constexpr int lin_pt_smem(bool staged) {
+  return (CHUNK_SLOTS * 9 + (staged ? FA_CAMS * FA_CT + CHUNK_PTS * 3 : 0)) * (int)sizeof(T);
+}
 
 // Device-resident LM / PCG state; every field is written by exactly one
 // thread of one kernel and read by later kernels.
@@ -703,19 +717,62 @@ __device__ __forceinline__ void lin_pt_obs(int q, int O, const int32_t* __restri
   }
 }
 
+// lin_pt_obs with the camera table ct and the point X from shared memory.
+template <typename T>
+__device__ __forceinline__ void lin_pt_obs_staged(int q, int O, const T* __restrict__ pm_px, const T* ct, T X0, T X1,
+                                                  T X2, T delta, T* __restrict__ sw_out, T (&v)[9]) {
+  Fac<T> o;
+  T r0, r1, hr, sw;
+  lin_obs(ct, X0, X1, X2, pm_px[q], pm_px[(long long)O + q], delta, o, r0, r1, hr, sw);
+  if (sw_out) sw_out[q] = sw;
+  T Jp[6];
+  jp_from(o.A, ct, Jp);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+#pragma unroll
+    for (int b = a; b < 3; ++b) v[sym3(a, b)] = Jp[a] * Jp[b] + Jp[3 + a] * Jp[3 + b];
+    v[6 + a] = Jp[a] * r0 + Jp[3 + a] * r1;
+  }
+}
+
 template <typename T>
 static __global__ void __launch_bounds__(CHUNK_THREADS)
 k_lin_pt(const int32_t* __restrict__ pchunk, int O, const int32_t* __restrict__ rowptr_pt,
          const int32_t* __restrict__ pm_cam, const int32_t* __restrict__ pm_pt, const T* __restrict__ pm_px,
          const T* __restrict__ pts_buf, const T* __restrict__ camtab, const DevState* __restrict__ st, int P,
-         int gate, T delta, T* __restrict__ sw_out, double* __restrict__ V, double* __restrict__ gp) {
+         int gate, T delta, T* __restrict__ sw_out, double* __restrict__ V, double* __restrict__ gp,
+         const int4* __restrict__ chunk_hdr, const int16_t* __restrict__ pm_lc,
+         const int32_t* __restrict__ chunk_cams) {
   if (gate && !st->need_lin) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sv = reinterpret_cast<T*>(smem_raw);  // [CHUNK_SLOTS][9]
   const T* pts = pts_buf + (long long)st->cur * 3 * P;
   const int j0 = pchunk[blockIdx.x], j1 = pchunk[blockIdx.x + 1];
   const int s0 = rowptr_pt[j0], s1 = rowptr_pt[j1];
-  if (s1 - s0 <= CHUNK_SLOTS) {
+  if (s1 - s0 <= CHUNK_SLOTS && chunk_hdr) {
+    // with the fused pass's chunk headers: the chunk's camera tables and its
+    // (consecutive) points staged in shared memory, as in k_pass_fa
+    T* sct = sv + CHUNK_SLOTS * 9;  // [FA_CAMS][FA_CT]
+    T* sX = sct + FA_CAMS * FA_CT;   // [CHUNK_PTS][3]
+    const int4 h1 = chunk_hdr[2 * blockIdx.x + 1];
+    const int c0 = h1.x, nc = h1.y, cmin = h1.z;
+    for (int i = threadIdx.x; i < nc * 16; i += CHUNK_THREADS) {
+      const int l = i >> 4, e = i & 15;
+      const int cam = cmin >= 0 ? cmin + l : chunk_cams[c0 + l];
+      if (e < 15) sct[l * FA_CT + e] = camtab[(long long)CT * cam + e];
+    }
+    for (int i = threadIdx.x; i < 3 * (j1 - j0); i += CHUNK_THREADS) sX[i] = pts[3LL * j0 + i];
+    __syncthreads();
+    for (int q = s0 + threadIdx.x; q < s1; q += CHUNK_THREADS) {
+      const int jl = pm_pt[q] - j0;
+      T v[9];
+      lin_pt_obs_staged<T>(q, O, pm_px, sct + pm_lc[q] * FA_CT, sX[3 * jl], sX[3 * jl + 1], sX[3 * jl + 2], delta,
+                           sw_out, v);
+#pragma unroll
+      for (int i = 0; i < 9; ++i) sv[(q - s0) * 9 + i] = v[i];
+    }
+    __syncthreads();
+  } else if (s1 - s0 <= CHUNK_SLOTS) {
     for (int q = s0 + threadIdx.x; q < s1; q += CHUNK_THREADS) {
       T v[9];
       lin_pt_obs<T>(q, O, pm_cam, pm_pt, pm_px, pts, camtab, delta, sw_out, v);
@@ -723,6 +780,8 @@ k_lin_pt(const int32_t* __restrict__ pchunk, int O, const int32_t* __restrict__ 
       for (int i = 0; i < 9; ++i) sv[(q - s0) * 9 + i] = v[i];
     }
     __syncthreads();
+  }
+  if (s1 - s0 <= CHUNK_SLOTS) {
     for (int j = j0 + threadIdx.x; j < j1; j += CHUNK_THREADS) {
       T acc[9];
 #pragma unroll
@@ -1344,12 +1403,6 @@ k_pass_a2(const int32_t* __restrict__ pchunk, int P, const int32_t* __restrict__
 // of its point before the first barrier.  The per-observation products and
 // the per-point sums are those of passes A1 and A2 (same order).  MODE as in
 // k_pass_a2.
-constexpr int FA_CAMS = 128;
-constexpr int FA_CT = 17;  // padded strides: different cameras in different banks
-constexpr int FA_XV = 13;
-// dynamic shared memory of k_pass_fa: z per slot, then the chunk's points
-template <typename T>
-constexpr int fa_smem() { return (CHUNK_SLOTS + CHUNK_PTS) * 4 * (int)sizeof(T); }
 
 template <typename T, int MODE>
 static __global__ void __launch_bounds__(CHUNK_THREADS, sizeof(T) == 4 ? 5 : 1)
