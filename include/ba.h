@@ -123,7 +123,8 @@ ba_status ba_problem_destroy(ba_problem* h);
 /* One LM trial (Alg. 1 loop body): linearise if theta changed (a1, a2),
  * damp and reduce (a3), solve the reduced camera system by block-Jacobi PCG
  * with implicit S x (a4), back-substitute (a5), evaluate the trial and
- * accept or reject it, update lambda (a6).  No host synchronisation. */
+ * accept or reject it, update lambda (a6).  With use_graph, one replay of
+ * the trial graph that ba_solve captures.  No host synchronisation. */
 ba_status ba_lm_step(ba_problem* h, void* stream);
 
 /* iters LM trials; with use_graph the trial is captured once as a CUDA graph
@@ -131,12 +132,16 @@ ba_status ba_lm_step(ba_problem* h, void* stream);
 ba_status ba_solve(ba_problem* h, int iters, void* stream);
 
 /* Copy the current (last accepted) parameters to cams_out [C][9] and
- * points_out [P][3] (any). Either may be NULL. */
+ * points_out [P][3] (any). Either may be NULL.  Stream-ordered (no host
+ * synchronisation): into pinned or device memory the copy completes on the
+ * stream; the caller synchronises before reading. */
 ba_status ba_get_params(ba_problem* h, void* cams_out, void* points_out,
                         void* stream);
 
 /* Replace the parameters (any; either may be NULL to keep it) and
- * re-evaluate the cost; the next trial re-linearises.  lambda is kept. */
+ * re-evaluate the cost; the next trial re-linearises.  lambda is kept.
+ * Stream-ordered: a pinned or device source must stay valid until the
+ * stream reaches the copy. */
 ba_status ba_set_params(ba_problem* h, const void* cams, const void* points,
                         void* stream);
 

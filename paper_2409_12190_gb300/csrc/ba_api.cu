@@ -434,6 +434,7 @@ ba_status create_impl(ba_problem* h, const void* cams, const void* points, const
   CU(h->alloc(&h->pnew, P * 4));
   CU(h->alloc(&h->pnewpos, P * 4));
   CU(h->alloc(&h->pts_tmp, 3 * P * ts));
+  CU(h->alloc(&h->cams_tmp, 9 * C * ts));
   {
     const long long nmax = std::max(O, P);
     void* scratch = nullptr;
@@ -647,13 +648,39 @@ ba_status run_cost(ba_problem* h) {
 }
 
 ba_status set_flag(ba_problem* h, size_t offset, int value) {
-  // write one int of DevState (pageable source: copied before return)
-  CU(cudaMemcpyAsync(reinterpret_cast<char*>(h->st) + offset, &value, sizeof(int), cudaMemcpyHostToDevice, h->s));
-  CU(cudaStreamSynchronize(h->s));
+  // write one int of DevState, stream-ordered
+  k_set_int<<<1, 32, 0, h->s>>>(reinterpret_cast<int*>(reinterpret_cast<char*>(h->st) + offset), value);
+  count_launch();
+  CU(cudaGetLastError());
   return BA_OK;
 }
 
 // Copy caller-ordered points (any memory) into parameter buffer `buf`.
+// Cameras (cams_tmp) or points (pts_tmp, caller's order) into (store) or out
+// of the current parameter buffer.
+void params_cur(ba_problem* h, bool cams, bool points, bool store = true) {
+  if (cams) {
+    const long long n = 9LL * h->C;
+    if (h->prec == BA_PREC_F32)
+      k_cams_cur<float><<<nblk(n, 256), 256, 0, h->s>>>(n, h->st, (const float*)h->cams_tmp, (float*)h->cams,
+                                                         store ? 1 : 0);
+    else
+      k_cams_cur<double><<<nblk(n, 256), 256, 0, h->s>>>(n, h->st, (const double*)h->cams_tmp, (double*)h->cams,
+                                                          store ? 1 : 0);
+    count_launch();
+  }
+  if (points) {
+    const int32_t* idx = store ? h->pnew : h->pnewpos;
+    if (h->prec == BA_PREC_F32)
+      k_points_cur<float><<<nblk(h->P, 256), 256, 0, h->s>>>(h->P, idx, h->st, (float*)h->pts_tmp, (float*)h->pts,
+                                                             store ? 1 : 0);
+    else
+      k_points_cur<double><<<nblk(h->P, 256), 256, 0, h->s>>>(h->P, idx, h->st, (double*)h->pts_tmp,
+                                                              (double*)h->pts, store ? 1 : 0);
+    count_launch();
+  }
+}
+
 ba_status load_points(ba_problem* h, const void* points, int buf) {
   const size_t pb = 3ull * h->P * h->tsize;
   CU(cudaMemcpyAsync(h->pts_tmp, points, pb, cudaMemcpyDefault, h->s));
@@ -811,12 +838,8 @@ ba_status ba_problem_destroy(ba_problem* h) {
 }
 
 ba_status ba_lm_step(ba_problem* h, void* stream) {
-  if (!h) return fail(BA_ERR_INVALID_ARG, "NULL problem");
-  ba_status st = enter(h, stream);
-  if (st != BA_OK) return st;
-  enqueue_trial_any(h);
-  CU(cudaGetLastError());
-  return leave(h, stream);
+  // one trial: a replay of the captured trial graph (as ba_solve(1))
+  return ba_solve(h, 1, stream);
 }
 
 ba_status ba_solve(ba_problem* h, int iters, void* stream) {
@@ -858,22 +881,15 @@ ba_status ba_get_params(ba_problem* h, void* cams_out, void* points_out, void* s
   if (!h) return fail(BA_ERR_INVALID_ARG, "NULL problem");
   ba_status st = enter(h, stream);
   if (st != BA_OK) return st;
-  int cur = 0;
-  CU(cudaMemcpyAsync(&cur, &h->st->cur, sizeof(int), cudaMemcpyDeviceToHost, h->s));
-  CU(cudaStreamSynchronize(h->s));
+  // from the current buffer (its index read on the device), points back to
+  // the caller's order
   const size_t cb = 9ull * h->C * h->tsize, pb = 3ull * h->P * h->tsize;
-  if (cams_out)
-    CU(cudaMemcpyAsync(cams_out, (char*)h->cams + cur * cb, cb, cudaMemcpyDefault, h->s));
+  if (cams_out) {
+    params_cur(h, true, false, false);
+    CU(cudaMemcpyAsync(cams_out, h->cams_tmp, cb, cudaMemcpyDefault, h->s));
+  }
   if (points_out) {
-    // back to the caller's point order
-    const void* src = (const char*)h->pts + cur * pb;
-    if (h->prec == BA_PREC_F32)
-      k_gather_rows<float, 3><<<nblk(h->P, 256), 256, 0, h->s>>>(h->P, h->pnewpos, (const float*)src,
-                                                                 (float*)h->pts_tmp);
-    else
-      k_gather_rows<double, 3><<<nblk(h->P, 256), 256, 0, h->s>>>(h->P, h->pnewpos, (const double*)src,
-                                                                  (double*)h->pts_tmp);
-    count_launch();
+    params_cur(h, false, true, false);
     CU(cudaMemcpyAsync(points_out, h->pts_tmp, pb, cudaMemcpyDefault, h->s));
   }
   return leave(h, stream);
@@ -883,16 +899,16 @@ ba_status ba_set_params(ba_problem* h, const void* cams, const void* points, voi
   if (!h) return fail(BA_ERR_INVALID_ARG, "NULL problem");
   ba_status st = enter(h, stream);
   if (st != BA_OK) return st;
-  int cur = 0;
-  CU(cudaMemcpyAsync(&cur, &h->st->cur, sizeof(int), cudaMemcpyDeviceToHost, h->s));
-  CU(cudaStreamSynchronize(h->s));
+  // into the current buffer, its index read on the device (no host round trip)
   const size_t cb = 9ull * h->C * h->tsize, pb = 3ull * h->P * h->tsize;
-  if (cams) CU(cudaMemcpyAsync((char*)h->cams + cur * cb, cams, cb, cudaMemcpyDefault, h->s));
-  if (points) {
-    st = load_points(h, points, cur);
-    if (st != BA_OK) return st;
+  if (cams) {
+    CU(cudaMemcpyAsync(h->cams_tmp, cams, cb, cudaMemcpyDefault, h->s));
+    params_cur(h, true, false);
   }
-  (void)pb;
+  if (points) {
+    CU(cudaMemcpyAsync(h->pts_tmp, points, pb, cudaMemcpyDefault, h->s));
+    params_cur(h, false, true);
+  }
   st = set_flag(h, offsetof(DevState, need_lin), 1);
   if (st != BA_OK) return st;
   st = run_cost(h);

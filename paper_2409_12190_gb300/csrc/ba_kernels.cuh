@@ -586,6 +586,39 @@ static __global__ void k_gather_i32(int n, const int32_t* __restrict__ idx, cons
 }
 
 // dst[i][:] = src[idx[i]][:] for rows of W values
+// One int of the device state (stream-ordered, no host round trip).
+static __global__ void k_set_int(int* p, int v) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *p = v;
+}
+
+// Parameters in and out of the current buffer of the double-buffered
+// parameter arrays, the buffer index read on the device: cameras [C][9] are
+// copied, points [P][3] are gathered between the caller's numbering (rows
+// of tmp) and the internal one (idx: internal -> caller row for the load,
+// caller -> internal row for the store).
+template <typename T>
+static __global__ void k_cams_cur(long long n, const DevState* __restrict__ st, const T* __restrict__ src,
+                                  T* __restrict__ cams, int store) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  T* buf = cams + (long long)st->cur * n;
+  if (store) buf[i] = src[i];
+  else const_cast<T*>(src)[i] = buf[i];
+}
+template <typename T>
+static __global__ void k_points_cur(int P, const int32_t* __restrict__ idx, const DevState* __restrict__ st,
+                                    T* __restrict__ tmp, T* __restrict__ pts, int store) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= P) return;
+  T* buf = pts + (long long)st->cur * 3 * P;
+  const long long r = idx[i];
+#pragma unroll
+  for (int w = 0; w < 3; ++w) {
+    if (store) buf[3 * i + w] = tmp[3 * r + w];
+    else tmp[3 * i + w] = buf[3 * r + w];
+  }
+}
+
 template <typename X, int W>
 static __global__ void k_gather_rows(int n, const int32_t* __restrict__ idx, const X* __restrict__ src,
                               X* __restrict__ dst) {
