@@ -138,15 +138,17 @@ ba_status ba_solve(ba_problem* h, int iters, void* stream);
 ba_status ba_get_params(ba_problem* h, void* cams_out, void* points_out,
                         void* stream);
 
-/* Replace the parameters (any; either may be NULL to keep it) and
- * re-evaluate the cost; the next trial re-linearises.  lambda is kept.
- * Stream-ordered: a pinned or device source must stay valid until the
- * stream reaches the copy. */
+/* Replace the parameters (any; either may be NULL to keep it); the cost is
+ * re-evaluated by the next trial or by the next call that reads it
+ * (ba_get_scalars, ba_get_state), and the next trial re-linearises.  lambda
+ * is kept.  Stream-ordered: a pinned or device source must stay valid until
+ * the stream reaches the copy. */
 ba_status ba_set_params(ba_problem* h, const void* cams, const void* points,
                         void* stream);
 
 /* Replace the observed pixels (any, [O][2]); the observation structure is
- * kept, the cost is re-evaluated and the next trial re-linearises. */
+ * kept; the cost is re-evaluated as after ba_set_params and the next trial
+ * re-linearises. */
 ba_status ba_set_pixels(ba_problem* h, const void* pixels, void* stream);
 
 /* Copy up to cap statistics records (oldest first among the last cap

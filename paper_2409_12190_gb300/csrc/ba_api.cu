@@ -277,8 +277,21 @@ void enqueue_solve(ba_problem* h, const double* lam_ptr, int maxiter, double tol
   count_launch(3);
 }
 
+// F at theta into the device state; gated: only if marked stale.
+template <typename T, bool MF>
+void enqueue_cost(ba_problem* h, bool gated = false) {
+  const T delta = (T)(h->opt.huber_delta > 0 ? h->opt.huber_delta : 0.0);
+  k_cost_cam<T, false, MF><<<h->npieces, PIECE_THREADS, 0, h->s>>>(
+      h->piece_cam, h->piece_beg, h->piece_end, h->cm_pt, (const T*)h->cm_px, (const T*)h->cams,
+      (const T*)h->pts, h->st, gated ? 2 : 0, delta, h->C, h->P, h->O, nullptr, nullptr, nullptr, nullptr, nullptr,
+      h->part);
+  k_cost_finalize<<<1, 256, 0, h->s>>>(h->npieces, h->part, h->st, gated ? 1 : 0);
+  count_launch(2);
+}
+
 template <typename T, bool MF>
 void enqueue_trial(ba_problem* h) {
+  enqueue_cost<T, MF>(h, true);  // F if the parameters or pixels were replaced
   enqueue_lin<T, MF>(h, 1);
   enqueue_solve<T, MF>(h, &h->st->lam, h->opt.pcg_maxiter, h->opt.pcg_tol, h->learned);
   const T delta = (T)(h->opt.huber_delta > 0 ? h->opt.huber_delta : 0.0);
@@ -298,15 +311,6 @@ void enqueue_trial(ba_problem* h) {
   count_launch(2);
 }
 
-template <typename T, bool MF>
-void enqueue_cost(ba_problem* h) {
-  const T delta = (T)(h->opt.huber_delta > 0 ? h->opt.huber_delta : 0.0);
-  k_cost_cam<T, false, MF><<<h->npieces, PIECE_THREADS, 0, h->s>>>(
-      h->piece_cam, h->piece_beg, h->piece_end, h->cm_pt, (const T*)h->cm_px, (const T*)h->cams,
-      (const T*)h->pts, h->st, 0, delta, h->C, h->P, h->O, nullptr, nullptr, nullptr, nullptr, nullptr, h->part);
-  k_cost_finalize<<<1, 256, 0, h->s>>>(h->npieces, h->part, h->st);
-  count_launch(2);
-}
 
 // Call FN<T, MF>(h, args...) for the problem's precision and Jacobian mode.
 #define BA_DISPATCH(h, FN, ...)                        \
@@ -641,9 +645,12 @@ ba_status create_impl(ba_problem* h, const void* cams, const void* points, const
   return BA_OK;
 }
 
-ba_status run_cost(ba_problem* h) {
-  BA_DISPATCH(h, enqueue_cost);
+// The stale cost, before a call reads F on the host.
+ba_status settle_cost(ba_problem* h) {
+  if (!h->cost_pending) return BA_OK;
+  BA_DISPATCH(h, enqueue_cost, true);
   CU(cudaGetLastError());
+  h->cost_pending = false;
   return BA_OK;
 }
 
@@ -847,6 +854,7 @@ ba_status ba_solve(ba_problem* h, int iters, void* stream) {
   if (iters < 0) return fail(BA_ERR_INVALID_ARG, "iters < 0");
   ba_status st = enter(h, stream);
   if (st != BA_OK) return st;
+  if (iters > 0) h->cost_pending = false;  // every trial starts with the stale cost
   if (!h->opt.use_graph) {
     for (int i = 0; i < iters; ++i) enqueue_trial_any(h);
     CU(cudaGetLastError());
@@ -911,8 +919,10 @@ ba_status ba_set_params(ba_problem* h, const void* cams, const void* points, voi
   }
   st = set_flag(h, offsetof(DevState, need_lin), 1);
   if (st != BA_OK) return st;
-  st = run_cost(h);
+  // F is evaluated lazily: by the next trial, or by a call that reads it
+  st = set_flag(h, offsetof(DevState, need_cost), 1);
   if (st != BA_OK) return st;
+  h->cost_pending = true;
   return leave(h, stream);
 }
 
@@ -933,8 +943,10 @@ ba_status ba_set_pixels(ba_problem* h, const void* pixels, void* stream) {
   count_launch();
   st = set_flag(h, offsetof(DevState, need_lin), 1);
   if (st != BA_OK) return st;
-  st = run_cost(h);
+  // F is evaluated lazily: by the next trial, or by a call that reads it
+  st = set_flag(h, offsetof(DevState, need_cost), 1);
   if (st != BA_OK) return st;
+  h->cost_pending = true;
   return leave(h, stream);
 }
 
@@ -960,6 +972,8 @@ ba_status ba_get_stats(ba_problem* h, ba_iter_stats* host_out, int cap, int* n_o
 
 ba_status ba_get_scalars(ba_problem* h, double* cost, double* lambda) {
   if (!h) return fail(BA_ERR_INVALID_ARG, "NULL problem");
+  ba_status st0 = settle_cost(h);
+  if (st0 != BA_OK) return st0;
   DevState ds;
   CU(cudaMemcpyAsync(&ds, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, h->s));
   CU(cudaStreamSynchronize(h->s));
@@ -979,6 +993,8 @@ size_t ba_state_size(const ba_problem* h) { return h ? 9ull * h->C + 3ull * h->P
 
 ba_status ba_get_state(ba_problem* h, double* out) {
   if (!h || !out) return fail(BA_ERR_INVALID_ARG, "NULL argument");
+  ba_status st0 = settle_cost(h);
+  if (st0 != BA_OK) return st0;
   DevState ds;
   CU(cudaMemcpyAsync(&ds, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, h->s));
   CU(cudaStreamSynchronize(h->s));

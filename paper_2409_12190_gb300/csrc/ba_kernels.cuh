@@ -107,7 +107,7 @@ struct DevState {
   int fallbacks;     // block-Jacobi blocks replaced by diag(U*) this trial
   long long trials;
   int err;           // bit 0: index out of range, bit 1: non-finite input
-  int pad;
+  int need_cost;     // F is stale (parameters or pixels replaced since)
 };
 
 __host__ __device__ constexpr int sym9(int i, int j) { return 9 * i - (i * (i - 1)) / 2 + (j - i); }
@@ -1961,13 +1961,14 @@ k_cost_cam(const int32_t* __restrict__ piece_cam, const int32_t* __restrict__ pi
            const DevState* __restrict__ st, int which, T delta, int C, int P, int O,
            const T* __restrict__ Jcm, const T* __restrict__ cm_sw, const T* __restrict__ camtab,
            const T* __restrict__ xT, const T* __restrict__ dp, double* __restrict__ part) {
+  if (which == 2 && !st->need_cost) return;  // cost at theta only if stale
   __shared__ T sct[CT];   // camera of the evaluated parameters
   __shared__ T sold[CT];  // camera of the linearisation (model term)
   __shared__ T sdc[PV];
   const int b = blockIdx.x;
   const int c = piece_cam[b];
   const int cur = st->cur;
-  const int buf = which ? 1 - cur : cur;
+  const int buf = which == 1 ? 1 - cur : cur;
   if (threadIdx.x == 0) camera_table(cams_buf + (long long)buf * 9 * C + 9LL * c, sct);
   if (MODEL && threadIdx.x >= 32 && threadIdx.x < 32 + CT)
     sold[threadIdx.x - 32] = camtab[(long long)CT * c + threadIdx.x - 32];
@@ -1984,10 +1985,12 @@ k_cost_cam(const int32_t* __restrict__ piece_cam, const int32_t* __restrict__ pi
 }
 
 // Sum the cost pieces into st->F (initial cost / after set_params).
-static __global__ void k_cost_finalize(int npieces, const double* __restrict__ part, DevState* st) {
+static __global__ void k_cost_finalize(int npieces, const double* __restrict__ part, DevState* st, int gate) {
+  if (gate && !st->need_cost) return;
   const double F = block_sum_array(part, npieces, PART);
   if (threadIdx.x == 0) {
     st->F = F;
+    st->need_cost = 0;
     if (!isfinite(F)) st->err |= 2;
   }
 }

@@ -31,6 +31,7 @@ struct ba_problem {
   int32_t *xperm_cam = nullptr, *xperm_pt = nullptr, *xrowptr_pt = nullptr;
   void* pts_tmp = nullptr;  // [P][3] staging for reordering parameters
   void* cams_tmp = nullptr;  // [C][9] staging for parameters in and out
+  bool cost_pending = false;  // DevState::need_cost set and not yet evaluated
   uint8_t* fixed = nullptr;  // [C][9] frozen camera parameters, or NULL
   uint8_t* fixed_buf = nullptr;
   int32_t *cm_pt = nullptr, *pm_cam = nullptr, *pm_pt = nullptr;
