@@ -127,6 +127,15 @@ __device__ __forceinline__ void bred_store(float (&v)[NV], double* scratch, doub
   float2* red = reinterpret_cast<float2*>(scratch);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   constexpr int nw = BT / 32;
+  if constexpr (PRECISE && NV > 32 && NV <= 64) {
+    float w[64];
+#pragma unroll
+    for (int i = 0; i < 64; ++i) w[i] = i < NV ? v[i] : 0.f;
+    float h0, l0, h1, l1;
+    warp_rs64_ff(w, h0, l0, h1, l1);
+    if (2 * lane < NV) red[warp * NV + 2 * lane] = make_float2(h0, l0);
+    if (2 * lane + 1 < NV) red[warp * NV + 2 * lane + 1] = make_float2(h1, l1);
+  } else {
 #pragma unroll
   for (int i = 0; i < NV; ++i) {
     float hi = v[i], lo = 0.f;
@@ -141,6 +150,7 @@ __device__ __forceinline__ void bred_store(float (&v)[NV], double* scratch, doub
       }
     }
     if (lane == 0) red[warp * NV + i] = make_float2(hi, lo);
+  }
   }
   __syncthreads();
   for (int i = threadIdx.x; i < NV; i += BT) {

@@ -136,6 +136,45 @@ __device__ __forceinline__ void ff_add(float& hi, float& lo, float h2, float l2)
   lo = e - (hi - s);
 }
 
+// Warp reduce-scatter of 64 float-float values: five shuffle steps, each
+// halving the values a lane keeps (its partner lane takes the other half),
+// 62 shuffled pairs in all instead of 5 x 64.  Lane l returns the warp totals
+// of values 2l and 2l + 1 (after the step of offset o a lane keeps the upper
+// half iff its lane bit o is set, so the kept block starts at 2l).  The order
+// of the additions depends on the lane numbers only.
+template <int N, int OFF>
+__device__ __forceinline__ void rs_ff_step(float (&h)[32], float (&l)[32], int lane) {
+  const bool up = (lane & OFF) != 0;
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    float kh = up ? h[N + i] : h[i], kl = up ? l[N + i] : l[i];
+    const float gh = up ? h[i] : h[N + i], gl = up ? l[i] : l[N + i];
+    const float rh = __shfl_xor_sync(0xffffffffu, gh, OFF), rl = __shfl_xor_sync(0xffffffffu, gl, OFF);
+    ff_add(kh, kl, rh, rl);
+    h[i] = kh;
+    l[i] = kl;
+  }
+}
+__device__ __forceinline__ void warp_rs64_ff(const float (&v)[64], float& h0, float& l0, float& h1, float& l1) {
+  const int lane = threadIdx.x & 31;
+  float h[32], l[32];
+  const bool up = (lane & 16) != 0;
+#pragma unroll
+  for (int i = 0; i < 32; ++i) {
+    const float keep = up ? v[32 + i] : v[i];
+    const float give = up ? v[i] : v[32 + i];
+    two_sum(keep, __shfl_xor_sync(0xffffffffu, give, 16), h[i], l[i]);
+  }
+  rs_ff_step<16, 8>(h, l, lane);
+  rs_ff_step<8, 4>(h, l, lane);
+  rs_ff_step<4, 2>(h, l, lane);
+  rs_ff_step<2, 1>(h, l, lane);
+  h0 = h[0];
+  l0 = l[0];
+  h1 = h[1];
+  l1 = l[1];
+}
+
 // Sum NV per-thread values over the block and write them to out (NV
 // doubles), warps then the warps in order.  Doubles are reduced in double.
 // blockDim.x <= 1024.
@@ -168,6 +207,15 @@ __device__ __forceinline__ void block_sum_store(float (&v)[NV], double* __restri
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const int nw = (blockDim.x + 31) >> 5;
+  if constexpr (PRECISE && NV > 32 && NV <= 64) {
+    float w[64];
+#pragma unroll
+    for (int i = 0; i < 64; ++i) w[i] = i < NV ? v[i] : 0.f;
+    float h0, l0, h1, l1;
+    warp_rs64_ff(w, h0, l0, h1, l1);
+    if (2 * lane < NV) redf[warp][2 * lane] = make_float2(h0, l0);
+    if (2 * lane + 1 < NV) redf[warp][2 * lane + 1] = make_float2(h1, l1);
+  } else {
 #pragma unroll
   for (int i = 0; i < NV; ++i) {
     float hi = v[i], lo = 0.f;
@@ -182,6 +230,7 @@ __device__ __forceinline__ void block_sum_store(float (&v)[NV], double* __restri
       }
     }
     if (lane == 0) redf[warp][i] = make_float2(hi, lo);
+  }
   }
   __syncthreads();
   for (int i = threadIdx.x; i < NV; i += blockDim.x) {
