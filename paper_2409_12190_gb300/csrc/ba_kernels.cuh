@@ -155,6 +155,31 @@ __device__ __forceinline__ void rs_ff_step(float (&h)[32], float (&l)[32], int l
     l[i] = kl;
   }
 }
+// The same reduce-scatter for 16 plain floats (four steps, 15 shuffles):
+// lane l returns the warp total of value l >> 1 (lanes 2m and 2m + 1 both
+// hold value m).
+template <int N, int OFF>
+__device__ __forceinline__ void rs_f_step(float (&h)[16], int lane) {
+  const bool up = (lane & OFF) != 0;
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    const float k = up ? h[N + i] : h[i];
+    const float g = up ? h[i] : h[N + i];
+    h[i] = k + __shfl_xor_sync(0xffffffffu, g, OFF);
+  }
+}
+__device__ __forceinline__ float warp_rs16_f(const float (&v)[16]) {
+  const int lane = threadIdx.x & 31;
+  float h[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) h[i] = v[i];
+  rs_f_step<8, 16>(h, lane);
+  rs_f_step<4, 8>(h, lane);
+  rs_f_step<2, 4>(h, lane);
+  rs_f_step<1, 2>(h, lane);
+  return h[0] + __shfl_xor_sync(0xffffffffu, h[0], 1);
+}
+
 __device__ __forceinline__ void warp_rs64_ff(const float (&v)[64], float& h0, float& l0, float& h1, float& l1) {
   const int lane = threadIdx.x & 31;
   float h[32], l[32];
@@ -215,6 +240,12 @@ __device__ __forceinline__ void block_sum_store(float (&v)[NV], double* __restri
     warp_rs64_ff(w, h0, l0, h1, l1);
     if (2 * lane < NV) redf[warp][2 * lane] = make_float2(h0, l0);
     if (2 * lane + 1 < NV) redf[warp][2 * lane + 1] = make_float2(h1, l1);
+  } else if constexpr (!PRECISE && NV > 4 && NV <= 16) {
+    float w[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) w[i] = i < NV ? v[i] : 0.f;
+    const float s = warp_rs16_f(w);
+    if ((lane & 1) == 0 && (lane >> 1) < NV) redf[warp][lane >> 1] = make_float2(s, 0.f);
   } else {
 #pragma unroll
   for (int i = 0; i < NV; ++i) {
