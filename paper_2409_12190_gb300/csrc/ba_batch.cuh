@@ -135,6 +135,12 @@ __device__ __forceinline__ void bred_store(float (&v)[NV], double* scratch, doub
     warp_rs64_ff(w, h0, l0, h1, l1);
     if (2 * lane < NV) red[warp * NV + 2 * lane] = make_float2(h0, l0);
     if (2 * lane + 1 < NV) red[warp * NV + 2 * lane + 1] = make_float2(h1, l1);
+  } else if constexpr (!PRECISE && NV > 4 && NV <= 16) {
+    float w[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) w[i] = i < NV ? v[i] : 0.f;
+    const float s = warp_rs16_f(w);
+    if ((lane & 1) == 0 && (lane >> 1) < NV) red[warp * NV + (lane >> 1)] = make_float2(s, 0.f);
   } else {
 #pragma unroll
   for (int i = 0; i < NV; ++i) {
