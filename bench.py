@@ -54,7 +54,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--e2e-steps", type=int, default=0,
+                    help="trials of the end-to-end leg (default: --steps, the timed trials)")
     ap.add_argument("--profile-trials", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--jacobian", choices=["auto", "recompute", "store"], default="auto")
@@ -291,6 +292,8 @@ def run_ours(args):
     prob.solve(args.warmup)
     torch.cuda.synchronize()
     prob.stats()
+    # the end-to-end leg below replays the timed trials from this state
+    state0 = prob.get_state()
 
     stream = torch.cuda.current_stream()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -352,7 +355,11 @@ def run_ours(args):
     roofline["iteration_gbs"] = it_bytes / (prof_ms / 1000.0) / 1e9
     roofline["iteration_frac"] = roofline["iteration_gbs"] / peak
 
-    # end to end through the public API: pinned host inputs in, result out
+    # end to end through the public API: the same trials as the timed region
+    # (restarted from its starting state), each step uploading parameters and
+    # pixels from pinned host memory and reading parameters and cost back
+    e2e_steps = args.e2e_steps if args.e2e_steps > 0 else args.steps
+    prob.set_state(state0)
     hc = torch.empty((C, 9), dtype=torch.float32).pin_memory()
     hp = torch.empty((P, 3), dtype=torch.float32).pin_memory()
     hx = pix.cpu().pin_memory()
@@ -360,7 +367,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     barrier()
     t0 = time.perf_counter()
-    for _ in range(args.e2e_steps):
+    for _ in range(e2e_steps):
         prob.set_params(hc, hp)
         prob.set_pixels(hx)
         prob.lm_step()
@@ -369,9 +376,13 @@ def run_ours(args):
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     e2e_s = rank_max(e2e_s, dev, world)
-    e2e = {"value": world * args.e2e_steps / e2e_s, "unit": UNIT,
+    e2e_trials = prob.stats(cap=e2e_steps)
+    same = ([t["pcg_iters"] for t in e2e_trials] == [t["pcg_iters"] for t in trials[:e2e_steps]]
+            and [t["accepted"] for t in e2e_trials] == [t["accepted"] for t in trials[:e2e_steps]])
+    e2e = {"value": world * e2e_steps / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": (9 * C + 3 * P + 2 * O) * 4,
-           "d2h_bytes_per_step": (9 * C + 3 * P) * 4 + 8, "steps": args.e2e_steps}
+           "d2h_bytes_per_step": (9 * C + 3 * P) * 4 + 8, "steps": e2e_steps,
+           "same_trials_as_timed": same}
 
     if rank != 0:
         return
@@ -390,6 +401,7 @@ def run_ours(args):
                        "precision": "f32 per-observation, f64 reductions", "loss": "squared",
                        "pcg": f"block-Jacobi, maxiter {PCG_MAXITER}, tol {PCG_TOL}",
                        "pcg_iters_mean": statistics.mean(pcg) if pcg else None,
+                       "pcg_iters_total": sum(pcg),
                        "accepted": sum(t["accepted"] for t in trials),
                        "l2": "inputs larger than L2 (each PCG pass streams >0.6 GB of "
                              "per-observation data; L2 129 MB)",
@@ -499,8 +511,9 @@ def run_batch(args):
     oc = torch.empty((C, 9), dtype=torch.float32).pin_memory()
     op = torch.empty((P, 3), dtype=torch.float32).pin_memory()
     torch.cuda.synchronize()
+    e2e_steps = args.e2e_steps if args.e2e_steps > 0 else args.steps
     t0 = time.perf_counter()
-    for _ in range(args.e2e_steps):
+    for _ in range(e2e_steps):
         bt.reset(hc, hp)
         bt.solve(BATCH_ITERS)
         cams_d, pts_d = bt.params(split=False)
@@ -508,9 +521,9 @@ def run_batch(args):
         op.copy_(pts_d, non_blocking=True)
         torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    e2e = {"value": world * n_prob * BATCH_ITERS * args.e2e_steps / e2e_s, "unit": "problem LM iters/s",
+    e2e = {"value": world * n_prob * BATCH_ITERS * e2e_steps / e2e_s, "unit": "problem LM iters/s",
            "h2d_bytes_per_step": (9 * C + 3 * P) * 4, "d2h_bytes_per_step": (9 * C + 3 * P) * 4,
-           "steps": args.e2e_steps}
+           "steps": e2e_steps}
 
     if rank != 0:
         return

@@ -158,7 +158,8 @@ void enqueue_schur_product(ba_problem* h, const T* xc, int k, int check_done) {
       Prof pr(h, BA_K_PASS_B, k);
       // FP32 recompute mode: two gathers in flight per thread, next indices prefetched
       constexpr int UB = (MF && std::is_same<T, float>::value) ? 2 : 1;
-      k_pass_b<T, MF, UB, (UB > 1)><<<h->npieces, PIECE_THREADS, 0, s>>>(
+      constexpr int NT = UB > 1 ? PASSB_THREADS : PIECE_THREADS;
+      k_pass_b<T, MF, UB, (UB > 1), NT><<<h->npieces, NT, 0, s>>>(
           h->piece_cam, h->piece_beg, h->piece_end, h->cm_pt, (const T*)h->Jcm, (const T*)h->cm_sw,
           (const T*)h->ptab, (const T*)h->camtab, h->st, check_done, h->O, h->part);
     }
@@ -180,7 +181,8 @@ void enqueue_schur_product(ba_problem* h, const T* xc, int k, int check_done) {
   {
     Prof pr(h, BA_K_PASS_B, k);
     constexpr int UB = (MF && std::is_same<T, float>::value) ? 2 : 1;
-    k_pass_b<T, MF, UB, (UB > 1)><<<h->npieces, PIECE_THREADS, 0, s>>>(
+    constexpr int NT = UB > 1 ? PASSB_THREADS : PIECE_THREADS;
+    k_pass_b<T, MF, UB, (UB > 1), NT><<<h->npieces, NT, 0, s>>>(
         h->piece_cam, h->piece_beg, h->piece_end, h->cm_pt, (const T*)h->Jcm, (const T*)h->cm_sw,
         (const T*)h->ptab, (const T*)h->camtab, h->st, check_done, h->O, h->part);
   }
@@ -305,7 +307,9 @@ void enqueue_trial(ba_problem* h) {
   const ba_options& o = h->opt;
   {
     Prof pr(h, BA_K_OTHER);
-    k_lm_control<<<1, 256, 0, h->s>>>(h->npieces, h->part, h->ncb, h->dot_gc, h->nchunks, h->dot_gp, o.up, o.down,
+    // one block sums the per-piece and per-chunk partials (a few thousand
+    // strided doubles): 1024 threads keep more of those loads in flight
+    k_lm_control<<<1, 1024, 0, h->s>>>(h->npieces, h->part, h->ncb, h->dot_gc, h->nchunks, h->dot_gp, o.up, o.down,
                                       o.rho_good, o.rho_bad, o.lambda_min, o.lambda_max, h->st, h->stats, h->cap);
   }
   count_launch(2);

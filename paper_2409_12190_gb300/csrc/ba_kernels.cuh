@@ -63,6 +63,7 @@ namespace ba {
 
 constexpr int PIECE = 2048;          // max camera-major slots per piece
 constexpr int PIECE_THREADS = 256;
+constexpr int PASSB_THREADS = 128;    // pass B, FP32 recompute mode
 // The linearisation and Schur-block passes reduce 54 values per piece in
 // float-float arithmetic; fewer threads per piece spread that reduction over
 // more slots per thread.
@@ -1754,9 +1755,11 @@ __device__ __forceinline__ void pass_b_range(int beg, int end, const int32_t* __
 }
 
 // Pass B (camera-major): per piece, sum_k Jc_k^T (Jp_k t_p(k)); UB, PF as in
-// pass_b_range.
-template <typename T, bool MF, int UB = 1, bool PF = false>
-static __global__ void __launch_bounds__(PIECE_THREADS, UB > 1 ? 4 : 1)
+// pass_b_range.  NT threads per piece: the FP32 recompute mode runs 128
+// (16 slots per thread, the per-piece reduction amortised over twice the
+// work of a 256-thread CTA; 8 CTAs per SM at the same 64-register cap).
+template <typename T, bool MF, int UB = 1, bool PF = false, int NT = PIECE_THREADS>
+static __global__ void __launch_bounds__(NT, UB > 1 ? 1024 / NT : 1)
 k_pass_b(const int32_t* __restrict__ piece_cam, const int32_t* __restrict__ piece_beg,
          const int32_t* __restrict__ piece_end, const int32_t* __restrict__ cm_pt,
          const T* __restrict__ Jcm, const T* __restrict__ cm_sw, const T* __restrict__ ptab,
@@ -1774,7 +1777,7 @@ k_pass_b(const int32_t* __restrict__ piece_cam, const int32_t* __restrict__ piec
   T acc[9];
 #pragma unroll
   for (int i = 0; i < 9; ++i) acc[i] = T(0);
-  pass_b_range<T, MF, PIECE_THREADS, UB, PF>(piece_beg[b], piece_end[b], cm_pt, Jcm, cm_sw, ptab, ctl, O, acc);
+  pass_b_range<T, MF, NT, UB, PF>(piece_beg[b], piece_end[b], cm_pt, Jcm, cm_sw, ptab, ctl, O, acc);
   block_sum_store<9, false>(acc, part + (long long)PART * b);
 }
 
