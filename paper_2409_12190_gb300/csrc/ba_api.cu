@@ -299,7 +299,9 @@ void enqueue_trial(ba_problem* h) {
   const T delta = (T)(h->opt.huber_delta > 0 ? h->opt.huber_delta : 0.0);
   {
     Prof pr(h, BA_K_COST);
-    k_cost_cam<T, true, MF><<<h->npieces, PIECE_THREADS, 0, h->s>>>(
+    // FP32 recompute mode: 16 slots per thread, as in pass B
+    constexpr int NT = (MF && std::is_same<T, float>::value) ? PASSB_THREADS : PIECE_THREADS;
+    k_cost_cam<T, true, MF, NT><<<h->npieces, NT, 0, h->s>>>(
         h->piece_cam, h->piece_beg, h->piece_end, h->cm_pt, (const T*)h->cm_px, (const T*)h->cams,
         (const T*)h->pts, h->st, 1, delta, h->C, h->P, h->O, (const T*)h->Jcm, (const T*)h->cm_sw,
         (const T*)h->camtab, (const T*)h->xT, (const T*)h->dp, h->part);

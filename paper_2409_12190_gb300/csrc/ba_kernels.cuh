@@ -63,7 +63,7 @@ namespace ba {
 
 constexpr int PIECE = 2048;          // max camera-major slots per piece
 constexpr int PIECE_THREADS = 256;
-constexpr int PASSB_THREADS = 128;    // pass B, FP32 recompute mode
+constexpr int PASSB_THREADS = 128;    // pass B and the cost pass, FP32 recompute mode
 // The linearisation and Schur-block passes reduce 54 values per piece in
 // float-float arithmetic; fewer threads per piece spread that reduction over
 // more slots per thread.
@@ -1479,9 +1479,11 @@ k_pass_a2(const int32_t* __restrict__ pchunk, int P, const int32_t* __restrict__
       T z0 = 0, z1 = 0, z2 = 0;
       const int q1 = rowptr_pt[j + 1];
       for (int q = rowptr_pt[j]; q < q1; ++q) {
-        z0 += sz[4 * (q - s0)];
-        z1 += sz[4 * (q - s0) + 1];
-        z2 += sz[4 * (q - s0) + 2];
+        T a, b, c, pad;
+        load4(sz + 4 * (q - s0), a, b, c, pad);
+        z0 += a;
+        z1 += b;
+        z2 += c;
       }
       gd += pass_a_point<T, MODE>(j, P, z0, z1, z2, Vinv, ptab, dp, y0, gp, pts_buf, cur);
     }
@@ -1602,9 +1604,11 @@ k_pass_fa(const int32_t* __restrict__ pchunk, int P, const int32_t* __restrict__
       }
       T z0 = 0, z1 = 0, z2 = 0;
       for (int q = p0; q < p1; ++q) {
-        z0 += sz[4 * (q - s0)];
-        z1 += sz[4 * (q - s0) + 1];
-        z2 += sz[4 * (q - s0) + 2];
+        T a, b, c, pad;
+        load4(sz + 4 * (q - s0), a, b, c, pad);
+        z0 += a;
+        z1 += b;
+        z2 += c;
       }
       if (j == jp && MODE == 0) {
         // V*^{-1} already in registers: t_j as in pass_a_point
@@ -2036,8 +2040,8 @@ __device__ __forceinline__ void cost_cam_range(int beg, int end, const int32_t* 
 // Camera-major pass over the pieces: cost 1/2 sum rho at the parameters in
 // buffer (which == 0: current, 1: trial), and with MODEL the quadratic term
 // sum_k |Jc_k dc + Jp_k dp|^2 of the model reduction (weights folded in).
-template <typename T, bool MODEL, bool MF>
-static __global__ void __launch_bounds__(PIECE_THREADS)
+template <typename T, bool MODEL, bool MF, int NT = PIECE_THREADS>
+static __global__ void __launch_bounds__(NT)
 k_cost_cam(const int32_t* __restrict__ piece_cam, const int32_t* __restrict__ piece_beg,
            const int32_t* __restrict__ piece_end, const int32_t* __restrict__ cm_pt,
            const T* __restrict__ cm_px, const T* __restrict__ cams_buf, const T* __restrict__ pts_buf,
@@ -2061,7 +2065,8 @@ k_cost_cam(const int32_t* __restrict__ piece_cam, const int32_t* __restrict__ pi
   const T* pts = pts_buf + (long long)buf * 3 * P;
   const T* pts_old = pts_buf + (long long)cur * 3 * P;
   double cost = 0.0, quad = 0.0;
-  cost_cam_range<T, MODEL, MF, PIECE_THREADS>(piece_beg[b], piece_end[b], cm_pt, cm_px, pts, pts_old, sct, sold,
+  static_assert(NT >= 64 + CT + PV, "the staging of the model term needs 64 + CT + PV threads");
+  cost_cam_range<T, MODEL, MF, NT>(piece_beg[b], piece_end[b], cm_pt, cm_px, pts, pts_old, sct, sold,
                                               sdc, delta, O, Jcm, cm_sw, dp, cost, quad);
   double v[2] = {cost, quad};
   block_sum_store<2>(v, part + (long long)PART * b);
