@@ -149,7 +149,8 @@ void enqueue_schur_product(ba_problem* h, const T* xc, int k, int check_done) {
   if (MF && h->fa) {
     {
       Prof pr(h, BA_K_PASS_FA, k);
-      k_pass_fa<T, 0><<<h->nchunks, CHUNK_THREADS, fa_smem<T>(), s>>>(
+      auto fa = h->pm_sw ? k_pass_fa<T, 0, true> : k_pass_fa<T, 0, false>;
+      fa<<<h->nchunks, CHUNK_THREADS, fa_smem<T>(), s>>>(
           h->pchunk, h->P, h->rowptr_pt, h->pm_pt, h->pm_lc, (const T*)h->pm_sw, h->chunk_cams, h->chunk_cam_ptr,
           (const T*)h->camtab, xc, (const T*)h->Vinv, h->st, check_done, (T*)h->ptab, nullptr, nullptr, nullptr,
           nullptr, nullptr, h->chunk_hdr);
@@ -159,7 +160,8 @@ void enqueue_schur_product(ba_problem* h, const T* xc, int k, int check_done) {
       // FP32 recompute mode: two gathers in flight per thread, next indices prefetched
       constexpr int UB = (MF && std::is_same<T, float>::value) ? 2 : 1;
       constexpr int NT = UB > 1 ? PASSB_THREADS : PIECE_THREADS;
-      k_pass_b<T, MF, UB, (UB > 1), NT><<<h->npieces, NT, 0, s>>>(
+      auto pb = h->cm_sw ? k_pass_b<T, MF, UB, (UB > 1), NT, true> : k_pass_b<T, MF, UB, (UB > 1), NT, false>;
+      pb<<<h->npieces, NT, 0, s>>>(
           h->piece_cam, h->piece_beg, h->piece_end, h->cm_pt, (const T*)h->Jcm, (const T*)h->cm_sw,
           (const T*)h->ptab, (const T*)h->camtab, h->st, check_done, h->O, h->part);
     }
@@ -182,7 +184,8 @@ void enqueue_schur_product(ba_problem* h, const T* xc, int k, int check_done) {
     Prof pr(h, BA_K_PASS_B, k);
     constexpr int UB = (MF && std::is_same<T, float>::value) ? 2 : 1;
     constexpr int NT = UB > 1 ? PASSB_THREADS : PIECE_THREADS;
-    k_pass_b<T, MF, UB, (UB > 1), NT><<<h->npieces, NT, 0, s>>>(
+    auto pb = h->cm_sw ? k_pass_b<T, MF, UB, (UB > 1), NT, true> : k_pass_b<T, MF, UB, (UB > 1), NT, false>;
+    pb<<<h->npieces, NT, 0, s>>>(
         h->piece_cam, h->piece_beg, h->piece_end, h->cm_pt, (const T*)h->Jcm, (const T*)h->cm_sw,
         (const T*)h->ptab, (const T*)h->camtab, h->st, check_done, h->O, h->part);
   }
@@ -257,7 +260,8 @@ void enqueue_solve(ba_problem* h, const double* lam_ptr, int maxiter, double tol
   }
   if (MF && h->fa) {
     Prof pr(h, BA_K_BACKSUB);
-    k_pass_fa<T, 1><<<h->nchunks, CHUNK_THREADS, fa_smem<T>(), s>>>(
+    auto fa = h->pm_sw ? k_pass_fa<T, 1, true> : k_pass_fa<T, 1, false>;
+    fa<<<h->nchunks, CHUNK_THREADS, fa_smem<T>(), s>>>(
         h->pchunk, h->P, h->rowptr_pt, h->pm_pt, h->pm_lc, (const T*)h->pm_sw, h->chunk_cams, h->chunk_cam_ptr,
         (const T*)h->camtab, (const T*)h->xT, (const T*)h->Vinv, h->st, 0, (T*)h->ptab, (T*)h->dp, (const T*)h->y0,
         h->gp, (T*)h->pts, h->dot_gp, h->chunk_hdr);
@@ -531,8 +535,10 @@ ba_status create_impl(ba_problem* h, const void* cams, const void* points, const
   }
   if (lin_pt_smem<T>(true) > 48 * 1024)
     CU(cudaFuncSetAttribute(k_lin_pt<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, lin_pt_smem<T>(true)));
-  CU(cudaFuncSetAttribute(k_pass_fa<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, fa_smem<T>()));
-  CU(cudaFuncSetAttribute(k_pass_fa<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, fa_smem<T>()));
+  CU(cudaFuncSetAttribute(k_pass_fa<T, 0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, fa_smem<T>()));
+  CU(cudaFuncSetAttribute(k_pass_fa<T, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, fa_smem<T>()));
+  CU(cudaFuncSetAttribute(k_pass_fa<T, 0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, fa_smem<T>()));
+  CU(cudaFuncSetAttribute(k_pass_fa<T, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, fa_smem<T>()));
 
 
   // observation data in both orders

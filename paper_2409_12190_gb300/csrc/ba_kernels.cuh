@@ -1518,9 +1518,10 @@ k_pass_a2(const int32_t* __restrict__ pchunk, int P, const int32_t* __restrict__
 // intermediate leave the SM.  Each thread issues all loads of its slots and
 // of its point before the first barrier.  The per-observation products and
 // the per-point sums are those of passes A1 and A2 (same order).  MODE as in
-// k_pass_a2.
+// k_pass_a2.  SW = false (no robust loss, sqrt(w) = 1) compiles the weight's
+// loads and products out; the results are the same bits.
 
-template <typename T, int MODE>
+template <typename T, int MODE, bool SW = true>
 static __global__ void __launch_bounds__(CHUNK_THREADS, sizeof(T) == 4 ? 5 : 1)
 k_pass_fa(const int32_t* __restrict__ pchunk, int P, const int32_t* __restrict__ rowptr_pt,
           const int32_t* __restrict__ pm_pt, const int16_t* __restrict__ pm_lc, const T* __restrict__ pm_sw,
@@ -1530,6 +1531,7 @@ k_pass_fa(const int32_t* __restrict__ pchunk, int P, const int32_t* __restrict__
           const T* __restrict__ y0, const double* __restrict__ gp, T* __restrict__ pts_buf,
           double* __restrict__ dot_gp, const int4* __restrict__ chunk_hdr) {
   if (MODE == 0 && check_done && st->pcg_done) return;
+  if (!SW) pm_sw = nullptr;  // no robust loss: sqrt(w) = 1 folds away
   __shared__ T sct[FA_CAMS * FA_CT];
   __shared__ T sxv[FA_CAMS * FA_XV];
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1762,7 +1764,8 @@ __device__ __forceinline__ void pass_b_range(int beg, int end, const int32_t* __
 // pass_b_range.  NT threads per piece: the FP32 recompute mode runs 128
 // (16 slots per thread, the per-piece reduction amortised over twice the
 // work of a 256-thread CTA; 8 CTAs per SM at the same 64-register cap).
-template <typename T, bool MF, int UB = 1, bool PF = false, int NT = PIECE_THREADS>
+// SW as in k_pass_fa.
+template <typename T, bool MF, int UB = 1, bool PF = false, int NT = PIECE_THREADS, bool SW = true>
 static __global__ void __launch_bounds__(NT, UB > 1 ? 1024 / NT : 1)
 k_pass_b(const int32_t* __restrict__ piece_cam, const int32_t* __restrict__ piece_beg,
          const int32_t* __restrict__ piece_end, const int32_t* __restrict__ cm_pt,
@@ -1770,6 +1773,7 @@ k_pass_b(const int32_t* __restrict__ piece_cam, const int32_t* __restrict__ piec
          const T* __restrict__ camtab, const DevState* __restrict__ st, int check_done, int O,
          double* __restrict__ part) {
   if (check_done && st->pcg_done) return;
+  if (!SW) cm_sw = nullptr;  // no robust loss: sqrt(w) = 1 folds away
   __shared__ T sct[16];
   const int b = blockIdx.x;
   const int c = piece_cam[b];
