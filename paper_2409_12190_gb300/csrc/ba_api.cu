@@ -150,10 +150,10 @@ void enqueue_schur_product(ba_problem* h, const T* xc, int k, int check_done) {
     {
       Prof pr(h, BA_K_PASS_FA, k);
       auto fa = h->pm_sw ? k_pass_fa<T, 0, true> : k_pass_fa<T, 0, false>;
-      fa<<<h->nchunks, CHUNK_THREADS, fa_smem<T>(), s>>>(
+      fa<<<h->nchunks, CHUNK_THREADS, fa_smem<T>(h->fa_nc), s>>>(
           h->pchunk, h->P, h->rowptr_pt, h->pm_pt, h->pm_lc, (const T*)h->pm_sw, h->chunk_cams, h->chunk_cam_ptr,
           (const T*)h->camtab, xc, (const T*)h->Vinv, h->st, check_done, (T*)h->ptab, nullptr, nullptr, nullptr,
-          nullptr, nullptr, h->chunk_hdr);
+          nullptr, nullptr, h->chunk_hdr, h->fa_nc);
     }
     {
       Prof pr(h, BA_K_PASS_B, k);
@@ -261,10 +261,10 @@ void enqueue_solve(ba_problem* h, const double* lam_ptr, int maxiter, double tol
   if (MF && h->fa) {
     Prof pr(h, BA_K_BACKSUB);
     auto fa = h->pm_sw ? k_pass_fa<T, 1, true> : k_pass_fa<T, 1, false>;
-    fa<<<h->nchunks, CHUNK_THREADS, fa_smem<T>(), s>>>(
+    fa<<<h->nchunks, CHUNK_THREADS, fa_smem<T>(h->fa_nc), s>>>(
         h->pchunk, h->P, h->rowptr_pt, h->pm_pt, h->pm_lc, (const T*)h->pm_sw, h->chunk_cams, h->chunk_cam_ptr,
         (const T*)h->camtab, (const T*)h->xT, (const T*)h->Vinv, h->st, 0, (T*)h->ptab, (T*)h->dp, (const T*)h->y0,
-        h->gp, (T*)h->pts, h->dot_gp, h->chunk_hdr);
+        h->gp, (T*)h->pts, h->dot_gp, h->chunk_hdr, h->fa_nc);
     count_launch(2);
     return;
   }
@@ -535,10 +535,10 @@ ba_status create_impl(ba_problem* h, const void* cams, const void* points, const
   }
   if (lin_pt_smem<T>(true) > 48 * 1024)
     CU(cudaFuncSetAttribute(k_lin_pt<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, lin_pt_smem<T>(true)));
-  CU(cudaFuncSetAttribute(k_pass_fa<T, 0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, fa_smem<T>()));
-  CU(cudaFuncSetAttribute(k_pass_fa<T, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, fa_smem<T>()));
-  CU(cudaFuncSetAttribute(k_pass_fa<T, 0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, fa_smem<T>()));
-  CU(cudaFuncSetAttribute(k_pass_fa<T, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, fa_smem<T>()));
+  CU(cudaFuncSetAttribute(k_pass_fa<T, 0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, fa_smem<T>(FA_CAMS)));
+  CU(cudaFuncSetAttribute(k_pass_fa<T, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, fa_smem<T>(FA_CAMS)));
+  CU(cudaFuncSetAttribute(k_pass_fa<T, 0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, fa_smem<T>(FA_CAMS)));
+  CU(cudaFuncSetAttribute(k_pass_fa<T, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, fa_smem<T>(FA_CAMS)));
 
 
   // observation data in both orders
@@ -580,6 +580,7 @@ ba_status create_impl(ba_problem* h, const void* cams, const void* points, const
       }
       ptr[k] = (int32_t)list.size();
       list.insert(list.end(), tmp.begin(), tmp.end());
+      h->fa_nc = std::max(h->fa_nc, (int)tmp.size());
       for (int q = s0; q < s1; ++q)
         lc[q] = (int16_t)(std::lower_bound(tmp.begin(), tmp.end(), pmc[q]) - tmp.begin());
     }

@@ -83,9 +83,12 @@ constexpr int CHUNK_THREADS = 256;
 constexpr int FA_CAMS = 128;
 constexpr int FA_CT = 17;  // padded strides: different cameras in different banks
 constexpr int FA_XV = 13;
-// dynamic shared memory of k_pass_fa: z per slot, then the chunk's points
+// dynamic shared memory of k_pass_fa: z per slot, the chunk's points, then
+// the tables and vectors of at most nc cameras (the most any chunk sees)
 template <typename T>
-constexpr int fa_smem() { return (CHUNK_SLOTS + CHUNK_PTS) * 4 * (int)sizeof(T); }
+constexpr int fa_smem(int nc) {
+  return ((CHUNK_SLOTS + CHUNK_PTS) * 4 + nc * (FA_CT + FA_XV)) * (int)sizeof(T);
+}
 // dynamic shared memory of k_lin_pt: its per-slot sums, and with the chunk
 // headers the chunk's camera tables and points
 template <typename T>
@@ -1514,7 +1517,9 @@ k_pass_a2(const int32_t* __restrict__ pchunk, int P, const int32_t* __restrict__
 // numbered by their first camera): the chunk's cameras -- their tables and
 // vectors x_c -- are staged in shared memory (at most FA_CAMS of them, the
 // list built in the symbolic phase, pm_lc the position of each slot's camera
-// in it), so no per-observation camera data and no per-observation
+// in it; the staging area is sized by nc_max, the most cameras any chunk of
+// the problem sees, which leaves the rest of the SM's carveout to L1 for the
+// point gathers), so no per-observation camera data and no per-observation
 // intermediate leave the SM.  Each thread issues all loads of its slots and
 // of its point before the first barrier.  The per-observation products and
 // the per-point sums are those of passes A1 and A2 (same order).  MODE as in
@@ -1529,14 +1534,14 @@ k_pass_fa(const int32_t* __restrict__ pchunk, int P, const int32_t* __restrict__
           const T* __restrict__ camtab, const T* __restrict__ xc, const T* __restrict__ Vinv,
           const DevState* __restrict__ st, int check_done, T* __restrict__ ptab, T* __restrict__ dp,
           const T* __restrict__ y0, const double* __restrict__ gp, T* __restrict__ pts_buf,
-          double* __restrict__ dot_gp, const int4* __restrict__ chunk_hdr) {
+          double* __restrict__ dot_gp, const int4* __restrict__ chunk_hdr, int nc_max) {
   if (MODE == 0 && check_done && st->pcg_done) return;
   if (!SW) pm_sw = nullptr;  // no robust loss: sqrt(w) = 1 folds away
-  __shared__ T sct[FA_CAMS * FA_CT];
-  __shared__ T sxv[FA_CAMS * FA_XV];
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sz = reinterpret_cast<T*>(smem_raw);  // [CHUNK_SLOTS][4]
   T* sX = sz + 4 * CHUNK_SLOTS;            // [CHUNK_PTS][4]: the chunk's points
+  T* sct = sX + 4 * CHUNK_PTS;             // [nc_max][FA_CT]: camera tables
+  T* sxv = sct + nc_max * FA_CT;           // [nc_max][FA_XV]: camera vectors
   constexpr int U = CHUNK_SLOTS / CHUNK_THREADS;
   const int k = blockIdx.x;
   // the chunk's header: first/last point and slot, camera list, and the

@@ -42,6 +42,7 @@ struct ba_problem {
   // point chunk (chunk_cams[chunk_cam_ptr[k] ..]) and each point-major slot's
   // position in its chunk's list
   bool fa = false;
+  int fa_nc = 0;  // the most cameras one point chunk sees (fused pass A)
   int32_t *chunk_cams = nullptr, *chunk_cam_ptr = nullptr;
   int16_t* pm_lc = nullptr;
   int4* chunk_hdr = nullptr;  // [nchunks][2] headers of the fused pass
