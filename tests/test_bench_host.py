@@ -1,0 +1,61 @@
+"""Host logic of bench.py's roofline block, on the CPU: algorithmic bytes per
+launch, the committed ncu traffic used only for the kernel source it was
+taken on, and the peak taken from the measured-peaks file when present."""
+import json
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def test_fused_pass_a_bytes_are_its_arrays_read_or_written_once():
+    C, P, O = 4000, 1_200_000, 8_044_313
+    # per observation: point index (4) + camera position in the chunk (2);
+    # per point: rowptr (4), X (4 floats), V*^-1 (6 floats), t (4 floats)
+    assert bench.algorithmic_bytes("pass_fa", C, P, O, 4860, 4, True) == O * 6 + P * (4 + 4 * 14)
+    # a robust loss adds sqrt(w) per observation
+    assert (bench.algorithmic_bytes("pass_fa", C, P, O, 4860, 4, True, huber=True)
+            - bench.algorithmic_bytes("pass_fa", C, P, O, 4860, 4, True)) == 4 * O
+
+
+def test_pass_b_bytes_stored_planes_versus_recompute():
+    C, P, O, npc = 250, 60_000, 480_380, 300
+    rec = bench.algorithmic_bytes("pass_b", C, P, O, npc, 4, True)
+    sto = bench.algorithmic_bytes("pass_b", C, P, O, npc, 4, False)
+    # the stored mode streams 18 FP32 planes per observation on top
+    assert sto - rec == 18 * 4 * O
+    # FP64 doubles every floating-point array
+    assert bench.algorithmic_bytes("pass_b", C, P, O, npc, 8, True) > rec
+
+
+def test_measured_traffic_only_for_the_source_it_was_taken_on(tmp_path, monkeypatch):
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    (prof / "ncu_traffic.json").write_text(json.dumps(
+        {"pass_fa": {"dram_bytes_per_launch": 1.5e8, "source_hash": "abc"}}))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.measured_traffic("pass_fa", "abc") == 1.5e8
+    assert bench.measured_traffic("pass_fa", "def") is None
+    assert bench.measured_traffic("pass_b", "abc") is None
+
+
+def test_kernel_source_hash_is_stable_and_short():
+    h = bench.kernel_source_hash()
+    assert h == bench.kernel_source_hash() and len(h) == 16
+    int(h, 16)
+
+
+def test_peak_from_the_measured_file_else_the_fallback(tmp_path, monkeypatch):
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.peaks() == (6800.0, "fallback")
+    (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps({"hbm_gbs": 6807.2}))
+    assert bench.peaks() == (6807.2, "measured")
+
+
+@pytest.mark.parametrize("mhz,tflops", [(2070.0, 80.54784), (1000.0, 38.912)])
+def test_fp32_alu_peak(mhz, tflops):
+    assert bench.fp32_peak_tflops(mhz) == pytest.approx(tflops)
