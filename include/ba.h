@@ -100,7 +100,9 @@ typedef struct {
   int32_t reserved;
 } ba_iter_stats;
 
-/* Fill *opt with the defaults listed above. */
+/* Fill *opt with the defaults listed above (the trust-region factors and
+ * PCG settings of the paper's minimum code example, Sec. IV; the rest are
+ * this library's readings). */
 ba_status ba_options_default(ba_options* opt);
 
 /* Create a problem (C cameras, P points, O observations), run the cached
@@ -117,7 +119,8 @@ ba_status ba_problem_create(ba_problem** out, int C, int P, int O,
                             const void* pixels, const ba_options* opt,
                             void* stream);
 
-/* Free a problem and everything it owns (NULL is accepted). */
+/* Free a problem and everything it owns (NULL is accepted).  Resource
+ * management: no counterpart in the paper. */
 ba_status ba_problem_destroy(ba_problem* h);
 
 /* One LM trial (Alg. 1 loop body): linearise if theta changed (a1, a2),
@@ -131,14 +134,15 @@ ba_status ba_lm_step(ba_problem* h, void* stream);
  * (App. B) and replayed.  No host synchronisation. */
 ba_status ba_solve(ba_problem* h, int iters, void* stream);
 
-/* Copy the current (last accepted) parameters to cams_out [C][9] and
- * points_out [P][3] (any). Either may be NULL.  Stream-ordered (no host
+/* Copy the current (last accepted) parameters theta of Eq. 1 (Sec. III-A)
+ * to cams_out [C][9] and points_out [P][3] (any). Either may be NULL.  Stream-ordered (no host
  * synchronisation): into pinned or device memory the copy completes on the
  * stream; the caller synchronises before reading. */
 ba_status ba_get_params(ba_problem* h, void* cams_out, void* points_out,
                         void* stream);
 
-/* Replace the parameters (any; either may be NULL to keep it); the cost is
+/* Replace the parameters theta of Eq. 1 (any; either may be NULL to keep
+ * it); the cost is
  * re-evaluated by the next trial or by the next call that reads it
  * (ba_get_scalars, ba_get_state), and the next trial re-linearises.  lambda
  * is kept.  Stream-ordered: a pinned or device source must stay valid until
@@ -146,33 +150,38 @@ ba_status ba_get_params(ba_problem* h, void* cams_out, void* points_out,
 ba_status ba_set_params(ba_problem* h, const void* cams, const void* points,
                         void* stream);
 
-/* Replace the observed pixels (any, [O][2]); the observation structure is
+/* Replace the observed pixels x_k of Eq. 1 (any, [O][2]); the observation
+ * structure is
  * kept; the cost is re-evaluated as after ba_set_params and the next trial
  * re-linearises. */
 ba_status ba_set_pixels(ba_problem* h, const void* pixels, void* stream);
 
-/* Copy up to cap statistics records (oldest first among the last cap
- * trials) to host_out; *n_out = number copied.  Synchronises the stream of
+/* Copy up to cap statistics records, one per pass of Alg. 1's loop (Sec.
+ * III-B; the gain ratio is the ratio of actual to predicted reduction of
+ * Sec. IV), oldest first among the last cap trials, to host_out; *n_out = number copied.  Synchronises the stream of
  * the problem.  Returns BA_ERR_NONFINITE if a trial since the last call saw
  * a non-finite trial cost (such trials are rejected, theta is unchanged). */
 ba_status ba_get_stats(ba_problem* h, ba_iter_stats* host_out, int cap,
                        int* n_out);
 
-/* Current cost F(theta) and damping lambda, copied to the host.
- * Synchronises. */
+/* Current cost F(theta) (Eq. 1) and damping lambda (Eq. 2), copied to the
+ * host.  Synchronises. */
 ba_status ba_get_scalars(ba_problem* h, double* cost, double* lambda);
 
-/* Set the damping of the next trial (lambda > 0, e.g. to restart a solve
- * after new observations).  Synchronises. */
+/* Set the damping lambda of Eq. 2 for the next trial (lambda > 0, e.g. to
+ * restart a solve after new observations).  Synchronises. */
 ba_status ba_set_lambda(ba_problem* h, double lambda);
 
-/* Checkpoint: the number of doubles ba_get_state writes (9C + 3P + 4). */
+/* Checkpoint (no counterpart in the paper): the number of doubles
+ * ba_get_state writes (9C + 3P + 4). */
 size_t ba_state_size(const ba_problem* h);
-/* Write theta, cost, lambda and the trial counter to host_state (host,
+/* Checkpoint (no counterpart in the paper): write theta, cost, lambda and
+ * the trial counter to host_state (host,
  * ba_state_size doubles; parameters converted to double).  Synchronises. */
 ba_status ba_get_state(ba_problem* h, double* host_state);
-/* Restore a state written by ba_get_state on a problem with the same
- * C, P, O and precision.  Synchronises. */
+/* Resume (no counterpart in the paper): restore a state written by
+ * ba_get_state on a problem with the same C, P, O and precision.
+ * Synchronises. */
 ba_status ba_set_state(ba_problem* h, const double* host_state);
 
 /* Freeze camera parameters: mask (any, uint8 [C][9], nonzero = frozen) or
@@ -204,7 +213,8 @@ ba_status ba_backward(ba_problem* h, double lambda, int maxiter, double tol,
                       void* dL_dpoints0_out, int* iters, double* rel_res,
                       void* stream);
 
-/* Thread-local message of the last failing call ("" if none). */
+/* Thread-local message of the last failing call ("" if none).  Error
+ * reporting: no counterpart in the paper. */
 const char* ba_last_error(void);
 
 /* ---- step-level entry points (same arithmetic as ba_lm_step) ---------- */
@@ -242,7 +252,8 @@ ba_status ba_damped_solve(ba_problem* h, double lambda, int maxiter,
 
 /* ---- stand-alone operations -------------------------------------------- */
 
-/* pixels_out[k] = pi(cams[cam_idx[k]], points[pt_idx[k]]) for k < O.
+/* pixels_out[k] = pi(cams[cam_idx[k]], points[pt_idx[k]]) for k < O: the
+ * projection of Eq. 1 with the camera model above.
  * All pointers dev; precision selects float or double.  Indices are not
  * checked (they must be in range). */
 ba_status ba_project(int precision, int C, int P, int O, const void* cams,
@@ -278,7 +289,8 @@ ba_status ba_csr_build_noalloc(const int32_t* keys, int n, int n_keys,
                                void* stream);
 
 /* Number of kernel launches the library has issued in this process (for
- * launch accounting in benchmarks; graph replays count every node). */
+ * launch accounting in benchmarks; graph replays count every node).
+ * Measurement aid: no counterpart in the paper. */
 uint64_t ba_kernel_launch_count(void);
 
 /* Kernel classes timed by ba_profile_trials. */
@@ -302,7 +314,8 @@ typedef struct {
   double trial_ms;              /* event time of the whole trials */
 } ba_kernel_times;
 
-/* Run iters LM trials (same arithmetic and state changes as ba_solve) with
+/* Measurement aid (no counterpart in the paper).  Run iters LM trials
+ * (Alg. 1; same arithmetic and state changes as ba_solve) with
  * direct launches and a CUDA event pair around every kernel, on the
  * problem's stream, and sum the durations per kernel class into *out (host).
  * PCG launches after convergence (which exit at once) are not counted.
@@ -325,7 +338,9 @@ typedef struct ba_batch ba_batch; /* opaque, owned by the library */
 /* Cameras per problem accepted by the batched form. */
 #define BA_BATCH_MAX_CAMS 28
 
-/* Create a batch of nprob problems.  cam_counts, pt_counts, obs_counts
+/* Create a batch of nprob problems, each the problem of Eq. 1 with its own
+ * symbolic phase (Sec. IV-B); batching itself has no counterpart in the
+ * paper.  cam_counts, pt_counts, obs_counts
  * (host, [nprob]) give problem b's C_b in [1, BA_BATCH_MAX_CAMS], P_b >= 1
  * and O_b >= 1; the totals must fit in int32.  cams [sum C_b][9], points
  * [sum P_b][3], pixels [sum O_b][2] (any) and cam_idx, pt_idx [sum O_b]
@@ -342,27 +357,33 @@ ba_status ba_batch_create(ba_batch** out, int nprob, const int32_t* cam_counts,
                           const int32_t* cam_idx, const int32_t* pt_idx,
                           const void* pixels, const ba_options* opt,
                           void* stream);
+/* Free a batch (NULL is accepted).  Resource management: no counterpart in
+ * the paper. */
 ba_status ba_batch_destroy(ba_batch* h);
 
-/* Run iters LM trials of every problem: ONE persistent kernel launch
+/* Run iters LM trials (Alg. 1, Sec. III-B) of every problem: ONE persistent
+ * kernel launch
  * (replayed from a CUDA graph) in which each CTA takes whole problems
  * from a work list.  Stream-ordered. */
 ba_status ba_batch_solve(ba_batch* h, int iters, void* stream);
 
-/* Current parameters of every problem, concatenated in the caller's order
+/* Current parameters theta (Eq. 1) of every problem, concatenated in the
+ * caller's order
  * (cams_out [sum C_b][9], points_out [sum P_b][3], dev; either may be
  * NULL).  Stream-ordered. */
 ba_status ba_batch_get_params(ba_batch* h, void* cams_out, void* points_out,
                               void* stream);
 
-/* Restart every problem from the given parameters (any; NULL: the
+/* Restart every problem (Alg. 1 from its start) from the given parameters
+ * (any; NULL: the
  * parameters given at creation): damping lambda0, trial count and
  * statistics cleared, cost re-evaluated on the next solve.
  * Stream-ordered. */
 ba_status ba_batch_reset(ba_batch* h, const void* cams, const void* points,
                          void* stream);
 
-/* Per-problem statistics: host_out [nprob][cap] (host) receives, for each
+/* Per-problem statistics, the records of ba_get_stats (one per pass of
+ * Alg. 1's loop): host_out [nprob][cap] (host) receives, for each
  * problem, its last min(trials, cap, max_stats) trials oldest first in row
  * b; n_out [nprob] (host) their counts.  Synchronises.  Returns
  * BA_ERR_NONFINITE (after filling the outputs) if a trial of some problem
@@ -370,20 +391,25 @@ ba_status ba_batch_reset(ba_batch* h, const void* cams, const void* points,
 ba_status ba_batch_get_stats(ba_batch* h, ba_iter_stats* host_out, int cap,
                              int* n_out);
 
-/* Cost at the current parameters and next damping of every problem
+/* Cost F (Eq. 1) at the current parameters and next damping lambda (Eq. 2)
+ * of every problem
  * (host [nprob] each; either may be NULL).  Synchronises. */
 ba_status ba_batch_get_scalars(ba_batch* h, double* cost, double* lambda);
 
-/* Launch configuration of ba_batch_solve (results do not depend on it):
+/* Launch configuration of ba_batch_solve (no counterpart in the paper;
+ * results do not depend on it):
  * ctas_per_sm in [1, 64] CTAs per SM in the persistent grid (capped at
  * the number of problems), variant 0 or 1 (register budget for 1 or 2
  * resident CTAs per SM), order 0 (largest problems first) or 1 (the
  * caller's order).  Synchronises. */
 ba_status ba_batch_set_launch(ba_batch* h, int ctas_per_sm, int variant, int order);
+/* The current launch configuration and the persistent grid size (host
+ * outputs, any may be NULL; no counterpart in the paper). */
 ba_status ba_batch_get_launch(ba_batch* h, int* ctas_per_sm, int* variant, int* order,
                               int* grid);
 
-/* Autotuner: time `iters` trials of the batch under every launch
+/* Autotuner (no counterpart in the paper): time `iters` trials of the
+ * batch under every launch
  * configuration (variant x CTAs per SM up to the occupancy limit x
  * order), from the batch's current state each time, and keep the fastest;
  * the batch's state is restored afterwards.  With cache_path (host
@@ -421,15 +447,18 @@ ba_status ba_batch_autotune(ba_batch* h, int iters, const char* cache_path,
 #define BA_MLP_NPARAM 13293
 #define BA_MLP_KMAX 16
 
-/* Use the network with parameters params (any, FP32 [BA_MLP_NPARAM],
- * copied) for the preconditioner of every later ba_lm_step / ba_solve /
+/* Learned correction of the PCG preconditioner (Sec. IV-C uses a fixed
+ * diagonal one; this has no counterpart in the paper).  Use the network
+ * with parameters params (any, FP32 [BA_MLP_NPARAM], copied) for the
+ * preconditioner of every later ba_lm_step / ba_solve /
  * ba_damped_solve of h; NULL returns to block-Jacobi.  Cameras whose S_ii is
  * not positive definite, whose block is not finite or that have a frozen
  * parameter keep the block-Jacobi inverse (counted in precond_fallbacks).
  * ba_backward always uses block-Jacobi. */
 ba_status ba_set_preconditioner(ba_problem* h, const float* params, void* stream);
 
-/* Training data at the current parameters and damping lambda (> 0):
+/* Training data for the learned correction (no counterpart in the paper)
+ * at the current parameters and damping lambda (> 0):
  * X_out [C][96] features, Ahat_out [C][45] A = chol(S^_ii)^{-1} (packed
  * lower triangle, row-major), and for the K (0..BA_MLP_KMAX) probes zhat
  * [C][K][9] (+-1, FP32) the products Yhat_out [C][K][9] = S^ z^ (one
@@ -442,7 +471,9 @@ ba_status ba_set_preconditioner(ba_problem* h, const float* params, void* stream
 ba_status ba_learn_collect(ba_problem* h, double lambda, int K, const float* zhat, float* X_out,
                            float* Ahat_out, float* Yhat_out, double* D_out, void* stream);
 
-/* Probe vectors along the slow modes of the block-Jacobi PCG at the current
+/* Training probes for the learned correction (no counterpart in the
+ * paper): vectors along the slow modes of the block-Jacobi PCG (Sec. IV-C)
+ * at the current
  * parameters and damping lambda: x_ref = the PCG solution after maxiter_ref
  * iterations / relative tolerance tol_ref, x_k = the PCG iterate after
  * k = iters[j] iterations (iters host [n], n <= BA_MLP_KMAX), and
@@ -453,11 +484,13 @@ ba_status ba_learn_collect(ba_problem* h, double lambda, int K, const float* zha
 ba_status ba_learn_slow_probes(ba_problem* h, double lambda, int n, const int* iters, int maxiter_ref,
                                double tol_ref, float* zhat_out, void* stream);
 
-/* Network output E_out [n][45] for features X [n][96] (dev, FP32).
- * Stream-ordered. */
+/* Network output E_out [n][45] for features X [n][96] (dev, FP32) of the
+ * learned correction (no counterpart in the paper).  n >= 0; a NULL
+ * pointer with n > 0 gives BA_ERR_INVALID_ARG.  Stream-ordered. */
 ba_status ba_mlp_forward(const float* params, int n, const float* X, float* E_out, void* stream);
 
-/* Mean training loss over n samples (X [n][96], Ahat [n][45], Yhat, Zhat
+/* Learned correction (no counterpart in the paper): mean training loss
+ * over n samples (X [n][96], Ahat [n][45], Yhat, Zhat
  * [n][K][9], dev, FP32) into *loss_out (host, may be NULL) and its gradient
  * grad_out [BA_MLP_NPARAM] (dev, FP64; summed over fixed tiles of 64 samples
  * in a fixed order).  Synchronises. */
@@ -465,7 +498,8 @@ ba_status ba_mlp_loss_grad(const float* params, int n, int K, const float* X, co
                            const float* Yhat, const float* Zhat, double* grad_out, double* loss_out,
                            void* stream);
 
-/* Adam (beta1 0.9, beta2 0.999, eps 1e-8, learning rate lr) on params with
+/* Training of the learned correction (no counterpart in the paper): Adam
+ * (beta1 0.9, beta2 0.999, eps 1e-8, learning rate lr) on params with
  * moments adam_m, adam_v (dev, FP32 [BA_MLP_NPARAM], in/out; zero them for a
  * fresh start), over `epochs` passes of the n samples in minibatches of
  * `batch` consecutive samples (a shorter tail is skipped; shuffle the samples

@@ -29,6 +29,26 @@ def test_header_declares_the_boundary():
         assert n in names
 
 
+def test_every_declaration_cites_the_paper_or_says_it_has_no_counterpart():
+    """Each entry point's comment names the passage it implements (Sec., Eq.,
+    Alg., App.) or states that the paper has no counterpart."""
+    lines = open(os.path.join(ROOT, "include", "ba.h")).read().split("\n")
+    decl = re.compile(r"^(ba_status|const char\*|size_t|uint64_t)\s+(ba_[a-z_0-9]+)\s*\(")
+    cite = re.compile(r"Sec\.|Eq\.|Alg\.|App\.|no counterpart|[Nn]ot in the paper")
+    missing = []
+    for i, line in enumerate(lines):
+        m = decl.match(line)
+        if not m:
+            continue
+        j, comment = i - 1, []
+        while j >= 0 and lines[j].strip().startswith(("/*", "*")) or (j >= 0 and lines[j].strip().endswith("*/")):
+            comment.insert(0, lines[j])
+            j -= 1
+        if not cite.search(" ".join(comment)):
+            missing.append(m.group(2))
+    assert not missing, missing
+
+
 def test_every_declared_symbol_is_exported(lib):
     missing = [n for n in _declared() if not hasattr(lib, n)]
     assert not missing, missing
