@@ -3,6 +3,8 @@ entry point include/ba.h declares (no compute calls)."""
 import ctypes
 import os
 import re
+import shutil
+import subprocess
 
 import pytest
 
@@ -107,3 +109,18 @@ def test_batch_max_cams_matches_header():
     src = open(os.path.join(ROOT, "include", "ba.h")).read()
     m = re.search(r"#define BA_BATCH_MAX_CAMS (\d+)", src)
     assert m and int(m.group(1)) == _lib.BA_BATCH_MAX_CAMS
+
+
+def test_plain_c_program_uses_the_header_and_library(lib, tmp_path):
+    """The boundary needs neither Python nor torch: a C99 program compiled
+    against include/ba.h and linked to the library reads the defaults and
+    gets the documented argument errors (no GPU work)."""
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    libdir = os.path.dirname(lib._name)
+    exe = tmp_path / "abi_from_c"
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-I", os.path.join(ROOT, "include"),
+                    os.path.join(ROOT, "tests", "c", "abi_from_c.c"), "-L", libdir, "-lba_gb300",
+                    f"-Wl,-rpath,{libdir}", "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert out.returncode == 0 and out.stdout.strip() == "OK", out.stderr
