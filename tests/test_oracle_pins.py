@@ -432,3 +432,47 @@ def test_adjoint_schur_equals_dense():
                                fixed, 1.0, lam)
         for x, y in zip(d1[:3], d2[:3]):
             assert np.max(np.abs(x - y)) <= 1e-8 * max(np.max(np.abs(x)), 1e-30)
+
+
+@pytest.mark.parametrize("delta", [0.5, 1.0, 3.0])
+def test_huber_is_continuous_with_its_derivative_at_delta(delta):
+    """rho and rho' (the IRLS weight) meet at |r| = delta: no jump in the
+    loss or in the gradient where an observation turns into an outlier."""
+    s0 = delta * delta
+    eps = 1e-9
+    rho, w = orc.huber(np.array([s0 * (1 - eps), s0, s0 * (1 + eps)]), delta)
+    assert np.all(np.abs(rho - s0) <= 4 * eps * s0)
+    assert np.all(np.abs(w - 1.0) <= 4 * eps)
+    # rho'(s) by central differences on the outlier side equals the weight
+    s = np.array([2.0, 7.0, 30.0]) * s0
+    h = 1e-6 * s
+    d = (orc.huber(s + h, delta)[0] - orc.huber(s - h, delta)[0]) / (2 * h)
+    assert np.allclose(d, orc.huber(s, delta)[1], rtol=1e-7)
+
+
+def test_huber_gradient_is_the_gradient_of_the_cost():
+    """Under Huber's loss with outliers, the assembled g = sum_k w_k J_k^T r_k
+    is the gradient of F = 1/2 sum rho(|r|^2) (central differences of the
+    cost alone): this fixes the 1/2, the weight w = rho' and J together."""
+    sc, pix = _tiny_scene(31, C=3, P=8, delta=1.0, outliers=0.4)
+    args = (sc.cam_idx, sc.pt_idx, pix, sc.huber_delta)
+    # at the ground truth the residuals are the 1 px noise and the 20 px
+    # outliers, so both regimes of the loss are present
+    cams, pts = sc.cams_gt, sc.points_gt
+    blk = orc.assemble(cams, pts, sc.cam_idx, sc.pt_idx, pix, sc.huber_delta)
+    _, w = orc.huber(np.sum(blk["r"] ** 2, axis=1), sc.huber_delta)
+    assert np.any(w < 1.0) and np.any(w == 1.0)
+    g = np.concatenate([blk["gc"].reshape(-1), blk["gp"].reshape(-1)])
+    theta = np.concatenate([cams.reshape(-1), pts.reshape(-1)])
+    nc = cams.size
+
+    def F(t):
+        return orc.cost(t[:nc].reshape(cams.shape), t[nc:].reshape(pts.shape), *args)
+
+    num = np.empty_like(theta)
+    for i in range(theta.size):
+        h = 1e-6 * max(1.0, abs(theta[i]))
+        e = np.zeros_like(theta)
+        e[i] = h
+        num[i] = (F(theta + e) - F(theta - e)) / (2 * h)
+    assert np.max(np.abs(num - g)) <= 1e-6 * np.max(np.abs(g))
