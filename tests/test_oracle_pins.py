@@ -476,3 +476,37 @@ def test_huber_gradient_is_the_gradient_of_the_cost():
         e[i] = h
         num[i] = (F(theta + e) - F(theta - e)) / (2 * h)
     assert np.max(np.abs(num - g)) <= 1e-6 * np.max(np.abs(g))
+
+
+@pytest.mark.parametrize("seed", range(24))
+def test_random_tiny_scenes_blocks_and_schur_solve_equal_dense(seed):
+    """Fuzz over random tiny problems (2-5 cameras, 5-30 points, random
+    visibility, with or without Huber outliers, random damping): the block
+    assembly equals the dense J^T J / J^T r, and the Schur-complement solve
+    equals the dense solve of Eq. 2 built from the dense Jacobian."""
+    rng = np.random.default_rng(1000 + seed)
+    C = int(rng.integers(2, 6))
+    P = int(rng.integers(5, 31))
+    huber = bool(seed % 2)
+    sc = scenegen.arc_scene(C, P, seed=seed, views_lo=min(2, C), views_hi=C,
+                            huber_delta=1.0 if huber else 0.0)
+    pix = orc.pixels_from_scene(sc)
+    if huber:   # a few large residuals so both regimes of the loss occur
+        pix = pix + (rng.random((sc.O, 1)) < 0.3) * rng.normal(0.0, 15.0, size=(sc.O, 2))
+    lam = float(10.0 ** rng.uniform(-4, 0))
+    args = (sc.cams_init, sc.points_init, sc.cam_idx, sc.pt_idx, pix)
+    blk = orc.assemble(*args, sc.huber_delta)
+    J, rw = orc.dense_jacobian(*args, sc.huber_delta)
+    H = J.T @ J
+    g = J.T @ rw
+    nc = 9 * C
+    for key, ref in (("U", [H[9 * i:9 * i + 9, 9 * i:9 * i + 9] for i in range(C)]),
+                     ("V", [H[nc + 3 * j:nc + 3 * j + 3, nc + 3 * j:nc + 3 * j + 3] for j in range(P)])):
+        assert np.allclose(blk[key], np.array(ref), rtol=1e-12, atol=1e-12 * np.abs(H).max())
+    assert np.allclose(blk["gc"].reshape(-1), g[:nc], rtol=1e-12, atol=1e-12 * np.abs(g).max())
+    assert np.allclose(blk["gp"].reshape(-1), g[nc:], rtol=1e-12, atol=1e-12 * np.abs(g).max())
+    dc, dp, _, _ = orc.solve_damped(blk, sc.cam_idx, sc.pt_idx, lam, orc.LMOptions(solver="cholesky"))
+    dc_ref, dp_ref = orc.dense_lm_delta(*args, lam, sc.huber_delta)
+    scale = max(np.abs(dc_ref).max(), np.abs(dp_ref).max())
+    assert np.max(np.abs(dc - dc_ref)) <= 1e-8 * scale
+    assert np.max(np.abs(dp - dp_ref)) <= 1e-8 * scale
