@@ -173,16 +173,25 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
         self.f.seek(0)
-        rows = [r for r in csv.reader(io.StringIO(self.f.read())) if len(r) >= 9]
+        text = self.f.read()
         os.unlink(self.f.name)
-        if not rows:
-            return None
-        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].strip() == "Active"})
-        return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+        return parse_clock_samples(text)
+
+
+def parse_clock_samples(text):
+    """Summary of nvidia-smi samples in the ClockSampler.Q column order
+    (csv, no header, no units): median SM clock, the highest maximum clock,
+    the throttle reasons seen Active in any sample, and the sample count;
+    None without samples."""
+    rows = [r for r in csv.reader(io.StringIO(text)) if len(r) >= 9]
+    if not rows:
+        return None
+    sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+    mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].strip() == "Active"})
+    return {"sm_mhz": statistics.median(sm) if sm else None,
+            "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
 
 
 def algorithmic_bytes(kind, C, P, O, npieces, tsize, mf, huber=False):

@@ -59,3 +59,17 @@ def test_peak_from_the_measured_file_else_the_fallback(tmp_path, monkeypatch):
 @pytest.mark.parametrize("mhz,tflops", [(2070.0, 80.54784), (1000.0, 38.912)])
 def test_fp32_alu_peak(mhz, tflops):
     assert bench.fp32_peak_tflops(mhz) == pytest.approx(tflops)
+
+
+def test_clock_samples_summary():
+    text = ("0, 2070, 2070, 900.1, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active\n"
+            "0, 1980, 2070, 1390.5, 0x0000000000000004, Not Active, Not Active, Not Active, Active\n"
+            "0, 2070, 2070, 1200.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active\n"
+            "0, [N/A], [N/A], [N/A], [N/A], [N/A], [N/A], [N/A], [N/A]\n")
+    c = bench.parse_clock_samples(text)
+    assert c["sm_mhz"] == 2070.0 and c["sm_max_mhz"] == 2070.0 and c["samples"] == 4
+    # a power cap is kept and reported; "Not Active" is not a reason
+    assert c["reasons"] == ["sw_power_cap"]
+    hot = text.replace("Not Active, Not Active, Not Active, Active", "Active, Not Active, Not Active, Not Active")
+    assert bench.parse_clock_samples(hot)["reasons"] == ["hw_slowdown"]
+    assert bench.parse_clock_samples("") is None
