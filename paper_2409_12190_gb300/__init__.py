@@ -93,6 +93,19 @@ def _dev(t, dtype, device):
     return t.to(device=device, dtype=dtype).contiguous()
 
 
+def _check_problem_shapes(cams, points, cam_idx, pt_idx, pixels):
+    """The C ABI takes plain pointers and cannot see buffer sizes: check on
+    the host that the arrays agree, so that a wrong shape is an error here
+    and never a read past the end of a device buffer."""
+    C, P = int(cams.shape[0]), int(points.shape[0])
+    O = int(cam_idx.shape[0]) if cam_idx.dim() == 1 else -1
+    if tuple(cams.shape) != (C, 9) or tuple(points.shape) != (P, 3):
+        raise ValueError(f"cams must be [C, 9] and points [P, 3] (got {tuple(cams.shape)}, {tuple(points.shape)})")
+    if O < 0 or tuple(pt_idx.shape) != (O,) or tuple(pixels.shape) != (O, 2):
+        raise ValueError(f"cam_idx, pt_idx must be [O] and pixels [O, 2] (got {tuple(cam_idx.shape)}, "
+                         f"{tuple(pt_idx.shape)}, {tuple(pixels.shape)})")
+
+
 class Problem:
     """One bundle-adjustment problem resident on the GPU.
 
@@ -105,6 +118,7 @@ class Problem:
         self.options = options or Options()
         self.dtype = self.options.dtype
         self.device = torch.device(device)
+        _check_problem_shapes(*(torch.as_tensor(t) for t in (cams, points, cam_idx, pt_idx, pixels)))
         cams = _dev(cams, self.dtype, self.device)
         points = _dev(points, self.dtype, self.device)
         ci = _dev(cam_idx, torch.int32, self.device)
@@ -149,22 +163,30 @@ class Problem:
         _lib.check(_L().ba_get_params(self._h, _ptr(cams), _ptr(pts), _stream(stream)))
         return cams, pts
 
+    def _check(self, t, shape, what):
+        if t is None:
+            return
+        if t.dtype != self.dtype:
+            raise TypeError(f"{what}: expected {self.dtype}, got {t.dtype}")
+        if tuple(t.shape) != shape or not t.is_contiguous():
+            raise ValueError(f"{what}: expected a contiguous {list(shape)} tensor, got {list(t.shape)}")
+
     def get_params_into(self, cams_out, points_out, stream=None):
         """Copy theta into caller tensors (device or pinned host)."""
+        self._check(cams_out, (self.C, 9), "cams_out")
+        self._check(points_out, (self.P, 3), "points_out")
         _lib.check(_L().ba_get_params(self._h, _ptr(cams_out), _ptr(points_out), _stream(stream)))
 
     def set_params(self, cams=None, points=None, stream=None):
         c = None if cams is None else cams.contiguous()
         p = None if points is None else points.contiguous()
-        for t in (c, p):
-            if t is not None and t.dtype != self.dtype:
-                raise TypeError(f"expected {self.dtype}")
+        self._check(c, (self.C, 9), "cams")
+        self._check(p, (self.P, 3), "points")
         _lib.check(_L().ba_set_params(self._h, _ptr(c), _ptr(p), _stream(stream)))
 
     def set_pixels(self, pixels, stream=None):
         px = pixels.contiguous()
-        if px.dtype != self.dtype:
-            raise TypeError(f"expected {self.dtype}")
+        self._check(px, (self.O, 2), "pixels")
         _lib.check(_L().ba_set_pixels(self._h, _ptr(px), _stream(stream)))
 
     def stats(self, cap: int = 4096, raise_nonfinite: bool = True):
@@ -345,6 +367,8 @@ class Batch:
         ci = [torch.as_tensor(p[2]) for p in problems]
         pi = [torch.as_tensor(p[3]) for p in problems]
         px = [torch.as_tensor(p[4]) for p in problems]
+        for arrays in zip(cams, pts, ci, pi, px):
+            _check_problem_shapes(*arrays)
         self.n = len(problems)
         self.cam_counts = [int(c.shape[0]) for c in cams]
         self.pt_counts = [int(p.shape[0]) for p in pts]
@@ -473,6 +497,9 @@ def project(cams, points, cam_idx, pt_idx, stream=None):
     cams, points = cams.contiguous(), points.contiguous()
     ci = cam_idx.to(torch.int32).contiguous()
     pi = pt_idx.to(torch.int32).contiguous()
+    if cams.dim() != 2 or cams.shape[1] != 9 or points.dim() != 2 or points.shape[1] != 3 or \
+            ci.dim() != 1 or tuple(pi.shape) != tuple(ci.shape):
+        raise ValueError("project: cams [C, 9], points [P, 3], cam_idx and pt_idx [O]")
     out = torch.empty((ci.shape[0], 2), dtype=cams.dtype, device=cams.device)
     _lib.check(_L().ba_project(prec, cams.shape[0], points.shape[0], ci.shape[0], _ptr(cams),
                                _ptr(points), _ptr(ci), _ptr(pi), _ptr(out), _stream(stream)))

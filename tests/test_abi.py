@@ -124,3 +124,30 @@ def test_plain_c_program_uses_the_header_and_library(lib, tmp_path):
                     f"-Wl,-rpath,{libdir}", "-o", str(exe)], check=True)
     out = subprocess.run([str(exe)], capture_output=True, text=True)
     assert out.returncode == 0 and out.stdout.strip() == "OK", out.stderr
+
+
+@pytest.mark.parametrize("bad", ["cams", "points", "pt_idx", "pixels"])
+def test_binding_rejects_mismatched_shapes_before_any_library_call(bad):
+    """The C ABI sees plain pointers; the binding checks shapes on the host,
+    so a wrong shape is a ValueError and never a read past a buffer's end."""
+    import numpy as np
+    import paper_2409_12190_gb300 as ba
+    C, P, O = 3, 5, 7
+    arrays = dict(cams=np.zeros((C, 9)), points=np.zeros((P, 3)), cam_idx=np.zeros(O, np.int32),
+                  pt_idx=np.zeros(O, np.int32), pixels=np.zeros((O, 2)))
+    arrays[bad] = {"cams": np.zeros((C, 8)), "points": np.zeros((P, 2)), "pt_idx": np.zeros(O - 1, np.int32),
+                   "pixels": np.zeros((O - 1, 2))}[bad]
+    with pytest.raises(ValueError):
+        ba.Problem(arrays["cams"], arrays["points"], arrays["cam_idx"], arrays["pt_idx"], arrays["pixels"],
+                   device="cpu")
+    with pytest.raises(ValueError):
+        ba.Batch([(arrays["cams"], arrays["points"], arrays["cam_idx"], arrays["pt_idx"], arrays["pixels"])],
+                 device="cpu")
+
+
+def test_project_rejects_mismatched_index_lengths():
+    import torch
+    import paper_2409_12190_gb300 as ba
+    with pytest.raises(ValueError):
+        ba.project(torch.zeros(3, 9, dtype=torch.float64), torch.zeros(5, 3, dtype=torch.float64),
+                   torch.zeros(7, dtype=torch.int32), torch.zeros(6, dtype=torch.int32))
