@@ -266,6 +266,8 @@ class Problem:
         """Use the network with these parameters (FP32 [MLP_NPARAM]) for the
         PCG's block preconditioner; None returns to block-Jacobi."""
         p = None if params is None else _dev(params, torch.float32, self.device)
+        if p is not None:
+            _check_params(p)
         _lib.check(_L().ba_set_preconditioner(self._h, _ptr(p), _stream(stream)))
         torch.cuda.current_stream(self.device).synchronize()
 
@@ -274,7 +276,9 @@ class Problem:
         X [C, 96], A = chol(S^_ii)^{-1} [C, 45] and y^ = S^ z^ [C, K, 9] for the
         probes zhat [C, K, 9]; with scales=True also D = diag(S_ii) [C, 9]."""
         z = _dev(zhat, torch.float32, self.device)
-        K = int(z.shape[1]) if z.dim() == 3 else 0
+        K = int(z.shape[1]) if z.dim() == 3 else -1
+        if K < 0 or K > _lib.BA_MLP_KMAX or tuple(z.shape) != (self.C, K, 9):
+            raise ValueError(f"zhat must be [C, K, 9] with K <= {_lib.BA_MLP_KMAX}, got {list(z.shape)}")
         X = torch.empty((self.C, MLP_FIN), dtype=torch.float32, device=self.device)
         A = torch.empty((self.C, 45), dtype=torch.float32, device=self.device)
         Y = torch.empty((self.C, K, 9), dtype=torch.float32, device=self.device)
@@ -516,6 +520,26 @@ def csr_build(keys, n_keys: int, stream=None):
     return perm, rowptr
 
 
+def _check_params(params):
+    if params.dtype != torch.float32 or params.numel() != MLP_NPARAM or not params.is_contiguous():
+        raise ValueError(f"network parameters must be a contiguous float32 [{MLP_NPARAM}] tensor")
+
+
+def _check_samples(X, A=None, Y=None, Z=None):
+    """Sample arrays of the learned correction: X [n, 96], A [n, 45],
+    Y and Z [n, K, 9] with K <= BA_MLP_KMAX (sizes the library cannot see)."""
+    n = int(X.shape[0])
+    if tuple(X.shape) != (n, MLP_FIN):
+        raise ValueError(f"X must be [n, {MLP_FIN}], got {list(X.shape)}")
+    if A is not None and tuple(A.shape) != (n, MLP_FOUT):
+        raise ValueError(f"A must be [n, {MLP_FOUT}], got {list(A.shape)}")
+    if Y is not None:
+        K = int(Y.shape[1]) if Y.dim() == 3 else -1
+        if K < 0 or K > _lib.BA_MLP_KMAX or tuple(Y.shape) != (n, K, 9) or tuple(Z.shape) != (n, K, 9):
+            raise ValueError(f"Y and Z must be [n, K, 9] with K <= {_lib.BA_MLP_KMAX}, "
+                             f"got {list(Y.shape)}, {list(Z.shape)}")
+
+
 def mlp_init(seed: int = 0, device="cuda"):
     """Initial network parameters (FP32 [MLP_NPARAM]): uniform +-1/sqrt(fan_in)
     weights and biases in the hidden layers, a zero output layer (so the
@@ -533,18 +557,24 @@ def mlp_init(seed: int = 0, device="cuda"):
 def mlp_forward(params, X, stream=None):
     """Network output [n, 45] for features X [n, 96] (tensor-core kernel)."""
     X = X.to(torch.float32).contiguous()
+    params = params.contiguous()
+    _check_params(params)
+    _check_samples(X)
     E = torch.empty((X.shape[0], MLP_FOUT), dtype=torch.float32, device=X.device)
-    _lib.check(_L().ba_mlp_forward(_ptr(params.contiguous()), int(X.shape[0]), _ptr(X), _ptr(E), _stream(stream)))
+    _lib.check(_L().ba_mlp_forward(_ptr(params), int(X.shape[0]), _ptr(X), _ptr(E), _stream(stream)))
     return E
 
 
 def mlp_loss_grad(params, X, A, Y, Z, stream=None):
     """(mean probe loss, gradient [MLP_NPARAM] float64)."""
+    _check_samples(X, A, Y, Z)
+    params = params.contiguous()
+    _check_params(params)
     n, K = int(X.shape[0]), int(Y.shape[1])
     grad = torch.empty(MLP_NPARAM, dtype=torch.float64, device=X.device)
     loss = ct.c_double()
     args = [t.to(torch.float32).contiguous() for t in (X, A, Y, Z)]
-    _lib.check(_L().ba_mlp_loss_grad(_ptr(params.contiguous()), n, K, *(_ptr(t) for t in args), _ptr(grad),
+    _lib.check(_L().ba_mlp_loss_grad(_ptr(params), n, K, *(_ptr(t) for t in args), _ptr(grad),
                                      ct.byref(loss), _stream(stream)))
     return loss.value, grad
 
@@ -552,6 +582,7 @@ def mlp_loss_grad(params, X, A, Y, Z, stream=None):
 def mlp_train(params, adam_m, adam_v, X, A, Y, Z, epochs: int, batch: int, lr: float, stream=None):
     """Adam on params (in place, FP32 device tensors) over minibatches of
     consecutive samples; returns the per-epoch mean minibatch losses."""
+    _check_samples(X, A, Y, Z)
     n, K = int(X.shape[0]), int(Y.shape[1])
     hist = (ct.c_double * max(1, int(epochs)))()
     args = [t.to(torch.float32).contiguous() for t in (X, A, Y, Z)]

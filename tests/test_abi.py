@@ -151,3 +151,26 @@ def test_project_rejects_mismatched_index_lengths():
     with pytest.raises(ValueError):
         ba.project(torch.zeros(3, 9, dtype=torch.float64), torch.zeros(5, 3, dtype=torch.float64),
                    torch.zeros(7, dtype=torch.int32), torch.zeros(6, dtype=torch.int32))
+
+
+def test_learned_correction_bindings_reject_wrong_sizes():
+    import torch
+    import paper_2409_12190_gb300 as ba
+    p = torch.zeros(ba.MLP_NPARAM)
+    X = torch.zeros(4, ba.MLP_FIN)
+    A = torch.zeros(4, 45)
+    Y = torch.zeros(4, 2, 9)
+    with pytest.raises(ValueError):
+        ba.mlp_forward(p[:-1], X)                        # parameters too short
+    with pytest.raises(ValueError):
+        ba.mlp_forward(p.double(), X)                    # wrong parameter dtype
+    with pytest.raises(ValueError):
+        ba.mlp_forward(p, X[:, :-1])                     # features too narrow
+    with pytest.raises(ValueError):
+        ba.mlp_loss_grad(p, X, A[:3], Y, Y)              # A of another sample count
+    with pytest.raises(ValueError):
+        ba.mlp_loss_grad(p, X, A, Y, Y[:, :1])           # Z with other probes than Y
+    with pytest.raises(ValueError):
+        ba.mlp_loss_grad(p, X, A, torch.zeros(4, 17, 9), torch.zeros(4, 17, 9))   # K > BA_MLP_KMAX
+    with pytest.raises(ValueError):
+        ba.mlp_train(p, p.clone(), p.clone(), X, A, Y, Y[:3], epochs=1, batch=4, lr=1e-3)
