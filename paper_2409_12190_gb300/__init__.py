@@ -425,6 +425,9 @@ class Batch:
     def reset(self, cams=None, points=None, stream=None):
         c = None if cams is None else _dev(cams, self.dtype, self.device)
         p = None if points is None else _dev(points, self.dtype, self.device)
+        for t, shape, what in ((c, (self.C, 9), "cams"), (p, (self.P, 3), "points")):
+            if t is not None and tuple(t.shape) != shape:
+                raise ValueError(f"{what}: expected the concatenated {list(shape)}, got {list(t.shape)}")
         _lib.check(_L().ba_batch_reset(self._h, _ptr(c), _ptr(p), _stream(stream)))
 
     def stats(self, cap: int = 256, raise_nonfinite: bool = True):
