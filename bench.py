@@ -615,6 +615,24 @@ def _timed_trials(prob, trials, stream):
     return t, cost, [s["pcg_iters"] for s in st], bad
 
 
+def time_to_cost(runs, rel=1e-6):
+    """Time to a common cost: runs maps a name to (cumulative seconds after
+    each trial, cost after each trial, PCG iterations per trial, non-finite
+    trials).  The target is within rel of the best cost BOTH runs reach (the
+    higher of the runs' minima), so that each run has a time to it; a run's
+    time is the cumulative time of its first trial at or below the target."""
+    f_ref = max(min(r[1]) for r in runs.values())
+    out = {}
+    for name, (t, cost, pcg, bad) in runs.items():
+        hit = next((i for i, c in enumerate(cost) if c <= (1 + rel) * f_ref), None)
+        out[name] = {"time_to_cost_s": t[hit] if hit is not None else None,
+                     "trials_to_cost": None if hit is None else hit + 1,
+                     "pcg_iters_to_cost": None if hit is None else sum(pcg[:hit + 1]), "final_cost": cost[-1],
+                     "lowest_cost": min(cost), "ms_per_pcg_iter": 1000.0 * t[-1] / max(1, sum(pcg)),
+                     "pcg_iters_per_trial": pcg, "cost_per_trial": cost, "nonfinite_trials": bad}
+    return f_ref, out
+
+
 def run_learned(args):
     import torch
     import paper_2409_12190_gb300 as ba
@@ -665,16 +683,7 @@ def run_learned(args):
             pr.set_lambda(1e-4)
             pr.stats()
             runs[name] = _timed_trials(pr, LEARN_TRIALS, stream)
-    # target: within 1e-6 of the best cost BOTH runs reach (the higher of the
-    # two minima), so that each run has a time to it
-    f_ref = max(min(r[1]) for r in runs.values())
-    out = {}
-    for name, (t, cost, pcg, bad) in runs.items():
-        hit = next((i for i, c in enumerate(cost) if c <= (1 + 1e-6) * f_ref), None)
-        out[name] = {"time_to_cost_s": t[hit] if hit is not None else None, "trials_to_cost": None if hit is None else hit + 1,
-                     "pcg_iters_to_cost": None if hit is None else sum(pcg[:hit + 1]), "final_cost": cost[-1],
-                     "lowest_cost": min(cost), "ms_per_pcg_iter": 1000.0 * t[-1] / max(1, sum(pcg)),
-                     "pcg_iters_per_trial": pcg, "cost_per_trial": cost, "nonfinite_trials": bad}
+    f_ref, out = time_to_cost(runs)
     value = out["learned"]["time_to_cost_s"]
     line = {"metric": METRIC, "value": value, "unit": "s to 1e-6 relative cost", "n_gpus": 1,
             "steps": LEARN_TRIALS, "warmup": 1, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,

@@ -73,3 +73,18 @@ def test_clock_samples_summary():
     hot = text.replace("Not Active, Not Active, Not Active, Active", "Active, Not Active, Not Active, Not Active")
     assert bench.parse_clock_samples(hot)["reasons"] == ["hw_slowdown"]
     assert bench.parse_clock_samples("") is None
+
+
+def test_time_to_cost_uses_a_cost_both_runs_reach():
+    runs = {"a": ([0.1, 0.2, 0.3, 0.4], [10.0, 5.0, 4.0, 3.0], [5, 6, 7, 8], 0),
+            "b": ([0.15, 0.3, 0.45], [9.0, 4.5, 3.5], [4, 4, 4], 0)}
+    f_ref, out = bench.time_to_cost(runs)
+    # b never gets below 3.5, so the common target is 3.5 (1e-6 slack)
+    assert f_ref == 3.5
+    assert out["a"]["trials_to_cost"] == 4 and out["a"]["time_to_cost_s"] == 0.4
+    assert out["b"]["trials_to_cost"] == 3 and out["b"]["time_to_cost_s"] == 0.45
+    assert out["a"]["pcg_iters_to_cost"] == 26 and out["b"]["pcg_iters_to_cost"] == 12
+    # within the relative slack counts as reached
+    runs["a"][1][2] = 3.5 * (1 + 5e-7)
+    _, out = bench.time_to_cost(runs)
+    assert out["a"]["trials_to_cost"] == 3
