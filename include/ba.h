@@ -279,11 +279,14 @@ ba_status ba_csr_build(const int32_t* keys, int n, int n_keys,
  * Same arguments, output and errors as ba_csr_build (keys, perm_out,
  * rowptr_out dev; n in [0, BA_NOALLOC_MAX_KEYS], larger n gives
  * BA_ERR_INVALID_ARG); synchronises the stream.  Its scratch is one fixed
- * __device__ array of about 17 MB that every GPU loading the library holds
- * until exit; the first call on a device looks up that array's device
- * address with the device current, so make the first call before any
- * stream capture.  All calls share the array: calls whose GPU work overlaps
- * race and must be serialised by the caller. */
+ * __device__ array of about 17 MB.  The library's device code is loaded on
+ * a device lazily, so the FIRST call on a device (and the first after a
+ * cudaDeviceReset) loads it there and reserves the array, which the device
+ * then holds until exit: callers that may allocate only at start-up make one
+ * warm-up call then (n = 0 is enough), before any stream capture.  Every
+ * call looks up the array's device address with the caller's device
+ * current; no address is kept across calls.  All calls share the array:
+ * calls whose GPU work overlaps race and must be serialised by the caller. */
 ba_status ba_csr_build_noalloc(const int32_t* keys, int n, int n_keys,
                                int32_t* perm_out, int32_t* rowptr_out,
                                void* stream);

@@ -23,7 +23,7 @@ What it computes, by the paper's section:
   preconditioned conjugate gradient; the minimum code example fixes
   PCG(tol=1e-4, maxiter=250) and TrustRegion(up=2.0, down=0.5**4).
 
-Not in the paper, and read as follows (each reading is listed in the design doc):
+Not in the paper, and read as follows:
 
 * camera model: the 9-parameter BAL camera of the paper's benchmark data
   (angle-axis omega, translation t, focal f, radial k1, k2); X_cam = R(omega)X+t,

@@ -5,8 +5,7 @@ TEST INFRASTRUCTURE ONLY -- see the package docstring.
 The paper preconditions its PCG with a diagonal (Sec. IV-C); the plain method
 here uses the 9x9 block-Jacobi inverse of the reduced camera system S.  This
 form adds a small MLP that maps per-camera quantities of S to an SPD
-correction of that inverse.  None of it is in the paper; the readings (listed
-in DESIGN.md) are:
+correction of that inverse.  None of it is in the paper; the readings are:
 
 * Scaled coordinates.  D_i = diag(S_ii); S^ = D^{-1/2} S D^{-1/2}, so every
   block-diagonal entry of S^ is 1 and the quantities below do not depend on

@@ -10,9 +10,17 @@
 // temporary keys, values and digit histograms live in the array below.
 //
 // Costs and limits:
-//  - The array is a file-scope __device__ variable, so every GPU that loads
-//    this library holds BA_NOALLOC_MAX_KEYS * 16 bytes (+ histograms) of it
-//    until the process exits, whether or not the entry point is used.
+//  - The array is a file-scope __device__ variable.  The library's module is
+//    loaded on a device lazily, so the array is reserved there by the first
+//    call of this entry point on that device (the address lookup below loads
+//    the module); from then on the device holds BA_NOALLOC_MAX_KEYS * 16 bytes
+//    (+ histograms) of it until the process exits.  Callers that may allocate
+//    only at start-up make one warm-up call (n = 0 is enough) then, before any
+//    stream capture.
+//  - The device address is looked up on every call, with the caller's device
+//    current, so it stays right after a cudaDeviceReset or under another
+//    context (the module is loaded again and the array may move); after a
+//    reset the next call reserves the array again, like a first call.
 //  - All calls share the one array.  Two calls whose GPU work overlaps (on
 //    different streams, or from different host threads) corrupt each other's
 //    results; order them on one stream or synchronise between them.
@@ -20,8 +28,6 @@
 //    that must start at zero, the out-of-range flag, is cleared on every call;
 //    the histograms and temporary keys are fully rewritten before use.
 #include <cuda_runtime.h>
-
-#include <mutex>
 
 #include "ba.h"
 #include "ba_internal.h"
@@ -38,26 +44,16 @@ constexpr long long kScratchInts = kErrOffsetInts + 64;
 
 __device__ __align__(256) int32_t g_noalloc_scratch[kScratchInts];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_setup_mu;
-void* g_scratch_addr[kMaxDevices] = {nullptr};
-
-// Device address of g_noalloc_scratch on the current device.  In host code
-// the symbol itself is only a host-side stand-in, so the real address is
-// looked up once per device (with that device current) and cached.
+// Device address of g_noalloc_scratch in the current device's context.  In
+// host code the symbol itself is only a host-side stand-in, so the real
+// address is asked of the runtime, with the caller's device current, on every
+// call.  Once the module is loaded that is a table lookup; no address is
+// cached, because a device reset or a new context can move the array.
 cudaError_t scratch_address(void** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_setup_mu);
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return e;
-    g_scratch_addr[dev] = p;
-  }
-  *out = g_scratch_addr[dev];
+  *out = p;
   return cudaSuccess;
 }
 

@@ -75,16 +75,27 @@ def test_clock_samples_summary():
     assert bench.parse_clock_samples("") is None
 
 
-def test_time_to_cost_uses_a_cost_both_runs_reach():
+def test_time_to_cost_against_a_fixed_target():
     runs = {"a": ([0.1, 0.2, 0.3, 0.4], [10.0, 5.0, 4.0, 3.0], [5, 6, 7, 8], 0),
             "b": ([0.15, 0.3, 0.45], [9.0, 4.5, 3.5], [4, 4, 4], 0)}
-    f_ref, out = bench.time_to_cost(runs)
-    # b never gets below 3.5, so the common target is 3.5 (1e-6 slack)
-    assert f_ref == 3.5
+    out = bench.time_to_cost(runs, 3.5)
     assert out["a"]["trials_to_cost"] == 4 and out["a"]["time_to_cost_s"] == 0.4
     assert out["b"]["trials_to_cost"] == 3 and out["b"]["time_to_cost_s"] == 0.45
     assert out["a"]["pcg_iters_to_cost"] == 26 and out["b"]["pcg_iters_to_cost"] == 12
+    assert bench.speedup(out, "a", "b") == pytest.approx(0.4 / 0.45)
     # within the relative slack counts as reached
     runs["a"][1][2] = 3.5 * (1 + 5e-7)
-    _, out = bench.time_to_cost(runs)
+    out = bench.time_to_cost(runs, 3.5)
     assert out["a"]["trials_to_cost"] == 3
+
+
+def test_a_run_that_stalls_above_the_target_gets_no_time_and_no_speedup():
+    # the reference run (a) reaches 3.0; the other stalls at 3.1 -- close, but
+    # not within 1e-6, so it has no time to cost and no speedup is reported
+    runs = {"a": ([0.1, 0.2, 0.3, 0.4], [10.0, 5.0, 4.0, 3.0], [5, 6, 7, 8], 0),
+            "b": ([0.05, 0.1, 0.15], [9.0, 3.2, 3.1], [4, 4, 4], 0)}
+    f_ref = min(runs["a"][1])
+    out = bench.time_to_cost(runs, f_ref)
+    assert out["a"]["time_to_cost_s"] == 0.4
+    assert out["b"]["time_to_cost_s"] is None and out["b"]["trials_to_cost"] is None
+    assert bench.speedup(out, "a", "b") is None
