@@ -59,6 +59,10 @@ def parse():
     ap.add_argument("--profile-trials", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--jacobian", choices=["auto", "recompute", "store"], default="auto")
+    ap.add_argument("--precision", choices=["both", "f64", "f32"], default="both",
+                    help="both: the FP64 line (the paper's arithmetic) with the FP32 variant inside it")
+    ap.add_argument("--no-time-to-cost", action="store_true",
+                    help="skip F_ref and the time-to-cost runs (profiling only)")
     ap.add_argument("--points", type=int, default=0,
                     help="profiling only: same recipe with fewer points")
     ap.add_argument("--workload", choices=["ba4000", "batch512", "learned", "adjoint"], default="ba4000",
@@ -199,6 +203,7 @@ def algorithmic_bytes(kind, C, P, O, npieces, tsize, mf, huber=False):
     must read or write, each counted once (per-observation planes, indices
     and weights; per-point / per-camera vectors once)."""
     ob = 18 * tsize if not mf else (tsize if huber else 0)   # planes or sqrt(w)
+    sw = tsize if huber else 0
     if kind == "pass_b":   # cm_pt; point record (X, t) per point; camera table; partials
         return O * (4 + ob) + P * 8 * tsize + npieces * 9 * 8 + C * 16 * tsize
     if kind == "pass_a1":  # cm_pt (+ sqrt(w)) or planes in, one 4-vector out per obs; points once
@@ -206,7 +211,7 @@ def algorithmic_bytes(kind, C, P, O, npieces, tsize, mf, huber=False):
     if kind == "pass_a2":  # order map + one 4-vector per obs; rowptr, V*^-1, t out per point
         return O * (4 + 4 * tsize) + P * (4 + 6 * tsize + 4 * tsize)
     if kind == "pass_fa":  # point index + chunk camera position (+ sqrt(w)) per obs; X in, V*^-1, t out per point
-        return O * (4 + 2 + (tsize if huber else 0)) + P * (4 + 4 * tsize + 6 * tsize + 4 * tsize)
+        return O * (4 + 2 + sw) + P * (4 + 4 * tsize + 6 * tsize + 4 * tsize)
     if kind == "lin_cam":  # pixels + point index in; planes / weights out; points once; partials
         return O * (2 * tsize + 4 + ob) + P * 3 * tsize + npieces * 54 * 8
     if kind == "lin_pt":
@@ -221,9 +226,22 @@ def algorithmic_bytes(kind, C, P, O, npieces, tsize, mf, huber=False):
     return 0
 
 
-# FP32 operations per observation of the recompute-mode passes (an FMA counts
-# two): the factored Jacobian (61) plus the pass's products.
-FLOPS_PER_OBS = {"pass_b": 119, "pass_a1": 113, "pass_fa": 116}
+# Floating-point operations per observation of the PCG passes (an FMA counts
+# two), read off the kernels' arithmetic.  Recompute mode (FP32 default): the
+# factored Jacobian (58) plus the pass's products (the fused pass A adds the
+# 3 additions of its per-point sums).  Stored mode (FP64 default): products
+# with the stored planes only.
+FLOPS_PER_OBS = {"pass_b": 116, "pass_a1": 113, "pass_fa": 116}
+FLOPS_PER_OBS_STORED = {"pass_a1": 60, "pass_a2": 3, "pass_b": 61}
+# per point: V*^-1 times the summed 3-vector (9 FMA)
+FLOPS_PER_POINT = {"pass_a2": 18, "pass_fa": 18}
+
+
+def pass_flops(kind, O, P, mf):
+    per_obs = (FLOPS_PER_OBS if mf else FLOPS_PER_OBS_STORED).get(kind)
+    if per_obs is None:
+        return None
+    return per_obs * O + FLOPS_PER_POINT.get(kind, 0) * P
 
 
 def fp32_peak_tflops(sm_mhz):
@@ -263,6 +281,299 @@ def peaks():
         return 6800.0, "fallback"
 
 
+# F_ref (the converged FP64 cost of the ba4000 workload): the benchmark's FP32
+# run until it stalls, then FP64 trials with a tight PCG from its parameters
+# until an accepted trial lowers the cost by less than F_REF_STOP (relative).
+F_REF_F32_TRIALS = 150
+F_REF_PCG = (1500, 1e-12)
+F_REF_MAX_TRIALS = 12
+F_REF_STOP = 1e-9
+TTC_REL = 1e-6          # time to (1 + 1e-6) F_ref
+TTC_MAX_TRIALS = {"f64": 150, "f32": 250}
+
+
+def converged_cost(trace, F0):
+    """Lowest cost of an LM trace: the starting cost or an accepted trial's."""
+    acc = [t["cost_trial"] for t in trace if t["accepted"]]
+    return min([F0] + acc)
+
+
+def f_ref_stop(trace, rel=F_REF_STOP):
+    """True once the last accepted trial of a polishing run lowered the cost
+    by less than rel (relative)."""
+    acc = [t for t in trace if t["accepted"]]
+    return bool(acc) and (acc[-1]["cost"] - acc[-1]["cost_trial"]) <= rel * acc[-1]["cost"]
+
+
+def first_at_or_below(costs, target):
+    """Index of the first cost at or below target, else None."""
+    return next((i for i, c in enumerate(costs) if c <= target), None)
+
+
+def _scene_inputs(scene, dev):
+    """The scene's indices and its pixels (projection of the ground truth by
+    the library in FP64, plus the scene's noise), on the device."""
+    import torch
+    import paper_2409_12190_gb300 as ba
+    ci = torch.from_numpy(scene.cam_idx).to(dev)
+    pi = torch.from_numpy(scene.pt_idx).to(dev)
+    cams_gt = torch.tensor(scene.cams_gt, dtype=torch.float64, device=dev)
+    pts_gt = torch.tensor(scene.points_gt, dtype=torch.float64, device=dev)
+    pix = ba.project(cams_gt, pts_gt, ci, pi) + torch.tensor(scene.noise, dtype=torch.float64, device=dev)
+    return ci, pi, pix
+
+
+def _problem(scene, ci, pi, pix, prec, dev, jacobian="auto", maxiter=PCG_MAXITER, tol=PCG_TOL):
+    import torch
+    import paper_2409_12190_gb300 as ba
+    opts = ba.Options(precision=prec, pcg_maxiter=maxiter, pcg_tol=tol, use_graph=True, jacobian=jacobian)
+    dt = torch.float32 if prec == "f32" else torch.float64
+    return ba.Problem(scene.cams_init, scene.points_init, ci, pi, pix.to(dt), opts, device=dev)
+
+
+def compute_f_ref(scene, ci, pi, pix, dev):
+    """F_ref and how it was reached (see F_REF_*)."""
+    import torch
+    t0 = time.perf_counter()
+    with _problem(scene, ci, pi, pix, "f32", dev) as p32:
+        p32.solve(F_REF_F32_TRIALS)
+        cams, pts = p32.params()
+        F32, _ = p32.scalars()
+    with _problem(scene, ci, pi, pix, "f64", dev, maxiter=F_REF_PCG[0], tol=F_REF_PCG[1]) as p64:
+        p64.set_params(cams.double(), pts.double())
+        p64.set_lambda(1e-6)
+        n = 0
+        while n < F_REF_MAX_TRIALS:
+            p64.solve(1)
+            n += 1
+            if f_ref_stop(p64.stats(cap=n)):
+                break
+        trace = p64.stats(cap=n)
+        F, _ = p64.scalars()
+    torch.cuda.synchronize()
+    last = [t for t in trace if t["accepted"]]
+    return F, {"f_ref": F, "rule": (f"FP32 benchmark run for {F_REF_F32_TRIALS} trials (cost {F32:.9g}), then FP64 "
+                                    f"trials with PCG maxiter {F_REF_PCG[0]} / tol {F_REF_PCG[1]:g} until an accepted "
+                                    f"trial lowers the cost by less than {F_REF_STOP:g} relative"),
+               "fp64_trials": n, "last_accepted_decrease_rel": ((last[-1]["cost"] - last[-1]["cost_trial"])
+                                                                / last[-1]["cost"]) if last else None,
+               "seconds": time.perf_counter() - t0}
+
+
+def time_to_f_ref(prob, state0, f_ref, max_trials, stream):
+    """From the starting state: LM trials one by one (graph replay) with an
+    event after each, until the cost is within TTC_REL of f_ref."""
+    import torch
+    prob.set_state(state0)
+    torch.cuda.synchronize()
+    prob.stats()
+    target = (1.0 + TTC_REL) * f_ref
+    e0 = torch.cuda.Event(enable_timing=True)
+    evs = []
+    costs = []
+    e0.record(stream)
+    chunk = 10
+    while len(costs) < max_trials:
+        for _ in range(min(chunk, max_trials - len(costs))):
+            prob.solve(1)
+            ev = torch.cuda.Event(enable_timing=True)
+            ev.record(stream)
+            evs.append(ev)
+        torch.cuda.synchronize()
+        st = prob.stats(cap=len(evs) - len(costs))
+        costs += [t["cost_trial"] if t["accepted"] else t["cost"] for t in st]
+        if first_at_or_below(costs, target) is not None:
+            break
+    hit = first_at_or_below(costs, target)
+    return {"time_to_cost_s": e0.elapsed_time(evs[hit]) / 1000.0 if hit is not None else None,
+            "trials_to_cost": None if hit is None else hit + 1, "target": target, "trials_run": len(costs),
+            "final_cost": costs[-1], "rel_gap_at_end": costs[-1] / f_ref - 1.0}
+
+
+def kernel_table(per, C, P, O, lay, tsize, mf, huber, alu_peak):
+    """Per kernel class: launches, mean CUDA-event time, share, algorithmic
+    GB/s and (PCG passes) TFLOP/s with their fractions."""
+    total = sum(v[0] for v in per.values())
+    out = {}
+    for name, (kms, n) in per.items():
+        if n == 0:
+            continue
+        b = algorithmic_bytes(name, C, P, O, lay["pieces"], tsize, mf, huber)
+        avg = kms / n
+        row = {"launches": n, "avg_us": 1000.0 * avg, "share": kms / total,
+               "gbs": (b / (avg / 1000.0) / 1e9) if b else None, "bytes_per_launch": b or None}
+        fl = pass_flops(name, O, P, mf)
+        if fl:
+            row["tflops"] = fl / (avg / 1000.0) / 1e12
+            row["flops_per_launch"] = fl
+            row["alu_frac"] = row["tflops"] / alu_peak
+        out[name] = row
+    return out
+
+
+def roofline_of(kernels, per, hbm_peak, hbm_kind, alu_peak, alu_source, src_hash, prof_ms, it_bytes):
+    """Roofline block of the dominant kernel (largest share of the profiled
+    time among the kernels with an algorithmic byte count): its HBM and ALU
+    fractions; "bound" is the larger of the two."""
+    dom = max((k for k in kernels if kernels[k]["gbs"]), key=lambda k: per[k][0])
+    kr = kernels[dom]
+    hbm = {"achieved": kr["gbs"], "peak": hbm_peak, "unit": "GB/s", "frac": kr["gbs"] / hbm_peak,
+           "peak_source": hbm_kind}
+    roof = {"bound": "hbm", "kernel": dom, **hbm, "bytes_per_launch": kr["bytes_per_launch"],
+            "traffic": measured_traffic(dom, src_hash), "kernel_source": src_hash, "hbm": hbm}
+    if "tflops" in kr:
+        alu = {"achieved": kr["tflops"], "peak": alu_peak, "unit": "TFLOP/s", "frac": kr["alu_frac"],
+               "flops_per_launch": kr["flops_per_launch"], "peak_source": alu_source}
+        roof["alu"] = alu
+        if alu["frac"] > hbm["frac"]:
+            roof.update({"bound": "alu", "achieved": alu["achieved"], "peak": alu_peak, "unit": "TFLOP/s",
+                         "frac": alu["frac"], "peak_source": alu_source})
+    roof["iteration_gbs"] = it_bytes / (prof_ms / 1000.0) / 1e9
+    roof["iteration_frac"] = roof["iteration_gbs"] / hbm_peak
+    return roof
+
+
+def run_precision(args, prec, scene, ci, pi, pix, dev, world, f_ref, peaks_d, barrier, clocks_for_rank):
+    """One precision of the benchmark: timed trials, per-kernel profile and
+    roofline, time to F_ref, and the end-to-end leg through the public API."""
+    import torch
+    import paper_2409_12190_gb300 as ba
+    C, P, O = scene.C, scene.P, scene.O
+    tsize = 4 if prec == "f32" else 8
+    prob = _problem(scene, ci, pi, pix, prec, dev, jacobian=args.jacobian)
+    torch.cuda.synchronize()
+    lay = prob.layout()
+    mf = not lay["stored"]
+    state_init = prob.get_state()
+    prob.solve(args.warmup)   # captures the trial graph on first use
+    torch.cuda.synchronize()
+    prob.stats()
+    state0 = prob.get_state()  # the end-to-end leg replays the timed trials from here
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    clocks = clocks_for_rank()
+    time.sleep(0.3 if clocks else 0)
+    barrier()
+    torch.cuda.synchronize()
+    n0 = ba.kernel_launch_count()
+    e0.record(stream)
+    prob.solve(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    launches = ba.kernel_launch_count() - n0
+    clk = clocks.stop() if clocks else None
+    ms = rank_max(e0.elapsed_time(e1), dev, world)
+    trials = prob.stats(cap=args.steps)
+    value = world * args.steps / (ms / 1000.0)
+
+    # per-kernel CUDA-event timing of real trials (direct launches)
+    per, prof_ms = prob.profile_trials(args.profile_trials)
+    sm_mhz = (clk or {}).get("sm_max_mhz") or 2070.0
+    if prec == "f32":
+        alu_peak, alu_source = fp32_peak_tflops(sm_mhz), f"152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz"
+    else:
+        alu_peak = peaks_d["fp64_fma_tflops"]
+        alu_source = "measured (ba_measure_fma_peak: FP64 FMA chains on every SM, best of 3)"
+    huber = scene.huber_delta > 0
+    kernels = kernel_table(per, C, P, O, lay, tsize, mf, huber, alu_peak)
+    it_bytes = sum(algorithmic_bytes(k, C, P, O, lay["pieces"], tsize, mf, huber) * per[k][1] for k in per)
+    roof = roofline_of(kernels, per, peaks_d["hbm_gbs"], peaks_d["hbm_kind"], alu_peak, alu_source,
+                       kernel_source_hash(), prof_ms, it_bytes)
+
+    # end to end through the public API: the same trials as the timed region
+    # (restarted from its starting state), each step uploading parameters and
+    # pixels from pinned host memory and reading parameters and cost back
+    e2e_steps = args.e2e_steps if args.e2e_steps > 0 else args.steps
+    dt = torch.float32 if prec == "f32" else torch.float64
+    prob.set_state(state0)
+    hc = torch.empty((C, 9), dtype=dt).pin_memory()
+    hp = torch.empty((P, 3), dtype=dt).pin_memory()
+    hx = pix.to(dt).cpu().pin_memory()
+    prob.get_params_into(hc, hp)
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        prob.set_params(hc, hp)
+        prob.set_pixels(hx)
+        prob.lm_step()
+        prob.get_params_into(hc, hp)
+        prob.scalars()
+    torch.cuda.synchronize()
+    e2e_s = rank_max(time.perf_counter() - t0, dev, world)
+    e2e_trials = prob.stats(cap=e2e_steps)
+    same = ([t["pcg_iters"] for t in e2e_trials] == [t["pcg_iters"] for t in trials[:e2e_steps]]
+            and [t["accepted"] for t in e2e_trials] == [t["accepted"] for t in trials[:e2e_steps]])
+    e2e = {"value": world * e2e_steps / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": (9 * C + 3 * P + 2 * O) * tsize,
+           "d2h_bytes_per_step": (9 * C + 3 * P) * tsize + 8, "steps": e2e_steps,
+           "same_trials_as_timed": same}
+
+    # time to (1 + 1e-6) F_ref from the scene's initial parameters
+    ttc = time_to_f_ref(prob, state_init, f_ref, TTC_MAX_TRIALS[prec], stream) if f_ref else None
+    prob.close()
+    pcg = [t["pcg_iters"] for t in trials]
+    cfg = {"workload": scene.name, "cameras": C, "points": P, "observations": O,
+           "precision": ("f32 per-observation, f64 reductions" if prec == "f32" else "f64 throughout"),
+           "loss": "squared", "pcg": f"block-Jacobi, maxiter {PCG_MAXITER}, tol {PCG_TOL}",
+           "pcg_iters_mean": statistics.mean(pcg) if pcg else None, "pcg_iters_total": sum(pcg),
+           "accepted": sum(t["accepted"] for t in trials),
+           "l2": "inputs larger than L2 (each PCG pass streams >0.1 GB of per-observation data; L2 129 MB)",
+           "parallelism": "replicas" if world > 1 else "single GPU", "graph": "one CUDA graph per LM trial",
+           "jacobian": "recomputed in every pass" if mf else "stored planes",
+           "schur_product": "fused pass A + pass B" if (mf and lay["fused_a"]) else "passes A1, A2, B"}
+    return {"value": value, "ms_per_step": ms / args.steps, "dtype": prec, "config": cfg, "gpu_launches": launches,
+            "clocks": clk, "roofline": roof, "kernels": kernels, "e2e": e2e, "time_to_cost": ttc}
+
+
+def _oracle_sample_job(job):
+    """One bounded oracle run (a spawned worker): LM trials/s on a sample of
+    the scene, scaled to the full scene by its observation count."""
+    scene, n_obs, seed, trials = job
+    import oracle as orc
+    n_pts = max(50, int(round(n_obs * scene.P / scene.O)))
+    sub = scenegen.subsample_points(scene, n_pts, seed=seed)
+    pix = orc.pixels_from_scene(sub)
+    opts = orc.LMOptions(solver="pcg", pcg_tol=0.0, pcg_maxiter=PCG_MAXITER, huber_delta=sub.huber_delta)
+    t0 = time.perf_counter()
+    orc.lm(sub.cams_init, sub.points_init, sub.cam_idx, sub.pt_idx, pix, trials, opts)
+    dt = time.perf_counter() - t0
+    return {"rate_full": trials / dt * sub.O / scene.O, "seconds": dt, "O": sub.O, "P": sub.P}
+
+
+def cpu_baseline(scene, n_obs_single=500_000, n_obs_each=250_000):
+    """The oracle on the host cores: one thread on one sample, then one
+    single-threaded process per core (spawned), each on its own sample, run
+    together (the host's throughput); plus one full ba250 trial, unscaled."""
+    import multiprocessing as mp
+    import oracle as orc
+    ncores = os.cpu_count() or 1
+    single = _oracle_sample_job((scene, n_obs_single, 123, 1))
+    with mp.get_context("spawn").Pool(ncores) as pool:
+        t0 = time.perf_counter()
+        many = pool.map(_oracle_sample_job, [(scene, n_obs_each, 1000 + i, 1) for i in range(ncores)])
+        wall = time.perf_counter() - t0
+    total_rate = sum(r["O"] for r in many) / scene.O / wall   # full-scene trials/s of all processes together
+    b250 = scenegen.config_scene("ba250")
+    pix = orc.pixels_from_scene(b250)
+    t0 = time.perf_counter()
+    orc.lm(b250.cams_init, b250.points_init, b250.cam_idx, b250.pt_idx, pix, 1,
+           orc.LMOptions(solver="pcg", pcg_tol=1e-4, pcg_maxiter=PCG_MAXITER, huber_delta=b250.huber_delta))
+    t250 = time.perf_counter() - t0
+    return {"value": total_rate, "unit": UNIT, "cores": ncores, "kind": "oracle",
+            "sample": (f"{ncores} single-threaded oracle processes (one per host core, spawned), each one LM "
+                       f"trial (PCG fixed at {PCG_MAXITER} iterations) on its own sample of ~{n_obs_each} of "
+                       f"{scene.O} observations with all {scene.C} cameras, run together in {wall:.1f} s; "
+                       f"throughput scaled by O_full/O_sample"),
+            "nproc": ncores,
+            "single_thread": {"value": single["rate_full"], "cores": 1,
+                              "sample": f"1 trial on {single['O']} observations, {single['seconds']:.1f} s, "
+                                        f"scaled by O_full/O_sample"},
+            "ba250_full_trial_s": t250}
+
+
 def run_ours(args):
     import torch
     import paper_2409_12190_gb300 as ba
@@ -285,142 +596,33 @@ def run_ours(args):
         scene = scenegen.ring_scene(4000, args.points, seed=3, view_p=1.0 / 5.7, name="ba4000-small")
     else:
         scene = scenegen.config_scene(WORKLOAD)
-    C, P, O = scene.C, scene.P, scene.O
-    ci = torch.from_numpy(scene.cam_idx).to(dev)
-    pi = torch.from_numpy(scene.pt_idx).to(dev)
-    cams_gt = torch.tensor(scene.cams_gt, dtype=torch.float32, device=dev)
-    pts_gt = torch.tensor(scene.points_gt, dtype=torch.float32, device=dev)
-    pix = ba.project(cams_gt, pts_gt, ci, pi) + torch.tensor(scene.noise, dtype=torch.float32, device=dev)
-    opts = ba.Options(precision="f32", pcg_maxiter=PCG_MAXITER, pcg_tol=PCG_TOL, use_graph=True,
-                      jacobian=args.jacobian)
-    mf = args.jacobian in ("auto", "recompute")
-    prob = ba.Problem(scene.cams_init, scene.points_init, ci, pi, pix, opts, device=dev)
-    torch.cuda.synchronize()
-
-    # warm-up (captures the trial graph on first use)
-    prob.solve(args.warmup)
-    torch.cuda.synchronize()
-    prob.stats()
-    # the end-to-end leg below replays the timed trials from this state
-    state0 = prob.get_state()
-
-    stream = torch.cuda.current_stream()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    clocks = ClockSampler(local) if rank == 0 else None
-    time.sleep(0.3 if clocks else 0)
-    barrier()
-    torch.cuda.synchronize()
-    n0 = ba.kernel_launch_count()
-    e0.record(stream)
-    prob.solve(args.steps)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    barrier()
-    launches = ba.kernel_launch_count() - n0
-    clk = clocks.stop() if clocks else None
-    ms = e0.elapsed_time(e1)
-    ms = rank_max(ms, dev, world)
-    trials = prob.stats(cap=args.steps)
-    value = world * args.steps / (ms / 1000.0)
-
-    # per-kernel CUDA-event timing of the same trials (direct launches)
-    per, prof_ms = prob.profile_trials(args.profile_trials)
-    tsize = 4
-    npieces = sum(max(1, math.ceil(n / 2048)) if n > 0 else 0 for n in np.bincount(scene.cam_idx, minlength=C))
-    total = sum(v[0] for v in per.values())
-    kernels = {}
-    peak, peak_kind = peaks()
-    sm_mhz = (clk or {}).get("sm_max_mhz") or 2070.0
-    alu_peak = fp32_peak_tflops(sm_mhz)
-    for name, (kms, n) in per.items():
-        if n == 0:
-            continue
-        b = algorithmic_bytes(name, C, P, O, npieces, tsize, mf)
-        avg = kms / n
-        kernels[name] = {"launches": n, "avg_us": 1000.0 * avg, "share": kms / total,
-                         "gbs": (b / (avg / 1000.0) / 1e9) if b else None}
-        if mf and name in FLOPS_PER_OBS:
-            kernels[name]["tflops"] = FLOPS_PER_OBS[name] * O / (avg / 1000.0) / 1e12
-    dom = max((k for k in kernels if kernels[k]["gbs"]), key=lambda k: per[k][0])
-    src_hash = kernel_source_hash()
-    ach = kernels[dom]["gbs"]
-    roofline = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak, "unit": "GB/s",
-                "frac": ach / peak, "peak_source": peak_kind,
-                "bytes_per_launch": algorithmic_bytes(dom, C, P, O, npieces, tsize, mf),
-                "traffic": measured_traffic(dom, src_hash), "kernel_source": src_hash}
-    if "tflops" in kernels[dom]:
-        alu = {"achieved": kernels[dom]["tflops"], "peak": alu_peak, "unit": "TFLOP/s",
-               "frac": kernels[dom]["tflops"] / alu_peak,
-               "flops_per_launch": FLOPS_PER_OBS[dom] * O,
-               "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz"}
-        roofline["hbm"] = {k: roofline[k] for k in ("achieved", "peak", "unit", "frac")}
-        roofline["alu"] = alu
-        if alu["frac"] > roofline["frac"]:
-            roofline.update({"bound": "alu", "achieved": alu["achieved"], "peak": alu["peak"],
-                             "unit": alu["unit"], "frac": alu["frac"], "peak_source": alu["peak_source"]})
-    # whole-iteration algorithmic bandwidth (bytes of all big passes / trial time)
-    it_bytes = sum(algorithmic_bytes(k, C, P, O, npieces, tsize, mf) * per[k][1] for k in per)
-    roofline["iteration_gbs"] = it_bytes / (prof_ms / 1000.0) / 1e9
-    roofline["iteration_frac"] = roofline["iteration_gbs"] / peak
-
-    # end to end through the public API: the same trials as the timed region
-    # (restarted from its starting state), each step uploading parameters and
-    # pixels from pinned host memory and reading parameters and cost back
-    e2e_steps = args.e2e_steps if args.e2e_steps > 0 else args.steps
-    prob.set_state(state0)
-    hc = torch.empty((C, 9), dtype=torch.float32).pin_memory()
-    hp = torch.empty((P, 3), dtype=torch.float32).pin_memory()
-    hx = pix.cpu().pin_memory()
-    prob.get_params_into(hc, hp)
-    torch.cuda.synchronize()
-    barrier()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        prob.set_params(hc, hp)
-        prob.set_pixels(hx)
-        prob.lm_step()
-        prob.get_params_into(hc, hp)
-        cost, _ = prob.scalars()
-    torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    e2e_s = rank_max(e2e_s, dev, world)
-    e2e_trials = prob.stats(cap=e2e_steps)
-    same = ([t["pcg_iters"] for t in e2e_trials] == [t["pcg_iters"] for t in trials[:e2e_steps]]
-            and [t["accepted"] for t in e2e_trials] == [t["accepted"] for t in trials[:e2e_steps]])
-    e2e = {"value": world * e2e_steps / e2e_s, "unit": UNIT,
-           "h2d_bytes_per_step": (9 * C + 3 * P + 2 * O) * 4,
-           "d2h_bytes_per_step": (9 * C + 3 * P) * 4 + 8, "steps": e2e_steps,
-           "same_trials_as_timed": same}
-
+    ci, pi, pix = _scene_inputs(scene, dev)
+    hbm, hbm_kind = peaks()
+    peaks_d = {"hbm_gbs": hbm, "hbm_kind": hbm_kind, "fp64_fma_tflops": ba.measure_fma_peak("f64"),
+               "fp32_fma_tflops": ba.measure_fma_peak("f32")}
+    f_ref, f_ref_info = (None, None) if args.no_time_to_cost else compute_f_ref(scene, ci, pi, pix, dev)
+    precs = ["f64", "f32"] if args.precision == "both" else [args.precision]
+    res = {}
+    for p in precs:
+        res[p] = run_precision(args, p, scene, ci, pi, pix, dev, world, f_ref, peaks_d, barrier,
+                               lambda: ClockSampler(local) if rank == 0 else None)
     if rank != 0:
         return
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        r = oracle_sample_rate(scene, 500_000, trials=1)
-        cpu = {"value": r["rate_full"], "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": (f"1 LM trial on {r['P']} of {P} points with their {r['O']} of {O} "
-                          f"observations, all {C} cameras, PCG fixed at {PCG_MAXITER} iterations, "
-                          f"{r['seconds']:.1f} s; rate scaled by O_full/O_sample")}
-    pcg = [t["pcg_iters"] for t in trials]
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": scene.name, "cameras": C, "points": P, "observations": O,
-                       "precision": "f32 per-observation, f64 reductions", "loss": "squared",
-                       "pcg": f"block-Jacobi, maxiter {PCG_MAXITER}, tol {PCG_TOL}",
-                       "pcg_iters_mean": statistics.mean(pcg) if pcg else None,
-                       "pcg_iters_total": sum(pcg),
-                       "accepted": sum(t["accepted"] for t in trials),
-                       "l2": "inputs larger than L2 (each PCG pass streams >0.6 GB of "
-                             "per-observation data; L2 129 MB)",
-                       "parallelism": "replicas" if world > 1 else "single GPU",
-                       "graph": "one CUDA graph per LM trial",
-                       "jacobian": "recomputed in every pass" if mf else "stored planes"},
-            "gpu_launches": launches, "clocks": clk, "roofline": roofline,
-            "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e}
+        cpu = cpu_baseline(scene)
+    head = res[precs[0]]
+    line = {"metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": head["dtype"], "data": "synthetic",
+            "config": dict(head["config"], f_ref=f_ref_info),
+            "gpu_launches": head["gpu_launches"], "clocks": head["clocks"], "roofline": head["roofline"],
+            "kernels": head["kernels"], "cpu_baseline": cpu, "e2e": head["e2e"],
+            "time_to_cost": head["time_to_cost"],
+            "measured_peaks": {k: v for k, v in peaks_d.items()}}
+    if len(precs) > 1:
+        line["variants"] = {p: res[p] for p in precs[1:]}
     print(json.dumps(line), flush=True)
-    prob.close()
 
 
 # --------------------------------------------------------------------------

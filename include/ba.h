@@ -296,6 +296,29 @@ ba_status ba_csr_build_noalloc(const int32_t* keys, int n, int n_keys,
  * Measurement aid: no counterpart in the paper. */
 uint64_t ba_kernel_launch_count(void);
 
+/* Entries of ba_get_layout. */
+enum {
+  BA_LAYOUT_PIECES = 0,  /* camera-major pieces (per-piece partials of the camera passes) */
+  BA_LAYOUT_CHUNKS = 1,  /* point chunks (one CTA each in the point-major passes) */
+  BA_LAYOUT_FUSED_A = 2, /* 1 if pass A runs fused (point-major, recompute mode) */
+  BA_LAYOUT_STORED = 3,  /* 1 if the Jacobian blocks are stored (BA_JAC_STORE) */
+  BA_LAYOUT_COUNT = 4
+};
+
+/* Layout counts of problem h (see the enum above) into out[0 .. n) (host;
+ * entries past BA_LAYOUT_COUNT are 0), for algorithmic-byte accounting in
+ * benchmarks.  Measurement aid: no counterpart in the paper. */
+ba_status ba_get_layout(const ba_problem* h, int64_t* out, int n);
+
+/* Measured FMA throughput of the CUDA cores in TFLOP/s (2 flops per fused
+ * multiply-add), for precision BA_PREC_F64 (double) or BA_PREC_F32
+ * (float), into *tflops_out (host): the best of three timed launches of
+ * independent FMA chains on every SM, after one warm-up launch.  The
+ * denominator of the ALU roofline of kernels bound by arithmetic.
+ * Measurement aid: no counterpart in the paper.  Allocates a few bytes and
+ * synchronises the stream. */
+ba_status ba_measure_fma_peak(int precision, double* tflops_out, void* stream);
+
 /* Kernel classes timed by ba_profile_trials. */
 enum {
   BA_K_LIN_CAM = 0,   /* a1+a2 camera-major linearisation pass */

@@ -253,6 +253,13 @@ class Problem:
                                     _stream(stream)))
         return dpix, dc0, dp0, it.value, rel.value
 
+    def layout(self):
+        """Layout counts: pieces, chunks, fused_a (1/0), stored (1/0)."""
+        out = (ct.c_int64 * 4)()
+        _lib.check(_L().ba_get_layout(self._h, out, 4))
+        names = ("pieces", "chunks", "fused_a", "stored")
+        return {k: int(v) for k, v in zip(names, out)}
+
     def profile_trials(self, iters: int):
         """Run iters LM trials with a CUDA event pair around every launch;
         returns {kernel class: (total ms, launches)} and the trials' total ms."""
@@ -596,6 +603,16 @@ def mlp_train(params, adam_m, adam_v, X, A, Y, Z, epochs: int, batch: int, lr: f
                                  int(epochs), int(batch), float(lr), ct.cast(hist, ct.c_void_p),
                                  _stream(stream)))
     return list(hist)[:int(epochs)]
+
+
+def measure_fma_peak(precision: str = "f64", stream=None) -> float:
+    """Measured FMA throughput of the CUDA cores in TFLOP/s ("f64" or "f32")."""
+    if precision not in ("f32", "f64"):
+        raise ValueError("precision must be 'f32' or 'f64'")
+    out = ct.c_double()
+    _lib.check(_L().ba_measure_fma_peak(BA_PREC_F32 if precision == "f32" else BA_PREC_F64, ct.byref(out),
+                                        _stream(stream)))
+    return out.value
 
 
 def kernel_launch_count() -> int:

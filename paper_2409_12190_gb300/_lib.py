@@ -90,6 +90,8 @@ SIGNATURES = {
     "ba_csr_build_noalloc": (_S, [_VP, _I, _I, _VP, _VP, _VP]),
     "ba_kernel_launch_count": (ct.c_uint64, []),
     "ba_profile_trials": (_S, [_VP, _I, ct.POINTER(ba_kernel_times)]),
+    "ba_measure_fma_peak": (_S, [_I, ct.POINTER(_D), _VP]),
+    "ba_get_layout": (_S, [_VP, _VP, _I]),
     "ba_set_fixed": (_S, [_VP, _VP, _VP]),
     "ba_set_lambda": (_S, [_VP, _D]),
     "ba_backward": (_S, [_VP, _D, _I, _D, _VP, _VP, _VP, _VP, _VP, ct.POINTER(_I), ct.POINTER(_D), _VP]),

@@ -1278,6 +1278,13 @@ ba_status ba_learn_slow_probes(ba_problem* h, double lambda, int n, const int* i
 
 uint64_t ba_kernel_launch_count(void) { return ba::g_launches.load(); }
 
+ba_status ba_get_layout(const ba_problem* h, int64_t* out, int n) {
+  if (!h || !out || n < 0) return fail(BA_ERR_INVALID_ARG, "bad argument");
+  const int64_t v[BA_LAYOUT_COUNT] = {h->npieces, h->nchunks, h->fa ? 1 : 0, h->mf ? 0 : 1};
+  for (int i = 0; i < n; ++i) out[i] = i < BA_LAYOUT_COUNT ? v[i] : 0;
+  return BA_OK;
+}
+
 ba_status ba_profile_trials(ba_problem* h, int iters, ba_kernel_times* out) {
   if (!h || !out || iters < 0) return fail(BA_ERR_INVALID_ARG, "bad argument");
   memset(out, 0, sizeof(*out));

@@ -22,6 +22,24 @@ def test_fused_pass_a_bytes_are_its_arrays_read_or_written_once():
             - bench.algorithmic_bytes("pass_fa", C, P, O, 4860, 4, True)) == 4 * O
 
 
+def test_pass_flops_recompute_and_stored():
+    O, P = 1000, 150
+    assert bench.pass_flops("pass_fa", O, P, True) == 116 * O + 18 * P
+    assert bench.pass_flops("pass_b", O, P, False) == 61 * O
+    assert bench.pass_flops("pass_a2", O, P, False) == 3 * O + 18 * P
+    assert bench.pass_flops("lin_cam", O, P, True) is None
+
+
+def test_f_ref_rules():
+    tr = [dict(cost=10.0, cost_trial=9.0, accepted=True), dict(cost=9.0, cost_trial=9.5, accepted=False)]
+    assert bench.converged_cost(tr, 10.0) == 9.0
+    assert not bench.f_ref_stop(tr, 1e-9)
+    tr.append(dict(cost=9.0, cost_trial=9.0 - 1e-9, accepted=True))
+    assert bench.f_ref_stop(tr, 1e-9)
+    assert bench.first_at_or_below([5.0, 4.0, 3.0], 4.0) == 1
+    assert bench.first_at_or_below([5.0, 4.0], 3.9) is None
+
+
 def test_pass_b_bytes_stored_planes_versus_recompute():
     C, P, O, npc = 250, 60_000, 480_380, 300
     rec = bench.algorithmic_bytes("pass_b", C, P, O, npc, 4, True)
