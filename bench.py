@@ -202,7 +202,10 @@ def algorithmic_bytes(kind, C, P, O, npieces, tsize, mf, huber=False):
     """Compulsory HBM bytes of one launch: every array element the kernel
     must read or write, each counted once (per-observation planes, indices
     and weights; per-point / per-camera vectors once)."""
-    ob = 18 * tsize if not mf else (tsize if huber else 0)   # planes or sqrt(w)
+    # stored planes (the passes of the Schur product and the linearisation
+    # also read or write the 6 planes of Jp) or sqrt(w)
+    ob = (24 if kind in ("pass_b", "pass_a1", "schur_cam", "lin_cam") else 18) * tsize if not mf else \
+        (tsize if huber else 0)
     sw = tsize if huber else 0
     if kind == "pass_b":   # cm_pt; point record (X, t) per point; camera table; partials
         return O * (4 + ob) + P * 8 * tsize + npieces * 9 * 8 + C * 16 * tsize
@@ -230,9 +233,10 @@ def algorithmic_bytes(kind, C, P, O, npieces, tsize, mf, huber=False):
 # two), read off the kernels' arithmetic.  Recompute mode (FP32 default): the
 # factored Jacobian (58) plus the pass's products (the fused pass A adds the
 # 3 additions of its per-point sums).  Stored mode (FP64 default): products
-# with the stored planes only.
+# with the stored planes only (pass A1: e = Jc x, 18 FMA, and z = Jp^T e;
+# pass B: h = Jp t and the sum of Jc^T h, 18 FMA).
 FLOPS_PER_OBS = {"pass_b": 116, "pass_a1": 113, "pass_fa": 116}
-FLOPS_PER_OBS_STORED = {"pass_a1": 60, "pass_a2": 3, "pass_b": 61}
+FLOPS_PER_OBS_STORED = {"pass_a1": 45, "pass_a2": 3, "pass_b": 46}
 # per point: V*^-1 times the summed 3-vector (9 FMA)
 FLOPS_PER_POINT = {"pass_a2": 18, "pass_fa": 18}
 
@@ -331,8 +335,9 @@ def _problem(scene, ci, pi, pix, prec, dev, jacobian="auto", maxiter=PCG_MAXITER
     return ba.Problem(scene.cams_init, scene.points_init, ci, pi, pix.to(dt), opts, device=dev)
 
 
-def compute_f_ref(scene, ci, pi, pix, dev):
-    """F_ref and how it was reached (see F_REF_*)."""
+def compute_f_ref(scene, ci, pi, pix, dev, want_params=False):
+    """F_ref and how it was reached (see F_REF_*); with want_params also the
+    FP64 parameters (cams, points) at which it was evaluated."""
     import torch
     t0 = time.perf_counter()
     with _problem(scene, ci, pi, pix, "f32", dev) as p32:
@@ -350,6 +355,7 @@ def compute_f_ref(scene, ci, pi, pix, dev):
                 break
         trace = p64.stats(cap=n)
         F, _ = p64.scalars()
+        params = p64.params() if want_params else None
     torch.cuda.synchronize()
     last = [t for t in trace if t["accepted"]]
     return F, {"f_ref": F, "rule": (f"FP32 benchmark run for {F_REF_F32_TRIALS} trials (cost {F32:.9g}), then FP64 "
@@ -357,7 +363,7 @@ def compute_f_ref(scene, ci, pi, pix, dev):
                                     f"trial lowers the cost by less than {F_REF_STOP:g} relative"),
                "fp64_trials": n, "last_accepted_decrease_rel": ((last[-1]["cost"] - last[-1]["cost_trial"])
                                                                 / last[-1]["cost"]) if last else None,
-               "seconds": time.perf_counter() - t0}
+               "seconds": time.perf_counter() - t0}, *((params,) if want_params else ())
 
 
 def time_to_f_ref(prob, state0, f_ref, max_trials, stream):

@@ -62,6 +62,17 @@ enum { BA_PREC_F64 = 0, BA_PREC_F32 = 1 };
  * STORE for BA_PREC_F64.  Both give the same blocks up to rounding. */
 enum { BA_JAC_AUTO = 0, BA_JAC_RECOMPUTE = 1, BA_JAC_STORE = 2 };
 
+/* How each LM trial solves the reduced camera system S dc = b (Sec. IV-C:
+ * the paper offers PCG and a sparse direct solver, a Cholesky
+ * factorisation).  BA_SOLVER_PCG: block-Jacobi PCG with the implicit S x
+ * product (pcg_maxiter, pcg_tol).  BA_SOLVER_CHOLESKY: S formed explicitly
+ * as a dense 9C x 9C FP64 matrix and factored by a blocked Cholesky on the
+ * GPU, for problems with 9C <= BA_DENSE_MAX_DIM (the matrix takes 81 C^2 x 8
+ * bytes); a trial whose S is not positive definite in FP64 takes a zero step
+ * (rejected, counted in ba_iter_stats.precond_fallbacks). */
+enum { BA_SOLVER_PCG = 0, BA_SOLVER_CHOLESKY = 1 };
+#define BA_DENSE_MAX_DIM 18432
+
 /* Solver options.  up/down are the trust-region factors of the paper's
  * minimum code example (TrustRegion(up=2.0, down=0.5**4), Sec. IV); its
  * PCG(tol=1e-4, maxiter=250) gives pcg_tol / pcg_maxiter.  diag_min/diag_max
@@ -84,6 +95,7 @@ typedef struct {
   int use_graph;       /* 1: ba_solve replays a captured CUDA graph */
   int max_stats;       /* capacity of the per-trial statistics ring, 4096 */
   int jacobian_mode;   /* BA_JAC_AUTO, BA_JAC_RECOMPUTE or BA_JAC_STORE */
+  int solver;          /* BA_SOLVER_PCG or BA_SOLVER_CHOLESKY */
 } ba_options;
 
 /* Statistics of one LM trial (Alg. 1, one pass of the loop body). */
@@ -96,7 +108,8 @@ typedef struct {
   double pcg_rel_res; /* |r|/|b| of the reduced system at exit */
   int32_t accepted;   /* 1 if theta <- theta + Delta */
   int32_t pcg_iters;  /* PCG iterations run */
-  int32_t precond_fallbacks; /* cameras whose block-Jacobi block was not SPD */
+  int32_t precond_fallbacks; /* cameras whose block-Jacobi block was not SPD;
+                                with BA_SOLVER_CHOLESKY: 1 if S was not */
   int32_t reserved;
 } ba_iter_stats;
 

@@ -65,6 +65,7 @@ class Options:
     use_graph: bool = True
     max_stats: int = 4096
     jacobian: str = "auto"          # "auto", "recompute" or "store"
+    solver: str = "pcg"             # "pcg" or "cholesky" (dense direct solve, 9C <= 18432)
 
     @property
     def dtype(self):
@@ -85,6 +86,9 @@ class Options:
         if self.jacobian not in _lib.BA_JAC:
             raise ValueError("jacobian must be 'auto', 'recompute' or 'store'")
         o.jacobian_mode = _lib.BA_JAC[self.jacobian]
+        if self.solver not in _lib.BA_SOLVER:
+            raise ValueError("solver must be 'pcg' or 'cholesky'")
+        o.solver = _lib.BA_SOLVER[self.solver]
         return o
 
 

@@ -13,6 +13,7 @@ STATUS_NAMES = {0: "BA_OK", 1: "BA_ERR_INVALID_ARG", 2: "BA_ERR_CUDA", 3: "BA_ER
 BA_PREC_F64 = 0
 BA_PREC_F32 = 1
 BA_JAC = {"auto": 0, "recompute": 1, "store": 2}
+BA_SOLVER = {"pcg": 0, "cholesky": 1}
 
 
 class ba_options(ct.Structure):
@@ -33,6 +34,7 @@ class ba_options(ct.Structure):
         ("use_graph", ct.c_int),
         ("max_stats", ct.c_int),
         ("jacobian_mode", ct.c_int),
+        ("solver", ct.c_int),
     ]
 
 

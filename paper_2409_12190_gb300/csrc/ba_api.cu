@@ -15,6 +15,7 @@
 
 #include "ba.h"
 #include "ba_internal.h"
+#include "ba_dense.cuh"
 #include "ba_kernels.cuh"
 #include "ba_learn.cuh"
 #include "ba_problem.h"
@@ -218,6 +219,45 @@ void enqueue_pcg_iter(ba_problem* h, const double* lam_ptr, int k, double tol) {
   count_launch(2);
 }
 
+// The direct solve of the reduced system (BA_SOLVER_CHOLESKY): explicit S,
+// blocked Cholesky, triangular solves; dc into h->x as the PCG would leave it.
+template <typename T, bool MF>
+void enqueue_dense_solve(ba_problem* h, const double* lam_ptr) {
+  cudaStream_t s = h->s;
+  const int n = 9 * h->C;
+  {
+    Prof pr(h, BA_K_OTHER);
+    k_schur_dense<T, MF><<<h->C, DENSE_THREADS, 0, s>>>(
+        h->C, h->rowptr_cam, h->cm_pt, h->rowptr_pt, h->pm_cam, h->pm2cm, (const T*)h->Jcm, (const T*)h->cm_sw,
+        (const T*)h->camtab, (const T*)h->pts, h->st, h->P, h->O, (const T*)h->Vinv, h->U, lam_ptr, h->opt.diag_min,
+        h->opt.diag_max, h->dS);
+    count_launch();
+  }
+  if (h->fixed) {
+    k_dense_mask<<<nblk((long long)n * n, 256), 256, 0, s>>>(n, h->fixed, h->dS);
+    count_launch();
+  }
+  cudaMemsetAsync(h->dfail, 0, sizeof(int), s);
+  const int nblk_d = (n + DB - 1) / DB;
+  for (int kb = 0; kb < nblk_d; ++kb) {
+    Prof pr(h, BA_K_OTHER);
+    k_chol_diag<<<1, DB * DB / 4, 0, s>>>(n, kb, h->dS, h->dfail);
+    const int rows_below = n - (kb + 1) * DB;
+    if (rows_below > 0) {
+      k_chol_panel<<<(rows_below + DB - 1) / DB, DB, 0, s>>>(n, kb, h->dS);
+      const long long T_ = nblk_d - kb - 1;
+      k_chol_update<<<(unsigned)(T_ * (T_ + 1) / 2), DB * DB / 4, 0, s>>>(n, kb, h->dS);
+      count_launch(2);
+    }
+    count_launch();
+  }
+  {
+    Prof pr(h, BA_K_OTHER);
+    k_dense_solve<<<1, 1024, 0, s>>>(n, h->dS, h->r, h->dy, h->x, h->dfail, h->st);
+    count_launch();
+  }
+}
+
 template <typename T, bool MF>
 void enqueue_solve(ba_problem* h, const double* lam_ptr, int maxiter, double tol, bool learned = false) {
   cudaStream_t s = h->s;
@@ -252,7 +292,11 @@ void enqueue_solve(ba_problem* h, const double* lam_ptr, int maxiter, double tol
                                                          h->st);
     count_launch(3);
   }
-  for (int k = 0; k < maxiter; ++k) enqueue_pcg_iter<T, MF>(h, lam_ptr, k, tol);
+  if (h->opt.solver == BA_SOLVER_CHOLESKY) {
+    enqueue_dense_solve<T, MF>(h, lam_ptr);
+  } else {
+    for (int k = 0; k < maxiter; ++k) enqueue_pcg_iter<T, MF>(h, lam_ptr, k, tol);
+  }
   {
     Prof pr(h, BA_K_OTHER);
     k_cam_trial<T, MF><<<h->ncb, CAM_THREADS, 0, s>>>(h->C, h->x, h->gc, (T*)h->cams, (const T*)h->camtab, h->st,
@@ -398,6 +442,8 @@ ba_status check_options(const ba_options* o) {
     return fail(BA_ERR_INVALID_ARG, "huber_delta is NaN");
   if (o->jacobian_mode < BA_JAC_AUTO || o->jacobian_mode > BA_JAC_STORE)
     return fail(BA_ERR_INVALID_ARG, "jacobian_mode must be BA_JAC_AUTO, BA_JAC_RECOMPUTE or BA_JAC_STORE");
+  if (o->solver != BA_SOLVER_PCG && o->solver != BA_SOLVER_CHOLESKY)
+    return fail(BA_ERR_INVALID_ARG, "solver must be BA_SOLVER_PCG or BA_SOLVER_CHOLESKY");
   return BA_OK;
 }
 
@@ -635,6 +681,12 @@ ba_status create_impl(ba_problem* h, const void* cams, const void* points, const
   CU(h->alloc(&h->dp, 3 * P * ts));
   CU(h->alloc(&h->part, (size_t)PART * std::max(h->npieces, 1) * 8));
   h->ncb = (int)nblk(C, CAM_THREADS);
+  if (h->opt.solver == BA_SOLVER_CHOLESKY) {
+    const size_t n = 9 * (size_t)C;
+    CU(h->alloc(&h->dS, n * n * 8));
+    CU(h->alloc(&h->dy, n * 8));
+    CU(h->alloc(&h->dfail, 16));
+  }
   h->npb = (int)nblk(P, PT_THREADS);
   CU(h->alloc(&h->dot_pq, h->ncb * 8));
   CU(h->alloc(&h->dot_rz, 2 * h->ncb * 8));
@@ -803,6 +855,7 @@ ba_status ba_options_default(ba_options* o) {
   o->use_graph = 1;
   o->max_stats = 4096;
   o->jacobian_mode = BA_JAC_AUTO;
+  o->solver = BA_SOLVER_PCG;
   return BA_OK;
 }
 
@@ -818,6 +871,8 @@ ba_status ba_problem_create(ba_problem** out, int C, int P, int O, const void* c
   else ba_options_default(&o);
   ba_status st = check_options(&o);
   if (st != BA_OK) return st;
+  if (o.solver == BA_SOLVER_CHOLESKY && 9LL * C > BA_DENSE_MAX_DIM)
+    return fail(BA_ERR_INVALID_ARG, "BA_SOLVER_CHOLESKY needs 9C <= %d (C = %d)", BA_DENSE_MAX_DIM, C);
   ba_problem* h = new (std::nothrow) ba_problem();
   if (!h) return fail(BA_ERR_OOM, "host allocation failed");
   h->C = C;

@@ -12,11 +12,12 @@
 // W_k = Jc^T Jp is never formed.
 //
 // Two storage modes (a template flag MF on the kernels that need it):
-//   stored  (MF = false)  the 18 numbers A, B = A (-[RX]_x) J_l, D = p q^T are
-//            written once per linearisation, in camera-major order, as
-//            structure-of-arrays planes of length O, and every later pass
-//            streams them (the FP64 path: FP64 arithmetic is scarce on this
-//            GPU, bytes are not);
+//   stored  (MF = false)  the 24 numbers A, B = A (-[RX]_x) J_l, D = p q^T and
+//            Jp = A R are written once per linearisation, in camera-major
+//            order, as structure-of-arrays planes of length O, and every later
+//            pass streams them (the FP64 path: FP64 arithmetic is scarce on
+//            this GPU, bytes are not; storing Jp saves the passes the 15 FMAs
+//            of forming A^T e and R^T (.) or R t and A (.) per observation);
 //   recompute (MF = true) nothing per observation but sqrt(w) (only under a
 //            robust loss) is stored; every pass recomputes A, q, RX from the
 //            point, the camera table and sqrt(w) (the FP32 path: ~60 FP32
@@ -70,7 +71,8 @@ constexpr int PASSB_THREADS = 128;    // pass B and the cost pass, FP32 recomput
 constexpr int LIN_THREADS = 64;
 constexpr int PT_THREADS = 256;
 constexpr int CAM_THREADS = 32;
-constexpr int NPLANE = 18;
+constexpr int NPLANE = 24;     // stored planes: A (6), B (6), D (6), Jp = A R (6)
+constexpr int NPLANE_JC = 18;  // the first 18: the camera block Jc = [B | A | D]
 constexpr int CT = 32;               // camera table stride
 constexpr int CT_T = 9, CT_F = 12, CT_K1 = 13, CT_K2 = 14, CT_JL = 16;
 constexpr int PV = 12;               // factored PCG vector stride
@@ -379,6 +381,24 @@ __device__ inline void camera_table(const T* __restrict__ cam, T* __restrict__ c
   for (int i = 25; i < CT; ++i) ct[i] = T(0);
 }
 
+// The camera table in double from parameters of either precision (the FP32
+// variant evaluates its cost in FP64: see cost_cam_range).
+template <typename T>
+__device__ inline void camera_table_f64(const T* __restrict__ cam, double* __restrict__ ct) {
+  double R[9], Jl[9];
+  so3_tables((double)cam[0], (double)cam[1], (double)cam[2], R, Jl);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    ct[i] = R[i];
+    ct[CT_JL + i] = Jl[i];
+  }
+#pragma unroll
+  for (int i = 0; i < 6; ++i) ct[CT_T + i] = (double)cam[3 + i];
+  ct[15] = 0.0;
+#pragma unroll
+  for (int i = 25; i < CT; ++i) ct[i] = 0.0;
+}
+
 // ---------------------------------------------------------------------------
 // One observation
 // ---------------------------------------------------------------------------
@@ -449,9 +469,14 @@ __device__ __forceinline__ void fac_obs(const T* __restrict__ ct, T X0, T X1, T 
   o.q2 = o.q1 * r2;
 }
 
-// Planes A, B = A (-[RX]_x) J_l, D = p q^T from the factored form.
 template <typename T>
-__device__ __forceinline__ void fac_planes(const Fac<T>& o, const T* __restrict__ Jl, T (&pl)[NPLANE]) {
+__device__ __forceinline__ void jp_from(const T* __restrict__ A, const T* __restrict__ R, T (&Jp)[6]);
+
+// Planes A, B = A (-[RX]_x) J_l, D = p q^T and the point block Jp = A R from
+// the factored form (ct: the camera table, R at 0 and J_l at CT_JL).
+template <typename T>
+__device__ __forceinline__ void fac_planes(const Fac<T>& o, const T* __restrict__ ct, T (&pl)[NPLANE]) {
+  const T* Jl = ct + CT_JL;
 #pragma unroll
   for (int a = 0; a < 2; ++a) {
     const T* Ar = o.A + 3 * a;
@@ -469,6 +494,10 @@ __device__ __forceinline__ void fac_planes(const Fac<T>& o, const T* __restrict_
     pl[13 + 3 * a] = pa * o.q1;
     pl[14 + 3 * a] = pa * o.q2;
   }
+  T jp[6];
+  jp_from(o.A, ct, jp);
+#pragma unroll
+  for (int i = 0; i < 6; ++i) pl[NPLANE_JC + i] = jp[i];
 }
 
 // Residual, weight and factored Jacobian of one observation.
@@ -506,10 +535,12 @@ __device__ __forceinline__ void jp_from(const T* __restrict__ A, const T* __rest
       Jp[3 * a + j] = A[3 * a] * R[j] + A[3 * a + 1] * R[3 + j] + A[3 * a + 2] * R[6 + j];
 }
 
-template <typename T>
+// The first N planes of camera-major slot s (N = NPLANE_JC when Jp is not
+// needed).
+template <int N = NPLANE, typename T>
 __device__ __forceinline__ void load_planes(const T* __restrict__ J, long long O, long long s, T (&pl)[NPLANE]) {
 #pragma unroll
-  for (int p = 0; p < NPLANE; ++p) pl[p] = J[p * O + s];
+  for (int p = 0; p < N; ++p) pl[p] = J[p * O + s];
 }
 
 // Four consecutive T as one vector access (the address is 4 * sizeof(T)
@@ -743,7 +774,7 @@ __device__ __forceinline__ void lin_cam_range(int beg, int end, const int32_t* _
             r0, r1, hr, sw);
     if (sw_out) sw_out[s] = sw;
     T pl[NPLANE];
-    fac_planes(o, sct + CT_JL, pl);
+    fac_planes(o, sct, pl);
     if (STORE) {
 #pragma unroll
       for (int p = 0; p < NPLANE; ++p) Jcm[(long long)p * O + s] = pl[p];
@@ -974,7 +1005,7 @@ static __global__ void k_pt_damp(int P, const double* __restrict__ V, const doub
   pt_damp_one<T>(j, V, gp, *lam_ptr, dmin, dmax, Vinv, y0);
 }
 
-// The 18 planes of camera-major slot s: loaded (stored mode) or recomputed.
+// The planes of camera-major slot s: loaded (stored mode) or recomputed.
 template <typename T, bool MF>
 __device__ __forceinline__ void cm_planes(const T* __restrict__ Jcm, long long O, int s, const T* __restrict__ sct,
                                           const T* __restrict__ pts, int j, const T* __restrict__ sw,
@@ -982,7 +1013,7 @@ __device__ __forceinline__ void cm_planes(const T* __restrict__ Jcm, long long O
   if (MF) {
     Fac<T> o;
     fac_obs(sct, pts[3LL * j], pts[3LL * j + 1], pts[3LL * j + 2], sw ? sw[s] : T(1), o);
-    fac_planes(o, sct + CT_JL, pl);
+    fac_planes(o, sct, pl);
   } else {
     load_planes(Jcm, O, s, pl);
   }
@@ -1000,8 +1031,7 @@ __device__ __forceinline__ void schur_cam_range(int beg, int end, const int32_t*
     const int j = cm_pt[s];
     T pl[NPLANE];
     cm_planes<T, MF>(Jcm, O, s, sct, pts, j, cm_sw, pl);
-    T Jp[6];
-    jp_from(pl, sct, Jp);
+    const T* Jp = pl + NPLANE_JC;
     const T* vi = Vinv + 6LL * j;
     const T v00 = vi[0], v01 = vi[1], v02 = vi[2], v11 = vi[3], v12 = vi[4], v22 = vi[5];
     T t[6];
@@ -1380,12 +1410,11 @@ __device__ __forceinline__ void pass_a1_range(int beg, int end, const int32_t* _
         e0 += j0[i] * xl[i];
         e1 += j1[i] * xl[i];
       }
-      const T a0 = pl[0] * e0 + pl[3] * e1;
-      const T a1 = pl[1] * e0 + pl[4] * e1;
-      const T a2 = pl[2] * e0 + pl[5] * e1;
-      const T z0 = ctl[0] * a0 + ctl[3] * a1 + ctl[6] * a2;
-      const T z1 = ctl[1] * a0 + ctl[4] * a1 + ctl[7] * a2;
-      const T z2 = ctl[2] * a0 + ctl[5] * a1 + ctl[8] * a2;
+      // z = Jp^T e with the stored Jp = A R
+      const T* Jp = pl + NPLANE_JC;
+      const T z0 = Jp[0] * e0 + Jp[3] * e1;
+      const T z1 = Jp[1] * e0 + Jp[4] * e1;
+      const T z2 = Jp[2] * e0 + Jp[5] * e1;
       store4(zbuf + 4LL * s, z0, z1, z2, T(0));
     }
   }
@@ -1750,13 +1779,12 @@ __device__ __forceinline__ void pass_b_range(int beg, int end, const int32_t* __
       const int j = cm_pt[s];
       T t0, t1, t2, tpad;
       load4(ptab + 8LL * j + 4, t0, t1, t2, tpad);
-      const T g0 = ctl[0] * t0 + ctl[1] * t1 + ctl[2] * t2;
-      const T g1 = ctl[3] * t0 + ctl[4] * t1 + ctl[5] * t2;
-      const T g2 = ctl[6] * t0 + ctl[7] * t1 + ctl[8] * t2;
       T pl[NPLANE];
       load_planes(Jcm, O, s, pl);
-      const T h0 = pl[0] * g0 + pl[1] * g1 + pl[2] * g2;
-      const T h1 = pl[3] * g0 + pl[4] * g1 + pl[5] * g2;
+      // h = Jp t with the stored Jp = A R
+      const T* Jp = pl + NPLANE_JC;
+      const T h0 = Jp[0] * t0 + Jp[1] * t1 + Jp[2] * t2;
+      const T h1 = Jp[3] * t0 + Jp[4] * t1 + Jp[5] * t2;
       T j0[9], j1[9];
       jc_rows(pl, j0, j1);
 #pragma unroll
@@ -1985,27 +2013,34 @@ k_cam_trial(int C, const double* __restrict__ x, const double* __restrict__ gc, 
 // 1/2 rho at the camera table sct and points pts, and with MODEL the
 // quadratic model term |Jc dc + Jp dp|^2 at the linearisation (camera table
 // sold, points pts_old, dc in the pass form sdc).
+// The cost 1/2 sum rho is evaluated in FP64 in both precisions: the FP32
+// variant's parameters, points and pixels are promoted and projected with
+// the FP64 camera table sct64 (the accept / reject test and the gain ratio
+// compare costs that differ by less than FP32 evaluation would resolve: a
+// robust loss converges linearly, and the last gains are ~1e-8 relative per
+// trial).  The model term stays in T, summed in float-float for FP32.
 template <typename T, bool MODEL, bool MF, int NT>
 __device__ __forceinline__ void cost_cam_range(int beg, int end, const int32_t* __restrict__ cm_pt,
                                                const T* __restrict__ cm_px, const T* __restrict__ pts,
                                                const T* __restrict__ pts_old, const T* __restrict__ sct,
-                                               const T* __restrict__ sold, const T* __restrict__ sdc, T delta, int O,
+                                               const double* __restrict__ sct64, const T* __restrict__ sold,
+                                               const T* __restrict__ sdc, T delta, int O,
                                                const T* __restrict__ Jcm, const T* __restrict__ cm_sw,
                                                const T* __restrict__ dp, double& cost, double& quad) {
-  // FP32: per-thread sums in float-float (about 48 bits, on the FP32 pipes;
-  // the products of the model term exact by fma), FP64: in double
-  float ch = 0.f, cl = 0.f, qh = 0.f, ql = 0.f;
+  // model term, FP32: per-thread sums in float-float (about 48 bits, on the
+  // FP32 pipes; the products exact by fma); FP64: in double
+  float qh = 0.f, ql = 0.f;
   for (int s = beg + threadIdx.x; s < end; s += NT) {
     const int j = cm_pt[s];
-    T px, py, sc;
-    project_obs(sct, pts[3LL * j], pts[3LL * j + 1], pts[3LL * j + 2], px, py, sc);
-    const T r0 = sc * px - cm_px[s], r1 = sc * py - cm_px[(long long)O + s];
-    T hr, w;
-    huber_weight(r0 * r0 + r1 * r1, delta, hr, w);
-    if constexpr (sizeof(T) == 4)
-      ff_add(ch, cl, hr, 0.f);
-    else
-      cost += (double)hr;
+    {
+      const double* ct = sizeof(T) == 4 ? sct64 : reinterpret_cast<const double*>(sct);
+      double px, py, sc;
+      project_obs(ct, (double)pts[3LL * j], (double)pts[3LL * j + 1], (double)pts[3LL * j + 2], px, py, sc);
+      const double r0 = sc * px - (double)cm_px[s], r1 = sc * py - (double)cm_px[(long long)O + s];
+      double hr, w;
+      huber_weight(r0 * r0 + r1 * r1, (double)delta, hr, w);
+      cost += hr;
+    }
     if (MODEL) {
       const T d0 = dp[3LL * j], d1 = dp[3LL * j + 1], d2 = dp[3LL * j + 2];
       const T g0 = sold[0] * d0 + sold[1] * d1 + sold[2] * d2;
@@ -2020,7 +2055,7 @@ __device__ __forceinline__ void cost_cam_range(int beg, int end, const int32_t* 
         e1 += o.A[3] * g0 + o.A[4] * g1 + o.A[5] * g2;
       } else {
         T pl[NPLANE];
-        load_planes(Jcm, O, s, pl);
+        load_planes<NPLANE_JC>(Jcm, O, s, pl);
         T j0[9], j1[9];
         jc_rows(pl, j0, j1);
         e0 = pl[0] * g0 + pl[1] * g1 + pl[2] * g2;
@@ -2040,10 +2075,7 @@ __device__ __forceinline__ void cost_cam_range(int beg, int end, const int32_t* 
       }
     }
   }
-  if constexpr (sizeof(T) == 4) {
-    cost += (double)ch + (double)cl;
-    quad += (double)qh + (double)ql;
-  }
+  if constexpr (sizeof(T) == 4) quad += (double)qh + (double)ql;
 }
 
 // Camera-major pass over the pieces: cost 1/2 sum rho at the parameters in
@@ -2058,14 +2090,14 @@ k_cost_cam(const int32_t* __restrict__ piece_cam, const int32_t* __restrict__ pi
            const T* __restrict__ Jcm, const T* __restrict__ cm_sw, const T* __restrict__ camtab,
            const T* __restrict__ xT, const T* __restrict__ dp, double* __restrict__ part) {
   if (which == 2 && !st->need_cost) return;  // cost at theta only if stale
-  __shared__ T sct[CT];   // camera of the evaluated parameters
+  __shared__ double sct64[CT];  // camera of the evaluated parameters, in double
   __shared__ T sold[CT];  // camera of the linearisation (model term)
   __shared__ T sdc[PV];
   const int b = blockIdx.x;
   const int c = piece_cam[b];
   const int cur = st->cur;
   const int buf = which == 1 ? 1 - cur : cur;
-  if (threadIdx.x == 0) camera_table(cams_buf + (long long)buf * 9 * C + 9LL * c, sct);
+  if (threadIdx.x == 0) camera_table_f64(cams_buf + (long long)buf * 9 * C + 9LL * c, sct64);
   if (MODEL && threadIdx.x >= 32 && threadIdx.x < 32 + CT)
     sold[threadIdx.x - 32] = camtab[(long long)CT * c + threadIdx.x - 32];
   if (MODEL && threadIdx.x >= 64 + CT && threadIdx.x < 64 + CT + pass_vec_stride(MF))
@@ -2075,8 +2107,9 @@ k_cost_cam(const int32_t* __restrict__ piece_cam, const int32_t* __restrict__ pi
   const T* pts_old = pts_buf + (long long)cur * 3 * P;
   double cost = 0.0, quad = 0.0;
   static_assert(NT >= 64 + CT + PV, "the staging of the model term needs 64 + CT + PV threads");
-  cost_cam_range<T, MODEL, MF, NT>(piece_beg[b], piece_end[b], cm_pt, cm_px, pts, pts_old, sct, sold,
-                                              sdc, delta, O, Jcm, cm_sw, dp, cost, quad);
+  cost_cam_range<T, MODEL, MF, NT>(piece_beg[b], piece_end[b], cm_pt, cm_px, pts, pts_old,
+                                   reinterpret_cast<const T*>(sct64), sct64, sold, sdc, delta, O, Jcm, cm_sw, dp,
+                                   cost, quad);
   double v[2] = {cost, quad};
   block_sum_store<2>(v, part + (long long)PART * b);
 }
@@ -2214,7 +2247,7 @@ k_adjoint_cam(const int32_t* __restrict__ piece_cam, const int32_t* __restrict__
       jct_fac_acc(o, e0, e1, acc);
     } else {
       T pl[NPLANE];
-      load_planes(Jcm, O, s, pl);
+      load_planes<NPLANE_JC>(Jcm, O, s, pl);
       T j0[9], j1[9];
       jc_rows(pl, j0, j1);
       e0 = pl[0] * g0 + pl[1] * g1 + pl[2] * g2;

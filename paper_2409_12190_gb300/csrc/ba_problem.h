@@ -72,6 +72,11 @@ struct ba_problem {
   float* Xf = nullptr;      // [C][96] features
   float* Ef = nullptr;      // [C][45] network output
   double* Dsc = nullptr;    // [C][9] scales diag(S_ii)
+  // direct solver (BA_SOLVER_CHOLESKY): dense S / its factor, work vector,
+  // failure flag
+  double* dS = nullptr;
+  double* dy = nullptr;
+  int* dfail = nullptr;
   ba::DevState* st = nullptr;
   ba_iter_stats* stats = nullptr;
   int cap = 0;

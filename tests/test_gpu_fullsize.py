@@ -14,9 +14,9 @@
   computes one by one on the sub-problem made of every observation of every
   point those cameras see; then trials through the public API, checked for
   the properties of the LM rule at any size.
-* ``batch512`` (512 sliding-window problems, FP32, 10 trials, one persistent
-  launch): sampled problems against the oracle's FP64 LM on the same
-  problem.
+* ``batch512`` (512 sliding-window problems, FP32, run to convergence in
+  one persistent launch): sampled problems against the oracle's converged
+  FP64 LM on the same problem.
 """
 import numpy as np
 import pytest
@@ -173,14 +173,14 @@ def test_ba4000_bench_trials_follow_the_lm_rule(ba4000):
 # --------------------------------------------------------------------------
 
 def test_batch512_sampled_problems_reach_the_oracle_cost():
-    """512 problems, FP32, 10 trials in one persistent launch.  For sampled
-    problems (the largest, the smallest and six more) the final cost is
-    within the FP32 bar of the oracle's FP64 LM on the same problem: 1e-6
-    relative plus what the oracle still gained over its last three trials
-    (a run that has not converged may lag by a rejected trial)."""
+    """512 problems, FP32, in one persistent launch.  Each problem is run
+    until converged (30 trials: the plain loss converges quadratically and
+    these problems are small); for sampled problems (the largest, the
+    smallest and six more) the final cost is within 1e-6 relative of the
+    oracle's converged FP64 LM on the same problem."""
     scenes = scenegen.batch_scenes(512, seed=4)
     inputs = [(s.cams_init, s.points_init, s.cam_idx, s.pt_idx, orc.pixels_from_scene(s)) for s in scenes]
-    iters = 10
+    iters = 30
     opts = ba.Options(precision="f32", pcg_maxiter=50, pcg_tol=1e-4)
     with ba.Batch(inputs, opts) as bt:
         bt.solve(iters)
@@ -194,6 +194,7 @@ def test_batch512_sampled_problems_reach_the_oracle_cost():
         check_lm_rule(stats[b], opts)
         _, _, ref = orc.lm(*inputs[b], iters, ropts)
         F_ref = min([ref[0]["cost"]] + [t["cost_trial"] for t in ref if t["accepted"]])
-        tail = ref[-3]["cost"] - F_ref
+        # converged: the oracle's last ten trials gained nothing measurable
+        assert ref[-10]["cost"] - F_ref <= 1e-12 * F_ref, b
         assert abs(stats[b][0]["cost"] - ref[0]["cost"]) <= 1e-6 * ref[0]["cost"], b
-        assert abs(costs[b] - F_ref) <= 1e-6 * F_ref + tail, (b, costs[b], F_ref, tail)
+        assert abs(costs[b] - F_ref) <= 1e-6 * F_ref, (b, costs[b], F_ref)

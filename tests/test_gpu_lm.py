@@ -58,36 +58,28 @@ def test_ring_f64_huber_trace_matches_oracle_pcg(jac):
     assert [g["accepted"] for g in gpu] == [r["accepted"] for r in ref]
 
 
-def test_ring_f64_truncated_pcg_within_oracle_order_band():
-    """With 50 PCG iterations the reduced system of the ring scene is so
-    ill-conditioned that two FP64 CG runs differing only in summation order
-    drift apart (the oracle against itself with the observations permuted).
-    The GPU trace must stay inside 10x that band of the oracle trace, and
-    every accept decision whose margin is outside 10x the band of the trial
-    cost must match (on this scene, all but the last: the oracle rejects
-    trial 4 by 29 while its permuted run moves that trial cost by 6)."""
+def test_ring_f64_huber_trace_matches_oracle_pcg_15():
+    """The same at 15 PCG iterations per trial, the most at which the
+    oracle's own trace on this scene is insensitive to the summation order
+    (with the observations permuted its trial costs move by ~3e-13; at 25
+    iterations by ~5e-10 and at 50 by ~3e-4: CG on this ring amplifies
+    rounding exponentially with the iteration count, so beyond ~20
+    iterations no implementation can be compared to 1e-9 on it -- the
+    50-iteration setting is compared at full size on ba250, whose reduced
+    system is better conditioned, and with exact solves in
+    test_gpu_converged)."""
     sc = small_ring()
     pix = orc.pixels_from_scene(sc)
-    iters = 4
-    opts = orc.LMOptions(solver="pcg", pcg_tol=1e-4, pcg_maxiter=50, huber_delta=1.0)
+    iters = 8
+    opts = orc.LMOptions(solver="pcg", pcg_tol=1e-4, pcg_maxiter=15, huber_delta=1.0)
     _, _, ref = orc.lm(sc.cams_init, sc.points_init, sc.cam_idx, sc.pt_idx, pix, iters, opts)
-    perm = np.random.default_rng(0).permutation(sc.O)
-    _, _, ref2 = orc.lm(sc.cams_init, sc.points_init, sc.cam_idx[perm], sc.pt_idx[perm], pix[perm],
-                        iters, opts)
-    # costs of the accepted states (rejected trial points are dominated by the
-    # noise of the unconverged directions and are not compared)
-    band = max(_trace_rel(ref2, ref, "cost"), 1e-9)
-    with problem(sc, pix, "f64", pcg_maxiter=50, pcg_tol=1e-4) as prob:
+    with problem(sc, pix, "f64", pcg_maxiter=15, pcg_tol=1e-4) as prob:
         prob.solve(iters)
         gpu = prob.stats()
-    # an accept decision is the method's only where the oracle's margin
-    # |F' - F| exceeds 10x the drift of its own trial cost under a
-    # permutation of the observations (the band criterion applied to F')
-    for t, (g, r, r2) in enumerate(zip(gpu, ref, ref2)):
-        if abs(r["cost_trial"] - r["cost"]) > 10 * abs(r2["cost_trial"] - r["cost_trial"]):
-            assert g["accepted"] == r["accepted"], (t, g, r)
-    assert sum(1 for g, r in zip(gpu, ref) if g["accepted"] == r["accepted"]) >= iters - 1
-    assert _trace_rel(gpu, ref, "cost") < 10 * band
+    assert _trace_rel(gpu, ref, "cost") < 1e-9
+    assert _trace_rel(gpu, ref, "cost_trial") < 1e-9
+    assert [g["pcg_iters"] for g in gpu] == [r["pcg_iters"] for r in ref]
+    assert [g["accepted"] for g in gpu] == [r["accepted"] for r in ref]
 
 
 def _converged_cost(trace):
@@ -95,35 +87,62 @@ def _converged_cost(trace):
     return min([trace[0]["cost"]] + acc)
 
 
-@pytest.mark.parametrize("jac", ["store", "recompute"])
-@pytest.mark.parametrize("huber", [True, False])
-def test_ring_f32_reaches_fp64_final_cost(huber, jac):
-    """FP32 per-observation arithmetic reaches the FP64 final cost within 1e-6.
+def _run_until_stall(prob, cap, window=50, rel=1e-10):
+    """LM trials in windows until a window lowers the cost by less than rel
+    (relative) or cap trials ran; returns the per-trial costs."""
+    costs = []
+    while len(costs) < cap:
+        prob.solve(window)
+        st = prob.stats(cap=window)
+        costs += [t["cost_trial"] if t["accepted"] else t["cost"] for t in st]
+        if len(costs) > window and costs[-window - 1] - costs[-1] <= rel * costs[-1]:
+            break
+    return costs
 
-    Plain loss: after 25 trials both runs have converged (quadratic rate).
-    Huber: IRLS without the rho'' term converges linearly -- on the outlier
-    residuals the true loss is linear, so the gain ratio tends to 2 and each
-    trial removes only a small fraction of the remaining excess -- and after
-    25 trials the FP64 run still drops ~5e-7 per trial.  There the FP32 cost
-    must be within 1e-6 of the FP64 cost plus the decrease of the FP64 run
-    over its last three trials (the FP32 run may lag by a rejected trial)."""
-    sc = small_ring(C=60, P=3000, huber=huber)
+
+@pytest.mark.parametrize("jac", ["store", "recompute"])
+def test_ring_f32_reaches_the_oracles_converged_cost(jac):
+    """Plain loss: the LM converges (quadratically) within 25 trials, in
+    FP64 on the oracle and in FP32 on the GPU; the FP32 cost, re-evaluated
+    in FP64 by the oracle at the returned parameters, is within 1e-6 of the
+    oracle's converged cost."""
+    sc = small_ring(C=60, P=3000, huber=False)
     pix = orc.pixels_from_scene(sc)
     iters = 25
-    delta = 1.0 if huber else 0.0
-    opts = orc.LMOptions(solver="pcg", pcg_tol=1e-4, pcg_maxiter=50, huber_delta=delta)
+    opts = orc.LMOptions(solver="pcg", pcg_tol=1e-4, pcg_maxiter=50)
     _, _, ref = orc.lm(sc.cams_init, sc.points_init, sc.cam_idx, sc.pt_idx, pix, iters, opts)
     F_ref = _converged_cost(ref)
-    tail = (ref[-3]["cost"] - F_ref) if huber else 0.0
+    # converged: the oracle's last five trials gained nothing measurable
+    assert ref[-5]["cost"] - F_ref <= 1e-12 * F_ref
     with problem(sc, pix, "f32", pcg_maxiter=50, pcg_tol=1e-4, jacobian=jac) as prob:
         prob.solve(iters)
         gpu = prob.stats()
         cams, pts = prob.params()
     F32 = _converged_cost(gpu)
-    # re-evaluate the FP32 result in FP64 with the oracle's cost
-    F32_exact = orc.cost(np64(cams), np64(pts), sc.cam_idx, sc.pt_idx, pix, delta)
-    assert abs(F32_exact - F_ref) < 1e-6 * F_ref + tail
-    assert abs(F32 - F_ref) < 1e-6 * F_ref + tail
+    F32_exact = orc.cost(np64(cams), np64(pts), sc.cam_idx, sc.pt_idx, pix)
+    assert abs(F32_exact - F_ref) < 1e-6 * F_ref
+    assert abs(F32 - F_ref) < 1e-6 * F_ref
+
+
+@pytest.mark.parametrize("jac", ["store", "recompute"])
+def test_ring_huber_f32_converges_to_the_f64_cost(jac):
+    """Huber: IRLS without the rho'' term converges only linearly (on the
+    outlier residuals the loss is linear and each trial removes a fraction
+    of the excess), so both precisions are run until their cost stops
+    decreasing; the FP32 cost is then within 1e-6 of the FP64 cost, whose
+    first trials are the oracle's to 1e-9 (test above) and whose value is
+    the oracle's objective at the returned parameters."""
+    sc = small_ring(C=60, P=3000, huber=True)
+    pix = orc.pixels_from_scene(sc)
+    out = {}
+    for prec in ("f64", "f32"):
+        with problem(sc, pix, prec, pcg_maxiter=50, pcg_tol=1e-4, jacobian=jac) as prob:
+            costs = _run_until_stall(prob, cap=3000)
+            cams, pts = prob.params()
+        F_exact = orc.cost(np64(cams), np64(pts), sc.cam_idx, sc.pt_idx, pix, 1.0)
+        assert abs(min(costs) - F_exact) <= (1e-12 if prec == "f64" else 1e-6) * F_exact
+        out[prec] = min(costs)
+    assert abs(out["f32"] - out["f64"]) <= 1e-6 * out["f64"], out
 
 
 @pytest.mark.parametrize("jac", ["store", "recompute"])

@@ -105,24 +105,25 @@ def test_damped_solve_truncated_pcg_matches_oracle_pcg(maxiter, tol, jac):
     assert rel_err(np64(dp), dp_ref) < 1e-9
 
 
-def test_pcg_rounding_sensitivity_is_the_systems_not_the_kernels():
-    """At 50 iterations the GPU iterate differs from the oracle's by no more
-    than the oracle's own iterate moves when only the summation order of the
-    observations changes."""
+@pytest.mark.parametrize("k", [15, 20])
+def test_truncated_pcg_iterate_matches_oracle_on_the_ring(k):
+    """The PCG iterate after k iterations on the small ring, at 1e-9.  Up to
+    20 iterations the oracle's own iterate moves by less than 1e-11 when
+    only the summation order of the observations changes (7e-13 at 15,
+    7e-12 at 20); beyond that CG on this ill-conditioned ring amplifies
+    rounding exponentially (5e-10 at 25, 3e-8 at 30, 6e-5 at 50), and the
+    comparison is no longer well posed for any implementation."""
     sc = small_ring()
     pix = orc.pixels_from_scene(sc)
     lam = 1e-4
-    opts = orc.LMOptions(solver="pcg", pcg_tol=0.0, pcg_maxiter=50)
+    opts = orc.LMOptions(solver="pcg", pcg_tol=0.0, pcg_maxiter=k)
     blk = orc.assemble(sc.cams_init, sc.points_init, sc.cam_idx, sc.pt_idx, pix, sc.huber_delta)
-    dc_ref, _, _, _ = orc.solve_damped(blk, sc.cam_idx, sc.pt_idx, lam, opts)
-    perm = np.random.default_rng(1).permutation(sc.O)
-    blk2 = orc.assemble(sc.cams_init, sc.points_init, sc.cam_idx[perm], sc.pt_idx[perm], pix[perm],
-                        sc.huber_delta)
-    dc_ref2, _, _, _ = orc.solve_damped(blk2, sc.cam_idx[perm], sc.pt_idx[perm], lam, opts)
-    band = rel_err(dc_ref2, dc_ref)
+    dc_ref, dp_ref, its_ref, _ = orc.solve_damped(blk, sc.cam_idx, sc.pt_idx, lam, opts)
     with problem(sc, pix, "f64") as prob:
-        dc, _, _, _ = prob.damped_solve(lam, 50, 0.0)
-    assert rel_err(np64(dc), dc_ref) < 10 * band
+        dc, dp, its, _ = prob.damped_solve(lam, k, 0.0)
+    assert its == its_ref == k
+    assert rel_err(np64(dc), dc_ref) < 1e-9
+    assert rel_err(np64(dp), dp_ref) < 1e-9
 
 
 @pytest.mark.parametrize("scene", ["banded", "scattered"])
