@@ -1,18 +1,24 @@
 #!/usr/bin/env python
 """Benchmark: LM bundle-adjustment iterations per second on one synthetic
 scene of 4,000 cameras, 1.2M points and ~8.04M observations (the ba4000
-workload: views per point 2+Geom0(1/5.7), 1 px noise), FP32 per-observation
-arithmetic with FP64 reductions, block-Jacobi PCG capped at 50 iterations.
+workload: views per point 2+Geom0(1/5.7), 1 px noise), block-Jacobi PCG
+capped at 50 iterations, and the time to reach (1 + 1e-6) F_ref, F_ref the
+converged FP64 cost.  The headline is the FP64 path (the paper's
+arithmetic); the FP32 variant (FP32 per-observation arithmetic, FP64
+reductions and cost) is reported in the same line.
 
 A step is one LM trial: linearisation (when theta changed), block assembly,
 Schur reduction, PCG on the reduced camera system, back-substitution, trial
 cost and accept/reject -- all through the library's C ABI.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--precision both|f64|f32] [--mode partition|replicas]
 
-Prints one JSON line (rank 0).  Under torchrun each rank solves its own
-replica of the scene (no collective on the data path); value counts the
-trials of all ranks over the slowest rank's time.
+Prints one JSON line (rank 0).  Under torchrun (N > 1) the ranks by default
+solve ONE problem partitioned by points (every camera on every rank, NCCL
+all-reduce at the exchanges of a trial: strong scaling, value = the whole
+problem's trials over the slowest rank's time); --mode replicas gives each
+rank its own replica instead (weak scaling).
 """
 from __future__ import annotations
 
@@ -61,6 +67,9 @@ def parse():
     ap.add_argument("--jacobian", choices=["auto", "recompute", "store"], default="auto")
     ap.add_argument("--precision", choices=["both", "f64", "f32"], default="both",
                     help="both: the FP64 line (the paper's arithmetic) with the FP32 variant inside it")
+    ap.add_argument("--mode", choices=["partition", "replicas"], default="partition",
+                    help="N > 1: one problem partitioned by points over the GPUs (strong scaling), or one "
+                         "replica of the problem per GPU (weak scaling)")
     ap.add_argument("--no-time-to-cost", action="store_true",
                     help="skip F_ref and the time-to-cost runs (profiling only)")
     ap.add_argument("--points", type=int, default=0,
@@ -69,6 +78,7 @@ def parse():
                     help="batch512: 512 sliding-window problems solved by one persistent launch; "
                          "learned: time to 1e-6 relative cost with the learned block-Jacobi correction")
     ap.add_argument("--train-scenes", type=int, default=200, help="learned: training scenes")
+    ap.add_argument("--seeds", type=int, default=3, help="learned: training seeds (initialisation and shuffle)")
     ap.add_argument("--batch-problems", type=int, default=512,
                     help="batch512: problems per rank (profiling only: a smaller batch of the same recipe)")
     ap.add_argument("--no-sequential", action="store_true",
@@ -204,7 +214,7 @@ def algorithmic_bytes(kind, C, P, O, npieces, tsize, mf, huber=False):
     and weights; per-point / per-camera vectors once)."""
     # stored planes (the passes of the Schur product and the linearisation
     # also read or write the 6 planes of Jp) or sqrt(w)
-    ob = (24 if kind in ("pass_b", "pass_a1", "schur_cam", "lin_cam") else 18) * tsize if not mf else \
+    ob = (24 if kind in ("pass_b", "pass_a1", "pass_fa", "schur_cam", "lin_cam") else 18) * tsize if not mf else \
         (tsize if huber else 0)
     sw = tsize if huber else 0
     if kind == "pass_b":   # cm_pt; point record (X, t) per point; camera table; partials
@@ -213,7 +223,10 @@ def algorithmic_bytes(kind, C, P, O, npieces, tsize, mf, huber=False):
         return O * (4 + ob + 4 * tsize) + (P * 4 * tsize if mf else 0) + C * (16 + 12) * tsize
     if kind == "pass_a2":  # order map + one 4-vector per obs; rowptr, V*^-1, t out per point
         return O * (4 + 4 * tsize) + P * (4 + 6 * tsize + 4 * tsize)
-    if kind == "pass_fa":  # point index + chunk camera position (+ sqrt(w)) per obs; X in, V*^-1, t out per point
+    if kind == "pass_fa":
+        if not mf:  # stored: the point-major planes + camera position per obs; rowptr, V*^-1 in, t out per point
+            return O * (ob + 2) + P * (4 + 6 * tsize + 4 * tsize) + C * 9 * tsize
+        # recompute: point index + chunk camera position (+ sqrt(w)) per obs; X in, V*^-1, t out per point
         return O * (4 + 2 + sw) + P * (4 + 4 * tsize + 6 * tsize + 4 * tsize)
     if kind == "lin_cam":  # pixels + point index in; planes / weights out; points once; partials
         return O * (2 * tsize + 4 + ob) + P * 3 * tsize + npieces * 54 * 8
@@ -236,7 +249,7 @@ def algorithmic_bytes(kind, C, P, O, npieces, tsize, mf, huber=False):
 # with the stored planes only (pass A1: e = Jc x, 18 FMA, and z = Jp^T e;
 # pass B: h = Jp t and the sum of Jc^T h, 18 FMA).
 FLOPS_PER_OBS = {"pass_b": 116, "pass_a1": 113, "pass_fa": 116}
-FLOPS_PER_OBS_STORED = {"pass_a1": 45, "pass_a2": 3, "pass_b": 46}
+FLOPS_PER_OBS_STORED = {"pass_a1": 45, "pass_a2": 3, "pass_fa": 48, "pass_b": 46}
 # per point: V*^-1 times the summed 3-vector (9 FMA)
 FLOPS_PER_POINT = {"pass_a2": 18, "pass_fa": 18}
 
@@ -327,24 +340,36 @@ def _scene_inputs(scene, dev):
     return ci, pi, pix
 
 
-def _problem(scene, ci, pi, pix, prec, dev, jacobian="auto", maxiter=PCG_MAXITER, tol=PCG_TOL):
+def _problem(scene, ci, pi, pix, prec, dev, jacobian="auto", maxiter=PCG_MAXITER, tol=PCG_TOL, part=None):
+    """The benchmark's problem in precision prec; with part = (bounds, rank,
+    allreduce) this rank's part of the point-partitioned problem."""
     import torch
     import paper_2409_12190_gb300 as ba
     opts = ba.Options(precision=prec, pcg_maxiter=maxiter, pcg_tol=tol, use_graph=True, jacobian=jacobian)
     dt = torch.float32 if prec == "f32" else torch.float64
-    return ba.Problem(scene.cams_init, scene.points_init, ci, pi, pix.to(dt), opts, device=dev)
+    if part is None:
+        return ba.Problem(scene.cams_init, scene.points_init, ci, pi, pix.to(dt), opts, device=dev)
+    from paper_2409_12190_gb300.partition import PartProblem
+    bounds, rank, allreduce = part
+    lo, hi = int(bounds[rank]), int(bounds[rank + 1])
+    obs = torch.nonzero((pi >= lo) & (pi < hi)).flatten()
+    prob = PartProblem(scene.cams_init, scene.points_init[lo:hi], ci[obs], pi[obs] - lo, pix[obs].to(dt),
+                       allreduce, opts, device=dev)
+    prob.pix_part = pix[obs]
+    return prob
 
 
-def compute_f_ref(scene, ci, pi, pix, dev, want_params=False):
+def compute_f_ref(scene, ci, pi, pix, dev, want_params=False, part=None):
     """F_ref and how it was reached (see F_REF_*); with want_params also the
-    FP64 parameters (cams, points) at which it was evaluated."""
+    FP64 parameters (cams, points) at which it was evaluated (this part's
+    points for a partitioned problem)."""
     import torch
     t0 = time.perf_counter()
-    with _problem(scene, ci, pi, pix, "f32", dev) as p32:
+    with _problem(scene, ci, pi, pix, "f32", dev, part=part) as p32:
         p32.solve(F_REF_F32_TRIALS)
         cams, pts = p32.params()
         F32, _ = p32.scalars()
-    with _problem(scene, ci, pi, pix, "f64", dev, maxiter=F_REF_PCG[0], tol=F_REF_PCG[1]) as p64:
+    with _problem(scene, ci, pi, pix, "f64", dev, maxiter=F_REF_PCG[0], tol=F_REF_PCG[1], part=part) as p64:
         p64.set_params(cams.double(), pts.double())
         p64.set_lambda(1e-6)
         n = 0
@@ -439,14 +464,16 @@ def roofline_of(kernels, per, hbm_peak, hbm_kind, alu_peak, alu_source, src_hash
     return roof
 
 
-def run_precision(args, prec, scene, ci, pi, pix, dev, world, f_ref, peaks_d, barrier, clocks_for_rank):
+def run_precision(args, prec, scene, ci, pi, pix, dev, world, f_ref, peaks_d, barrier, clocks_for_rank, part=None):
     """One precision of the benchmark: timed trials, per-kernel profile and
-    roofline, time to F_ref, and the end-to-end leg through the public API."""
+    roofline, time to F_ref, and the end-to-end leg through the public API.
+    With part, every rank solves its part of one point-partitioned problem
+    (strong scaling: the value counts the whole problem's trials once)."""
     import torch
     import paper_2409_12190_gb300 as ba
-    C, P, O = scene.C, scene.P, scene.O
+    prob = _problem(scene, ci, pi, pix, prec, dev, jacobian=args.jacobian, part=part)
+    C, P, O = prob.C, prob.P, prob.O       # this rank's share of the work
     tsize = 4 if prec == "f32" else 8
-    prob = _problem(scene, ci, pi, pix, prec, dev, jacobian=args.jacobian)
     torch.cuda.synchronize()
     lay = prob.layout()
     mf = not lay["stored"]
@@ -472,7 +499,8 @@ def run_precision(args, prec, scene, ci, pi, pix, dev, world, f_ref, peaks_d, ba
     clk = clocks.stop() if clocks else None
     ms = rank_max(e0.elapsed_time(e1), dev, world)
     trials = prob.stats(cap=args.steps)
-    value = world * args.steps / (ms / 1000.0)
+    copies = 1 if part is not None else world   # replicas: every rank solves a whole problem
+    value = copies * args.steps / (ms / 1000.0)
 
     # per-kernel CUDA-event timing of real trials (direct launches)
     per, prof_ms = prob.profile_trials(args.profile_trials)
@@ -496,7 +524,7 @@ def run_precision(args, prec, scene, ci, pi, pix, dev, world, f_ref, peaks_d, ba
     prob.set_state(state0)
     hc = torch.empty((C, 9), dtype=dt).pin_memory()
     hp = torch.empty((P, 3), dtype=dt).pin_memory()
-    hx = pix.to(dt).cpu().pin_memory()
+    hx = getattr(prob, "pix_part", pix).to(dt).cpu().pin_memory()
     prob.get_params_into(hc, hp)
     torch.cuda.synchronize()
     barrier()
@@ -512,7 +540,7 @@ def run_precision(args, prec, scene, ci, pi, pix, dev, world, f_ref, peaks_d, ba
     e2e_trials = prob.stats(cap=e2e_steps)
     same = ([t["pcg_iters"] for t in e2e_trials] == [t["pcg_iters"] for t in trials[:e2e_steps]]
             and [t["accepted"] for t in e2e_trials] == [t["accepted"] for t in trials[:e2e_steps]])
-    e2e = {"value": world * e2e_steps / e2e_s, "unit": UNIT,
+    e2e = {"value": copies * e2e_steps / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": (9 * C + 3 * P + 2 * O) * tsize,
            "d2h_bytes_per_step": (9 * C + 3 * P) * tsize + 8, "steps": e2e_steps,
            "same_trials_as_timed": same}
@@ -527,26 +555,34 @@ def run_precision(args, prec, scene, ci, pi, pix, dev, world, f_ref, peaks_d, ba
            "pcg_iters_mean": statistics.mean(pcg) if pcg else None, "pcg_iters_total": sum(pcg),
            "accepted": sum(t["accepted"] for t in trials),
            "l2": "inputs larger than L2 (each PCG pass streams >0.1 GB of per-observation data; L2 129 MB)",
-           "parallelism": "replicas" if world > 1 else "single GPU", "graph": "one CUDA graph per LM trial",
+           "parallelism": (f"points partitioned over {world} GPUs (cameras replicated, NCCL all-reduce at the "
+                           f"six exchanges of a trial)" if part is not None else
+                           ("replicas" if world > 1 else "single GPU")),
+           "graph": "direct launches (exchanges)" if part is not None else "one CUDA graph per LM trial",
            "jacobian": "recomputed in every pass" if mf else "stored planes",
-           "schur_product": "fused pass A + pass B" if (mf and lay["fused_a"]) else "passes A1, A2, B"}
+           "schur_product": "fused point-major pass A + pass B" if lay["fused_a"] else "passes A1, A2, B"}
     return {"value": value, "ms_per_step": ms / args.steps, "dtype": prec, "config": cfg, "gpu_launches": launches,
             "clocks": clk, "roofline": roof, "kernels": kernels, "e2e": e2e, "time_to_cost": ttc}
 
 
 def _oracle_sample_job(job):
-    """One bounded oracle run (a spawned worker): LM trials/s on a sample of
-    the scene, scaled to the full scene by its observation count."""
-    scene, n_obs, seed, trials = job
+    """One bounded oracle run (a spawned worker): LM trials/s of the oracle on
+    a sample of the scene, scaled to the full scene by its observation count.
+    The sample is drawn by the parent, so only it crosses the process
+    boundary."""
+    sub, O_full, trials = job
     import oracle as orc
-    n_pts = max(50, int(round(n_obs * scene.P / scene.O)))
-    sub = scenegen.subsample_points(scene, n_pts, seed=seed)
     pix = orc.pixels_from_scene(sub)
     opts = orc.LMOptions(solver="pcg", pcg_tol=0.0, pcg_maxiter=PCG_MAXITER, huber_delta=sub.huber_delta)
     t0 = time.perf_counter()
     orc.lm(sub.cams_init, sub.points_init, sub.cam_idx, sub.pt_idx, pix, trials, opts)
     dt = time.perf_counter() - t0
-    return {"rate_full": trials / dt * sub.O / scene.O, "seconds": dt, "O": sub.O, "P": sub.P}
+    return {"rate_full": trials / dt * sub.O / O_full, "seconds": dt, "O": sub.O, "P": sub.P}
+
+
+def _sample(scene, n_obs, seed):
+    n_pts = max(50, int(round(n_obs * scene.P / scene.O)))
+    return scenegen.subsample_points(scene, n_pts, seed=seed)
 
 
 def cpu_baseline(scene, n_obs_single=500_000, n_obs_each=250_000):
@@ -556,11 +592,13 @@ def cpu_baseline(scene, n_obs_single=500_000, n_obs_each=250_000):
     import multiprocessing as mp
     import oracle as orc
     ncores = os.cpu_count() or 1
-    single = _oracle_sample_job((scene, n_obs_single, 123, 1))
+    single = _oracle_sample_job((_sample(scene, n_obs_single, 123), scene.O, 1))
+    jobs = [(_sample(scene, n_obs_each, 1000 + i), scene.O, 1) for i in range(ncores)]
     with mp.get_context("spawn").Pool(ncores) as pool:
         t0 = time.perf_counter()
-        many = pool.map(_oracle_sample_job, [(scene, n_obs_each, 1000 + i, 1) for i in range(ncores)])
+        many = pool.map(_oracle_sample_job, jobs)
         wall = time.perf_counter() - t0
+    del jobs
     total_rate = sum(r["O"] for r in many) / scene.O / wall   # full-scene trials/s of all processes together
     b250 = scenegen.config_scene("ba250")
     pix = orc.pixels_from_scene(b250)
@@ -571,8 +609,8 @@ def cpu_baseline(scene, n_obs_single=500_000, n_obs_each=250_000):
     return {"value": total_rate, "unit": UNIT, "cores": ncores, "kind": "oracle",
             "sample": (f"{ncores} single-threaded oracle processes (one per host core, spawned), each one LM "
                        f"trial (PCG fixed at {PCG_MAXITER} iterations) on its own sample of ~{n_obs_each} of "
-                       f"{scene.O} observations with all {scene.C} cameras, run together in {wall:.1f} s; "
-                       f"throughput scaled by O_full/O_sample"),
+                       f"{scene.O} observations with all {scene.C} cameras, run together in {wall:.1f} s "
+                       f"(spawn and imports included); throughput scaled by O_full/O_sample"),
             "nproc": ncores,
             "single_thread": {"value": single["rate_full"], "cores": 1,
                               "sample": f"1 trial on {single['O']} observations, {single['seconds']:.1f} s, "
@@ -603,15 +641,20 @@ def run_ours(args):
     else:
         scene = scenegen.config_scene(WORKLOAD)
     ci, pi, pix = _scene_inputs(scene, dev)
+    part = None
+    if world > 1 and args.mode == "partition":
+        from paper_2409_12190_gb300.partition import dist_allreduce, partition_points
+        bounds, _ = partition_points(scene.pt_idx, scene.P, world)
+        part = (bounds, rank, dist_allreduce())
     hbm, hbm_kind = peaks()
     peaks_d = {"hbm_gbs": hbm, "hbm_kind": hbm_kind, "fp64_fma_tflops": ba.measure_fma_peak("f64"),
                "fp32_fma_tflops": ba.measure_fma_peak("f32")}
-    f_ref, f_ref_info = (None, None) if args.no_time_to_cost else compute_f_ref(scene, ci, pi, pix, dev)
+    f_ref, f_ref_info = (None, None) if args.no_time_to_cost else compute_f_ref(scene, ci, pi, pix, dev, part=part)
     precs = ["f64", "f32"] if args.precision == "both" else [args.precision]
     res = {}
     for p in precs:
         res[p] = run_precision(args, p, scene, ci, pi, pix, dev, world, f_ref, peaks_d, barrier,
-                               lambda: ClockSampler(local) if rank == 0 else None)
+                               lambda: ClockSampler(local) if rank == 0 else None, part=part)
     if rank != 0:
         return
     cpu = None
@@ -620,7 +663,8 @@ def run_ours(args):
     head = res[precs[0]]
     line = {"metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": head["dtype"], "data": "synthetic",
+            "scaling": "strong" if part is not None else "weak", "vs_baseline": None, "dtype": head["dtype"],
+            "data": "synthetic",
             "config": dict(head["config"], f_ref=f_ref_info),
             "gpu_launches": head["gpu_launches"], "clocks": head["clocks"], "roofline": head["roofline"],
             "kernels": head["kernels"], "cpu_baseline": cpu, "e2e": head["e2e"],
@@ -878,17 +922,19 @@ def run_learned(args):
             samples.append(learned.collect(pr, seed=i))
     t_collect = time.perf_counter() - t0
     n_samples = sum(s[0].shape[0] for s in samples)
-    t0 = time.perf_counter()
-    params, hist = learned.train(samples, epochs=100, lr=2e-3)
-    torch.cuda.synchronize()
-    t_train = time.perf_counter() - t0
+    trained = []
+    for seed in range(args.seeds):
+        t0 = time.perf_counter()
+        params, hist = learned.train(samples, epochs=100, lr=2e-3, seed=seed)
+        torch.cuda.synchronize()
+        trained.append((seed, params, hist, time.perf_counter() - t0))
     del samples
 
-    # evaluation on the bench scene: block-Jacobi, then the learned blocks
+    # evaluation on the bench scene: block-Jacobi, then each trained network
     scene = scenegen.config_scene(WORKLOAD)
     stream = torch.cuda.current_stream()
-    runs = {}
-    for name, par in (("block_jacobi", None), ("learned", params)):
+
+    def evaluate(par):
         with make(scene, tol=LEARN_PCG_TOL, maxiter=LEARN_PCG_MAXITER) as pr:
             pr.set_preconditioner(par)
             pr.solve(1)  # warm-up: captures the trial graph
@@ -896,23 +942,35 @@ def run_learned(args):
                           torch.tensor(scene.points_init, dtype=torch.float32, device=dev))
             pr.set_lambda(1e-4)
             pr.stats()
-            runs[name] = _timed_trials(pr, LEARN_TRIALS, stream)
-    # the target is the plain method's own best cost: the learned run must
+            return _timed_trials(pr, LEARN_TRIALS, stream)
+
+    runs = {"block_jacobi": evaluate(None)}
+    for seed, params, _, _ in trained:
+        runs[f"learned_seed{seed}"] = evaluate(params)
+    # the target is the plain method's own best cost: a learned run must
     # reach what block-Jacobi reaches, to 1e-6 relative
     f_ref = min(runs["block_jacobi"][1])
     out = time_to_cost(runs, f_ref)
-    value = out["learned"]["time_to_cost_s"]
+    names = [f"learned_seed{sd}" for sd, _, _, _ in trained]
+    times = [out[n]["time_to_cost_s"] for n in names]
+    reached = [t for t in times if t is not None]
+    value = statistics.mean(reached) if reached and len(reached) == len(times) else None
     line = {"metric": METRIC, "value": value, "unit": "s to 1e-6 relative cost", "n_gpus": 1,
             "steps": LEARN_TRIALS, "warmup": 1, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": scene.name, "cameras": scene.C, "points": scene.P, "observations": scene.O,
                        "pcg": f"tol {LEARN_PCG_TOL}, maxiter {LEARN_PCG_MAXITER}",
-                       "f_ref": f_ref, "f_ref_rule": "block-Jacobi's lowest cost; the learned run has no time if it never reaches it",
+                       "f_ref": f_ref,
+                       "f_ref_rule": "block-Jacobi's lowest cost; a learned run has no time if it never reaches it",
                        "training": {"scenes": args.train_scenes, "cameras": "500-2000", "points_per_camera": 30,
-                                    "samples": n_samples, "epochs": 100, "collect_s": t_collect, "train_s": t_train,
-                                    "loss_first_last": [hist[0], hist[-1]]}},
-            "block_jacobi": out["block_jacobi"], "learned": out["learned"],
-            "speedup_time_to_cost": speedup(out, "block_jacobi", "learned")}
+                                    "samples": n_samples, "epochs": 100, "collect_s": t_collect,
+                                    "seeds": [{"seed": sd, "train_s": ts, "loss_first_last": [h[0], h[-1]]}
+                                              for sd, _, h, ts in trained]}},
+            "block_jacobi": out["block_jacobi"],
+            "learned": {n: out[n] for n in names},
+            "time_to_cost_by_seed": dict(zip(names, times)),
+            "spread_s": (max(reached) - min(reached)) if reached else None,
+            "speedup_by_seed": {n: speedup(out, "block_jacobi", n) for n in names}}
     print(json.dumps(line), flush=True)
 
 

@@ -219,7 +219,12 @@ ba_status ba_set_fixed(ba_problem* h, const uint8_t* mask, void* stream);
  * NULL = zero); outputs dL_dpixels_out [O][2] (required),
  * dL_dcams0_out [C][9], dL_dpoints0_out [P][3] (dev, may be NULL); iters /
  * rel_res (host, may be NULL: then no synchronisation).  The next LM trial
- * re-linearises. */
+ * re-linearises.  For a BA_PREC_F32 problem the adjoint system is solved in
+ * FP64 (its rounding amplification, condition x cancellation of the
+ * implicit Schur product, is ~1e6): the first call builds an FP64 copy of
+ * the problem (same observations, the FP32 parameters and pixels promoted;
+ * it allocates and synchronises), later calls refresh its parameters,
+ * pixels and frozen mask; inputs and outputs stay FP32. */
 ba_status ba_backward(ba_problem* h, double lambda, int maxiter, double tol,
                       const void* dL_dcams, const void* dL_dpoints,
                       void* dL_dpixels_out, void* dL_dcams0_out,
@@ -229,6 +234,38 @@ ba_status ba_backward(ba_problem* h, double lambda, int maxiter, double tol,
 /* Thread-local message of the last failing call ("" if none).  Error
  * reporting: no counterpart in the paper. */
 const char* ba_last_error(void);
+
+/* ---- point-partitioned problems (several GPUs) -------------------------
+ *
+ * One problem split by points: each part holds a subset of the points with
+ * ALL of their observations and every camera (cameras replicated, the same
+ * values in every part).  The LM iteration of Alg. 1 then needs sums over
+ * all parts at six places of a trial: U and gc of the linearisation, the
+ * Schur pass's per-camera sums (b and the block-Jacobi blocks), the pass-B
+ * sum of every PCG iteration (9C values), and the cost, model and gp . dp
+ * scalars of the trial and of a stale cost; everything else (the PCG
+ * vectors and dot products, the decision, lambda) is computed identically
+ * in every part from those sums.  Not in the paper (it runs on one GPU).
+ *
+ * fn(n, stream, ctx) must replace the first n doubles of xbuf (the caller's
+ * device buffer, which the library fills first) by their sum over all parts,
+ * ordered on stream (a cudaStream_t as void*: enqueue, e.g. an NCCL
+ * all-reduce, or synchronise), and return 0 (nonzero: the trial fails with
+ * BA_ERR_CUDA).  Every part must call the same entry points in the same
+ * order.  xbuf must hold cap >= BA_EXCHANGE_CAP(C) doubles. */
+typedef int (*ba_exchange_fn)(size_t n, void* stream, void* ctx);
+#define BA_EXCHANGE_CAP(C) (64 * (size_t)(C) + 8)
+
+/* Make h one part of a point-partitioned problem (fn, ctx, xbuf, cap as
+ * above; fn NULL returns to a problem of its own).  The LM iteration is the
+ * one of Alg. 1 (Sec. III-B); the partitioning has no counterpart in the
+ * paper.  From then on ba_lm_step
+ * and ba_solve run with direct launches (no graph) and call fn at each
+ * exchange; the cost is re-evaluated (summed) at the next trial.  The
+ * step-level entry points, the learned preconditioner, the direct solver and
+ * ba_backward act on this part alone and are not for partitioned use.
+ * Synchronises. */
+ba_status ba_set_exchange(ba_problem* h, ba_exchange_fn fn, void* ctx, double* xbuf, size_t cap);
 
 /* ---- step-level entry points (same arithmetic as ba_lm_step) ---------- */
 

@@ -15,7 +15,11 @@ correction of that inverse.  None of it is in the paper; the readings are:
   scaled point-elimination term R^ = D^{-1/2} (U*_i - S_ii) D^{-1/2} (how
   much of camera i's information its points carry, the coupling to other
   cameras through them); ln D_a minus its mean over a, / 10; log10(lambda) / 8;
-  log10(1 + observations of camera i) / 4; the constant 1; zero padding.
+  log10(1 + observations of camera i) / 4; the constant 1; the coupling of
+  camera i to the other cameras, log10(1 + kappa_i) / 4 with kappa_i^2 an
+  estimate of sum_{j != i} |S^_ij|_F^2 (the off-diagonal norm summary: for
+  Rademacher probes z, E |(S^ z)_i - S^_ii z_i|^2 is exactly that sum; two
+  probes, drawn by SplitMix64 from a counter, ``coupling``); zero padding.
 * Network: h1 = relu(W1 x + b1), h2 = relu(W2 h1 + b2), e = W3 h2 + b3 with
   widths 96 -> 64 -> 64 -> 45.  Flat parameter layout W1 [64][96], b1 [64],
   W2 [64][64], b2 [64], W3 [45][64], b3 [45] (NPARAM = 13293).
@@ -40,9 +44,12 @@ import numpy as np
 FIN, H, FOUT = 96, 64, 45
 NPARAM = H * FIN + H + H * H + H + FOUT * H + FOUT
 
-__all__ = ["FIN", "H", "FOUT", "NPARAM", "bf16_round", "unpack", "lower_index", "pack_lower",
-           "unpack_lower", "features", "mlp_forward", "g_from_e", "precond_blocks",
-           "probe_loss", "probe_loss_grad", "solve_damped_learned"]
+__all__ = ["FIN", "H", "FOUT", "NPARAM", "COUPLING_PROBES", "bf16_round", "unpack", "lower_index",
+           "pack_lower", "unpack_lower", "splitmix64", "rademacher", "coupling", "features", "mlp_forward",
+           "g_from_e", "precond_blocks", "probe_loss", "probe_loss_grad", "solve_damped_learned"]
+
+COUPLING_PROBES = 2
+_M64 = (1 << 64) - 1
 
 
 def bf16_round(x):
@@ -88,13 +95,56 @@ def unpack_lower(v):
     return L
 
 
-def features(Sii, Us, lam, nobs):
+def splitmix64(x):
+    """The SplitMix64 output function of counter x (Steele, Lea and Flood,
+    "Fast splittable pseudorandom number generators", OOPSLA 2014): add the
+    golden-ratio increment, then two xor-shift-multiply rounds and a final
+    xor-shift, all modulo 2^64."""
+    z = (int(x) + 0x9E3779B97F4A7C15) & _M64
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _M64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _M64
+    return z ^ (z >> 31)
+
+
+def rademacher(k, C):
+    """Coupling probe k: [C, 9] entries +-1, entry (c, a) the sign bit of
+    splitmix64(k << 40 | c << 4 | a) (1 -> -1)."""
+    z = np.empty((C, 9))
+    for c in range(C):
+        for a in range(9):
+            z[c, a] = -1.0 if splitmix64((k << 40) | (c << 4) | a) >> 63 else 1.0
+    return z
+
+
+def coupling(S, Sii, K=COUPLING_PROBES):
+    """kappa_i: sqrt of the mean over K probes of |(S^ z)_i - S^_ii z_i|^2
+    per camera, S^ = D^{-1/2} S D^{-1/2}, D = diag(S_ii): an estimate of the
+    Frobenius norm of camera i's block row of S^ without its diagonal block
+    (E of its square is exactly sum_{j != i} |S^_ij|_F^2).  S: the explicit
+    reduced system [9C, 9C]; Sii: [C, 9, 9]; a camera with a non-positive
+    diagonal gets 0."""
+    Sii = np.asarray(Sii, dtype=np.float64)
+    C = Sii.shape[0]
+    d = np.einsum("cii->ci", Sii).reshape(-1)
+    s = np.where(d > 0, 1.0 / np.sqrt(np.where(d > 0, d, 1.0)), 0.0)
+    Sh = np.asarray(S, dtype=np.float64) * s[:, None] * s[None, :]
+    blocks = np.stack([Sh[9 * c:9 * c + 9, 9 * c:9 * c + 9] for c in range(C)])
+    acc = np.zeros(C)
+    for k in range(K):
+        z = rademacher(k, C)
+        off = (Sh @ z.reshape(-1)).reshape(C, 9) - np.einsum("cab,cb->ca", blocks, z)
+        acc += np.sum(off * off, axis=1)
+    return np.sqrt(acc / K)
+
+
+def features(Sii, Us, lam, nobs, kappa=None):
     """Features x [C, FIN], scaled inverse factors A = chol(S^_ii)^{-1}
     [C, 45] (packed lower) and the scales D [C, 9].
 
     Sii: [C, 9, 9] diagonal blocks of S; Us: [C, 9, 9] damped U*;
-    nobs: [C] observations per camera.  A camera whose S_ii is not positive
-    definite gets x = 0, A = 0 (it keeps the block-Jacobi fallback)."""
+    nobs: [C] observations per camera; kappa: [C] coupling (``coupling``;
+    None: 0).  A camera whose S_ii is not positive definite gets x = 0,
+    A = 0 (it keeps the block-Jacobi fallback)."""
     Sii = np.asarray(Sii, dtype=np.float64)
     C = Sii.shape[0]
     X = np.zeros((C, FIN))
@@ -122,6 +172,7 @@ def features(Sii, Us, lam, nobs):
         X[i, 90] = np.log10(lam) / 8.0
         X[i, 91] = np.log10(1.0 + nobs[i]) / 4.0
         X[i, 92] = 1.0
+        X[i, 93] = 0.0 if kappa is None else np.log10(1.0 + kappa[i]) / 4.0
         A[i] = pack_lower(np.linalg.inv(Lh))
         D[i] = d
     return X, A, D
@@ -228,7 +279,8 @@ def solve_damped_learned(blk, cam_idx, pt_idx, lam, opts, params, bf16=True):
         cam_idx, np.einsum("oij,oj->oi", blk["W"], np.einsum("pij,pj->pi", Vinv, blk["gp"])[pt_idx]), C)
     Sii = Us - bo.segment_sum(cam_idx, blk["W"] @ Vinv[pt_idx] @ np.transpose(blk["W"], (0, 2, 1)), C)
     nobs = np.bincount(cam_idx, minlength=C)
-    X, _, _ = features(Sii, Us, lam, nobs)
+    S, _, _, _ = bo.schur_explicit(blk, cam_idx, pt_idx, lam, opts.diag_min, opts.diag_max)
+    X, _, _ = features(Sii, Us, lam, nobs, coupling(S, Sii))
     e, _ = mlp_forward(params, X, bf16)
     M = precond_blocks(e, Sii)
     dc, its, rel = bo.pcg(lambda x: bo.schur_matvec(x, Us, Vinv, blk["W"], cam_idx, pt_idx),

@@ -66,6 +66,9 @@ _I = ct.c_int
 _D = ct.c_double
 _S = ct.c_int  # ba_status
 
+# ba_exchange_fn: int (*)(size_t n, void* stream, void* ctx)
+EXCHANGE_FN = ct.CFUNCTYPE(ct.c_int, ct.c_size_t, ct.c_void_p, ct.c_void_p)
+
 # name -> (restype, argtypes)
 SIGNATURES = {
     "ba_options_default": (_S, [ct.POINTER(ba_options)]),
@@ -94,6 +97,7 @@ SIGNATURES = {
     "ba_profile_trials": (_S, [_VP, _I, ct.POINTER(ba_kernel_times)]),
     "ba_measure_fma_peak": (_S, [_I, ct.POINTER(_D), _VP]),
     "ba_get_layout": (_S, [_VP, _VP, _I]),
+    "ba_set_exchange": (_S, [_VP, EXCHANGE_FN, _VP, _VP, ct.c_size_t]),
     "ba_set_fixed": (_S, [_VP, _VP, _VP]),
     "ba_set_lambda": (_S, [_VP, _D]),
     "ba_backward": (_S, [_VP, _D, _I, _D, _VP, _VP, _VP, _VP, _VP, ct.POINTER(_I), ct.POINTER(_D), _VP]),

@@ -110,6 +110,22 @@ struct Prof {
   }
 };
 
+// One exchange of a point-partitioned problem: buf[0 .. n) <- its sum over
+// every part (the caller's all-reduce on the problem's stream).  The first
+// failure is kept in h->xerr and reported after the trial.
+void xchg(ba_problem* h, double* buf, size_t n) {
+  if (h->xerr) return;
+  if (n > h->xcap || cudaMemcpyAsync(h->xbuf, buf, n * 8, cudaMemcpyDeviceToDevice, h->s) != cudaSuccess) {
+    h->xerr = 1;
+    return;
+  }
+  if (h->xch(n, (void*)h->s, h->xctx) != 0) {
+    h->xerr = 2;
+    return;
+  }
+  if (cudaMemcpyAsync(buf, h->xbuf, n * 8, cudaMemcpyDeviceToDevice, h->s) != cudaSuccess) h->xerr = 1;
+}
+
 template <typename T, bool MF>
 void enqueue_lin(ba_problem* h, int gate) {
   cudaStream_t s = h->s;
@@ -130,7 +146,21 @@ void enqueue_lin(ba_problem* h, int gate) {
   }
   {
     Prof pr(h, BA_K_OTHER, -2);
-    k_cam_combine_lin<<<nblk(h->C, 128), 128, 0, s>>>(h->C, h->cam_piece_ptr, h->part, h->st, gate, h->U, h->gc);
+    k_cam_combine_lin<<<nblk(h->C, 128), 128, 0, s>>>(h->C, h->cam_piece_ptr, h->part, h->st, gate,
+                                                      h->xch ? h->U_loc : h->U, h->xch ? h->gc_loc : h->gc);
+  }
+  if (h->xch) {
+    // U and gc over every part (this part's, kept, summed again each trial:
+    // a skipped linearisation leaves the same sums)
+    cudaMemcpyAsync(h->U, h->U_loc, 45ull * h->C * 8, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(h->gc, h->gc_loc, 9ull * h->C * 8, cudaMemcpyDeviceToDevice, s);
+    xchg(h, h->U, 45ull * h->C);
+    xchg(h, h->gc, 9ull * h->C);
+  }
+  if (!MF && h->Jpm) {
+    Prof pr(h, BA_K_OTHER, -2);
+    k_planes_pm<T><<<nblk(h->O, 256), 256, 0, s>>>(h->O, h->st, gate, h->pm2cm, (const T*)h->Jcm, (T*)h->Jpm);
+    count_launch();
   }
   {
     Prof pr(h, BA_K_LIN_PT, -2);
@@ -169,6 +199,22 @@ void enqueue_schur_product(ba_problem* h, const T* xc, int k, int check_done) {
     count_launch(2);
     return;
   }
+  if (!MF && h->Jpm) {
+    {
+      Prof pr(h, BA_K_PASS_FA, k);
+      k_pass_fs<T><<<h->nchunks, CHUNK_THREADS, fs_smem<T>(h->fa_nc), s>>>(
+          h->rowptr_pt, h->pm_lc, h->chunk_cams, (const T*)h->Jpm, h->O, xc, (const T*)h->Vinv, h->st,
+          check_done, (T*)h->ptab, h->chunk_hdr, h->fa_nc);
+    }
+    {
+      Prof pr(h, BA_K_PASS_B, k);
+      k_pass_b<T, MF><<<h->npieces, PIECE_THREADS, 0, s>>>(
+          h->piece_cam, h->piece_beg, h->piece_end, h->cm_pt, (const T*)h->Jcm, (const T*)h->cm_sw,
+          (const T*)h->ptab, (const T*)h->camtab, h->st, check_done, h->O, h->part);
+    }
+    count_launch(2);
+    return;
+  }
   {
     Prof pr(h, BA_K_PASS_A, k);
     k_pass_a1<T, MF><<<h->npieces, PIECE_THREADS, 0, s>>>(
@@ -199,7 +245,15 @@ void enqueue_pcg_iter(ba_problem* h, const double* lam_ptr, int k, double tol) {
   cudaStream_t s = h->s;
   const double dmin = h->opt.diag_min, dmax = h->opt.diag_max;
   enqueue_schur_product<T, MF>(h, (const T*)h->pT, k, 1);
-  {
+  if (h->xch) {
+    // the pass-B sums of every part (9C values), one row per camera
+    k_cam_sum_parts<<<nblk(9LL * h->C, 256), 256, 0, s>>>(h->C, h->cam_piece_ptr, h->part, 9, 9, h->camsum);
+    count_launch();
+    xchg(h, h->camsum, 9ull * h->C);
+    Prof pr(h, BA_K_OTHER, k);
+    k_pcg_q<T, MF, 9><<<h->ncb, VT, 0, s>>>(h->C, h->ident_ptr, h->camsum, h->U, (const T*)h->camtab, lam_ptr,
+                                           dmin, dmax, h->p, h->q, h->dot_pq, h->fixed, h->st, 1);
+  } else {
     Prof pr(h, BA_K_OTHER, k);
     k_pcg_q<T, MF><<<h->ncb, VT, 0, s>>>(h->C, h->cam_piece_ptr, h->part, h->U, (const T*)h->camtab, lam_ptr,
                                         dmin, dmax, h->p, h->q, h->dot_pq, h->fixed, h->st, 1);
@@ -217,6 +271,23 @@ void enqueue_pcg_iter(ba_problem* h, const double* lam_ptr, int k, double tol) {
                                                          h->st);
   }
   count_launch(2);
+}
+
+// The learned correction's coupling feature: COUPLING_PROBES implicit
+// Schur products with the SplitMix64 probes, summed per camera into h->kap
+// (needs h->Sii; uses the PCG's p, pT and q, which the PCG start rewrites).
+template <typename T, bool MF>
+void enqueue_coupling(ba_problem* h, const double* lam_ptr) {
+  cudaStream_t s = h->s;
+  const double dmin = h->opt.diag_min, dmax = h->opt.diag_max;
+  for (int k = 0; k < COUPLING_PROBES; ++k) {
+    k_coup_probe_in<T, MF><<<nblk(h->C, 128), 128, 0, s>>>(h->C, k, h->Sii, (const T*)h->camtab, h->p, (T*)h->pT);
+    enqueue_schur_product<T, MF>(h, (const T*)h->pT, -1, 0);
+    k_pcg_q<T, MF><<<h->ncb, VT, 0, s>>>(h->C, h->cam_piece_ptr, h->part, h->U, (const T*)h->camtab, lam_ptr,
+                                        dmin, dmax, h->p, h->q, nullptr, h->fixed, h->st, 0);
+    k_coup_acc<<<nblk(h->C, 128), 128, 0, s>>>(h->C, k, h->Sii, h->q, h->kap);
+    count_launch(3);
+  }
 }
 
 // The direct solve of the reduced system (BA_SOLVER_CHOLESKY): explicit S,
@@ -273,10 +344,20 @@ void enqueue_solve(ba_problem* h, const double* lam_ptr, int maxiter, double tol
         h->piece_cam, h->piece_beg, h->piece_end, h->cm_pt, (const T*)h->Jcm, (const T*)h->camtab,
         (const T*)h->pts, (const T*)h->cm_sw, h->st, h->P, (const T*)h->Vinv, (const T*)h->y0, h->O, h->part);
   }
+  const int32_t* sptr = h->cam_piece_ptr;
+  const double* spart = h->part;
+  if (h->xch) {
+    // the per-camera Schur sums over every part, one row per camera
+    k_cam_sum_parts<<<nblk(54LL * h->C, 256), 256, 0, s>>>(h->C, h->cam_piece_ptr, h->part, 54, PART, h->camsum);
+    count_launch();
+    xchg(h, h->camsum, (size_t)PART * h->C);
+    sptr = h->ident_ptr;
+    spart = h->camsum;
+  }
   {
     Prof pr(h, BA_K_OTHER);
     k_cam_combine_schur<T, MF><<<h->ncb, CAM_THREADS, 0, s>>>(
-        h->C, h->cam_piece_ptr, h->part, h->U, h->gc, (const T*)h->camtab, lam_ptr, dmin, dmax, h->Minv, h->x,
+        h->C, sptr, spart, h->U, h->gc, (const T*)h->camtab, lam_ptr, dmin, dmax, h->Minv, h->x,
         h->r, h->z, h->p, (T*)h->pT, h->dot_rz + h->ncb, h->dot_bb, h->fixed, h->st, learned ? h->Sii : nullptr);
   }
   count_launch(3);
@@ -284,8 +365,9 @@ void enqueue_solve(ba_problem* h, const double* lam_ptr, int maxiter, double tol
     // the learned correction of the block-Jacobi blocks: features, network
     // (tensor cores), SPD blocks and the PCG start with them
     Prof pr(h, BA_K_OTHER);
+    enqueue_coupling<T, MF>(h, lam_ptr);
     k_learn_features<<<h->ncb, CAM_THREADS, 0, s>>>(h->C, h->Sii, h->U, lam_ptr, dmin, dmax, h->rowptr_cam, h->Xf,
-                                                    nullptr, nullptr);
+                                                    nullptr, nullptr, h->kap);
     k_mlp_forward<<<nblk(h->C, MLP_ROWS), MLP_THREADS, MLP_SMEM_FWD, s>>>(h->C, h->mlp, h->Xf, h->Ef);
     k_learn_start<T, MF><<<h->ncb, CAM_THREADS, 0, s>>>(h->C, h->Sii, h->Ef, (const T*)h->camtab, h->Minv, h->r,
                                                          h->z, h->p, (T*)h->pT, h->dot_rz + h->ncb, h->fixed,
@@ -335,6 +417,14 @@ void enqueue_cost(ba_problem* h, bool gated = false) {
       h->piece_cam, h->piece_beg, h->piece_end, h->cm_pt, (const T*)h->cm_px, (const T*)h->cams,
       (const T*)h->pts, h->st, gated ? 2 : 0, delta, h->C, h->P, h->O, nullptr, nullptr, nullptr, nullptr, nullptr,
       h->part);
+  if (h->xch) {
+    // the cost over every part (0 from each part when F is not stale)
+    k_part_cost_sum<<<1, 256, 0, h->s>>>(h->npieces, h->part, h->st, gated ? 1 : 0, h->xscal + 4);
+    xchg(h, h->xscal + 4, 1);
+    k_cost_set<<<1, 1, 0, h->s>>>(h->st, gated ? 1 : 0, h->xscal + 4);
+    count_launch(3);
+    return;
+  }
   k_cost_finalize<<<1, 256, 0, h->s>>>(h->npieces, h->part, h->st, gated ? 1 : 0);
   count_launch(2);
 }
@@ -359,8 +449,14 @@ void enqueue_trial(ba_problem* h) {
     Prof pr(h, BA_K_OTHER);
     // one block sums the per-piece and per-chunk partials (a few thousand
     // strided doubles): 1024 threads keep more of those loads in flight
+    if (h->xch) {
+      k_part_trial_sums<<<1, 1024, 0, h->s>>>(h->npieces, h->part, h->nchunks, h->dot_gp, h->xscal);
+      count_launch();
+      xchg(h, h->xscal, 3);
+    }
     k_lm_control<<<1, 1024, 0, h->s>>>(h->npieces, h->part, h->ncb, h->dot_gc, h->nchunks, h->dot_gp, o.up, o.down,
-                                      o.rho_good, o.rho_bad, o.lambda_min, o.lambda_max, h->st, h->stats, h->cap);
+                                      o.rho_good, o.rho_bad, o.lambda_min, o.lambda_max, h->st, h->stats, h->cap,
+                                      h->xch ? h->xscal : nullptr);
   }
   count_launch(2);
 }
@@ -608,9 +704,9 @@ ba_status create_impl(ba_problem* h, const void* cams, const void* points, const
   }
   count_launch(3);
 
-  // fused point-major pass A (recompute mode): every chunk's distinct
-  // cameras, if no chunk has more than FA_CAMS of them
-  if (h->mf) {
+  // fused point-major pass A (both modes): every chunk's distinct cameras,
+  // if no chunk has more than FA_CAMS of them
+  {
     std::vector<int32_t> pmc(O), list, ptr(h->nchunks + 1), tmp;
     std::vector<int16_t> lc(O);
     CU(cudaMemcpy(pmc.data(), h->pm_cam, O * 4, cudaMemcpyDeviceToHost));
@@ -659,6 +755,12 @@ ba_status create_impl(ba_problem* h, const void* cams, const void* points, const
   CU(h->alloc(&h->zbuf, 4 * O * ts));
   if (!h->mf) {
     CU(h->alloc(&h->Jcm, (size_t)NPLANE * O * ts));
+    if (h->fa) {
+      // the planes in point-major order for the fused stored pass A
+      CU(h->alloc(&h->Jpm, (size_t)NPLANE * O * ts));
+      if (fs_smem<T>(FA_CAMS) > 48 * 1024)
+        CU(cudaFuncSetAttribute(k_pass_fs<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, fs_smem<T>(FA_CAMS)));
+    }
   } else if (h->opt.huber_delta > 0) {
     CU(h->alloc(&h->cm_sw, O * ts));
     CU(h->alloc(&h->pm_sw, O * ts));
@@ -790,8 +892,9 @@ void enqueue_collect(ba_problem* h, const double* lam_ptr, int K, const float* z
   k_cam_combine_schur<T, MF><<<h->ncb, CAM_THREADS, 0, s>>>(
       h->C, h->cam_piece_ptr, h->part, h->U, h->gc, (const T*)h->camtab, lam_ptr, dmin, dmax, h->Minv, h->x, h->r,
       h->z, h->p, (T*)h->pT, h->dot_rz + h->ncb, h->dot_bb, h->fixed, h->st, h->Sii);
+  enqueue_coupling<T, MF>(h, lam_ptr);
   k_learn_features<<<h->ncb, CAM_THREADS, 0, s>>>(h->C, h->Sii, h->U, lam_ptr, dmin, dmax, h->rowptr_cam, X, Ahat,
-                                                  h->Dsc);
+                                                  h->Dsc, h->kap);
   count_launch(4);
   for (int k = 0; k < K; ++k) {
     k_probe_in<T, MF><<<nblk(h->C, 128), 128, 0, s>>>(h->C, K, k, zhat, h->Dsc, (const T*)h->camtab, h->p,
@@ -829,11 +932,101 @@ ba_status ensure_learn_buffers(ba_problem* h) {
   CU(h->alloc(&h->Xf, (size_t)MLP_FIN * h->C * 4));
   CU(h->alloc(&h->Ef, (size_t)MLP_FOUT * h->C * 4));
   CU(h->alloc(&h->Dsc, 9ull * h->C * 8));
+  CU(h->alloc(&h->kap, (size_t)h->C * 8));
   CU(cudaFuncSetAttribute(k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MLP_SMEM_FWD));
   return BA_OK;
 }
 
 }  // namespace
+
+static __global__ void k_f2d(long long n, const float* __restrict__ a, double* __restrict__ b) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (double)a[i];
+}
+static __global__ void k_d2f(long long n, const double* __restrict__ a, float* __restrict__ b) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (float)a[i];
+}
+
+extern "C" ba_status ba_backward(ba_problem* h, double lambda, int maxiter, double tol, const void* dL_dcams,
+                                 const void* dL_dpoints, void* dL_dpixels_out, void* dL_dcams0_out,
+                                 void* dL_dpoints0_out, int* iters, double* rel_res, void* stream);
+
+// The adjoint of an FP32 problem, solved in FP64.  Its system H v = dL/dtheta
+// is ill-conditioned and its implicit Schur product cancels (measured on the
+// 64-camera workload: condition ~5.5e3 after block-Jacobi scaling, |U* v| /
+// |S v| ~ 190), which would turn FP32 rounding of the Jacobian into ~1e-2
+// relative gradient errors.  So the first call builds an FP64 twin of the
+// problem (the same observations; the FP32 parameters and pixels promoted,
+// exactly), later calls refresh its parameters, pixels and frozen mask, and
+// the twin's FP64 adjoint is returned in FP32.  Scratch is allocated per call.
+ba_status backward_via_f64(ba_problem* h, double lambda, int maxiter, double tol, const float* dLc,
+                           const float* dLp, float* dpix_out, float* dc0_out, float* dp0_out, int* iters,
+                           double* rel_res, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  const long long C = h->C, P = h->P, O = h->O;
+  std::vector<void*> tmp;
+  auto grab = [&](size_t bytes) -> void* {
+    void* p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
+    tmp.push_back(p);
+    return p;
+  };
+  auto release = [&]() {
+    cudaStreamSynchronize(s);
+    for (void* p : tmp) cudaFree(p);
+  };
+  float* c32 = (float*)grab(9 * C * 4);
+  float* p32 = (float*)grab(3 * P * 4);
+  double* c64 = (double*)grab(9 * C * 8);
+  double* p64 = (double*)grab(3 * P * 8);
+  double* x64 = (double*)grab(2 * O * 8);
+  double* gc64 = dLc ? (double*)grab(9 * C * 8) : nullptr;
+  double* gp64 = dLp ? (double*)grab(3 * P * 8) : nullptr;
+  double* px64 = (double*)grab(2 * O * 8);
+  double* dc64 = dc0_out ? (double*)grab(9 * C * 8) : nullptr;
+  double* dp64 = dp0_out ? (double*)grab(3 * P * 8) : nullptr;
+  int32_t* ptc = (int32_t*)grab(O * 4);
+  if (!c32 || !p32 || !c64 || !p64 || !x64 || (dLc && !gc64) || (dLp && !gp64) || !px64 || (dc0_out && !dc64) ||
+      (dp0_out && !dp64) || !ptc) {
+    release();
+    return fail(BA_ERR_OOM, "scratch of the FP64 adjoint");
+  }
+  ba_status st = ba_get_params(h, c32, p32, stream);
+  if (st == BA_OK) {
+    // (ordered after the problem's stream by ba_get_params)
+    k_f2d<<<nblk(9 * C, 256), 256, 0, s>>>(9 * C, c32, c64);
+    k_f2d<<<nblk(3 * P, 256), 256, 0, s>>>(3 * P, p32, p64);
+    k_f2d<<<nblk(2 * O, 256), 256, 0, s>>>(2 * O, (const float*)h->px_in, x64);
+    k_gather_i32<<<nblk(O, 256), 256, 0, s>>>((int)O, h->pt_idx, h->pnew, ptc);  // the caller's point numbering
+    if (dLc) k_f2d<<<nblk(9 * C, 256), 256, 0, s>>>(9 * C, dLc, gc64);
+    if (dLp) k_f2d<<<nblk(3 * P, 256), 256, 0, s>>>(3 * P, dLp, gp64);
+    count_launch(4 + (dLc ? 1 : 0) + (dLp ? 1 : 0));
+    if (cudaGetLastError() != cudaSuccess) st = fail(BA_ERR_CUDA, "promotion kernels failed");
+  }
+  if (st == BA_OK && !h->twin) {
+    ba_options o = h->opt;
+    o.precision = BA_PREC_F64;
+    o.jacobian_mode = BA_JAC_AUTO;
+    o.solver = BA_SOLVER_PCG;
+    st = ba_problem_create(&h->twin, (int)C, (int)P, (int)O, c64, p64, h->cam_idx, ptc, x64, &o, stream);
+  } else if (st == BA_OK) {
+    st = ba_set_params(h->twin, c64, p64, stream);
+    if (st == BA_OK) st = ba_set_pixels(h->twin, x64, stream);
+  }
+  if (st == BA_OK) st = ba_set_fixed(h->twin, h->fixed, stream);
+  if (st == BA_OK)
+    st = ba_backward(h->twin, lambda, maxiter, tol, gc64, gp64, px64, dc64, dp64, iters, rel_res, stream);
+  if (st == BA_OK) {
+    k_d2f<<<nblk(2 * O, 256), 256, 0, s>>>(2 * O, px64, dpix_out);
+    if (dc0_out) k_d2f<<<nblk(9 * C, 256), 256, 0, s>>>(9 * C, dc64, dc0_out);
+    if (dp0_out) k_d2f<<<nblk(3 * P, 256), 256, 0, s>>>(3 * P, dp64, dp0_out);
+    count_launch(1 + (dc0_out ? 1 : 0) + (dp0_out ? 1 : 0));
+    if (cudaGetLastError() != cudaSuccess) st = fail(BA_ERR_CUDA, "conversion kernels failed");
+  }
+  release();
+  return st;
+}
 
 extern "C" {
 
@@ -923,6 +1116,16 @@ ba_status ba_solve(ba_problem* h, int iters, void* stream) {
   ba_status st = enter(h, stream);
   if (st != BA_OK) return st;
   if (iters > 0) h->cost_pending = false;  // every trial starts with the stale cost
+  if (h->xch) {
+    // a part of a point-partitioned problem: direct launches, the caller's
+    // all-reduce at each exchange
+    h->xerr = 0;
+    for (int i = 0; i < iters && !h->xerr; ++i) enqueue_trial_any(h);
+    CU(cudaGetLastError());
+    if (h->xerr)
+      return fail(BA_ERR_CUDA, h->xerr == 2 ? "the exchange callback failed" : "exchange buffer too small or copy failed");
+    return leave(h, stream);
+  }
   if (!h->opt.use_graph) {
     for (int i = 0; i < iters; ++i) enqueue_trial_any(h);
     CU(cudaGetLastError());
@@ -1242,6 +1445,10 @@ ba_status ba_backward(ba_problem* h, double lambda, int maxiter, double tol, con
   if (!h || !dL_dpixels_out) return fail(BA_ERR_INVALID_ARG, "NULL argument");
   if (maxiter < 0 || maxiter > 100000 || !(tol >= 0) || !(lambda >= 0))
     return fail(BA_ERR_INVALID_ARG, "bad lambda/maxiter/tol");
+  if (h->prec == BA_PREC_F32)
+    return backward_via_f64(h, lambda, maxiter, tol, (const float*)dL_dcams, (const float*)dL_dpoints,
+                            (float*)dL_dpixels_out, (float*)dL_dcams0_out, (float*)dL_dpoints0_out, iters, rel_res,
+                            stream);
   ba_status st = enter(h, stream);
   if (st != BA_OK) return st;
   st = set_probe_lambda(h, lambda);
@@ -1332,6 +1539,41 @@ ba_status ba_learn_slow_probes(ba_problem* h, double lambda, int n, const int* i
 }
 
 uint64_t ba_kernel_launch_count(void) { return ba::g_launches.load(); }
+
+ba_status ba_set_exchange(ba_problem* h, ba_exchange_fn fn, void* ctx, double* xbuf, size_t cap) {
+  if (!h) return fail(BA_ERR_INVALID_ARG, "NULL problem");
+  if (fn && (!xbuf || cap < BA_EXCHANGE_CAP(h->C)))
+    return fail(BA_ERR_INVALID_ARG, "the exchange buffer must hold BA_EXCHANGE_CAP(C) = %zu doubles",
+                (size_t)BA_EXCHANGE_CAP(h->C));
+  if (fn && (h->learned || h->opt.solver != BA_SOLVER_PCG))
+    return fail(BA_ERR_INVALID_ARG, "a partitioned problem uses block-Jacobi PCG");
+  if (fn && !h->ident_ptr) {
+    std::vector<int32_t> id(h->C + 1);
+    for (int c = 0; c <= h->C; ++c) id[c] = c;
+    CU(h->alloc(&h->ident_ptr, (h->C + 1) * 4));
+    CU(cudaMemcpy(h->ident_ptr, id.data(), (h->C + 1) * 4, cudaMemcpyHostToDevice));
+    CU(h->alloc(&h->camsum, (size_t)PART * h->C * 8));
+    CU(h->alloc(&h->U_loc, 45ull * h->C * 8));
+    CU(h->alloc(&h->gc_loc, 9ull * h->C * 8));
+    CU(h->alloc(&h->xscal, 8 * 8));
+  }
+  CU(cudaStreamSynchronize(h->s));
+  h->xch = fn;
+  h->xctx = ctx;
+  h->xbuf = xbuf;
+  h->xcap = fn ? cap : 0;
+  h->xerr = 0;
+  if (h->gexec) {
+    cudaGraphExecDestroy(h->gexec);
+    h->gexec = nullptr;
+  }
+  // the cost is a sum over the parts now (or this problem's alone again);
+  // the linearisation's sums too
+  ba_status st = set_flag(h, offsetof(DevState, need_cost), 1);
+  if (st == BA_OK) st = set_flag(h, offsetof(DevState, need_lin), 1);
+  if (st == BA_OK) CU(cudaStreamSynchronize(h->s));
+  return st;
+}
 
 ba_status ba_get_layout(const ba_problem* h, int64_t* out, int n) {
   if (!h || !out || n < 0) return fail(BA_ERR_INVALID_ARG, "bad argument");

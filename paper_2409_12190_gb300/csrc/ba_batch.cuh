@@ -101,6 +101,7 @@ struct BShared {
   T pT[BMAXC][PV];  // PCG direction in the passes' form
   T xT[BMAXC][PV];  // camera step in the passes' form
   double sce64[CT]; // camera table of the evaluated parameters (cost, in double)
+  FFCam sceff;      // the same split into float-float pairs (FP32 cost)
   // recompute mode: padded copies of the camera tables and of the vector a
   // point-major pass reads (neighbouring slots use different cameras), and
   // the per-observation products of one point chunk
@@ -449,12 +450,14 @@ __device__ void batch_cost(const BatchArgs<T>& a, const BRange<T>& R, BShared<T>
   for (int q = R.q0; q < R.q1; ++q) {
     const int cg = a.piece_cam[q];
     const int c = cg - R.c0;
-    if (threadIdx.x == 0) camera_table_f64(a.cams + (long long)buf * 9 * a.C + 9LL * cg, S.sce64);
+    if (threadIdx.x == 0) {
+      camera_table_f64(a.cams + (long long)buf * 9 * a.C + 9LL * cg, S.sce64);
+      ffcam_from(S.sce64, S.sceff);
+    }
     __syncthreads();
     double cost = 0.0, quad = 0.0;
-    cost_cam_range<T, MODEL, MF, BT>(a.piece_beg[q], a.piece_end[q], a.cm_pt, a.cm_px, pts, pts_old,
-                                     reinterpret_cast<const T*>(S.sce64), S.sce64, S.ct[c], S.xT[c], a.delta, a.O,
-                                     a.Jcm, a.cm_sw, a.dp, cost, quad);
+    cost_cam_range<T, MODEL, MF, BT>(a.piece_beg[q], a.piece_end[q], a.cm_pt, a.cm_px, pts, pts_old, &S.sceff,
+                                     S.sce64, S.ct[c], S.xT[c], a.delta, a.O, a.Jcm, a.cm_sw, a.dp, cost, quad);
     double v[2] = {cost, quad};
     bred_store<2, true>(v, S.red, a.part + (long long)PART * q);
   }

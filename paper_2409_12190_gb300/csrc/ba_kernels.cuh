@@ -142,6 +142,29 @@ __device__ __forceinline__ void ff_add(float& hi, float& lo, float h2, float l2)
   lo = e - (hi - s);
 }
 
+// Float-float products (Dekker's product with the exact FMA remainder):
+// (hi, lo) = (ah, al) * (bh, bl), and the same with a plain float b.
+__device__ __forceinline__ void ff_mul(float ah, float al, float bh, float bl, float& hi, float& lo) {
+  const float p = ah * bh;
+  const float e = fmaf(ah, bh, -p) + (ah * bl + al * bh);
+  hi = p + e;
+  lo = e - (hi - p);
+}
+__device__ __forceinline__ void ff_mulf(float ah, float al, float b, float& hi, float& lo) {
+  const float p = ah * b;
+  const float e = fmaf(ah, b, -p) + al * b;
+  hi = p + e;
+  lo = e - (hi - p);
+}
+// (hi, lo) = 1 / (bh, bl): a reciprocal and one Newton correction.
+__device__ __forceinline__ void ff_rcp(float bh, float bl, float& hi, float& lo) {
+  const float q = 1.0f / bh;
+  const float r = fmaf(-bh, q, 1.0f) - bl * q;  // 1 - b q, to first order
+  const float c = r * q;
+  hi = q + c;
+  lo = c - (hi - q);
+}
+
 // Warp reduce-scatter of 64 float-float values: five shuffle steps, each
 // halving the values a lane keeps (its partner lane takes the other half),
 // 62 shuffled pairs in all instead of 5 x 64.  Lane l returns the warp totals
@@ -416,6 +439,65 @@ __device__ __forceinline__ void project_obs(const T* __restrict__ ct, T X0, T X1
   s = ct[CT_F] * (T(1) + r2 * (ct[CT_K1] + ct[CT_K2] * r2));
 }
 
+// A camera table (R, t, f, k1, k2: the first 15 entries of the double
+// table) split into float-float pairs, for the FP32 variant's cost.
+struct FFCam {
+  float h[15], l[15];
+};
+__device__ __forceinline__ void ffcam_from(const double* __restrict__ ct, FFCam& o) {
+#pragma unroll
+  for (int i = 0; i < 15; ++i) {
+    o.h[i] = (float)ct[i];
+    o.l[i] = (float)(ct[i] - (double)o.h[i]);
+  }
+}
+
+// Squared residual |pi(theta_c, X) - x|^2 in float-float arithmetic (about
+// 44 significant bits after the division), returned as a double; X and the
+// pixel are FP32 values (exact in float-float).  The projection of
+// project_obs, step for step.
+__device__ __forceinline__ double sq_residual_ff(const FFCam& c, float X0, float X1, float X2, float u0, float u1) {
+  float Ph[3], Pl[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    float h, l, h2, l2;
+    ff_mulf(c.h[3 * a], c.l[3 * a], X0, h, l);
+    ff_mulf(c.h[3 * a + 1], c.l[3 * a + 1], X1, h2, l2);
+    ff_add(h, l, h2, l2);
+    ff_mulf(c.h[3 * a + 2], c.l[3 * a + 2], X2, h2, l2);
+    ff_add(h, l, h2, l2);
+    ff_add(h, l, c.h[CT_T + a], c.l[CT_T + a]);
+    Ph[a] = h;
+    Pl[a] = l;
+  }
+  float izh, izl, pxh, pxl, pyh, pyl;
+  ff_rcp(Ph[2], Pl[2], izh, izl);
+  ff_mul(-Ph[0], -Pl[0], izh, izl, pxh, pxl);
+  ff_mul(-Ph[1], -Pl[1], izh, izl, pyh, pyl);
+  float r2h, r2l, th, tl;
+  ff_mul(pxh, pxl, pxh, pxl, r2h, r2l);
+  ff_mul(pyh, pyl, pyh, pyl, th, tl);
+  ff_add(r2h, r2l, th, tl);
+  // s = f (1 + r2 (k1 + k2 r2))
+  float dh, dl;
+  ff_mul(c.h[CT_K2], c.l[CT_K2], r2h, r2l, dh, dl);
+  ff_add(dh, dl, c.h[CT_K1], c.l[CT_K1]);
+  ff_mul(dh, dl, r2h, r2l, th, tl);
+  ff_add(th, tl, 1.0f, 0.0f);
+  float sh, sl;
+  ff_mul(c.h[CT_F], c.l[CT_F], th, tl, sh, sl);
+  float r0h, r0l, r1h, r1l;
+  ff_mul(sh, sl, pxh, pxl, r0h, r0l);
+  ff_mul(sh, sl, pyh, pyl, r1h, r1l);
+  ff_add(r0h, r0l, -u0, 0.0f);
+  ff_add(r1h, r1l, -u1, 0.0f);
+  float qh, ql;
+  ff_mul(r0h, r0l, r0h, r0l, qh, ql);
+  ff_mul(r1h, r1l, r1h, r1l, th, tl);
+  ff_add(qh, ql, th, tl);
+  return (double)qh + (double)ql;
+}
+
 // Huber on |r|: half_rho = 1/2 rho(s); returns sqrt(w), w = rho'(s).
 template <typename T>
 __device__ __forceinline__ T huber_weight(T sq, T delta, T& half_rho, T& w) {
@@ -535,12 +617,32 @@ __device__ __forceinline__ void jp_from(const T* __restrict__ A, const T* __rest
       Jp[3 * a + j] = A[3 * a] * R[j] + A[3 * a + 1] * R[3 + j] + A[3 * a + 2] * R[6 + j];
 }
 
-// The first N planes of camera-major slot s (N = NPLANE_JC when Jp is not
-// needed).
+// The stored planes are interleaved in pairs: plane p of slot s is
+// J[((p / 2) O + s) 2 + p % 2], so a thread reads two planes with one
+// 2-vector load and a warp still reads contiguous memory.
+template <typename T>
+struct Vec2;
+template <>
+struct Vec2<float> {
+  using type = float2;
+};
+template <>
+struct Vec2<double> {
+  using type = double2;
+};
+
+// The first N planes (N even) of camera-major slot s (N = NPLANE_JC when Jp
+// is not needed).
 template <int N = NPLANE, typename T>
 __device__ __forceinline__ void load_planes(const T* __restrict__ J, long long O, long long s, T (&pl)[NPLANE]) {
+  static_assert(N % 2 == 0, "planes are read in pairs");
+  using V2 = typename Vec2<T>::type;
 #pragma unroll
-  for (int p = 0; p < N; ++p) pl[p] = J[p * O + s];
+  for (int q = 0; q < N / 2; ++q) {
+    const V2 v = reinterpret_cast<const V2*>(J)[(long long)q * O + s];
+    pl[2 * q] = v.x;
+    pl[2 * q + 1] = v.y;
+  }
 }
 
 // Four consecutive T as one vector access (the address is 4 * sizeof(T)
@@ -776,8 +878,14 @@ __device__ __forceinline__ void lin_cam_range(int beg, int end, const int32_t* _
     T pl[NPLANE];
     fac_planes(o, sct, pl);
     if (STORE) {
+      using V2 = typename Vec2<T>::type;
 #pragma unroll
-      for (int p = 0; p < NPLANE; ++p) Jcm[(long long)p * O + s] = pl[p];
+      for (int q = 0; q < NPLANE / 2; ++q) {
+        V2 v;
+        v.x = pl[2 * q];
+        v.y = pl[2 * q + 1];
+        reinterpret_cast<V2*>(Jcm)[(long long)q * O + s] = v;
+      }
     }
     T j0[9], j1[9];
     jc_rows(pl, j0, j1);
@@ -1680,6 +1788,128 @@ k_pass_fa(const int32_t* __restrict__ pchunk, int P, const int32_t* __restrict__
   }
 }
 
+// ---------------------------------------------------------------------------
+// Stored mode: pass A fused point-major (A1 + A2 in one kernel)
+// ---------------------------------------------------------------------------
+
+// The stored planes in point-major slot order: Jpm[q] = Jcm[pm2cm[q]] (both
+// pair-interleaved), gathered once per linearisation (gated like it).
+template <typename T>
+static __global__ void k_planes_pm(long long O, const DevState* __restrict__ st, int gate,
+                                   const int32_t* __restrict__ pm2cm, const T* __restrict__ Jcm,
+                                   T* __restrict__ Jpm) {
+  if (gate && !st->need_lin) return;
+  using V2 = typename Vec2<T>::type;
+  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= O) return;
+  const long long s = pm2cm[q];
+#pragma unroll
+  for (int p = 0; p < NPLANE / 2; ++p)
+    reinterpret_cast<V2*>(Jpm)[p * O + q] = reinterpret_cast<const V2*>(Jcm)[p * O + s];
+}
+
+// Fused pass A of the stored mode (point-major, one CTA per chunk of
+// points):  t_j = V*_j^{-1} sum_{k in pt j} Jp_k^T (Jc_k x_c(k)),  the
+// products of k_pass_a1 on the point-major copy of the planes, the chunk's
+// camera vectors staged in shared memory (the chunk lists of k_pass_fa),
+// and the per-point sums of k_pass_a2 in slot order -- without the
+// per-observation z written to and gathered back from global memory.  A
+// chunk of one point with more than CHUNK_SLOTS observations is reduced by
+// the block.
+template <typename T>
+static __global__ void __launch_bounds__(CHUNK_THREADS)
+k_pass_fs(const int32_t* __restrict__ rowptr_pt, const int16_t* __restrict__ pm_lc,
+          const int32_t* __restrict__ chunk_cams, const T* __restrict__ Jpm, long long O, const T* __restrict__ xc,
+          const T* __restrict__ Vinv, const DevState* __restrict__ st, int check_done, T* __restrict__ ptab,
+          const int4* __restrict__ chunk_hdr, int nc_max) {
+  if (check_done && st->pcg_done) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sz = reinterpret_cast<T*>(smem_raw);  // [CHUNK_SLOTS][4]
+  T* sxv = sz + 4 * CHUNK_SLOTS;           // [nc_max][9]: the chunk's camera vectors
+  const int k = blockIdx.x;
+  const int4 h0 = chunk_hdr[2 * k], h1 = chunk_hdr[2 * k + 1];
+  const int j0 = h0.x, j1 = h0.y, s0 = h0.z, s1 = h0.w, c0 = h1.x, nc = h1.y, cmin = h1.z;
+  const bool small = s1 - s0 <= CHUNK_SLOTS;
+  // this thread's slots' camera positions, loaded before the staging
+  // barrier (every later load depends on the header only)
+  constexpr int U = CHUNK_SLOTS / CHUNK_THREADS;
+  int ll[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int q = s0 + threadIdx.x + u * CHUNK_THREADS;
+    ll[u] = (small && q < s1) ? pm_lc[q] : 0;
+  }
+  for (int i = threadIdx.x; i < nc * 9; i += CHUNK_THREADS) {
+    const int l = i / 9, e = i % 9;
+    const int cam = cmin >= 0 ? cmin + l : chunk_cams[c0 + l];
+    sxv[i] = xc[9LL * cam + e];
+  }
+  __syncthreads();
+  T za = 0, zb = 0, zc = 0;  // large chunk: this thread's share
+  for (int q = s0 + threadIdx.x, u = 0; q < s1; q += CHUNK_THREADS, ++u) {
+    T pl[NPLANE];
+    load_planes(Jpm, O, q, pl);
+    int lq = 0;
+#pragma unroll
+    for (int v = 0; v < U; ++v)
+      if (v == u) lq = ll[v];
+    const T* xv = sxv + 9 * (small ? lq : pm_lc[q]);
+    T j0r[9], j1r[9];
+    jc_rows(pl, j0r, j1r);
+    T e0 = 0, e1 = 0;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      e0 += j0r[i] * xv[i];
+      e1 += j1r[i] * xv[i];
+    }
+    const T* Jp = pl + NPLANE_JC;
+    const T z0 = Jp[0] * e0 + Jp[3] * e1;
+    const T z1 = Jp[1] * e0 + Jp[4] * e1;
+    const T z2 = Jp[2] * e0 + Jp[5] * e1;
+    if (small) {
+      store4(sz + 4 * (q - s0), z0, z1, z2, T(0));
+    } else {
+      za += z0;
+      zb += z1;
+      zc += z2;
+    }
+  }
+  if (small) {
+    __syncthreads();
+    for (int j = j0 + threadIdx.x; j < j1; j += CHUNK_THREADS) {
+      T z0 = 0, z1 = 0, z2 = 0;
+      const int q1 = rowptr_pt[j + 1];
+      for (int q = rowptr_pt[j]; q < q1; ++q) {
+        T a, b, c, pad;
+        load4(sz + 4 * (q - s0), a, b, c, pad);
+        z0 += a;
+        z1 += b;
+        z2 += c;
+      }
+      const T* vi = Vinv + 6LL * j;
+      const T t0 = vi[0] * z0 + vi[1] * z1 + vi[2] * z2;
+      const T t1 = vi[1] * z0 + vi[3] * z1 + vi[4] * z2;
+      const T t2 = vi[2] * z0 + vi[4] * z1 + vi[5] * z2;
+      store4(ptab + 8LL * j + 4, t0, t1, t2, T(0));
+    }
+  } else {
+    double dd[3] = {(double)za, (double)zb, (double)zc};
+    block_sum_all<3>(dd);
+    if (threadIdx.x == 0) {
+      const T* vi = Vinv + 6LL * j0;
+      const T z0 = (T)dd[0], z1 = (T)dd[1], z2 = (T)dd[2];
+      store4(ptab + 8LL * j0 + 4, vi[0] * z0 + vi[1] * z1 + vi[2] * z2, vi[1] * z0 + vi[3] * z1 + vi[4] * z2,
+             vi[2] * z0 + vi[4] * z1 + vi[5] * z2, T(0));
+    }
+  }
+}
+
+// dynamic shared memory of k_pass_fs: z per slot and nc camera vectors
+template <typename T>
+constexpr int fs_smem(int nc) {
+  return (CHUNK_SLOTS * 4 + nc * 9) * (int)sizeof(T);
+}
+
 // Pass B over camera-major slots [beg, end), NT threads striding: per-thread
 // partial sum_k Jc_k^T (Jp_k t_p(k)) (9 values; in the recompute mode the
 // first three are still to be multiplied by J_l^T).
@@ -1787,8 +2017,9 @@ __device__ __forceinline__ void pass_b_range(int beg, int end, const int32_t* __
       const T h1 = Jp[3] * t0 + Jp[4] * t1 + Jp[5] * t2;
       T j0[9], j1[9];
       jc_rows(pl, j0, j1);
+      // two fused multiply-adds per component
 #pragma unroll
-      for (int i = 0; i < 9; ++i) acc[i] += j0[i] * h0 + j1[i] * h1;
+      for (int i = 0; i < 9; ++i) acc[i] = fma(j1[i], h1, fma(j0[i], h0, acc[i]));
     }
   }
 }
@@ -1829,9 +2060,11 @@ constexpr int VT = CAM_THREADS * 9;
 
 __device__ __forceinline__ int sym9_rt(int i, int j) { return i <= j ? sym9(i, j) : sym9(j, i); }
 
-// q = U* p - sum of pass-B pieces (J_l^T applied to their first three in the
-// recompute mode); per-block partial p.q.
-template <typename T, bool MF>
+// q = U* p - sum of pass-B partials (J_l^T applied to their first three in
+// the recompute mode); per-block partial p.q.  Camera c's partials are rows
+// cam_piece_ptr[c] .. cam_piece_ptr[c + 1] of part (row stride PS): per
+// piece, or one row per camera already summed (a point-partitioned problem).
+template <typename T, bool MF, int PS = PART>
 static __global__ void __launch_bounds__(VT)
 k_pcg_q(int C, const int32_t* __restrict__ cam_piece_ptr, const double* __restrict__ part,
         const double* __restrict__ U, const T* __restrict__ camtab, const double* __restrict__ lam_ptr, double dmin,
@@ -1846,7 +2079,7 @@ k_pcg_q(int C, const int32_t* __restrict__ cam_piece_ptr, const double* __restri
   if (ok) {
     pv = p[9LL * c + i];
     const int p1 = cam_piece_ptr[c + 1];
-    for (int k = cam_piece_ptr[c]; k < p1; ++k) sum += part[(long long)PART * k + i];
+    for (int k = cam_piece_ptr[c]; k < p1; ++k) sum += part[(long long)PS * k + i];
   }
   sp[lc][i] = pv;
   ss[lc][i] = sum;
@@ -2013,16 +2246,18 @@ k_cam_trial(int C, const double* __restrict__ x, const double* __restrict__ gc, 
 // 1/2 rho at the camera table sct and points pts, and with MODEL the
 // quadratic model term |Jc dc + Jp dp|^2 at the linearisation (camera table
 // sold, points pts_old, dc in the pass form sdc).
-// The cost 1/2 sum rho is evaluated in FP64 in both precisions: the FP32
-// variant's parameters, points and pixels are promoted and projected with
-// the FP64 camera table sct64 (the accept / reject test and the gain ratio
-// compare costs that differ by less than FP32 evaluation would resolve: a
-// robust loss converges linearly, and the last gains are ~1e-8 relative per
-// trial).  The model term stays in T, summed in float-float for FP32.
+// The cost 1/2 sum rho is evaluated to about FP64 accuracy in both
+// precisions (the accept / reject test and the gain ratio compare costs
+// that differ by less than FP32 evaluation would resolve: a robust loss
+// converges linearly, and its last gains are ~1e-8 relative per trial).
+// FP64: in double with the camera table sct64.  FP32: the squared residual
+// in float-float arithmetic on the FP32 pipes from the split table ffc (the
+// FP32 parameters and pixels are exact in it), then rho and the sum in
+// double.  The model term stays in T, summed in float-float for FP32.
 template <typename T, bool MODEL, bool MF, int NT>
 __device__ __forceinline__ void cost_cam_range(int beg, int end, const int32_t* __restrict__ cm_pt,
                                                const T* __restrict__ cm_px, const T* __restrict__ pts,
-                                               const T* __restrict__ pts_old, const T* __restrict__ sct,
+                                               const T* __restrict__ pts_old, const FFCam* __restrict__ ffc,
                                                const double* __restrict__ sct64, const T* __restrict__ sold,
                                                const T* __restrict__ sdc, T delta, int O,
                                                const T* __restrict__ Jcm, const T* __restrict__ cm_sw,
@@ -2033,12 +2268,21 @@ __device__ __forceinline__ void cost_cam_range(int beg, int end, const int32_t* 
   for (int s = beg + threadIdx.x; s < end; s += NT) {
     const int j = cm_pt[s];
     {
-      const double* ct = sizeof(T) == 4 ? sct64 : reinterpret_cast<const double*>(sct);
-      double px, py, sc;
-      project_obs(ct, (double)pts[3LL * j], (double)pts[3LL * j + 1], (double)pts[3LL * j + 2], px, py, sc);
-      const double r0 = sc * px - (double)cm_px[s], r1 = sc * py - (double)cm_px[(long long)O + s];
+      double sq = 0.0;
+      bool done = false;
+      if constexpr (sizeof(T) == 4) {
+        sq = sq_residual_ff(*ffc, pts[3LL * j], pts[3LL * j + 1], pts[3LL * j + 2], cm_px[s], cm_px[(long long)O + s]);
+        // outside float range (a trial point near the camera plane): in double
+        done = isfinite(sq);
+      }
+      if (!done) {
+        double px, py, sc;
+        project_obs(sct64, (double)pts[3LL * j], (double)pts[3LL * j + 1], (double)pts[3LL * j + 2], px, py, sc);
+        const double r0 = sc * px - (double)cm_px[s], r1 = sc * py - (double)cm_px[(long long)O + s];
+        sq = r0 * r0 + r1 * r1;
+      }
       double hr, w;
-      huber_weight(r0 * r0 + r1 * r1, (double)delta, hr, w);
+      huber_weight(sq, (double)delta, hr, w);
       cost += hr;
     }
     if (MODEL) {
@@ -2091,13 +2335,17 @@ k_cost_cam(const int32_t* __restrict__ piece_cam, const int32_t* __restrict__ pi
            const T* __restrict__ xT, const T* __restrict__ dp, double* __restrict__ part) {
   if (which == 2 && !st->need_cost) return;  // cost at theta only if stale
   __shared__ double sct64[CT];  // camera of the evaluated parameters, in double
+  __shared__ FFCam sff;         // and split into float-float pairs (FP32)
   __shared__ T sold[CT];  // camera of the linearisation (model term)
   __shared__ T sdc[PV];
   const int b = blockIdx.x;
   const int c = piece_cam[b];
   const int cur = st->cur;
   const int buf = which == 1 ? 1 - cur : cur;
-  if (threadIdx.x == 0) camera_table_f64(cams_buf + (long long)buf * 9 * C + 9LL * c, sct64);
+  if (threadIdx.x == 0) {
+    camera_table_f64(cams_buf + (long long)buf * 9 * C + 9LL * c, sct64);
+    ffcam_from(sct64, sff);
+  }
   if (MODEL && threadIdx.x >= 32 && threadIdx.x < 32 + CT)
     sold[threadIdx.x - 32] = camtab[(long long)CT * c + threadIdx.x - 32];
   if (MODEL && threadIdx.x >= 64 + CT && threadIdx.x < 64 + CT + pass_vec_stride(MF))
@@ -2107,11 +2355,57 @@ k_cost_cam(const int32_t* __restrict__ piece_cam, const int32_t* __restrict__ pi
   const T* pts_old = pts_buf + (long long)cur * 3 * P;
   double cost = 0.0, quad = 0.0;
   static_assert(NT >= 64 + CT + PV, "the staging of the model term needs 64 + CT + PV threads");
-  cost_cam_range<T, MODEL, MF, NT>(piece_beg[b], piece_end[b], cm_pt, cm_px, pts, pts_old,
-                                   reinterpret_cast<const T*>(sct64), sct64, sold, sdc, delta, O, Jcm, cm_sw, dp,
-                                   cost, quad);
+  cost_cam_range<T, MODEL, MF, NT>(piece_beg[b], piece_end[b], cm_pt, cm_px, pts, pts_old, &sff, sct64, sold, sdc,
+                                   delta, O, Jcm, cm_sw, dp, cost, quad);
   double v[2] = {cost, quad};
   block_sum_store<2>(v, part + (long long)PART * b);
+}
+
+// ---------------------------------------------------------------------------
+// Point-partitioned problems (ba_set_exchange): the part of the problem's
+// sums that this problem's observations contribute, laid out for one
+// all-reduce each.
+// ---------------------------------------------------------------------------
+
+// out[c * os + i] = sum over camera c's pieces of part[. * PART + i], i < nv.
+static __global__ void k_cam_sum_parts(int C, const int32_t* __restrict__ cam_piece_ptr,
+                                       const double* __restrict__ part, int nv, int os, double* __restrict__ out) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)C * nv) return;
+  const int c = (int)(t / nv), i = (int)(t % nv);
+  double sum = 0.0;
+  for (int k = cam_piece_ptr[c]; k < cam_piece_ptr[c + 1]; ++k) sum += part[(long long)PART * k + i];
+  out[(long long)os * c + i] = sum;
+}
+
+// The trial's sums over this part: out[0] cost (pieces), out[1] the model's
+// quadratic term (pieces), out[2] gp . dp (chunks).
+static __global__ void k_part_trial_sums(int npieces, const double* __restrict__ part, int npb,
+                                         const double* __restrict__ dot_gp, double* __restrict__ out) {
+  const double a = block_sum_array(part, npieces, PART);
+  const double b = block_sum_array(part + 1, npieces, PART);
+  const double c = block_sum_array(dot_gp, npb, 1);
+  if (threadIdx.x == 0) {
+    out[0] = a;
+    out[1] = b;
+    out[2] = c;
+  }
+}
+
+// The cost over this part into out[0] (0 when gated off: F is not stale).
+static __global__ void k_part_cost_sum(int npieces, const double* __restrict__ part, const DevState* st, int gate,
+                                       double* __restrict__ out) {
+  const bool skip = gate && !st->need_cost;
+  const double F = skip ? 0.0 : block_sum_array(part, npieces, PART);
+  if (threadIdx.x == 0) out[0] = F;
+}
+
+// st->F = the summed cost (when not gated off).
+static __global__ void k_cost_set(DevState* st, int gate, const double* __restrict__ tot) {
+  if (gate && !st->need_cost) return;
+  st->F = tot[0];
+  st->need_cost = 0;
+  if (!isfinite(tot[0])) st->err |= 2;
 }
 
 // Sum the cost pieces into st->F (initial cost / after set_params).
@@ -2157,13 +2451,16 @@ __device__ __forceinline__ bool lm_decide(double F, double Ft, double quad, doub
 }
 
 // Gain ratio, accept / reject and the damping update (one block).
+// tot (a point-partitioned problem, else NULL): the trial cost, the model's
+// quadratic term and gp . dp already summed over every part of the problem.
 static __global__ void k_lm_control(int npieces, const double* __restrict__ part, int ncb,
                              const double* __restrict__ dot_gc, int npb, const double* __restrict__ dot_gp,
                              double up, double down, double rho_good, double rho_bad, double lam_min,
-                             double lam_max, DevState* st, ba_iter_stats* __restrict__ stats, int cap) {
-  const double Ft = block_sum_array(part, npieces, PART);
-  const double quad = block_sum_array(part + 1, npieces, PART);
-  const double lin = block_sum_array(dot_gc, ncb, 1) + block_sum_array(dot_gp, npb, 1);
+                             double lam_max, DevState* st, ba_iter_stats* __restrict__ stats, int cap,
+                             const double* __restrict__ tot) {
+  const double Ft = tot ? tot[0] : block_sum_array(part, npieces, PART);
+  const double quad = tot ? tot[1] : block_sum_array(part + 1, npieces, PART);
+  const double lin = block_sum_array(dot_gc, ncb, 1) + (tot ? tot[2] : block_sum_array(dot_gp, npb, 1));
   if (threadIdx.x != 0) return;
   const double F = st->F;
   const long long t = st->trials;

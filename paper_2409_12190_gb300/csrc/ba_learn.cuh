@@ -83,15 +83,19 @@ __device__ inline bool chol_inv9(const double* __restrict__ A, double* __restric
   return true;
 }
 
+// probes of the coupling feature (k_coup_probe_in, k_coup_acc)
+constexpr int COUPLING_PROBES = 2;
+
 // Features x (FP32 [C][96]) and, when Ahat is given, A = chol(S^_ii)^{-1}
 // (FP32 [C][45], packed lower row-major) and D (double [C][9]).  Sii and U
-// are packed upper triangles [C][45]; lam the damping of U*.  A camera whose
-// S_ii is not positive definite gets x = 0, A = 0, D = 0.
+// are packed upper triangles [C][45]; lam the damping of U*; kap the
+// coupling sums of k_coup_acc (NULL: coupling 0).  A camera whose S_ii is
+// not positive definite gets x = 0, A = 0, D = 0.
 static __global__ void __launch_bounds__(CAM_THREADS)
 k_learn_features(int C, const double* __restrict__ Sii, const double* __restrict__ U,
                  const double* __restrict__ lam_ptr, double dmin, double dmax,
                  const int32_t* __restrict__ rowptr_cam, float* __restrict__ X, float* __restrict__ Ahat,
-                 double* __restrict__ Dout) {
+                 double* __restrict__ Dout, const double* __restrict__ kap) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= C) return;
   const double lam = *lam_ptr;
@@ -140,6 +144,7 @@ k_learn_features(int C, const double* __restrict__ Sii, const double* __restrict
   x[f++] = (float)(log10(lam) / 8.0);
   x[f++] = (float)(log10(1.0 + (double)(rowptr_cam[c + 1] - rowptr_cam[c])) / 4.0);
   x[f++] = 1.f;
+  x[f++] = kap ? (float)(log10(1.0 + sqrt(kap[c] / COUPLING_PROBES)) / 4.0) : 0.f;
   while (f < MLP_FIN) x[f++] = 0.f;
   if (Ahat)
     for (int a = 0; a < 9; ++a)
@@ -660,6 +665,66 @@ k_learn_start(int C, const double* __restrict__ Sii, const float* __restrict__ E
 
 // Probe vectors: p = D^{-1/2} z^_k (z^ [C][K][9] FP32) into the solver's p
 // and its pass form; zero for cameras without a scale.
+// The coupling feature (off-diagonal norm summary of camera i's block row
+// of S^ = D^{-1/2} S D^{-1/2}): kappa_i^2 = mean over COUPLING_PROBES
+// Rademacher probes z of |(S^ z)_i - S^_ii z_i|^2, whose expectation is
+// sum_{j != i} |S^_ij|_F^2.  Probe k's entry (c, a) is the sign bit of the
+// SplitMix64 output for the counter k << 40 | c << 4 | a (Steele, Lea and
+// Flood, OOPSLA 2014: golden-ratio increment, two xor-shift-multiply rounds,
+// a final xor-shift), the oracle's generator.
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long x) {
+  unsigned long long z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+__device__ __forceinline__ double coupling_sign(int k, int c, int a) {
+  const unsigned long long ctr = ((unsigned long long)k << 40) | ((unsigned long long)c << 4) | (unsigned long long)a;
+  return (splitmix64(ctr) >> 63) ? -1.0 : 1.0;
+}
+
+// p = D^{-1/2} z_k (D = diag(S_ii) from the packed blocks), also in the
+// passes' form.
+template <typename T, bool MF>
+static __global__ void k_coup_probe_in(int C, int k, const double* __restrict__ Sii, const T* __restrict__ camtab,
+                                       double* __restrict__ p, T* __restrict__ pT) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= C) return;
+  double x[9];
+  for (int a = 0; a < 9; ++a) {
+    const double d = Sii[45LL * c + sym9(a, a)];
+    x[a] = d > 0.0 ? coupling_sign(k, c, a) / sqrt(d) : 0.0;
+    p[9LL * c + a] = x[a];
+  }
+  write_pass_vec<T, MF>(camtab + (long long)CT * c, x, pT + (long long)pass_vec_stride(MF) * c);
+}
+
+// kap[c] (+)= |D^{-1/2} q_c - S^_cc z_k,c|^2 with q = S p (k = 0 starts the sum).
+static __global__ void k_coup_acc(int C, int k, const double* __restrict__ Sii, const double* __restrict__ q,
+                                  double* __restrict__ kap) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= C) return;
+  const double* S = Sii + 45LL * c;
+  double s[9], z[9];
+  bool ok = true;
+  for (int a = 0; a < 9; ++a) {
+    const double d = S[sym9(a, a)];
+    ok = ok && d > 0.0;
+    s[a] = d > 0.0 ? 1.0 / sqrt(d) : 0.0;
+    z[a] = coupling_sign(k, c, a);
+  }
+  double acc = 0.0;
+  if (ok) {
+    for (int a = 0; a < 9; ++a) {
+      double own = 0.0;
+      for (int b = 0; b < 9; ++b) own += S[sym9_rt(a, b)] * s[a] * s[b] * z[b];
+      const double off = q[9LL * c + a] * s[a] - own;
+      acc += off * off;
+    }
+  }
+  kap[c] = (k == 0 ? 0.0 : kap[c]) + acc;
+}
+
 template <typename T, bool MF>
 static __global__ void k_probe_in(int C, int K, int k, const float* __restrict__ zhat, const double* __restrict__ D,
                            const T* __restrict__ camtab, double* __restrict__ p, T* __restrict__ pT) {

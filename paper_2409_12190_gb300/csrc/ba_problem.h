@@ -53,6 +53,7 @@ struct ba_problem {
   void *cams = nullptr, *pts = nullptr;
   // linearisation
   void *camtab = nullptr, *Jcm = nullptr;
+  void* Jpm = nullptr;  // stored mode: the planes in point-major order (fused pass A)
   void *ptab = nullptr;  // [P][8]: X, 0, t, 0
   void *zbuf = nullptr;  // [O][4]: pass A1 output, camera-major
   void *cm_sw = nullptr, *pm_sw = nullptr;  // sqrt(w) per observation (recompute mode, robust loss)
@@ -72,6 +73,7 @@ struct ba_problem {
   float* Xf = nullptr;      // [C][96] features
   float* Ef = nullptr;      // [C][45] network output
   double* Dsc = nullptr;    // [C][9] scales diag(S_ii)
+  double* kap = nullptr;    // [C] coupling sums of the probes (feature 93)
   // direct solver (BA_SOLVER_CHOLESKY): dense S / its factor, work vector,
   // failure flag
   double* dS = nullptr;
@@ -101,7 +103,23 @@ struct ba_problem {
     }
     return e;
   }
+  // FP32 problems: an FP64 copy for the adjoint solve (ba_backward)
+  ba_problem* twin = nullptr;
+  // point-partitioned problem (ba_set_exchange): the caller's all-reduce and
+  // its device buffer; identity piece pointers and the per-camera /
+  // scalar partials exchanged; the first exchange error of a trial
+  ba_exchange_fn xch = nullptr;
+  void* xctx = nullptr;
+  double* xbuf = nullptr;
+  size_t xcap = 0;
+  int32_t* ident_ptr = nullptr;  // [C+1] = 0..C: one summed row per camera
+  double* camsum = nullptr;      // [C][PART] Schur-pass sums; [C][9] pass-B sums
+  double* U_loc = nullptr;       // [C][45] this part's U, [C][9] its gc
+  double* gc_loc = nullptr;
+  double* xscal = nullptr;       // [8] trial and cost sums
+  int xerr = 0;
   ~ba_problem() {
+    if (twin) ba_problem_destroy(twin);
     if (gexec) cudaGraphExecDestroy(gexec);
     for (void* v : allocs) cudaFree(v);
     if (ev_in) cudaEventDestroy(ev_in);

@@ -107,7 +107,9 @@ def test_learn_collect_matches_oracle():
     blk = orc.assemble(sc.cams_init, sc.points_init, sc.cam_idx, sc.pt_idx, pix)
     S, _, Us, _ = orc.schur_explicit(blk, sc.cam_idx, sc.pt_idx, lam)
     Sii = np.stack([S[9 * i:9 * i + 9, 9 * i:9 * i + 9] for i in range(sc.C)])
-    Xo, Ao, Do = pc.features(Sii, Us, lam, np.bincount(sc.cam_idx, minlength=sc.C))
+    # the coupling feature: the same SplitMix64 probes through the explicit S
+    Xo, Ao, Do = pc.features(Sii, Us, lam, np.bincount(sc.cam_idx, minlength=sc.C), pc.coupling(S, Sii))
+    assert np.all(Xo[:, 93] > 0.0)
     s = 1.0 / np.sqrt(Do.reshape(-1))
     Sh = S * s[:, None] * s[None, :]
     # y^ = S^ z^ with the explicit S of the oracle, probe by probe

@@ -148,3 +148,55 @@ def test_learned_solve_with_zero_network_is_block_jacobi_pcg(huber):
     dc0, dp0, its0, rel0 = orc.solve_damped(blk, sc.cam_idx, sc.pt_idx, 1e-3, opts)
     assert its == its0
     assert np.max(np.abs(dc - dc0)) <= 1e-9 * np.max(np.abs(dc0))
+
+
+def _random_spd_blocks(rng, C, coupling_scale=0.3):
+    n = 9 * C
+    A = rng.normal(size=(n, n))
+    S = A @ A.T + n * np.eye(n)
+    # weaken the coupling between cameras
+    mask = np.kron(np.eye(C), np.ones((9, 9)))
+    S = S * (mask + coupling_scale * (1 - mask))
+    Sii = np.stack([S[9 * c:9 * c + 9, 9 * c:9 * c + 9] for c in range(C)])
+    return S, Sii
+
+
+def test_coupling_is_the_off_diagonal_block_row_norm_in_expectation():
+    """E |(S^ z)_i - S^_ii z_i|^2 over Rademacher z is sum_{j != i} |S^_ij|_F^2:
+    with many probes the estimate converges to it (1/sqrt(K) relative)."""
+    rng = np.random.default_rng(5)
+    C = 5
+    S, Sii = _random_spd_blocks(rng, C)
+    d = np.diag(S)
+    Sh = S / np.sqrt(d[:, None] * d[None, :])
+    exact = np.array([sum(np.sum(Sh[9 * i:9 * i + 9, 9 * j:9 * j + 9] ** 2) for j in range(C) if j != i)
+                      for i in range(C)])
+    est = pc.coupling(S, Sii, K=3000) ** 2
+    assert np.max(np.abs(est - exact) / exact) < 0.08
+    # two probes (the features' setting): the right order of magnitude
+    two = pc.coupling(S, Sii) ** 2
+    assert np.all(two > 0.1 * exact) and np.all(two < 10 * exact)
+
+
+def test_coupling_vanishes_without_coupling_and_ignores_scales():
+    rng = np.random.default_rng(6)
+    C = 4
+    S, Sii = _random_spd_blocks(rng, C, coupling_scale=0.0)
+    # zero up to the rounding of the two products
+    assert np.all(pc.coupling(S, Sii) < 1e-12)
+    S, Sii = _random_spd_blocks(rng, C)
+    scale = np.exp(rng.normal(size=9 * C) * 3)
+    S2 = S * scale[:, None] * scale[None, :]
+    Sii2 = np.stack([S2[9 * c:9 * c + 9, 9 * c:9 * c + 9] for c in range(C)])
+    assert np.allclose(pc.coupling(S2, Sii2), pc.coupling(S, Sii), rtol=1e-12)
+
+
+def test_rademacher_probes_are_balanced_signs():
+    z0 = pc.rademacher(0, 1500)
+    z1 = pc.rademacher(1, 1500)
+    assert set(np.unique(z0)) == {-1.0, 1.0}
+    assert abs(z0.mean()) < 0.03 and abs(z1.mean()) < 0.03
+    # different probes are uncorrelated
+    assert abs(np.mean(z0 * z1)) < 0.03
+    # and neighbouring components of one probe too
+    assert abs(np.mean(z0[:, :-1] * z0[:, 1:])) < 0.03
