@@ -955,6 +955,12 @@ def run_learned(args):
     times = [out[n]["time_to_cost_s"] for n in names]
     reached = [t for t in times if t is not None]
     value = statistics.mean(reached) if reached and len(reached) == len(times) else None
+    # the preconditioners' own measure: PCG iterations over the leading
+    # trials in which block-Jacobi stays below the iteration cap (later
+    # trials all run to the cap, and their steps drift apart by truncation)
+    pcg_bj = out["block_jacobi"]["pcg_iters_per_trial"]
+    lead = next((i for i, n in enumerate(pcg_bj) if n >= LEARN_PCG_MAXITER), len(pcg_bj))
+    lead_iters = {n: sum(out[n]["pcg_iters_per_trial"][:lead]) for n in ["block_jacobi"] + names}
     line = {"metric": METRIC, "value": value, "unit": "s to 1e-6 relative cost", "n_gpus": 1,
             "steps": LEARN_TRIALS, "warmup": 1, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
@@ -970,7 +976,11 @@ def run_learned(args):
             "learned": {n: out[n] for n in names},
             "time_to_cost_by_seed": dict(zip(names, times)),
             "spread_s": (max(reached) - min(reached)) if reached else None,
-            "speedup_by_seed": {n: speedup(out, "block_jacobi", n) for n in names}}
+            "speedup_by_seed": {n: speedup(out, "block_jacobi", n) for n in names},
+            "uncapped_trials": lead,
+            "pcg_iters_uncapped": lead_iters,
+            "pcg_iters_change_by_seed": {n: lead_iters[n] / max(1, lead_iters["block_jacobi"]) - 1.0
+                                         for n in names}}
     print(json.dumps(line), flush=True)
 
 

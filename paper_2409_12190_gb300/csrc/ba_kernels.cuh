@@ -1830,15 +1830,6 @@ k_pass_fs(const int32_t* __restrict__ rowptr_pt, const int16_t* __restrict__ pm_
   const int4 h0 = chunk_hdr[2 * k], h1 = chunk_hdr[2 * k + 1];
   const int j0 = h0.x, j1 = h0.y, s0 = h0.z, s1 = h0.w, c0 = h1.x, nc = h1.y, cmin = h1.z;
   const bool small = s1 - s0 <= CHUNK_SLOTS;
-  // this thread's slots' camera positions, loaded before the staging
-  // barrier (every later load depends on the header only)
-  constexpr int U = CHUNK_SLOTS / CHUNK_THREADS;
-  int ll[U];
-#pragma unroll
-  for (int u = 0; u < U; ++u) {
-    const int q = s0 + threadIdx.x + u * CHUNK_THREADS;
-    ll[u] = (small && q < s1) ? pm_lc[q] : 0;
-  }
   for (int i = threadIdx.x; i < nc * 9; i += CHUNK_THREADS) {
     const int l = i / 9, e = i % 9;
     const int cam = cmin >= 0 ? cmin + l : chunk_cams[c0 + l];
@@ -1846,14 +1837,10 @@ k_pass_fs(const int32_t* __restrict__ rowptr_pt, const int16_t* __restrict__ pm_
   }
   __syncthreads();
   T za = 0, zb = 0, zc = 0;  // large chunk: this thread's share
-  for (int q = s0 + threadIdx.x, u = 0; q < s1; q += CHUNK_THREADS, ++u) {
+  for (int q = s0 + threadIdx.x; q < s1; q += CHUNK_THREADS) {
     T pl[NPLANE];
     load_planes(Jpm, O, q, pl);
-    int lq = 0;
-#pragma unroll
-    for (int v = 0; v < U; ++v)
-      if (v == u) lq = ll[v];
-    const T* xv = sxv + 9 * (small ? lq : pm_lc[q]);
+    const T* xv = sxv + 9 * pm_lc[q];
     T j0r[9], j1r[9];
     jc_rows(pl, j0r, j1r);
     T e0 = 0, e1 = 0;

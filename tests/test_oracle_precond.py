@@ -191,6 +191,15 @@ def test_coupling_vanishes_without_coupling_and_ignores_scales():
     assert np.allclose(pc.coupling(S2, Sii2), pc.coupling(S, Sii), rtol=1e-12)
 
 
+def test_splitmix64_matches_the_published_sequence():
+    """SplitMix64 seeded with 0 yields 0xe220a8397b1dcdaf, 0x6e789e6aa1b965f4,
+    0x06c45d188009454f (the generator's published first outputs; output n is
+    the mix of n+1 golden-ratio increments, i.e. splitmix64(n * golden))."""
+    golden, m64 = 0x9E3779B97F4A7C15, (1 << 64) - 1
+    want = [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+    assert [pc.splitmix64((n * golden) & m64) for n in range(3)] == want
+
+
 def test_rademacher_probes_are_balanced_signs():
     z0 = pc.rademacher(0, 1500)
     z1 = pc.rademacher(1, 1500)
