@@ -274,16 +274,17 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def measured_traffic(kernel, src_hash):
-    """dram bytes per launch of the kernel from a committed ncu summary, only
-    if it was taken on the current kernel source."""
+def measured_traffic(kernel, src_hash, prec):
+    """dram bytes per launch of the kernel class at this precision from a
+    committed ncu summary, only if it was taken on the current kernel
+    source."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         with open(path) as fh:
             d = json.load(fh)
     except (OSError, ValueError):
         return None
-    e = d.get(kernel)
+    e = d.get(f"{kernel}_{prec}")
     if not e or e.get("source_hash") != src_hash:
         return None
     return e.get("dram_bytes_per_launch")
@@ -442,7 +443,7 @@ def kernel_table(per, C, P, O, lay, tsize, mf, huber, alu_peak):
     return out
 
 
-def roofline_of(kernels, per, hbm_peak, hbm_kind, alu_peak, alu_source, src_hash, prof_ms, it_bytes):
+def roofline_of(kernels, per, hbm_peak, hbm_kind, alu_peak, alu_source, src_hash, prof_ms, it_bytes, prec):
     """Roofline block of the dominant kernel (largest share of the profiled
     time among the kernels with an algorithmic byte count): its HBM and ALU
     fractions; "bound" is the larger of the two."""
@@ -451,7 +452,7 @@ def roofline_of(kernels, per, hbm_peak, hbm_kind, alu_peak, alu_source, src_hash
     hbm = {"achieved": kr["gbs"], "peak": hbm_peak, "unit": "GB/s", "frac": kr["gbs"] / hbm_peak,
            "peak_source": hbm_kind}
     roof = {"bound": "hbm", "kernel": dom, **hbm, "bytes_per_launch": kr["bytes_per_launch"],
-            "traffic": measured_traffic(dom, src_hash), "kernel_source": src_hash, "hbm": hbm}
+            "traffic": measured_traffic(dom, src_hash, prec), "kernel_source": src_hash, "hbm": hbm}
     if "tflops" in kr:
         alu = {"achieved": kr["tflops"], "peak": alu_peak, "unit": "TFLOP/s", "frac": kr["alu_frac"],
                "flops_per_launch": kr["flops_per_launch"], "peak_source": alu_source}
@@ -514,7 +515,7 @@ def run_precision(args, prec, scene, ci, pi, pix, dev, world, f_ref, peaks_d, ba
     kernels = kernel_table(per, C, P, O, lay, tsize, mf, huber, alu_peak)
     it_bytes = sum(algorithmic_bytes(k, C, P, O, lay["pieces"], tsize, mf, huber) * per[k][1] for k in per)
     roof = roofline_of(kernels, per, peaks_d["hbm_gbs"], peaks_d["hbm_kind"], alu_peak, alu_source,
-                       kernel_source_hash(), prof_ms, it_bytes)
+                       kernel_source_hash(), prof_ms, it_bytes, prec)
 
     # end to end through the public API: the same trials as the timed region
     # (restarted from its starting state), each step uploading parameters and

@@ -585,6 +585,110 @@ ba_status ba_mlp_train(float* params, float* adam_m, float* adam_v, int n, int K
                        const float* Ahat, const float* Yhat, const float* Zhat, int epochs, int batch,
                        double lr, double* loss_hist, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Pose-graph optimisation (Sec. IV-D, "Generalization to Other
+ * Optimization Problems", Eqs. 3-4): poses zeta_i in SE(3), edges e = (i,
+ * j) with a measured relative pose T_e and a 6 x 6 information matrix
+ * Omega_e; minimise F = 1/2 sum_e r_e^T Omega_e r_e with
+ * r_e = Log(zeta_i^{-1} zeta_j T_e^{-1}), by the LM loop of Alg. 1 with
+ * the bundle-adjustment loop's options, statistics and decision rule.
+ *
+ * Conventions (readings: the paper leaves them to its Lie-group library):
+ *  - a pose is 7 doubles (tx, ty, tz, qx, qy, qz, qw); quaternions are
+ *    normalised on input and returned unit with qw >= 0;
+ *  - tangent vectors are (rho, phi), translation first; an LM step updates
+ *    zeta_i <- Exp(delta_i) zeta_i (left retraction);
+ *  - info is the upper triangle of Omega_e, row by row, 21 doubles;
+ *  - fixed (optional, uint8 [N], nonzero = fixed) holds poses in place: the
+ *    cost is invariant under a common SE(3) motion of all poses (gauge), so
+ *    a problem normally fixes one.
+ * Everything is FP64 (ba_options.precision must be BA_PREC_F64, huber_delta
+ * 0).  BA_SOLVER_PCG runs block-Jacobi PCG (6 x 6 blocks) on the implicit
+ * product (H x)_i = sum_{e at i} B_e (x_i - x_other), B_e = A_e^T Omega_e
+ * A_e, in one cooperative launch whose grid barriers wait at most about a
+ * second (BA_ERR_TIMEOUT); BA_SOLVER_CHOLESKY factors the dense 6N x 6N
+ * system H + D, for 6N <= BA_DENSE_MAX_DIM.
+ * ------------------------------------------------------------------------ */
+typedef struct ba_pgo ba_pgo; /* opaque, owned by the library */
+
+/* Create a pose graph (Sec. IV-D, Eq. 3) of N >= 2 poses and E >= 1 edges:
+ * poses (any,
+ * [N][7]), ei / ej (any, int32 [E], distinct nodes in [0, N)), meas (any,
+ * [E][7], T_e), info (any, [E][21]), fixed (any, uint8 [N], or NULL: none).
+ * Evaluates the initial cost.  Errors: BA_ERR_INVALID_ARG (sizes, NULL
+ * arrays, an index out of range or an edge from a node to itself, options);
+ * BA_ERR_NONFINITE (a non-finite or zero-quaternion input, a non-finite
+ * cost); BA_ERR_OOM.  Synchronises the stream; on error *out is NULL. */
+ba_status ba_pgo_create(ba_pgo** out, int N, int E, const double* poses,
+                        const int32_t* ei, const int32_t* ej,
+                        const double* meas, const double* info,
+                        const uint8_t* fixed, const ba_options* opt,
+                        void* stream);
+
+/* Free a pose graph (NULL is accepted); not in the paper (resource
+ * management). */
+ba_status ba_pgo_destroy(ba_pgo* h);
+
+/* Run iters LM trials of the pose graph (Alg. 1, Sec. IV-D; a rejected
+ * trial counts as one).  Synchronises the stream at the end and reports a device error of any
+ * trial (BA_ERR_TIMEOUT for a PCG barrier that ran out). */
+ba_status ba_pgo_solve(ba_pgo* h, int iters, void* stream);
+
+/* Current poses Z of Eq. 3 into poses_out (any, [N][7]).  Synchronises. */
+ba_status ba_pgo_get_poses(ba_pgo* h, double* poses_out, void* stream);
+
+/* Replace the poses Z of Eq. 3 (any, [N][7]) and re-evaluate the cost;
+ * lambda and the statistics are kept.  Synchronises. */
+ba_status ba_pgo_set_poses(ba_pgo* h, const double* poses, void* stream);
+
+/* The last min(cap, trials run, max_stats) LM trial records (Alg. 1),
+ * oldest first, into host_out; *n_out gets the count.  Synchronises the
+ * device. */
+ba_status ba_pgo_get_stats(ba_pgo* h, ba_iter_stats* host_out, int cap,
+                           int* n_out);
+
+/* Cost F of Eq. 3 at the current poses and the damping of the next trial
+ * (Alg. 1).  Synchronises the device. */
+ba_status ba_pgo_get_scalars(ba_pgo* h, double* cost, double* lambda);
+
+/* Damping lambda of the next trial (Alg. 1, > 0).  Synchronises the
+ * device. */
+ba_status ba_pgo_set_lambda(ba_pgo* h, double lambda);
+
+/* Step-level access for parity checks (the residual of Eq. 4 and its
+ * Jacobian, Sec. IV-D), at the current poses (each output
+ * is any and optional, NULL to skip): r [E][6] residuals, A [E][36]
+ * row-major dr_e/d(delta_j) = J_l(r_e)^{-1} Ad(zeta_i^{-1}) (dr_e/d(delta_i)
+ * = -A), B [E][36] = A^T Omega A, Hd [N][21] the upper triangles of the
+ * diagonal blocks H_ii, g [N][6] = J^T Omega r, *cost = F.  Synchronises. */
+ba_status ba_pgo_linearize(ba_pgo* h, double* r, double* A, double* B,
+                           double* Hd, double* g, double* cost, void* stream);
+
+/* y = (H + D) x (the damped system of Alg. 1 for Eq. 3) at the current
+ * poses with D = lambda clamp(diag H_ii,
+ * diag_min, diag_max), over the free poses (x taken as 0 and y set to 0 at
+ * fixed ones); x, y any [N][6].  Synchronises. */
+ba_status ba_pgo_matvec(ba_pgo* h, double lambda, const double* x, double* y,
+                        void* stream);
+
+/* Solve (H + D) dx = -g (one LM step of Alg. 1, Sec. IV-C solvers) at the
+ * current poses (fixed poses: dx = 0) with the problem's solver (PCG: maxiter, tol; Cholesky: both ignored); dx any
+ * [N][6]; *iters, *rel (optional) the PCG iterations and |r|/|b| at exit.
+ * The LM state is not changed.  Synchronises. */
+ba_status ba_pgo_damped_solve(ba_pgo* h, double lambda, int maxiter,
+                              double tol, double* dx, int* iters, double* rel,
+                              void* stream);
+
+/* Synthetic inputs (not in the paper, which reads benchmark files) from
+ * given poses (any [N][7]): meas_out (any, [E][7]) =
+ * Exp(noise_e) zeta_i^{-1} zeta_j with noise (any, [E][6]) and, if
+ * init_out is not NULL, init_out (any, [N][7]) = Exp(drift_n) zeta_n with
+ * drift (any, [N][6]).  Synchronises. */
+ba_status ba_pgo_synthesize(int N, int E, const double* poses_gt,
+                            const int32_t* ei, const int32_t* ej,
+                            const double* noise, const double* drift,
+                            double* meas_out, double* init_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

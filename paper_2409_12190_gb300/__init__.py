@@ -23,7 +23,7 @@ from ._lib import BAError, BA_PREC_F32, BA_PREC_F64
 
 __all__ = ["Options", "Problem", "Batch", "project", "csr_build", "kernel_launch_count",
            "BAError", "library_path", "bundle_adjust", "MLP_NPARAM", "MLP_FIN", "mlp_init",
-           "mlp_forward", "mlp_loss_grad", "mlp_train"]
+           "mlp_forward", "mlp_loss_grad", "mlp_train", "PoseGraph"]
 
 MLP_NPARAM = _lib.BA_MLP_NPARAM
 MLP_FIN = _lib.BA_MLP_FIN
@@ -621,3 +621,6 @@ def measure_fma_peak(precision: str = "f64", stream=None) -> float:
 
 def kernel_launch_count() -> int:
     return int(_L().ba_kernel_launch_count())
+
+
+from .pgo import PoseGraph  # noqa: E402  (needs the helpers above)

@@ -118,6 +118,18 @@ SIGNATURES = {
     "ba_mlp_forward": (_S, [_VP, _I, _VP, _VP, _VP]),
     "ba_mlp_loss_grad": (_S, [_VP, _I, _I, _VP, _VP, _VP, _VP, _VP, ct.POINTER(_D), _VP]),
     "ba_mlp_train": (_S, [_VP, _VP, _VP, _I, _I, _VP, _VP, _VP, _VP, _I, _I, _D, _VP, _VP]),
+    "ba_pgo_create": (_S, [ct.POINTER(_VP), _I, _I, _VP, _VP, _VP, _VP, _VP, _VP, ct.POINTER(ba_options), _VP]),
+    "ba_pgo_destroy": (_S, [_VP]),
+    "ba_pgo_solve": (_S, [_VP, _I, _VP]),
+    "ba_pgo_get_poses": (_S, [_VP, _VP, _VP]),
+    "ba_pgo_set_poses": (_S, [_VP, _VP, _VP]),
+    "ba_pgo_get_stats": (_S, [_VP, ct.POINTER(ba_iter_stats), _I, ct.POINTER(_I)]),
+    "ba_pgo_get_scalars": (_S, [_VP, ct.POINTER(_D), ct.POINTER(_D)]),
+    "ba_pgo_set_lambda": (_S, [_VP, _D]),
+    "ba_pgo_linearize": (_S, [_VP, _VP, _VP, _VP, _VP, _VP, ct.POINTER(_D), _VP]),
+    "ba_pgo_matvec": (_S, [_VP, _D, _VP, _VP, _VP]),
+    "ba_pgo_damped_solve": (_S, [_VP, _D, _I, _D, _VP, ct.POINTER(_I), ct.POINTER(_D), _VP]),
+    "ba_pgo_synthesize": (_S, [_I, _I, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
 }
 
 BA_MLP_FIN = 96

@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libba_gb300.so")
-UNITS = ["ba_api.cu", "ba_sort.cu", "ba_noalloc.cu", "ba_batch.cu", "ba_learn.cu", "ba_measure.cu"]
+UNITS = ["ba_api.cu", "ba_sort.cu", "ba_noalloc.cu", "ba_batch.cu", "ba_learn.cu", "ba_measure.cu", "ba_pgo.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -30,7 +30,7 @@ import math
 import numpy as np
 
 __all__ = ["Scene", "ring_scene", "arc_scene", "batch_scenes", "config_scene",
-           "subsample_points"]
+           "subsample_points", "PoseGraph", "sphere_graph", "garage_graph", "pose_graph_config"]
 
 
 @dataclasses.dataclass
@@ -236,3 +236,144 @@ def config_scene(which: str, *, small: bool = False) -> Scene:
         return ring_scene(64, 1000 if small else 10000, seed=5,
                           view_p=1.0 / 7.0, name="ba64")
     raise ValueError(f"unknown scene {which!r}")
+
+
+# --------------------------------------------------------------------------
+# Pose graphs (the paper's PGO problem, Sec. IV-D)
+# --------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class PoseGraph:
+    """A seeded pose graph.  A caller builds the measured relative poses and
+    the initial estimate with its own SE(3) arithmetic as
+
+        T_ij   = Exp(noise_e) zeta_i^{-1} zeta_j      (left noise: at the
+                                                        truth r_e = -noise_e)
+        zeta_i(init) = Exp(drift_i) zeta_i
+
+    Tangent vectors are (translation, rotation); poses are (t, q) with the
+    quaternion (qx, qy, qz, qw); info is the upper triangle of each edge's
+    6 x 6 information matrix, row by row, matched to the noise's covariance."""
+    poses_gt: np.ndarray   # [N, 7]
+    ei: np.ndarray         # [E] int32
+    ej: np.ndarray         # [E] int32
+    noise: np.ndarray      # [E, 6]
+    info: np.ndarray       # [E, 21]
+    drift: np.ndarray      # [N, 6]
+    name: str = ""
+
+    @property
+    def N(self) -> int:
+        return int(self.poses_gt.shape[0])
+
+    @property
+    def E(self) -> int:
+        return int(self.ei.shape[0])
+
+
+def _yaw_pitch_quat(yaw, pitch):
+    """Unit quaternion (x, y, z, w) of Rz(yaw) Ry(pitch)."""
+    sz, cz = np.sin(0.5 * yaw), np.cos(0.5 * yaw)
+    sy, cy = np.sin(0.5 * pitch), np.cos(0.5 * pitch)
+    return np.stack([-sz * sy, cz * sy, sz * cy, cz * cy], -1)
+
+
+def _graph_noise(rng, E, sigma_t, sigma_r, full_info):
+    """Edge noise and the matching information matrices: covariance
+    Q diag(s^2) Q^T with s = (sigma_t x 3, sigma_r x 3) and Q = I, or a random
+    orthogonal Q (full_info); info = its inverse."""
+    s = np.array([sigma_t] * 3 + [sigma_r] * 3)
+    z = rng.normal(size=(E, 6)) * s
+    iu = np.triu_indices(6)
+    if not full_info:
+        info = np.zeros((E, 21))
+        info[:, [k for k, (a, b) in enumerate(zip(*iu)) if a == b]] = 1.0 / (s * s)
+        return z, info
+    Q, _ = np.linalg.qr(rng.normal(size=(E, 6, 6)))
+    noise = np.einsum("eab,eb->ea", Q, z)
+    Om = np.einsum("eab,b,ecb->eac", Q, 1.0 / (s * s), Q)
+    return noise, Om[:, iu[0], iu[1]]
+
+
+def _pick(rng, cand, n):
+    cand = np.asarray(cand, dtype=np.int64).reshape(-1, 2)
+    if n is not None and n < len(cand):
+        cand = cand[np.sort(rng.choice(len(cand), size=n, replace=False))]
+    return cand
+
+
+def _graph(rng, pos, quat, closures, *, sigma_t, sigma_r, drift_t, drift_r, full_info, name):
+    N = pos.shape[0]
+    odo = np.stack([np.arange(N - 1), np.arange(1, N)], 1)
+    edges = np.concatenate([odo, closures], 0)
+    noise, info = _graph_noise(rng, len(edges), sigma_t, sigma_r, full_info)
+    # initial estimate: a random walk along the node order (odometry drift),
+    # node 0 exact
+    steps = rng.normal(size=(N, 6)) * np.array([drift_t] * 3 + [drift_r] * 3)
+    steps[0] = 0.0
+    return PoseGraph(poses_gt=np.concatenate([pos, quat], 1), ei=edges[:, 0].astype(np.int32),
+                     ej=edges[:, 1].astype(np.int32), noise=noise, info=info, drift=np.cumsum(steps, 0),
+                     name=name)
+
+
+def sphere_graph(rings: int, per_ring: int, *, seed: int, n_closures=None, radius: float = 50.0,
+                 sigma_t: float = 0.05, sigma_r: float = 0.01, drift_t: float = 0.02,
+                 drift_r: float = 0.004, full_info: bool = False, name: str = "sphere") -> PoseGraph:
+    """Poses on a sphere, visited ring by ring (latitude rings of per_ring
+    nodes, heading along the ring): odometry edges between consecutive nodes
+    and loop closures from node (ring r, index m) to ring r+1 at indices
+    m-1, m, m+1 (a random n_closures of them)."""
+    rng = np.random.default_rng(seed)
+    k = np.arange(rings * per_ring)
+    ring, m = k // per_ring, k % per_ring
+    lat = -0.5 * np.pi + np.pi * (ring + 0.5) / rings
+    lon = 2.0 * np.pi * m / per_ring
+    pos = radius * np.stack([np.cos(lat) * np.cos(lon), np.cos(lat) * np.sin(lon), np.sin(lat)], 1)
+    quat = _yaw_pitch_quat(lon + 0.5 * np.pi, -lat)
+    cand = [(r * per_ring + a, (r + 1) * per_ring + (a + d) % per_ring)
+            for r in range(rings - 1) for a in range(per_ring) for d in (-1, 0, 1)]
+    return _graph(rng, pos, quat, _pick(rng, cand, n_closures), sigma_t=sigma_t, sigma_r=sigma_r,
+                  drift_t=drift_t, drift_r=drift_r, full_info=full_info, name=name)
+
+
+def garage_graph(laps: int, per_lap: int, *, seed: int, n_closures=None, side: float = 40.0,
+                 rise: float = 3.0, sigma_t: float = 0.02, sigma_r: float = 0.005, drift_t: float = 0.01,
+                 drift_r: float = 0.002, full_info: bool = False, name: str = "garage") -> PoseGraph:
+    """A drive round a square ramp (a parking garage): per_lap nodes per lap,
+    rising by `rise` per lap, heading along the path; odometry edges and loop
+    closures from each node to the previous lap's nodes at offsets -2..2 (a
+    random n_closures of them)."""
+    rng = np.random.default_rng(seed)
+    k = np.arange(laps * per_lap)
+    s = 4.0 * (k % per_lap) / per_lap            # position along the square, 0..4
+    side_i = np.floor(s).astype(int)
+    f = s - side_i
+    corners = side * np.array([[0.0, 0.0], [1.0, 0.0], [1.0, 1.0], [0.0, 1.0], [0.0, 0.0]])
+    xy = corners[side_i] + f[:, None] * (corners[side_i + 1] - corners[side_i])
+    z = rise * k / per_lap
+    pos = np.concatenate([xy, z[:, None]], 1)
+    yaw = 0.5 * np.pi * side_i
+    pitch = -np.arctan2(rise, 4.0 * side) * np.ones_like(yaw)
+    quat = _yaw_pitch_quat(yaw, pitch)
+    cand = [(a - per_lap + d, a) for a in range(per_lap, laps * per_lap) for d in (-2, -1, 0, 1, 2)
+            if 0 <= a - per_lap + d < a - 1]
+    return _graph(rng, pos, quat, _pick(rng, cand, n_closures), sigma_t=sigma_t, sigma_r=sigma_r,
+                  drift_t=drift_t, drift_r=drift_r, full_info=full_info, name=name)
+
+
+def pose_graph_config(which: str) -> PoseGraph:
+    """The named pose graphs (node and edge counts of the paper's PGO
+    benchmark files, Table VIII; synthetic geometry and noise).
+
+    ``sphere2500``  2,500 nodes (50 rings of 50), 9,799 edges, seed 21.
+    ``garage1661``  1,661 nodes (11 laps of 151), 6,275 edges, seed 22.
+    ``sphere100``   100 nodes (10 rings of 10), full information matrices,
+                    seed 23: the small case the oracle runs in seconds.
+    """
+    if which == "sphere2500":
+        return sphere_graph(50, 50, seed=21, n_closures=9799 - 2499, name="sphere2500")
+    if which == "garage1661":
+        return garage_graph(11, 151, seed=22, n_closures=6275 - 1660, name="garage1661")
+    if which == "sphere100":
+        return sphere_graph(10, 10, seed=23, radius=10.0, full_info=True, name="sphere100")
+    raise ValueError(f"unknown pose graph {which!r}")

@@ -54,11 +54,12 @@ def test_measured_traffic_only_for_the_source_it_was_taken_on(tmp_path, monkeypa
     prof = tmp_path / "profiles"
     prof.mkdir()
     (prof / "ncu_traffic.json").write_text(json.dumps(
-        {"pass_fa": {"dram_bytes_per_launch": 1.5e8, "source_hash": "abc"}}))
+        {"pass_fa_f64": {"dram_bytes_per_launch": 1.5e8, "source_hash": "abc"}}))
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    assert bench.measured_traffic("pass_fa", "abc") == 1.5e8
-    assert bench.measured_traffic("pass_fa", "def") is None
-    assert bench.measured_traffic("pass_b", "abc") is None
+    assert bench.measured_traffic("pass_fa", "abc", "f64") == 1.5e8
+    assert bench.measured_traffic("pass_fa", "def", "f64") is None
+    assert bench.measured_traffic("pass_fa", "abc", "f32") is None
+    assert bench.measured_traffic("pass_b", "abc", "f64") is None
 
 
 def test_kernel_source_hash_is_stable_and_short():
