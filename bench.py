@@ -74,7 +74,7 @@ def parse():
                     help="skip F_ref and the time-to-cost runs (profiling only)")
     ap.add_argument("--points", type=int, default=0,
                     help="profiling only: same recipe with fewer points")
-    ap.add_argument("--workload", choices=["ba4000", "batch512", "learned", "adjoint"], default="ba4000",
+    ap.add_argument("--workload", choices=["ba4000", "batch512", "learned", "adjoint", "pgo"], default="ba4000",
                     help="batch512: 512 sliding-window problems solved by one persistent launch; "
                          "learned: time to 1e-6 relative cost with the learned block-Jacobi correction")
     ap.add_argument("--train-scenes", type=int, default=200, help="learned: training scenes")
@@ -1053,6 +1053,148 @@ def run_adjoint(args):
     print(json.dumps(line), flush=True)
 
 
+# --------------------------------------------------------------------------
+# pgo: pose-graph optimisation (Sec. IV-D) on the paper's PGO graph sizes
+# --------------------------------------------------------------------------
+
+PGO_GRAPHS = ("sphere2500", "garage1661")
+PGO_PCG = (2000, 1e-6)        # PCG maxiter, tol per LM trial
+PGO_STOP = 1e-9               # converged: an accepted trial gains less than this (relative)
+PGO_MAX_TRIALS = 100
+
+
+def pgo_flops_per_iteration(N, E):
+    """FP64 flops of one PCG iteration on the pose graph: the product (each
+    edge's B (x_i - x_j) at both ends: 2 x (36 FMA + 6 subtractions)), the
+    damping term, the 6 x 6 block-Jacobi product per node, and the vector
+    updates and three dot products."""
+    return 156 * E + N * (6 + 72 + 4 * 6 + 2 * 6 + 3 * 2 * 6)
+
+
+def _pgo_solve_to_convergence(pg, stream):
+    """LM trials one at a time until an accepted trial gains less than
+    PGO_STOP (relative) or PGO_MAX_TRIALS; returns (seconds, trials, stats)."""
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    trials = 0
+    while trials < PGO_MAX_TRIALS:
+        pg.solve(1)
+        trials += 1
+        st = pg.stats(cap=1)[-1]
+        if st["accepted"] and st["cost"] - st["cost_trial"] <= PGO_STOP * st["cost"]:
+            break
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1000.0, trials, pg.stats(cap=PGO_MAX_TRIALS)
+
+
+def _pgo_oracle_trial(which):
+    """One LM trial of the oracle (PCG with the bench's settings) on the graph,
+    seconds; spawned so that its BLAS threads are its own."""
+    import oracle as orc
+    from oracle import pgo as opgo
+    g = scenegen.pose_graph_config(which)
+    Ts, Tms, infos, _ = opgo.graph_inputs(g)
+    fixed = np.zeros(g.N, bool)
+    fixed[0] = True
+    t0 = time.perf_counter()
+    opgo.lm(Ts, g.ei, g.ej, Tms, infos, 1, orc.LMOptions(solver="pcg", pcg_maxiter=PGO_PCG[0], pcg_tol=PGO_PCG[1]),
+            fixed)
+    return time.perf_counter() - t0
+
+
+def run_pgo(args):
+    import torch
+    import paper_2409_12190_gb300 as ba
+    from paper_2409_12190_gb300 import build as bbuild
+    from paper_2409_12190_gb300.pgo import PoseGraph, synthesize
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    bbuild.build()
+    stream = torch.cuda.current_stream()
+    graphs = {}
+    clocks = ClockSampler(local)
+    time.sleep(0.3)
+    n0 = ba.kernel_launch_count()
+    for which in PGO_GRAPHS:
+        g = scenegen.pose_graph_config(which)
+        meas, init = synthesize(g.poses_gt, g.ei, g.ej, g.noise, g.drift, device=dev)
+        out = {"nodes": g.N, "edges": g.E}
+        for solver in ("pcg", "cholesky"):
+            opts = ba.Options(precision="f64", solver=solver, pcg_maxiter=PGO_PCG[0], pcg_tol=PGO_PCG[1])
+            with PoseGraph(init, g.ei, g.ej, meas, g.info, options=opts, device=dev) as warm:
+                warm.solve(2)
+            with PoseGraph(init, g.ei, g.ej, meas, g.info, options=opts, device=dev) as pg:
+                F0, _ = pg.scalars()
+                secs, trials, st = _pgo_solve_to_convergence(pg, stream)
+                F, _ = pg.scalars()
+                rec = {"time_s": secs, "trials": trials, "ms_per_trial": 1000.0 * secs / trials,
+                       "initial_cost": F0, "final_cost": F, "chi2": 2.0 * F,
+                       "pcg_iters_total": int(sum(t["pcg_iters"] for t in st)),
+                       "accepted": int(sum(t["accepted"] for t in st))}
+                if solver == "pcg":
+                    # PCG iteration time: K iterations of the damped solve at the
+                    # converged poses, less the same call with no iteration
+                    pg.damped_solve(1e-6, 0, 0.0)
+                    times = {}
+                    for K in (0, 500):
+                        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                        e0.record(stream)
+                        for _ in range(3):
+                            pg.damped_solve(1e-6, K, 0.0)
+                        e1.record(stream)
+                        torch.cuda.synchronize()
+                        times[K] = e0.elapsed_time(e1) / 3.0
+                    it_us = 1000.0 * (times[500] - times[0]) / 500.0
+                    fl = pgo_flops_per_iteration(g.N, g.E)
+                    rec["pcg_iteration_us"] = it_us
+                    rec["pcg_iteration_tflops"] = fl / (it_us * 1e-6) / 1e12
+            out[solver] = rec
+        out["final_cost_rel_diff_pcg_vs_cholesky"] = abs(out["pcg"]["final_cost"] - out["cholesky"]["final_cost"]) / \
+            out["cholesky"]["final_cost"]
+        graphs[which] = out
+    launches = ba.kernel_launch_count() - n0
+    clk = clocks.stop()
+    peaks_d = measured_peaks_fp64(dev)
+    head = graphs[PGO_GRAPHS[0]]
+    fl = pgo_flops_per_iteration(head["nodes"], head["edges"])
+    roof = {"bound": "alu", "kernel": "k_pgo_pcg (one PCG iteration)", "achieved": head["pcg"]["pcg_iteration_tflops"],
+            "peak": peaks_d, "unit": "TFLOP/s", "frac": head["pcg"]["pcg_iteration_tflops"] / peaks_d,
+            "flops_per_iteration": fl, "peak_source": "measured (ba_measure_fma_peak, FP64)", "traffic": None,
+            "note": "the graph's arrays (B: 288 B per edge) stay in L2; the iteration is bound by FP64 issue and "
+                    "its two grid barriers"}
+    cpu = None
+    if not args.no_cpu_baseline:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(1) as pool:
+            t_or = pool.apply(_pgo_oracle_trial, ("garage1661",))
+        gpu_trial_s = graphs["garage1661"]["pcg"]["ms_per_trial"] / 1000.0
+        cpu = {"value": 1.0 / t_or, "unit": "LM trials/s", "cores": 1, "kind": "oracle",
+               "sample": f"one LM trial of the oracle on garage1661 (PCG maxiter {PGO_PCG[0]}, tol {PGO_PCG[1]}), "
+                         f"{t_or:.1f} s", "gpu_trials_per_s_same_graph": 1.0 / gpu_trial_s}
+    line = {"metric": "PGO time to converged cost (s), sphere2500 with PCG", "value": head["pcg"]["time_s"],
+            "unit": "s", "n_gpus": 1, "steps": head["pcg"]["trials"], "warmup": 2,
+            "ms_per_step": head["pcg"]["ms_per_trial"], "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "pgo", "graphs": {k: f"{v['nodes']} nodes, {v['edges']} edges"
+                                                     for k, v in graphs.items()},
+                       "pcg": f"block-Jacobi 6x6, maxiter {PGO_PCG[0]}, tol {PGO_PCG[1]}",
+                       "stop": f"first accepted trial gaining < {PGO_STOP} relative, at most {PGO_MAX_TRIALS} trials",
+                       "gauge": "pose 0 fixed", "l2": "the whole graph fits in L2 (problem sizes of the paper's PGO "
+                                                     "benchmark files)"},
+            "graphs": graphs, "gpu_launches": launches, "clocks": clk, "roofline": roof, "cpu_baseline": cpu}
+    print(json.dumps(line), flush=True)
+
+
+def measured_peaks_fp64(dev):
+    import paper_2409_12190_gb300 as ba
+    return ba.measure_fma_peak("f64")
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -1063,6 +1205,8 @@ def main():
         run_learned(args)
     elif args.workload == "adjoint":
         run_adjoint(args)
+    elif args.workload == "pgo":
+        run_pgo(args)
     else:
         run_ours(args)
 

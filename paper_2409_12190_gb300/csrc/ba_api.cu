@@ -324,7 +324,7 @@ void enqueue_dense_solve(ba_problem* h, const double* lam_ptr) {
   }
   {
     Prof pr(h, BA_K_OTHER);
-    k_dense_solve<<<1, 1024, 0, s>>>(n, h->dS, h->r, h->dy, h->x, h->dfail, h->st);
+    k_dense_solve<<<1, 1024, 0, s>>>(n, n - 1, h->dS, h->r, h->dy, h->x, h->dfail, h->st);
     count_launch();
   }
 }

@@ -235,11 +235,12 @@ k_chol_update(int n, int kb, double* __restrict__ A) {
 // x = (L L^T)^{-1} b (b = r, the reduced right-hand side); one CTA, by
 // blocks of DB unknowns: solve a block's DB x DB triangle (one thread, in
 // order), then update every remaining right-hand-side entry with the block
-// (coalesced rows of L).  With a failed factorisation x = 0 (the LM trial
-// is then a rejection) and the failure is counted in st->fallbacks.  Writes
-// the solve's statistics.
+// (coalesced rows of L).  bw: the half-bandwidth of L (L_ij = 0 for
+// i - j > bw; n - 1 for a dense matrix), which bounds those updates.  With a
+// failed factorisation x = 0 (the LM trial is then a rejection) and the
+// failure is counted in st->fallbacks.  Writes the solve's statistics.
 static __global__ void __launch_bounds__(1024)
-k_dense_solve(int n, const double* __restrict__ L, const double* __restrict__ b, double* __restrict__ y,
+k_dense_solve(int n, int bw, const double* __restrict__ L, const double* __restrict__ b, double* __restrict__ y,
               double* __restrict__ x, const int* __restrict__ fail, DevState* st) {
   __shared__ double sb[DB];
   const int tid = threadIdx.x;
@@ -260,7 +261,8 @@ k_dense_solve(int n, const double* __restrict__ L, const double* __restrict__ b,
         }
       }
       __syncthreads();
-      for (int i = k + nb + tid; i < n; i += blockDim.x) {
+      const int iend = min(n, k + nb + bw);
+      for (int i = k + nb + tid; i < iend; i += blockDim.x) {
         double v = 0.0;
         for (int c = 0; c < nb; ++c) v += L[(long long)i * n + k + c] * sb[c];
         y[i] -= v;
@@ -279,7 +281,7 @@ k_dense_solve(int n, const double* __restrict__ L, const double* __restrict__ b,
         }
       }
       __syncthreads();
-      for (int i = tid; i < k; i += blockDim.x) {
+      for (int i = max(0, k - bw) + tid; i < k; i += blockDim.x) {
         double v = 0.0;
         for (int c = 0; c < nb; ++c) v += L[(long long)(k + c) * n + i] * sb[c];
         y[i] -= v;

@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -30,11 +31,14 @@ inline unsigned nb(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
 // Per-incidence code from the stable sort of the 2E incidence keys
 // [ei..., ej...]: 2 e for an edge's first node, 2 e + 1 for its second.
-__global__ void k_pgo_inc_codes(int E, const int32_t* __restrict__ perm, int32_t* __restrict__ inc) {
+__global__ void k_pgo_inc_codes(int E, const int32_t* __restrict__ perm, const int32_t* __restrict__ ei,
+                                const int32_t* __restrict__ ej, int32_t* __restrict__ inc, int2* __restrict__ inc2) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= 2 * E) return;
   const int k = perm[s];
-  inc[s] = k < E ? 2 * k : 2 * (k - E) + 1;
+  const int e = k < E ? k : k - E;
+  inc[s] = k < E ? 2 * e : 2 * e + 1;
+  inc2[s] = make_int2(e, k < E ? ej[e] : ei[e]);  // (edge, the other node)
 }
 
 // (t, q) [N][7] -> pose buffer [N][8] with a unit quaternion, qw >= 0; sets
@@ -153,9 +157,11 @@ struct ba_pgo {
   int N = 0, E = 0;
   ba_options opt{};
   int nbe = 0, nbn = 0;  // blocks of the edge and node kernels
-  int pcg_grid = 0;
+  int pcg_grid = 0, pcg_npb = 0;  // PCG: blocks, nodes per block pass
+  int band = 0;                   // half-bandwidth of H in unknowns (node order)
   std::vector<void*> allocs;
   int32_t *ei = nullptr, *ej = nullptr, *rowptr = nullptr, *inc = nullptr;
+  int2* inc2 = nullptr;
   double *meas = nullptr, *info = nullptr, *poses = nullptr;
   double *B = nullptr, *qv = nullptr, *Hd = nullptr, *g = nullptr, *D = nullptr, *Minv = nullptr;
   double *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
@@ -236,7 +242,10 @@ ba_status enqueue_solve(ba_pgo* h, const double* lam_ptr, int maxiter, double to
                                                  h->opt.diag_max, h->D, h->Minv, h->x, h->r, h->dpart, h->st);
   count_launch();
   if (h->opt.solver == BA_SOLVER_CHOLESKY) {
+    // H + D is banded in the node order (half-bandwidth h->band): only the
+    // tiles within the band are factored, and the solve stays in the band
     const int n = 6 * h->N;
+    const int bw = h->band;
     k_pgo_dense<<<h->N, 256, 0, s>>>(h->N, h->rowptr, h->inc, h->ei, h->ej, h->B, h->Hd, h->D, h->dS);
     count_launch();
     if (h->fixed) {
@@ -247,26 +256,25 @@ ba_status enqueue_solve(ba_pgo* h, const double* lam_ptr, int maxiter, double to
     const int nblk_d = (n + DB - 1) / DB;
     for (int kb = 0; kb < nblk_d; ++kb) {
       k_chol_diag<<<1, DB * DB / 4, 0, s>>>(n, kb, h->dS, h->dfail);
-      const int rows_below = n - (kb + 1) * DB;
+      const int rows_below = std::min(n - (kb + 1) * DB, bw);
       if (rows_below > 0) {
         k_chol_panel<<<(rows_below + DB - 1) / DB, DB, 0, s>>>(n, kb, h->dS);
-        const long long T_ = nblk_d - kb - 1;
+        const long long T_ = (rows_below + DB - 1) / DB;
         k_chol_update<<<(unsigned)(T_ * (T_ + 1) / 2), DB * DB / 4, 0, s>>>(n, kb, h->dS);
         count_launch(2);
       }
       count_launch();
     }
-    k_dense_solve<<<1, 1024, 0, s>>>(n, h->dS, h->r, h->dy, h->x, h->dfail, h->st);
+    k_dense_solve<<<1, 1024, 0, s>>>(n, bw, h->dS, h->r, h->dy, h->x, h->dfail, h->st);
     count_launch();
     return BA_OK;
   }
   PCU(cudaMemsetAsync(h->bar, 0, sizeof(GridBar), s));
   PcgArgs a;
   a.N = h->N;
+  a.npb = h->pcg_npb;
   a.rowptr = h->rowptr;
-  a.inc = h->inc;
-  a.ei = h->ei;
-  a.ej = h->ej;
+  a.inc2 = h->inc2;
   a.B = h->B;
   a.D = h->D;
   a.Minv = h->Minv;
@@ -284,7 +292,7 @@ ba_status enqueue_solve(ba_pgo* h, const double* lam_ptr, int maxiter, double to
   a.bar = h->bar;
   a.st = h->st;
   void* args[] = {&a};
-  PCU(cudaLaunchCooperativeKernel((const void*)k_pgo_pcg, dim3(h->pcg_grid), dim3(PGO_PCG_THREADS), args, 0, s));
+  PCU(cudaLaunchCooperativeKernel((const void*)k_pgo_pcg, dim3(h->pcg_grid), dim3(6 * h->pcg_npb), args, 0, s));
   count_launch();
   return BA_OK;
 }
@@ -333,7 +341,9 @@ ba_status ba_pgo_create(ba_pgo** out, int N, int E, const double* poses, const i
   PCU(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
   PCU(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   if (!coop) return set_error(BA_ERR_CUDA, "the device does not support cooperative launches");
-  PCU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pgo_pcg, PGO_PCG_THREADS, 0));
+  // PCG: about one block per SM, npb consecutive nodes per block pass
+  const int npb = std::max(1, std::min(PGO_PCG_NODES, (N + nsm - 1) / nsm));
+  PCU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pgo_pcg, 6 * npb, 0));
   if (occ < 1) return set_error(BA_ERR_CUDA, "the PCG kernel cannot be resident");
   ba_pgo* h = new (std::nothrow) ba_pgo();
   if (!h) return set_error(BA_ERR_OOM, "host allocation failed");
@@ -346,7 +356,8 @@ ba_status ba_pgo_create(ba_pgo** out, int N, int E, const double* poses, const i
   h->opt = o;
   h->nbe = nb(E, PGO_EDGE_THREADS);
   h->nbn = nb(N, PGO_NODE_THREADS);
-  const int groups = (N + PGO_PCG_NODES - 1) / PGO_PCG_NODES;
+  const int groups = (N + npb - 1) / npb;
+  h->pcg_npb = npb;
   h->pcg_grid = std::max(1, std::min(groups, occ * nsm));
   cudaStream_t s = (cudaStream_t)stream;
   const long long n6 = 6LL * N;
@@ -358,6 +369,7 @@ ba_status ba_pgo_create(ba_pgo** out, int N, int E, const double* poses, const i
   A(&h->ej, 4ull * E);
   A(&h->rowptr, 4ull * (N + 1));
   A(&h->inc, 8ull * E);
+  A(&h->inc2, 16ull * E);
   A(&h->meas, 64ull * E);
   A(&h->info, 168ull * E);
   A(&h->poses, 128ull * N);
@@ -409,13 +421,23 @@ ba_status ba_pgo_create(ba_pgo** out, int N, int E, const double* poses, const i
   k_pgo_check_edges<<<h->nbe, PGO_EDGE_THREADS, 0, s>>>(N, E, h->ei, h->ej, h->info, h->derr);
   count_launch();
   if ((st = check_device_errors(h, s)) != BA_OK) return bail(st);
+  {
+    // half-bandwidth of H in the node order: 6 max |i - j| + 5 unknowns
+    std::vector<int32_t> hi(E), hj(E);
+    if ((e = cudaMemcpy(hi.data(), h->ei, 4ull * E, cudaMemcpyDeviceToHost)) != cudaSuccess ||
+        (e = cudaMemcpy(hj.data(), h->ej, 4ull * E, cudaMemcpyDeviceToHost)) != cudaSuccess)
+      return bail(set_error(BA_ERR_CUDA, "copy of the edges failed"));
+    long long bwn = 0;
+    for (int k = 0; k < E; ++k) bwn = std::max<long long>(bwn, std::llabs((long long)hi[k] - hj[k]));
+    h->band = (int)std::min<long long>(6 * bwn + 5, n6 - 1);
+  }
   // incidence CSR: stable sort of [ei..., ej...] by node
   if ((e = cudaMemcpyAsync(keys, h->ei, 4ull * E, cudaMemcpyDeviceToDevice, s)) != cudaSuccess ||
       (e = cudaMemcpyAsync(keys + E, h->ej, 4ull * E, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
     return bail(set_error(BA_ERR_CUDA, "copy failed"));
   if ((e = csr_build_async(keys, 2 * E, N, perm, h->rowptr, scratch, h->derr, s)) != cudaSuccess)
     return bail(set_error(BA_ERR_CUDA, "incidence sort failed: %s", cudaGetErrorString(e)));
-  k_pgo_inc_codes<<<nb(2LL * E, 256), 256, 0, s>>>(E, perm, h->inc);
+  k_pgo_inc_codes<<<nb(2LL * E, 256), 256, 0, s>>>(E, perm, h->ei, h->ej, h->inc, h->inc2);
   count_launch();
   // poses and measurements, quaternions normalised
   if ((st = copy_in(tmp7, poses, 56ull * N, s)) != BA_OK) return bail(st);

@@ -476,7 +476,8 @@ __device__ __forceinline__ bool grid_barrier(GridBar* gb, unsigned int nblocks) 
       __threadfence();
       atomicAdd(&gb->gen, 1u);
     } else {
-      // about 2^25 polls of >= 32 ns: a second or more before giving up
+      // 2^25 polls (all but the first 256 after a >= 32 ns sleep): a
+      // second or more before giving up
       unsigned int spins = 0;
       while (*vgen == g0) {
         if (*verr || ++spins > (1u << 25)) {
@@ -484,7 +485,7 @@ __device__ __forceinline__ bool grid_barrier(GridBar* gb, unsigned int nblocks) 
           atomicExch(&gb->err, 1);
           break;
         }
-        __nanosleep(32);
+        if (spins > 256) __nanosleep(32);
       }
     }
     __threadfence();
@@ -506,10 +507,9 @@ __device__ __forceinline__ void grid_total(const double* __restrict__ part, int 
 
 struct PcgArgs {
   int N;
+  int npb;             // nodes per block pass (blockDim.x = 6 npb)
   const int32_t* rowptr;
-  const int32_t* inc;
-  const int32_t* ei;
-  const int32_t* ej;
+  const int2* inc2;    // per incidence slot: (edge, other node)
   const double* B;
   const double* D;
   const double* Minv;
@@ -528,18 +528,28 @@ struct PcgArgs {
   DevState* st;
 };
 
+// Slots of neighbour directions staged in shared memory per pass.
+constexpr int PGO_PCG_STAGE = 256;
+
 // Block-Jacobi PCG on (H + D) x = b from x = 0, the iteration of the
 // oracle's pcg: stop after the first iteration with |r| <= tol |b|, after
 // maxiter, or (before updating x) when p^T (H + D) p is not positive.
-// Thread (node n, row a); the 6 rows of a node are in one block.  Two grid
-// barriers per iteration: the direction p = z + beta p_old of a neighbour is
-// formed on the fly from its z and p_old, both complete at the last barrier.
-static __global__ void __launch_bounds__(PGO_PCG_THREADS) k_pgo_pcg(PcgArgs a) {
+// A block takes npb consecutive nodes per pass, thread (node, row).  Two
+// grid barriers per iteration: the direction p = z + beta p_old of a
+// neighbour is formed on the fly from its z and p_old (both complete at the
+// last barrier).  The product first stages the neighbours' directions of
+// the block's incidence slots in shared memory (every load independent),
+// then each row sums B_e row . (p_i - p_other) over its node's slots in CSR
+// order.  Read-only arrays go through the non-coherent cache; arrays the
+// kernel writes are read from L2 (__ldcg).
+static __global__ void __launch_bounds__(PGO_PCG_THREADS, 1) k_pgo_pcg(PcgArgs a) {
   __shared__ double sr[PGO_PCG_NODES][6];
+  __shared__ double sp[PGO_PCG_STAGE][6];
   const unsigned int G = gridDim.x;
   const int N = a.N;
+  const int npb = a.npb;
   const long long n6 = 6LL * N;
-  const int groups = (N + PGO_PCG_NODES - 1) / PGO_PCG_NODES;
+  const int groups = (N + npb - 1) / npb;
   const int ln = threadIdx.x / 6, row = threadIdx.x % 6;
   double tot[2];
   grid_total<2>(a.bpart, a.nbp, tot);
@@ -557,14 +567,14 @@ static __global__ void __launch_bounds__(PGO_PCG_THREADS) k_pgo_pcg(PcgArgs a) {
   // z = M r, rz
   double rz_part = 0.0;
   for (int gi = blockIdx.x; gi < groups; gi += G) {
-    const int n = gi * PGO_PCG_NODES + ln;
-    const bool live = n < N;
+    const int n = gi * npb + ln;
+    const bool live = ln < npb && n < N;
     if (live) sr[ln][row] = a.r[6LL * n + row];
     __syncthreads();
     if (live) {
       const double* M = a.Minv + 36LL * n + 6 * row;
       double zz = 0.0;
-      for (int k = 0; k < 6; ++k) zz += M[k] * sr[ln][k];
+      for (int k = 0; k < 6; ++k) zz += __ldg(M + k) * sr[ln][k];
       a.z[6LL * n + row] = zz;
       pA[6LL * n + row] = 0.0;
       rz_part += zz * sr[ln][row];
@@ -593,30 +603,47 @@ static __global__ void __launch_bounds__(PGO_PCG_THREADS) k_pgo_pcg(PcgArgs a) {
     // phase A: p = z + beta p_old; q = (H + D) p; p . q
     double pq_part = 0.0;
     for (int gi = blockIdx.x; gi < groups; gi += G) {
-      const int n = gi * PGO_PCG_NODES + ln;
-      if (n < N) {
-        const long long o = 6LL * n + row;
-        const double pi_a = a.z[o] + beta * pold[o];
-        pcur[o] = pi_a;
-        double qa = 0.0;
-        if (!(a.fixed && a.fixed[n])) {
-          double pi[6];
-          for (int k = 0; k < 6; ++k) pi[k] = __ldcg(a.z + 6LL * n + k) + beta * __ldcg(pold + 6LL * n + k);
-          qa = a.D[o] * pi_a;
-          const int end = a.rowptr[n + 1];
-          for (int s = a.rowptr[n]; s < end; ++s) {
-            const int code = a.inc[s];
-            const int e = code >> 1;
-            const int other = (code & 1) ? a.ei[e] : a.ej[e];
+      const int n0 = gi * npb;
+      const int n = n0 + ln;
+      const bool live = ln < npb && n < N;
+      const bool free_n = live && !(a.fixed && a.fixed[n]);
+      double pi[6];
+      double pi_a = 0.0;
+      if (live) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) pi[k] = __ldcg(a.z + 6LL * n + k) + beta * __ldcg(pold + 6LL * n + k);
+        pi_a = __ldcg(a.z + 6LL * n + row) + beta * __ldcg(pold + 6LL * n + row);
+      }
+      double qa = 0.0;
+      const int nend = min(N, n0 + npb);
+      const int s_lo = __ldg(a.rowptr + n0), s_hi = __ldg(a.rowptr + nend);
+      const int my_lo = live ? __ldg(a.rowptr + n) : 0, my_hi = live ? __ldg(a.rowptr + n + 1) : 0;
+      for (int c0 = s_lo; c0 < s_hi; c0 += PGO_PCG_STAGE) {
+        const int c1 = min(s_hi, c0 + PGO_PCG_STAGE);
+        __syncthreads();
+        for (int e = threadIdx.x; e < (c1 - c0) * 6; e += blockDim.x) {
+          const int sl = e / 6, k = e % 6;
+          const int other = __ldg(&a.inc2[c0 + sl].y);
+          sp[sl][k] = __ldcg(a.z + 6LL * other + k) + beta * __ldcg(pold + 6LL * other + k);
+        }
+        __syncthreads();
+        if (free_n) {
+          const int lo = max(my_lo, c0), hi = min(my_hi, c1);
+          for (int sl = lo; sl < hi; ++sl) {
+            const int e = __ldg(&a.inc2[sl].x);
             const double* Br = a.B + 36LL * e + 6 * row;
             double acc = 0.0;
-            for (int k = 0; k < 6; ++k) {
-              const double po = __ldcg(a.z + 6LL * other + k) + beta * __ldcg(pold + 6LL * other + k);
-              acc += Br[k] * (pi[k] - po);
-            }
+#pragma unroll
+            for (int k = 0; k < 6; ++k) acc += __ldg(Br + k) * (pi[k] - sp[sl - c0][k]);
             qa += acc;
           }
         }
+      }
+      if (live) {
+        const long long o = 6LL * n + row;
+        pcur[o] = pi_a;
+        if (free_n) qa += __ldg(a.D + o) * pi_a;
+        else qa = 0.0;
         a.q[o] = qa;
         pq_part += pi_a * qa;
       }
@@ -639,8 +666,8 @@ static __global__ void __launch_bounds__(PGO_PCG_THREADS) k_pgo_pcg(PcgArgs a) {
     // phase B: x += alpha p, r -= alpha q, z = M r; r . r, r . z
     double rr_part = 0.0, rzp = 0.0;
     for (int gi = blockIdx.x; gi < groups; gi += G) {
-      const int n = gi * PGO_PCG_NODES + ln;
-      const bool live = n < N;
+      const int n = gi * npb + ln;
+      const bool live = ln < npb && n < N;
       if (live) {
         const long long o = 6LL * n + row;
         a.x[o] += alpha * pcur[o];
@@ -653,7 +680,7 @@ static __global__ void __launch_bounds__(PGO_PCG_THREADS) k_pgo_pcg(PcgArgs a) {
       if (live) {
         const double* M = a.Minv + 36LL * n + 6 * row;
         double zz = 0.0;
-        for (int k = 0; k < 6; ++k) zz += M[k] * sr[ln][k];
+        for (int k = 0; k < 6; ++k) zz += __ldg(M + k) * sr[ln][k];
         a.z[6LL * n + row] = zz;
         rzp += zz * sr[ln][row];
       }
@@ -694,7 +721,6 @@ static __global__ void __launch_bounds__(PGO_PCG_THREADS) k_pgo_pcg(PcgArgs a) {
     a.st->pcg_done = 1;
   }
 }
-
 
 // ---------------------------------------------------------------------------
 // Trial, cost and the LM decision

@@ -143,6 +143,37 @@ def test_exact_solves_match_the_oracle_cholesky(solver):
         assert rel <= 1e-13 and its > 10
 
 
+@pytest.mark.parametrize("kind", ["chain", "random"])
+def test_banded_cholesky_matches_the_oracle(kind):
+    """The Cholesky solver factors within the band of the node order: a
+    chain (half-bandwidth 11 unknowns, inside one 32-wide tile) and a random
+    graph (band = the whole matrix), against the oracle's dense Cholesky."""
+    rng = np.random.default_rng(21 if kind == "chain" else 22)
+    N = 70
+    if kind == "chain":
+        ei = np.arange(N - 1, dtype=np.int32)
+        ej = ei + 1
+    else:
+        ei = rng.integers(0, N, 250).astype(np.int32)
+        ej = ((ei + rng.integers(1, N, 250)) % N).astype(np.int32)
+        ei = np.concatenate([ei, np.arange(N - 1, dtype=np.int32), [0]]).astype(np.int32)
+        ej = np.concatenate([ej, np.arange(1, N, dtype=np.int32), [N - 1]]).astype(np.int32)
+    E = len(ei)
+    P7 = np.concatenate([rng.normal(size=(N, 3)) * 3, rng.normal(size=(N, 4))], 1)
+    Ts = pgo.poses_to_matrices(P7)
+    Tms = np.stack([pgo.se3_exp(rng.normal(size=6) * 0.1) @ pgo.se3_inv(Ts[i]) @ Ts[j] for i, j in zip(ei, ej)])
+    Om = np.stack([np.diag(rng.uniform(0.5, 2.0, 6)) for _ in range(E)])
+    info = np.stack([pgo.info_upper(M) for M in Om])
+    gg = scenegen.PoseGraph(poses_gt=P7, ei=ei, ej=ej, noise=np.zeros((E, 6)), info=info, drift=np.zeros((N, 6)))
+    blk = pgo.assemble(Ts, ei, ej, Tms, Om)
+    fixed = (0, 33)
+    want, _, _ = pgo.solve_damped(blk, 1e-3, LMOptions(solver="cholesky"), _mask(N, fixed))
+    with _make(gg, P7, pgo.matrices_to_poses(Tms), fixed=fixed, solver="cholesky") as pg:
+        dx, _, rel = pg.damped_solve(1e-3, 0, 0.0)
+    assert rel == 0.0
+    assert _rel(dx.cpu(), want) < 1e-9
+
+
 @pytest.mark.parametrize("solver", ["cholesky", "pcg"])
 def test_lm_trace_matches_the_oracle(solver):
     """sphere100, 8 trials with exact solves (Cholesky, or PCG to 1e-13):
