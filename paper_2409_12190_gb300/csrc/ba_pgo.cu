@@ -158,6 +158,7 @@ struct ba_pgo {
   ba_options opt{};
   int nbe = 0, nbn = 0;  // blocks of the edge and node kernels
   int pcg_grid = 0, pcg_npb = 0;  // PCG: blocks, nodes per block pass
+  size_t pcg_res_smem = 0;        // > 0: the register-resident PCG, its shared memory
   int band = 0;                   // half-bandwidth of H in unknowns (node order)
   std::vector<void*> allocs;
   int32_t *ei = nullptr, *ej = nullptr, *rowptr = nullptr, *inc = nullptr;
@@ -292,7 +293,11 @@ ba_status enqueue_solve(ba_pgo* h, const double* lam_ptr, int maxiter, double to
   a.bar = h->bar;
   a.st = h->st;
   void* args[] = {&a};
-  PCU(cudaLaunchCooperativeKernel((const void*)k_pgo_pcg, dim3(h->pcg_grid), dim3(6 * h->pcg_npb), args, 0, s));
+  if (h->pcg_res_smem)
+    PCU(cudaLaunchCooperativeKernel((const void*)k_pgo_pcg_res, dim3(h->pcg_grid), dim3(6 * h->pcg_npb), args,
+                                    h->pcg_res_smem, s));
+  else
+    PCU(cudaLaunchCooperativeKernel((const void*)k_pgo_pcg, dim3(h->pcg_grid), dim3(6 * h->pcg_npb), args, 0, s));
   count_launch();
   return BA_OK;
 }
@@ -439,6 +444,26 @@ ba_status ba_pgo_create(ba_pgo** out, int N, int E, const double* poses, const i
     return bail(set_error(BA_ERR_CUDA, "incidence sort failed: %s", cudaGetErrorString(e)));
   k_pgo_inc_codes<<<nb(2LL * E, 256), 256, 0, s>>>(E, perm, h->ei, h->ej, h->inc, h->inc2);
   count_launch();
+  {
+    // the register-resident PCG when every block can hold one node group
+    // with its incidence slots in shared memory, all blocks resident
+    std::vector<int32_t> rp(N + 1);
+    if ((e = cudaMemcpyAsync(rp.data(), h->rowptr, 4ull * (N + 1), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess)
+      return bail(set_error(BA_ERR_CUDA, "copy of the incidence rows failed"));
+    int max_slots = 0;
+    for (int g0 = 0; g0 < N; g0 += npb) max_slots = std::max(max_slots, rp[std::min(N, g0 + npb)] - rp[g0]);
+    const size_t smem = pgo_res_smem(max_slots);
+    int occ_res = 0;
+    if (smem <= 200u * 1024u &&
+        cudaFuncSetAttribute(k_pgo_pcg_res, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_res, k_pgo_pcg_res, 6 * npb, smem) == cudaSuccess &&
+        groups <= (long long)occ_res * nsm) {
+      h->pcg_res_smem = std::max<size_t>(smem, 16);
+      h->pcg_grid = groups;
+    }
+    cudaGetLastError();
+  }
   // poses and measurements, quaternions normalised
   if ((st = copy_in(tmp7, poses, 56ull * N, s)) != BA_OK) return bail(st);
   k_pgo_pack<<<nb(N, 128), 128, 0, s>>>(N, tmp7, h->poses, h->derr);

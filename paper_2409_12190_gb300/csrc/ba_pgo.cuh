@@ -722,6 +722,188 @@ static __global__ void __launch_bounds__(PGO_PCG_THREADS, 1) k_pgo_pcg(PcgArgs a
   }
 }
 
+// Shared memory of k_pgo_pcg_res for a block of `slots` incidence slots:
+// their B blocks (36), neighbour directions (6) and neighbour indices.
+__host__ __device__ constexpr size_t pgo_res_smem(int slots) { return (size_t)slots * (36 * 8 + 6 * 8 + 4); }
+
+// The same iteration as k_pgo_pcg when every block holds exactly one group
+// of npb nodes (gridDim.x = ceil(N / npb)): each thread keeps its entry of
+// x, r, z, p, D and its row of M for the whole solve in registers, the
+// block's B blocks and neighbour indices are staged in shared memory once,
+// and per iteration only the neighbours' z and p_old cross global memory.
+// Same arithmetic, in the same order, as k_pgo_pcg.
+static __global__ void __launch_bounds__(PGO_PCG_THREADS, 1) k_pgo_pcg_res(PcgArgs a) {
+  extern __shared__ __align__(16) unsigned char pgo_smem[];
+  __shared__ double sr[PGO_PCG_NODES][6];
+  const unsigned int G = gridDim.x;
+  const int N = a.N;
+  const int npb = a.npb;
+  const long long n6 = 6LL * N;
+  const int ln = threadIdx.x / 6, row = threadIdx.x % 6;
+  const int n0 = blockIdx.x * npb;
+  const int n = n0 + ln;
+  const bool live = ln < npb && n < N;
+  const bool free_n = live && !(a.fixed && a.fixed[n]);
+  const long long o = 6LL * n + row;
+  const int nend = min(N, n0 + npb);
+  const int s_lo = __ldg(a.rowptr + n0), s_hi = __ldg(a.rowptr + nend);
+  const int nsl = s_hi - s_lo;
+  double* sB = reinterpret_cast<double*>(pgo_smem);  // [nsl][36]
+  double* sp = sB + 36LL * nsl;                      // [nsl][6]
+  int* sother = reinterpret_cast<int*>(sp + 6LL * nsl);
+  for (int e = threadIdx.x; e < nsl * 36; e += blockDim.x) {
+    const int sl = e / 36, k = e % 36;
+    sB[e] = __ldg(a.B + 36LL * __ldg(&a.inc2[s_lo + sl].x) + k);
+  }
+  for (int sl = threadIdx.x; sl < nsl; sl += blockDim.x) sother[sl] = __ldg(&a.inc2[s_lo + sl].y);
+  const int my_lo = live ? __ldg(a.rowptr + n) - s_lo : 0, my_hi = live ? __ldg(a.rowptr + n + 1) - s_lo : 0;
+  double Mrow[6];
+  double Da = 0.0, ra = 0.0, xa = 0.0, za = 0.0, pa = 0.0;
+  if (live) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) Mrow[k] = __ldg(a.Minv + 36LL * n + 6 * row + k);
+    Da = __ldg(a.D + o);
+    ra = a.r[o];
+    sr[ln][row] = ra;
+  }
+  double tot[2];
+  grid_total<2>(a.bpart, a.nbp, tot);  // ends with a block barrier: sr and the stages are complete
+  const double bnorm = sqrt(tot[0]);
+  if (bnorm == 0.0 || a.maxiter <= 0) {
+    if (live) a.x[o] = 0.0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      a.st->pcg_iters = 0;
+      a.st->pcg_rel = bnorm == 0.0 ? 0.0 : 1.0;
+      a.st->pcg_done = 1;
+    }
+    return;
+  }
+  double* pold = a.p;
+  double* pcur = a.p + n6;
+  double rz_part = 0.0;
+  if (live) {
+    double zz = 0.0;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) zz += Mrow[k] * sr[ln][k];
+    za = zz;
+    a.z[o] = za;
+    pold[o] = 0.0;
+    rz_part = za * ra;
+  }
+  {
+    double v[1] = {rz_part};
+    block_sum_all<1>(v);
+    if (threadIdx.x == 0) a.part[4LL * blockIdx.x] = v[0];
+  }
+  if (!grid_barrier(a.bar, G)) return;
+  double rz;
+  {
+    double v[1] = {0.0};
+    for (int i = threadIdx.x; i < (int)G; i += blockDim.x) v[0] += __ldcg(a.part + 4LL * i);
+    block_sum_all<1>(v);
+    rz = v[0];
+  }
+  double beta = 0.0;
+  double rel = 1.0;
+  int it = 0;
+  while (it < a.maxiter) {
+    // phase A: p = z + beta p_old; q = (H + D) p; p . q
+    pa = za + beta * pa;
+    if (live) {
+      sr[ln][row] = pa;
+      pcur[o] = pa;
+    }
+    for (int e = threadIdx.x; e < nsl * 6; e += blockDim.x) {
+      const int sl = e / 6, k = e % 6;
+      const long long g = 6LL * sother[sl] + k;
+      sp[e] = __ldcg(a.z + g) + beta * __ldcg(pold + g);
+    }
+    __syncthreads();
+    double qa = 0.0;
+    if (free_n) {
+      double pi[6];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) pi[k] = sr[ln][k];
+      for (int sl = my_lo; sl < my_hi; ++sl) {
+        const double* Br = sB + 36LL * sl + 6 * row;
+        const double* po = sp + 6LL * sl;
+        double acc = 0.0;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) acc += Br[k] * (pi[k] - po[k]);
+        qa += acc;
+      }
+      qa += Da * pa;
+    }
+    double pq_part = live ? pa * qa : 0.0;
+    {
+      double v[1] = {pq_part};
+      block_sum_all<1>(v);
+      if (threadIdx.x == 0) a.part[4LL * blockIdx.x + 1] = v[0];
+    }
+    if (!grid_barrier(a.bar, G)) return;
+    double pq;
+    {
+      double v[1] = {0.0};
+      for (int i = threadIdx.x; i < (int)G; i += blockDim.x) v[0] += __ldcg(a.part + 4LL * i + 1);
+      block_sum_all<1>(v);
+      pq = v[0];
+    }
+    if (!(pq > 0.0)) break;
+    const double alpha = rz / pq;
+    // phase B: x += alpha p, r -= alpha q, z = M r; r . r, r . z
+    double rr_part = 0.0, rzp = 0.0;
+    if (live) {
+      xa += alpha * pa;
+      ra = ra - alpha * qa;
+      sr[ln][row] = ra;
+      rr_part = ra * ra;
+    }
+    __syncthreads();
+    if (live) {
+      double zz = 0.0;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) zz += Mrow[k] * sr[ln][k];
+      za = zz;
+      a.z[o] = za;
+      rzp = za * ra;
+    }
+    ++it;
+    {
+      double v[2] = {rr_part, rzp};
+      block_sum_all<2>(v);
+      if (threadIdx.x == 0) {
+        a.part[4LL * blockIdx.x + 2] = v[0];
+        a.part[4LL * blockIdx.x + 3] = v[1];
+      }
+    }
+    if (!grid_barrier(a.bar, G)) return;
+    double rr, rz_new;
+    {
+      double v[2] = {0.0, 0.0};
+      for (int i = threadIdx.x; i < (int)G; i += blockDim.x) {
+        v[0] += __ldcg(a.part + 4LL * i + 2);
+        v[1] += __ldcg(a.part + 4LL * i + 3);
+      }
+      block_sum_all<2>(v);
+      rr = v[0];
+      rz_new = v[1];
+    }
+    rel = sqrt(rr) / bnorm;
+    if (sqrt(rr) <= a.tol * bnorm) break;
+    beta = rz_new / rz;
+    rz = rz_new;
+    double* t = pold;
+    pold = pcur;
+    pcur = t;
+  }
+  if (live) a.x[o] = xa;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    a.st->pcg_iters = it;
+    a.st->pcg_rel = it == 0 ? 1.0 : rel;
+    a.st->pcg_done = 1;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Trial, cost and the LM decision
 // ---------------------------------------------------------------------------

@@ -143,6 +143,32 @@ def test_exact_solves_match_the_oracle_cholesky(solver):
         assert rel <= 1e-13 and its > 10
 
 
+def test_pcg_with_a_hub_node_matches_the_oracle():
+    """A star (node 0 joined to every node) plus a chain, 700 nodes: the
+    first node group's incidence slots exceed the shared-memory budget of
+    the register-resident PCG, so the general kernel runs; its iterates and
+    its converged solve against the oracle."""
+    rng = np.random.default_rng(31)
+    N = 700
+    ei = np.concatenate([np.zeros(N - 1, np.int32), np.arange(1, N - 1, dtype=np.int32)])
+    ej = np.concatenate([np.arange(1, N, dtype=np.int32), np.arange(2, N, dtype=np.int32)])
+    E = len(ei)
+    P7 = np.concatenate([rng.normal(size=(N, 3)) * 5, rng.normal(size=(N, 4))], 1)
+    Ts = pgo.poses_to_matrices(P7)
+    Tms = np.stack([pgo.se3_exp(rng.normal(size=6) * 0.05) @ pgo.se3_inv(Ts[i]) @ Ts[j] for i, j in zip(ei, ej)])
+    info = np.tile(pgo.info_upper(np.eye(6)), (E, 1))
+    gg = scenegen.PoseGraph(poses_gt=P7, ei=ei, ej=ej, noise=np.zeros((E, 6)), info=info, drift=np.zeros((N, 6)))
+    blk = pgo.assemble(Ts, ei, ej, Tms, np.tile(np.eye(6), (E, 1, 1)))
+    m = _mask(N, (5,))
+    it_ref, _, _ = pgo.solve_damped(blk, 1e-3, LMOptions(solver="pcg", pcg_tol=0.0, pcg_maxiter=12), m)
+    exact, _, _ = pgo.solve_damped(blk, 1e-3, LMOptions(solver="cholesky"), m)
+    with _make(gg, P7, pgo.matrices_to_poses(Tms), fixed=(5,)) as pg:
+        dx, its, _ = pg.damped_solve(1e-3, 12, 0.0)
+        dx2, _, rel = pg.damped_solve(1e-3, 5000, 1e-13)
+    assert its == 12 and _rel(dx.cpu(), it_ref) < 1e-9
+    assert rel <= 1e-13 and _rel(dx2.cpu(), exact) < 1e-8
+
+
 @pytest.mark.parametrize("kind", ["chain", "random"])
 def test_banded_cholesky_matches_the_oracle(kind):
     """The Cholesky solver factors within the band of the node order: a
