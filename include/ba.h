@@ -484,11 +484,27 @@ ba_status ba_batch_set_launch(ba_batch* h, int ctas_per_sm, int variant, int ord
 ba_status ba_batch_get_launch(ba_batch* h, int* ctas_per_sm, int* variant, int* order,
                               int* grid);
 
+/* Segment sizes of the batched solve (no counterpart in the paper; the
+ * symbolic phase's cut, Sec. IV-B): each camera's observations in equal
+ * pieces of at most piece_max slots (32..2048, default 2048) and each
+ * problem's points in chunks of at most chunk_slots observations (32..1024,
+ * default 1024) and chunk_pts points (1..512, default 512).  Another cut
+ * changes the order of some sums (results move by rounding).  Synchronises. */
+ba_status ba_batch_set_segments(ba_batch* h, int piece_max, int chunk_slots, int chunk_pts);
+
+/* The current segment sizes (host outputs, any may be NULL; no counterpart
+ * in the paper). */
+ba_status ba_batch_get_segments(ba_batch* h, int* piece_max, int* chunk_slots, int* chunk_pts);
+
 /* Autotuner (no counterpart in the paper): time `iters` trials of the
  * batch under every launch
  * configuration (variant x CTAs per SM up to the occupancy limit x
  * order), from the batch's current state each time, and keep the fastest;
- * the batch's state is restored afterwards.  With cache_path (host
+ * then, at that launch, every segment size of {256, 512, 1024, 2048} piece
+ * slots x {256 / 128, 512 / 256, 1024 / 512} chunk slots / points, keeping
+ * the fastest whose final cost of every problem is within 1e-6 (relative)
+ * of the current segments' (the gate on the rounding a cut changes); the
+ * batch's state is restored afterwards.  With cache_path (host
  * string, may be NULL) the choice is looked up first in, and then appended
  * to, a JSON-lines file keyed by the GPU name, precision, Jacobian mode and
  * a histogram of the problem sizes.  best_ms (host, may be NULL) receives

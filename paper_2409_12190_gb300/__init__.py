@@ -464,13 +464,25 @@ class Batch:
         _lib.check(_L().ba_batch_get_launch(self._h, ct.byref(c), ct.byref(v), ct.byref(o), ct.byref(g)))
         return dict(ctas_per_sm=c.value, variant=v.value, order=o.value, grid=g.value)
 
+    def set_segments(self, piece_max: int = 2048, chunk_slots: int = 1024, chunk_pts: int = 512):
+        """Segment sizes of the solve (pieces of camera-major slots, point
+        chunks); another cut moves results by rounding."""
+        _lib.check(_L().ba_batch_set_segments(self._h, int(piece_max), int(chunk_slots), int(chunk_pts)))
+
+    def segments(self):
+        p, s, t = ct.c_int(), ct.c_int(), ct.c_int()
+        _lib.check(_L().ba_batch_get_segments(self._h, ct.byref(p), ct.byref(s), ct.byref(t)))
+        return dict(piece_max=p.value, chunk_slots=s.value, chunk_pts=t.value)
+
     def autotune(self, iters: int, cache_path: str | None = None):
         """Pick the fastest launch configuration (results do not depend on
-        it); returns the chosen configuration and its time (0 if cached)."""
+        it), then the fastest segment sizes whose final costs stay within
+        1e-6 of the current ones; returns the chosen launch and segments and
+        the time (0 if cached)."""
         ms = ct.c_double()
         path = None if cache_path is None else str(cache_path).encode()
         _lib.check(_L().ba_batch_autotune(self._h, int(iters), path, ct.byref(ms)))
-        return self.launch(), ms.value
+        return {**self.launch(), **self.segments()}, ms.value
 
 
 class _BundleAdjust(torch.autograd.Function):

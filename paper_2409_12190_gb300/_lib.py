@@ -112,6 +112,8 @@ SIGNATURES = {
     "ba_batch_set_launch": (_S, [_VP, _I, _I, _I]),
     "ba_batch_get_launch": (_S, [_VP, ct.POINTER(_I), ct.POINTER(_I), ct.POINTER(_I), ct.POINTER(_I)]),
     "ba_batch_autotune": (_S, [_VP, _I, ct.c_char_p, ct.POINTER(_D)]),
+    "ba_batch_set_segments": (_S, [_VP, _I, _I, _I]),
+    "ba_batch_get_segments": (_S, [_VP, ct.POINTER(_I), ct.POINTER(_I), ct.POINTER(_I)]),
     "ba_set_preconditioner": (_S, [_VP, _VP, _VP]),
     "ba_learn_collect": (_S, [_VP, _D, _I, _VP, _VP, _VP, _VP, _VP, _VP]),
     "ba_learn_slow_probes": (_S, [_VP, _D, _I, _VP, _I, _D, _VP, _VP]),

@@ -37,6 +37,10 @@ struct ba_batch {
   void *cams0 = nullptr, *pts0 = nullptr;  // parameters at creation (internal order)
   // launch configuration
   int ctas_per_sm = 1, variant = 0, order = 0;
+  // segment sizes: camera-major pieces of at most piece_max slots, point
+  // chunks of at most chunk_slots slots and chunk_pts points
+  int piece_max = PIECE, chunk_slots = CHUNK_SLOTS, chunk_pts = CHUNK_PTS;
+  size_t piece_cap = 0, chunk_cap = 0;  // capacity of the piece and chunk arrays
   size_t smem = 0;
   // graph of one solve
   cudaGraphExec_t gexec = nullptr;
@@ -71,6 +75,28 @@ namespace {
   } while (0)
 
 inline unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+// Point chunks of each problem (runs of whole points with at most slots
+// observations and pts points; a point with more observations is a chunk
+// alone), the problems' ranges into b->chunk_off; rq: the point rows.
+std::vector<int32_t> cut_chunks(ba_batch* b, const std::vector<int32_t>& rq, int slots, int pts) {
+  std::vector<int32_t> bch;
+  b->chunk_off.assign(b->nprob + 1, 0);
+  for (int i = 0; i < b->nprob; ++i) {
+    b->chunk_off[i] = (int32_t)bch.size();
+    const int pend = b->pt_off[i + 1];
+    long long j = b->pt_off[i];
+    while (j < pend) {
+      bch.push_back((int32_t)j);
+      long long e = j + 1;
+      while (e < pend && e - j < pts && rq[e + 1] - rq[j] <= slots) ++e;
+      j = e;
+    }
+    bch.push_back(pend);
+  }
+  b->chunk_off[b->nprob] = (int32_t)bch.size();
+  return bch;
+}
 
 ba_status enter(ba_batch* b, void* stream) {
   BCU(cudaEventRecord(b->h->ev_in, (cudaStream_t)stream));
@@ -344,21 +370,9 @@ ba_status ba_batch_create(ba_batch** out, int nprob, const int32_t* cam_counts, 
   for (int j = 0; j < P; ++j)
     if (rq[j + 1] == rq[j]) return fail_out(BA_ERR_INVALID_ARG, "every point of a batched problem must be observed");
   // point chunks of each problem, cut as a problem of its own cuts them
-  std::vector<int32_t> bch;
-  b->chunk_off.assign(nprob + 1, 0);
-  for (int i = 0; i < nprob; ++i) {
-    b->chunk_off[i] = (int32_t)bch.size();
-    const int pend = b->pt_off[i + 1];
-    long long j = b->pt_off[i];
-    while (j < pend) {
-      bch.push_back((int32_t)j);
-      long long e = j + 1;
-      while (e < pend && e - j < CHUNK_PTS && rq[e + 1] - rq[j] <= CHUNK_SLOTS) ++e;
-      j = e;
-    }
-    bch.push_back(pend);
-  }
-  b->chunk_off[nprob] = (int32_t)bch.size();
+  std::vector<int32_t> bch = cut_chunks(b, rq, CHUNK_SLOTS, CHUNK_PTS);
+  b->chunk_cap = bch.size();
+  b->piece_cap = (size_t)h->npieces;
   b->cap = std::min(h->opt.max_stats, BA_BATCH_MAX_STATS);
   const size_t ts = h->tsize;
   cudaError_t e = b->alloc(&b->d_cam_off, (nprob + 1) * 4ull);
@@ -528,6 +542,71 @@ ba_status ba_batch_set_launch(ba_batch* b, int ctas_per_sm, int variant, int ord
   return BA_OK;
 }
 
+ba_status ba_batch_set_segments(ba_batch* b, int piece_max, int chunk_slots, int chunk_pts) {
+  if (!b) return set_error(BA_ERR_INVALID_ARG, "NULL batch");
+  if (piece_max < 32 || piece_max > PIECE || chunk_slots < 32 || chunk_slots > CHUNK_SLOTS || chunk_pts < 1 ||
+      chunk_pts > CHUNK_PTS)
+    return set_error(BA_ERR_INVALID_ARG, "piece_max in [32, %d], chunk_slots in [32, %d], chunk_pts in [1, %d]",
+                     PIECE, CHUNK_SLOTS, CHUNK_PTS);
+  ba_problem* h = b->h;
+  BCU(cudaStreamSynchronize(h->s));
+  if (piece_max == b->piece_max && chunk_slots == b->chunk_slots && chunk_pts == b->chunk_pts) return BA_OK;
+  const int C = h->C, P = h->P;
+  std::vector<int32_t> rp(C + 1), rq(P + 1);
+  BCU(cudaMemcpy(rp.data(), h->rowptr_cam, (C + 1) * 4ull, cudaMemcpyDeviceToHost));
+  BCU(cudaMemcpy(rq.data(), h->rowptr_pt, (P + 1) * 4ull, cudaMemcpyDeviceToHost));
+  // pieces: each camera's slots cut into equal runs of at most piece_max
+  // (the single problem's cut with its maximum replaced)
+  std::vector<int32_t> pc, pb, pe, cpp(C + 1);
+  for (int c = 0; c < C; ++c) {
+    cpp[c] = (int32_t)pc.size();
+    const int n = rp[c + 1] - rp[c];
+    const int k = (n + piece_max - 1) / piece_max;
+    for (int i = 0; i < k; ++i) {
+      pc.push_back(c);
+      pb.push_back(rp[c] + (int)((long long)n * i / k));
+      pe.push_back(rp[c] + (int)((long long)n * (i + 1) / k));
+    }
+  }
+  cpp[C] = (int32_t)pc.size();
+  if (pc.size() > b->piece_cap) {
+    BCU(b->alloc(&h->piece_cam, pc.size() * 4));
+    BCU(b->alloc(&h->piece_beg, pc.size() * 4));
+    BCU(b->alloc(&h->piece_end, pc.size() * 4));
+    BCU(b->alloc(&h->part, (size_t)PART * pc.size() * 8));
+    b->piece_cap = pc.size();
+  }
+  BCU(cudaMemcpy(h->piece_cam, pc.data(), pc.size() * 4, cudaMemcpyHostToDevice));
+  BCU(cudaMemcpy(h->piece_beg, pb.data(), pb.size() * 4, cudaMemcpyHostToDevice));
+  BCU(cudaMemcpy(h->piece_end, pe.data(), pe.size() * 4, cudaMemcpyHostToDevice));
+  BCU(cudaMemcpy(h->cam_piece_ptr, cpp.data(), (C + 1) * 4ull, cudaMemcpyHostToDevice));
+  h->npieces = (int)pc.size();
+  std::vector<int32_t> bch = cut_chunks(b, rq, chunk_slots, chunk_pts);
+  if (bch.size() > b->chunk_cap) {
+    BCU(b->alloc(&b->d_bchunk, bch.size() * 4));
+    BCU(b->alloc(&b->dot_gp, bch.size() * 8));
+    b->chunk_cap = bch.size();
+  }
+  BCU(cudaMemcpy(b->d_bchunk, bch.data(), bch.size() * 4, cudaMemcpyHostToDevice));
+  BCU(cudaMemcpy(b->d_chunk_off, b->chunk_off.data(), (b->nprob + 1) * 4ull, cudaMemcpyHostToDevice));
+  b->piece_max = piece_max;
+  b->chunk_slots = chunk_slots;
+  b->chunk_pts = chunk_pts;
+  if (b->gexec) {  // the captured solve holds the old arrays
+    cudaGraphExecDestroy(b->gexec);
+    b->gexec = nullptr;
+  }
+  return BA_OK;
+}
+
+ba_status ba_batch_get_segments(ba_batch* b, int* piece_max, int* chunk_slots, int* chunk_pts) {
+  if (!b) return set_error(BA_ERR_INVALID_ARG, "NULL batch");
+  if (piece_max) *piece_max = b->piece_max;
+  if (chunk_slots) *chunk_slots = b->chunk_slots;
+  if (chunk_pts) *chunk_pts = b->chunk_pts;
+  return BA_OK;
+}
+
 ba_status ba_batch_get_launch(ba_batch* b, int* ctas_per_sm, int* variant, int* order, int* grid) {
   if (!b) return set_error(BA_ERR_INVALID_ARG, "NULL batch");
   if (ctas_per_sm) *ctas_per_sm = b->ctas_per_sm;
@@ -547,9 +626,11 @@ ba_status ba_batch_autotune(ba_batch* b, int iters, const char* cache_path, doub
     const std::string pat = "\"key\": \"" + key + "\"";
     while (std::getline(in, line))
       if (line.find(pat) != std::string::npos) hit = line;  // the last entry wins
-    int c = 0, v = 0, o = 0;
+    int c = 0, v = 0, o = 0, pm = 0, cs = 0, cp = 0;
     if (!hit.empty() && json_int(hit, "ctas_per_sm", &c) && json_int(hit, "variant", &v) &&
-        json_int(hit, "order", &o) && ba_batch_set_launch(b, c, v, o) == BA_OK)
+        json_int(hit, "order", &o) && json_int(hit, "piece_max", &pm) && json_int(hit, "chunk_slots", &cs) &&
+        json_int(hit, "chunk_pts", &cp) && ba_batch_set_segments(b, pm, cs, cp) == BA_OK &&
+        ba_batch_set_launch(b, c, v, o) == BA_OK)
       return BA_OK;
   }
   ba_problem* h = b->h;
@@ -603,6 +684,55 @@ ba_status ba_batch_autotune(ba_batch* b, int iters, const char* cache_path, doub
       }
     }
   }
+  // segment sizes at the chosen launch: pieces of at most 256..2048
+  // camera-major slots, point chunks of 256 / 512 / 1024 slots.  Another cut
+  // changes the summation order, so a candidate is kept only if every
+  // problem's final cost is within 1e-6 (relative) of the current cut's.
+  int bp = b->piece_max, bs = b->chunk_slots, bpt = b->chunk_pts;
+  if (e == cudaSuccess && st == BA_OK) st = ba_batch_set_launch(b, bc, bv, bo);
+  std::vector<BState> ref(b->nprob), got(b->nprob);
+  auto timed_run = [&](float& ms, std::vector<BState>& fin) {
+    for (int rep = 0; rep < 2 && st == BA_OK && e == cudaSuccess; ++rep) {
+      e = restore();
+      if (e == cudaSuccess && rep == 1) e = cudaEventRecord(e0, h->s);
+      if (e == cudaSuccess) st = enqueue_solve(b, iters);
+      if (e == cudaSuccess && st == BA_OK && rep == 1) e = cudaEventRecord(e1, h->s);
+    }
+    if (e == cudaSuccess && st == BA_OK) e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess && st == BA_OK) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e == cudaSuccess && st == BA_OK)
+      e = cudaMemcpy(fin.data(), b->state, b->nprob * sizeof(BState), cudaMemcpyDeviceToHost);
+  };
+  float ref_ms = 0.f;
+  if (e == cudaSuccess && st == BA_OK) timed_run(ref_ms, ref);
+  if (e == cudaSuccess && st == BA_OK) best = std::min(best < 0.f ? ref_ms : best, ref_ms);
+  const int pieces[] = {256, 512, 1024, PIECE};
+  const int chunks[][2] = {{256, 128}, {512, 256}, {CHUNK_SLOTS, CHUNK_PTS}};
+  const int p0 = bp, s0 = bs, t0 = bpt;
+  float best_seg = ref_ms;
+  for (int pm : pieces) {
+    for (const auto& ck : chunks) {
+      if (e != cudaSuccess || st != BA_OK) break;
+      if (pm == p0 && ck[0] == s0 && ck[1] == t0) continue;
+      st = ba_batch_set_segments(b, pm, ck[0], ck[1]);
+      float ms = 0.f;
+      if (st == BA_OK) timed_run(ms, got);
+      if (e != cudaSuccess || st != BA_OK) break;
+      bool same = true;
+      for (int i = 0; i < b->nprob && same; ++i)
+        same = std::isfinite(got[i].F) && std::fabs(got[i].F - ref[i].F) <= 1e-6 * std::fabs(ref[i].F);
+      if (same && ms < best_seg) {
+        best_seg = ms;
+        bp = pm;
+        bs = ck[0];
+        bpt = ck[1];
+      }
+    }
+  }
+  if (e == cudaSuccess && st == BA_OK) {
+    st = ba_batch_set_segments(b, bp, bs, bpt);
+    best = best_seg;
+  }
   if (e == cudaSuccess) e = restore();
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->s);
   cudaFree(sc);
@@ -619,8 +749,10 @@ ba_status ba_batch_autotune(ba_batch* b, int iters, const char* cache_path, doub
   if (cache_path) {
     FILE* f = fopen(cache_path, "a");
     if (f) {
-      fprintf(f, "{\"key\": \"%s\", \"variant\": %d, \"ctas_per_sm\": %d, \"order\": %d, \"ms\": %.4f, \"iters\": %d}\n",
-              key.c_str(), bv, bc, bo, best, iters);
+      fprintf(f,
+              "{\"key\": \"%s\", \"variant\": %d, \"ctas_per_sm\": %d, \"order\": %d, \"piece_max\": %d, "
+              "\"chunk_slots\": %d, \"chunk_pts\": %d, \"ms\": %.4f, \"iters\": %d}\n",
+              key.c_str(), bv, bc, bo, bp, bs, bpt, best, iters);
       fclose(f);
     }
   }

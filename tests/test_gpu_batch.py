@@ -219,11 +219,22 @@ def test_batch_autotune_keeps_results_and_caches(tmp_path):
     with ba.Batch(inputs, opts) as bt:
         bt.solve(3)
         ref_stats, ref_params = bt.stats(), bt.params(split=False)
+        ref_cost = np.asarray(bt.scalars()[0])
         bt.reset()
         cfg, ms = bt.autotune(3, cache)
         assert ms > 0.0 and cache.exists()
+        assert {"piece_max", "chunk_slots", "chunk_pts", "ctas_per_sm", "variant", "order"} <= set(cfg)
         # the tuner restored the batch's state
         assert all(len(s) == 0 for s in bt.stats())
+        bt.solve(3)
+        # the chosen segments pass the tuner's gate: every final cost within
+        # 1e-6 of the default cut's
+        cost = np.asarray(bt.scalars()[0])
+        assert np.all(np.abs(cost - ref_cost) <= 1e-6 * np.abs(ref_cost))
+        # the launch configuration alone never changes a result: at the
+        # default segments the tuned launch reproduces the first run bit for bit
+        bt.set_segments()
+        bt.reset()
         bt.solve(3)
         for b in range(bt.n):
             _same_stats(ref_stats[b], bt.stats()[b], ctx=b)
@@ -232,6 +243,41 @@ def test_batch_autotune_keeps_results_and_caches(tmp_path):
     with ba.Batch(inputs, opts) as bt2:
         cfg2, ms2 = bt2.autotune(3, cache)
         assert ms2 == 0.0 and cfg2 == cfg
+
+
+@pytest.mark.parametrize("seg", [(256, 256, 128), (512, 512, 256), (1024, 1024, 512), (32, 32, 8)])
+def test_batch_segments_change_only_rounding(seg):
+    """Another cut of the pieces and point chunks reorders some sums only:
+    FP64 with a tight PCG follows the oracle's LM trial by trial at 1e-9 on
+    sampled problems (the heavy point, wider than a 32-slot chunk, takes the
+    block-reduced path), and the FP32 final costs of converged runs stay
+    within 1e-6 of the default cut's."""
+    scenes = _scenes()
+    inputs = _inputs(scenes)
+    opts = ba.Options(precision="f64", pcg_maxiter=300, pcg_tol=1e-12)
+    with ba.Batch(inputs, opts) as bt:
+        bt.set_segments(*seg)
+        assert bt.segments() == dict(piece_max=seg[0], chunk_slots=seg[1], chunk_pts=seg[2])
+        bt.solve(6)
+        bst = bt.stats()
+    for b in (0, 3, len(scenes) - 2, len(scenes) - 1):
+        s = scenes[b]
+        _, _, ref = orc.lm(s.cams_init, s.points_init, s.cam_idx, s.pt_idx, inputs[b][4], 6,
+                           orc.LMOptions(solver="cholesky", huber_delta=0.0))
+        F0 = ref[0]["cost"]
+        for t, (x, y) in enumerate(zip(bst[b], ref)):
+            assert abs(x["cost"] - y["cost"]) <= 1e-9 * y["cost"] + 1e-15 * F0, (s.name, t, x, y)
+    o32 = ba.Options(precision="f32", pcg_maxiter=40, pcg_tol=1e-6)
+    with ba.Batch(inputs, o32) as d, ba.Batch(inputs, o32) as c:
+        c.set_segments(*seg)
+        d.solve(40)
+        c.solve(40)
+        Fd = np.asarray(d.scalars()[0])
+        Fc = np.asarray(c.scalars()[0])
+    # an absolute floor of 1e-7 of the noise energy for the one-camera
+    # problem, whose minimum is zero
+    ok = np.abs(Fc - Fd) <= 1e-6 * Fd + 1e-7 * np.array([0.5 * float(np.sum(s.noise ** 2)) for s in scenes])
+    assert np.all(ok), (Fc, Fd)
 
 
 def test_batch_rejects_bad_inputs():
