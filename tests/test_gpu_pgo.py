@@ -169,6 +169,28 @@ def test_pcg_with_a_hub_node_matches_the_oracle():
     assert rel <= 1e-13 and _rel(dx2.cpu(), exact) < 1e-8
 
 
+def test_pcg_grid_stride_on_a_large_graph_matches_the_oracle():
+    """12,000 poses (a chain with closures every 50 poses): more node groups
+    than the PCG grid holds resident blocks, so blocks stride over several
+    groups; 10 iterations against the oracle's."""
+    rng = np.random.default_rng(41)
+    N = 12000
+    ei = np.concatenate([np.arange(N - 1), np.arange(0, N - 50, 7)]).astype(np.int32)
+    ej = np.concatenate([np.arange(1, N), np.arange(50, N, 7)]).astype(np.int32)
+    E = len(ei)
+    P7 = np.concatenate([rng.normal(size=(N, 3)) * 5, rng.normal(size=(N, 4))], 1)
+    Ts = pgo.poses_to_matrices(P7)
+    Tms = np.stack([pgo.se3_exp(rng.normal(size=6) * 0.05) @ pgo.se3_inv(Ts[i]) @ Ts[j] for i, j in zip(ei, ej)])
+    info = np.tile(pgo.info_upper(np.eye(6)), (E, 1))
+    gg = scenegen.PoseGraph(poses_gt=P7, ei=ei, ej=ej, noise=np.zeros((E, 6)), info=info, drift=np.zeros((N, 6)))
+    blk = pgo.assemble(Ts, ei, ej, Tms, np.tile(np.eye(6), (E, 1, 1)))
+    m = _mask(N, (0,))
+    want, _, _ = pgo.solve_damped(blk, 1e-3, LMOptions(solver="pcg", pcg_tol=0.0, pcg_maxiter=10), m)
+    with _make(gg, P7, pgo.matrices_to_poses(Tms)) as pg:
+        dx, its, _ = pg.damped_solve(1e-3, 10, 0.0)
+    assert its == 10 and _rel(dx.cpu(), want) < 1e-9
+
+
 @pytest.mark.parametrize("kind", ["chain", "random"])
 def test_banded_cholesky_matches_the_oracle(kind):
     """The Cholesky solver factors within the band of the node order: a
