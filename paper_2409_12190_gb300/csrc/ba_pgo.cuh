@@ -28,6 +28,7 @@
 //   k_pgo_dense      block row i of H + D, for the dense Cholesky solver
 #pragma once
 
+#include <cuda/atomic>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -460,36 +461,37 @@ struct GridBar {
 };
 
 // Bounded grid-wide barrier (all blocks co-resident: cooperative launch).
+// Thread 0 of each block arrives with an acquire-release increment of the
+// counter (its block's writes, ordered before it by the block barrier, are
+// released with it); the last block to arrive resets the counter and
+// releases the next generation, which the others poll with acquire loads.
 // Returns false if the wait ran out or another block's did (gb->err).
 __device__ __forceinline__ bool grid_barrier(GridBar* gb, unsigned int nblocks) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned int* vgen = &gb->gen;
-    volatile int* verr = &gb->err;
-    const unsigned int g0 = *vgen;
-    __threadfence();
-    const unsigned int arrived = atomicAdd(&gb->count, 1u);
+    cuda::atomic_ref<unsigned int, cuda::thread_scope_device> cnt(gb->count), gen(gb->gen);
+    cuda::atomic_ref<int, cuda::thread_scope_device> err(gb->err);
+    const unsigned int g0 = gen.load(cuda::memory_order_relaxed);
+    const unsigned int arrived = cnt.fetch_add(1u, cuda::memory_order_acq_rel);
     int ok = 1;
     if (arrived == nblocks - 1) {
-      atomicExch(&gb->count, 0u);
-      __threadfence();
-      atomicAdd(&gb->gen, 1u);
+      cnt.store(0u, cuda::memory_order_relaxed);
+      gen.fetch_add(1u, cuda::memory_order_release);
     } else {
       // 2^25 polls (all but the first 256 after a >= 32 ns sleep): a
       // second or more before giving up
       unsigned int spins = 0;
-      while (*vgen == g0) {
-        if (*verr || ++spins > (1u << 25)) {
+      while (gen.load(cuda::memory_order_acquire) == g0) {
+        if (err.load(cuda::memory_order_relaxed) || ++spins > (1u << 25)) {
           ok = 0;
-          atomicExch(&gb->err, 1);
+          err.store(1, cuda::memory_order_relaxed);
           break;
         }
         if (spins > 256) __nanosleep(32);
       }
     }
-    __threadfence();
-    s_ok = ok && !*verr;
+    s_ok = ok && !err.load(cuda::memory_order_relaxed);
   }
   __syncthreads();
   return s_ok != 0;

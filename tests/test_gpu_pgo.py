@@ -272,6 +272,48 @@ def test_set_poses_and_fixed_poses():
         assert abs(F - pgo.cost(Ts, g.ei, g.ej, Tms, infos)) <= 1e-12 * F
 
 
+@pytest.mark.parametrize("case", ["isolated", "duplicate", "two"])
+def test_degenerate_graphs_match_the_oracle(case):
+    """A pose with no edge (H_ii = 0: the damping's clamp keeps its block
+    SPD and its step is 0), two edges between the same pair (summed in
+    order), and the smallest graph (two poses, one edge)."""
+    rng = np.random.default_rng(51)
+    if case == "two":
+        N, ei, ej = 2, np.array([0], np.int32), np.array([1], np.int32)
+    else:
+        N = 12
+        ei = np.arange(N - 2, dtype=np.int32)
+        ej = ei + 1
+        if case == "duplicate":
+            ei = np.concatenate([ei, [3, 3]]).astype(np.int32)
+            ej = np.concatenate([ej, [7, 7]]).astype(np.int32)
+        # "isolated": pose N - 1 has no edge
+    E = len(ei)
+    P7 = np.concatenate([rng.normal(size=(N, 3)) * 3, rng.normal(size=(N, 4))], 1)
+    Ts = pgo.poses_to_matrices(P7)
+    Tms = np.stack([pgo.se3_exp(rng.normal(size=6) * 0.2) @ pgo.se3_inv(Ts[i]) @ Ts[j] for i, j in zip(ei, ej)])
+    Om = np.stack([np.diag(rng.uniform(0.5, 2.0, 6)) for _ in range(E)])
+    info = np.stack([pgo.info_upper(M) for M in Om])
+    gg = scenegen.PoseGraph(poses_gt=P7, ei=ei, ej=ej, noise=np.zeros((E, 6)), info=info, drift=np.zeros((N, 6)))
+    # two poses and one edge: the cost reaches 0 exactly after the second
+    # trial, where further decisions compare rounding noise
+    iters = 2 if case == "two" else 6
+    T_ref, ref = pgo.lm(Ts, ei, ej, Tms, Om, iters, LMOptions(solver="cholesky"), _mask(N, (0,)))
+    F0 = ref[0]["cost"]
+    for solver in ("cholesky", "pcg"):
+        with _make(gg, P7, pgo.matrices_to_poses(Tms), solver=solver, pcg_tol=1e-13, pcg_maxiter=500) as pg:
+            pg.solve(iters)
+            st = pg.stats()
+            poses = pgo.poses_to_matrices(pg.poses().cpu().numpy())
+        assert len(st) == iters
+        for t, (a, b) in enumerate(zip(st, ref)):
+            assert a["accepted"] == b["accepted"], (solver, t)
+            assert abs(a["cost_trial"] - b["cost_trial"]) <= 1e-9 * b["cost"] + 1e-15 * F0, (solver, t, a, b)
+        assert np.max(np.abs(poses - T_ref)) < 1e-8, solver
+        if case == "isolated":
+            assert np.max(np.abs(poses[N - 1] - Ts[N - 1])) < 1e-14
+
+
 def test_invalid_inputs_are_reported():
     g = _graph()
     _, _, _, _, P7, M7 = _inputs(g)
