@@ -1,6 +1,7 @@
 /* A C program that uses the library through include/ba.h alone: it reads
  * the defaults and checks the argument errors that need no GPU.  Built and
  * run by tests/test_abi.py. */
+#include <stdint.h>
 #include <stdio.h>
 #include <string.h>
 
@@ -32,6 +33,19 @@ int main(void) {
   CHECK(ba_csr_build(NULL, -1, 3, NULL, NULL, NULL) == BA_ERR_INVALID_ARG);
   CHECK(ba_csr_build_noalloc(NULL, BA_NOALLOC_MAX_KEYS + 1, 3, NULL, NULL, NULL) == BA_ERR_INVALID_ARG);
   CHECK(ba_problem_destroy(NULL) == BA_OK);
+  /* pose graphs: argument errors found before any device work */
+  ba_pgo* g = (ba_pgo*)1;
+  CHECK(ba_pgo_create(&g, 1, 1, NULL, NULL, NULL, NULL, NULL, NULL, &o, NULL) == BA_ERR_INVALID_ARG);
+  CHECK(g == NULL);
+  CHECK(ba_pgo_create(NULL, 4, 3, NULL, NULL, NULL, NULL, NULL, NULL, &o, NULL) == BA_ERR_INVALID_ARG);
+  ba_options o32 = o;
+  o32.precision = BA_PREC_F32;
+  double pose[14] = {0, 0, 0, 0, 0, 0, 1, 1, 0, 0, 0, 0, 0, 1};
+  int32_t ei = 0, ej = 1;
+  double info[21] = {0};
+  CHECK(ba_pgo_create(&g, 2, 1, pose, &ei, &ej, pose, info, NULL, &o32, NULL) == BA_ERR_INVALID_ARG);
+  CHECK(ba_pgo_solve(NULL, 1, NULL) == BA_ERR_INVALID_ARG);
+  CHECK(ba_pgo_destroy(NULL) == BA_OK);
   CHECK(ba_state_size(NULL) == 0);
   printf("%s\n", fails ? "FAIL" : "OK");
   return fails ? 1 : 0;

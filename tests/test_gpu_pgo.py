@@ -314,6 +314,51 @@ def test_degenerate_graphs_match_the_oracle(case):
             assert np.max(np.abs(poses[N - 1] - Ts[N - 1])) < 1e-14
 
 
+def test_c_program_solves_a_pose_graph(tmp_path):
+    """A C99 program solves sphere100 through include/ba.h with host
+    pointers only; its per-trial costs and final poses match the oracle's LM
+    with the Cholesky solve."""
+    import os
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    from paper_2409_12190_gb300 import build as b
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    libdir = os.path.dirname(b.build())
+    exe = tmp_path / "pgo_from_c"
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-I", os.path.join(root, "include"),
+                    os.path.join(root, "tests", "c", "pgo_from_c.c"), "-L", libdir, "-lba_gb300",
+                    f"-Wl,-rpath,{libdir}", "-o", str(exe)], check=True)
+    g = scenegen.pose_graph_config("sphere100")
+    Ts, Tms, infos, _, P7, M7 = _inputs(g)
+    iters = 8
+    fixed = np.zeros(g.N, np.uint8)
+    fixed[0] = 1
+    path = tmp_path / "graph.bin"
+    with open(path, "wb") as f:
+        np.array([g.N, g.E, iters, 1, 0], dtype=np.int32).tofile(f)  # solver 1: Cholesky
+        np.array([0.0], dtype=np.float64).tofile(f)
+        np.ascontiguousarray(P7, dtype=np.float64).tofile(f)
+        np.ascontiguousarray(g.ei, dtype=np.int32).tofile(f)
+        np.ascontiguousarray(g.ej, dtype=np.int32).tofile(f)
+        np.ascontiguousarray(M7, dtype=np.float64).tofile(f)
+        np.ascontiguousarray(g.info, dtype=np.float64).tofile(f)
+        fixed.tofile(f)
+    out = subprocess.run([str(exe), str(path)], capture_output=True, text=True, timeout=300)
+    assert out.returncode == 0, out.stderr
+    lines = out.stdout.split("\n")
+    trials = [ln.split() for ln in lines if ln.startswith("trial ")]
+    poses = np.array([float(ln.split()[1]) for ln in lines if ln.startswith("pose ")]).reshape(g.N, 7)
+    T_ref, ref = pgo.lm(Ts, g.ei, g.ej, Tms, infos, iters, LMOptions(solver="cholesky"), _mask(g.N, (0,)))
+    assert len(trials) == iters
+    for t, r in zip(trials, ref):
+        assert abs(float(t[2]) - r["cost"]) <= 1e-9 * r["cost"], (t, r)
+        assert abs(float(t[3]) - r["cost_trial"]) <= 1e-9 * r["cost"], (t, r)
+        assert bool(int(t[4])) == r["accepted"], (t, r)
+    assert np.max(np.abs(pgo.poses_to_matrices(poses) - T_ref)) < 1e-8
+
+
 def test_invalid_inputs_are_reported():
     g = _graph()
     _, _, _, _, P7, M7 = _inputs(g)
