@@ -159,7 +159,9 @@ struct ba_pgo {
   int nbe = 0, nbn = 0;  // blocks of the edge and node kernels
   int pcg_grid = 0, pcg_npb = 0;  // PCG: blocks, nodes per block pass
   size_t pcg_res_smem = 0;        // > 0: the register-resident PCG, its shared memory
-  int band = 0;                   // half-bandwidth of H in unknowns (node order)
+  int band = 0;                   // half-bandwidth of H + D in unknowns, in the factored order
+  int32_t* pos = nullptr;         // Cholesky: block position of each node (RCM), or NULL (node order)
+  double *rp = nullptr, *xp = nullptr;  // right-hand side and solution in the factored order
   std::vector<void*> allocs;
   int32_t *ei = nullptr, *ej = nullptr, *rowptr = nullptr, *inc = nullptr;
   int2* inc2 = nullptr;
@@ -195,6 +197,85 @@ namespace {
 ba_status copy_in(void* dst, const void* src, size_t bytes, cudaStream_t s) {
   PCU(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, s));
   return BA_OK;
+}
+
+// Reverse Cuthill-McKee order of the pose graph (the factored order of the
+// Cholesky solver): per connected component, a pseudo-peripheral start
+// (the lowest-degree node of the last breadth-first level, twice), then a
+// breadth-first walk visiting each node's unvisited neighbours by
+// increasing degree (ties by index), reversed.  Returns order[k] = the node
+// at position k.
+std::vector<int32_t> rcm_order(int N, const std::vector<int32_t>& ei, const std::vector<int32_t>& ej) {
+  std::vector<std::vector<int32_t>> adj(N);
+  for (size_t k = 0; k < ei.size(); ++k) {
+    adj[ei[k]].push_back(ej[k]);
+    adj[ej[k]].push_back(ei[k]);
+  }
+  std::vector<int32_t> deg(N);
+  for (int i = 0; i < N; ++i) {
+    std::sort(adj[i].begin(), adj[i].end());
+    adj[i].erase(std::unique(adj[i].begin(), adj[i].end()), adj[i].end());
+    deg[i] = (int32_t)adj[i].size();
+  }
+  std::vector<char> done(N, 0);
+  std::vector<int32_t> level(N, -1), order, touched, q;
+  order.reserve(N);
+  // breadth-first levels from s within the unplaced nodes; returns the last
+  // level's lowest-degree node and the eccentricity
+  auto far_node = [&](int s0, int& ecc) {
+    for (int v : touched) level[v] = -1;
+    touched.clear();
+    q.assign(1, s0);
+    level[s0] = 0;
+    touched.push_back(s0);
+    for (size_t h = 0; h < q.size(); ++h)
+      for (int w : adj[q[h]])
+        if (!done[w] && level[w] < 0) {
+          level[w] = level[q[h]] + 1;
+          touched.push_back(w);
+          q.push_back(w);
+        }
+    ecc = level[q.back()];
+    int best = q.back();
+    for (int v : q)
+      if (level[v] == ecc && (deg[v] < deg[best] || (deg[v] == deg[best] && v < best))) best = v;
+    return best;
+  };
+  for (;;) {
+    int start = -1;
+    for (int i = 0; i < N; ++i)
+      if (!done[i] && (start < 0 || deg[i] < deg[start])) start = i;
+    if (start < 0) break;
+    int ecc = 0;
+    int cand = far_node(start, ecc);
+    for (int rep = 0; rep < 2; ++rep) {
+      int e2 = 0;
+      const int c2 = far_node(cand, e2);
+      if (e2 <= ecc) break;
+      start = cand;
+      cand = c2;
+      ecc = e2;
+    }
+    start = cand;
+    // Cuthill-McKee walk of the component
+    q.assign(1, start);
+    done[start] = 1;
+    std::vector<int32_t> nb;
+    for (size_t h = 0; h < q.size(); ++h) {
+      const int v = q[h];
+      order.push_back(v);
+      nb.clear();
+      for (int w : adj[v])
+        if (!done[w]) nb.push_back(w);
+      std::sort(nb.begin(), nb.end(), [&](int a, int b) { return deg[a] != deg[b] ? deg[a] < deg[b] : a < b; });
+      for (int w : nb) {
+        done[w] = 1;
+        q.push_back(w);
+      }
+    }
+  }
+  std::reverse(order.begin(), order.end());
+  return order;
 }
 
 ba_status check_pgo_options(const ba_options* o) {
@@ -243,12 +324,21 @@ ba_status enqueue_solve(ba_pgo* h, const double* lam_ptr, int maxiter, double to
                                                  h->opt.diag_max, h->D, h->Minv, h->x, h->r, h->dpart, h->st);
   count_launch();
   if (h->opt.solver == BA_SOLVER_CHOLESKY) {
-    // H + D is banded in the node order (half-bandwidth h->band): only the
-    // tiles within the band are factored, and the solve stays in the band
+    // H + D is banded in the factored order (node order, or a reverse
+    // Cuthill-McKee order when that is narrower; half-bandwidth h->band):
+    // only the tiles within the band are factored, and the solve stays in it
     const int n = 6 * h->N;
     const int bw = h->band;
-    k_pgo_dense<<<h->N, 256, 0, s>>>(h->N, h->rowptr, h->inc, h->ei, h->ej, h->B, h->Hd, h->D, h->dS);
+    k_pgo_dense<<<h->N, 256, 0, s>>>(h->N, h->rowptr, h->inc, h->ei, h->ej, h->B, h->Hd, h->D, h->pos, h->dS);
     count_launch();
+    const double* rhs = h->r;
+    double* sol = h->x;
+    if (h->pos) {
+      k_pgo_permute<<<nb(n, 256), 256, 0, s>>>(h->N, h->pos, 0, h->r, h->rp);
+      count_launch();
+      rhs = h->rp;
+      sol = h->xp;
+    }
     if (h->fixed) {
       k_dense_mask<<<nb((long long)n * n, 256), 256, 0, s>>>(n, h->fixed6, h->dS);
       count_launch();
@@ -266,8 +356,12 @@ ba_status enqueue_solve(ba_pgo* h, const double* lam_ptr, int maxiter, double to
       }
       count_launch();
     }
-    k_dense_solve<<<1, 1024, 0, s>>>(n, bw, h->dS, h->r, h->dy, h->x, h->dfail, h->st);
+    k_dense_solve<<<1, 1024, 0, s>>>(n, bw, h->dS, rhs, h->dy, sol, h->dfail, h->st);
     count_launch();
+    if (h->pos) {
+      k_pgo_permute<<<nb(n, 256), 256, 0, s>>>(h->N, h->pos, 1, h->xp, h->x);
+      count_launch();
+    }
     return BA_OK;
   }
   PCU(cudaMemsetAsync(h->bar, 0, sizeof(GridBar), s));
@@ -406,6 +500,7 @@ ba_status ba_pgo_create(ba_pgo** out, int N, int E, const double* poses, const i
     A(&h->dy, 8ull * n6);
     A(&h->dfail, sizeof(int));
   }
+  std::vector<int32_t> hpos;  // Cholesky: block position of each node, empty for the node order
   int32_t* keys = nullptr;
   int32_t* perm = nullptr;
   void* scratch = nullptr;
@@ -435,6 +530,23 @@ ba_status ba_pgo_create(ba_pgo** out, int N, int E, const double* poses, const i
     long long bwn = 0;
     for (int k = 0; k < E; ++k) bwn = std::max<long long>(bwn, std::llabs((long long)hi[k] - hj[k]));
     h->band = (int)std::min<long long>(6 * bwn + 5, n6 - 1);
+    if (o.solver == BA_SOLVER_CHOLESKY) {
+      // the reverse Cuthill-McKee order when its band is narrower
+      const std::vector<int32_t> order = rcm_order(N, hi, hj);
+      hpos.assign(N, 0);
+      for (int k = 0; k < N; ++k) hpos[order[k]] = k;
+      long long bwr = 0;
+      for (int k = 0; k < E; ++k) bwr = std::max<long long>(bwr, std::llabs((long long)hpos[hi[k]] - hpos[hj[k]]));
+      if (bwr < bwn) {
+        h->band = (int)std::min<long long>(6 * bwr + 5, n6 - 1);
+        if ((e = h->alloc(&h->pos, 4ull * N)) != cudaSuccess || (e = h->alloc(&h->rp, 8ull * n6)) != cudaSuccess ||
+            (e = h->alloc(&h->xp, 8ull * n6)) != cudaSuccess ||
+            (e = cudaMemcpy(h->pos, hpos.data(), 4ull * N, cudaMemcpyHostToDevice)) != cudaSuccess)
+          return bail(set_error(e == cudaErrorMemoryAllocation ? BA_ERR_OOM : BA_ERR_CUDA, "reordering set-up failed"));
+      } else {
+        hpos.clear();  // node order
+      }
+    }
   }
   // incidence CSR: stable sort of [ei..., ej...] by node
   if ((e = cudaMemcpyAsync(keys, h->ei, 4ull * E, cudaMemcpyDeviceToDevice, s)) != cudaSuccess ||
@@ -476,7 +588,10 @@ ba_status ba_pgo_create(ba_pgo** out, int N, int E, const double* poses, const i
     if ((e = cudaMemcpyAsync(hf.data(), h->fixed, (size_t)N, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
         (e = cudaStreamSynchronize(s)) != cudaSuccess)
       return bail(set_error(BA_ERR_CUDA, "copy of the fixed mask failed"));
-    for (long long k = 0; k < n6; ++k) hf6[k] = hf[k / 6] ? 1 : 0;
+    for (long long k = 0; k < n6; ++k) {
+      const long long i = k / 6;
+      hf6[hpos.empty() ? k : 6LL * hpos[i] + k % 6] = hf[i] ? 1 : 0;
+    }
     if ((e = cudaMemcpyAsync(h->fixed6, hf6.data(), (size_t)n6, cudaMemcpyHostToDevice, s)) != cudaSuccess)
       return bail(set_error(BA_ERR_CUDA, "copy of the fixed mask failed"));
   }

@@ -906,6 +906,17 @@ static __global__ void __launch_bounds__(PGO_PCG_THREADS, 1) k_pgo_pcg_res(PcgAr
   }
 }
 
+// y[6 pos[i] + a] = x[6 i + a] (to the factored order), or back (inverse).
+static __global__ void k_pgo_permute(int N, const int32_t* __restrict__ pos, int inverse,
+                                     const double* __restrict__ x, double* __restrict__ y) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 6LL * N) return;
+  const int i = (int)(t / 6), a = (int)(t % 6);
+  const long long o = 6LL * pos[i] + a;
+  if (inverse) y[t] = x[o];
+  else y[o] = x[t];
+}
+
 // ---------------------------------------------------------------------------
 // Trial, cost and the LM decision
 // ---------------------------------------------------------------------------
@@ -1010,23 +1021,26 @@ static __global__ void k_pgo_control(int nbe, const double* __restrict__ epart, 
   st->trials = t + 1;
 }
 
-// Block row i (6 rows of the dense 6N x 6N matrix H + D): zero, H_ii + D_i
-// on the diagonal block, then -B_e into block (i, other(e)) for each
-// incident edge in CSR order (one thread per block entry: parallel edges
-// between the same two nodes accumulate in order).
+// Block row i (6 rows of the dense 6N x 6N matrix H + D, at block position
+// pos[i] of the factored order, or i without pos): zero, H_ii + D_i on the
+// diagonal block, then -B_e into block (i, other(e)) for each incident edge
+// in CSR order (one thread per block entry: parallel edges between the same
+// two nodes accumulate in order).
 static __global__ void __launch_bounds__(256)
 k_pgo_dense(int N, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ inc,
             const int32_t* __restrict__ ei, const int32_t* __restrict__ ej, const double* __restrict__ B,
-            const double* __restrict__ Hd, const double* __restrict__ D, double* __restrict__ S) {
+            const double* __restrict__ Hd, const double* __restrict__ D, const int32_t* __restrict__ pos,
+            double* __restrict__ S) {
   const int i = blockIdx.x;
   const long long n = 6LL * N;
-  double* row = S + 6LL * i * n;
+  const int pi = pos ? pos[i] : i;  // node i's block position in the factored order
+  double* row = S + 6LL * pi * n;
   for (long long k = threadIdx.x; k < 6 * n; k += blockDim.x) row[k] = 0.0;
   __syncthreads();
   const int t = threadIdx.x;
   if (t < 36) {
     const int a = t / 6, b = t % 6;
-    double* dst = row + (long long)a * n + 6LL * i + b;
+    double* dst = row + (long long)a * n + 6LL * pi + b;
     *dst = Hd[21LL * i + (a <= b ? sym6(a, b) : sym6(b, a))] + (a == b ? D[6LL * i + a] : 0.0);
   }
   __syncthreads();
@@ -1037,7 +1051,8 @@ k_pgo_dense(int N, const int32_t* __restrict__ rowptr, const int32_t* __restrict
       const int code = inc[s];
       const int e = code >> 1;
       const int other = (code & 1) ? ei[e] : ej[e];
-      row[(long long)a * n + 6LL * other + b] -= B[36LL * e + 6 * a + b];
+      const int po = pos ? pos[other] : other;
+      row[(long long)a * n + 6LL * po + b] -= B[36LL * e + 6 * a + b];
     }
   }
 }

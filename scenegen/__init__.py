@@ -30,7 +30,8 @@ import math
 import numpy as np
 
 __all__ = ["Scene", "ring_scene", "arc_scene", "batch_scenes", "config_scene",
-           "subsample_points", "PoseGraph", "sphere_graph", "garage_graph", "pose_graph_config"]
+           "subsample_points", "PoseGraph", "sphere_graph", "garage_graph", "pose_graph_config", "relabel",
+           "relabel_perm"]
 
 
 @dataclasses.dataclass
@@ -359,6 +360,23 @@ def garage_graph(laps: int, per_lap: int, *, seed: int, n_closures=None, side: f
             if 0 <= a - per_lap + d < a - 1]
     return _graph(rng, pos, quat, _pick(rng, cand, n_closures), sigma_t=sigma_t, sigma_r=sigma_r,
                   drift_t=drift_t, drift_r=drift_r, full_info=full_info, name=name)
+
+
+def relabel_perm(N: int, *, seed: int) -> np.ndarray:
+    """The seeded random renumbering of relabel: node n becomes perm[n]."""
+    return np.random.default_rng(seed).permutation(N)
+
+
+def relabel(graph: PoseGraph, *, seed: int) -> PoseGraph:
+    """The same graph with its nodes renumbered by a seeded random
+    permutation (node n becomes relabel_perm(N, seed)[n]; edges, noise and
+    information keep their order)."""
+    perm = relabel_perm(graph.N, seed=seed)
+    inv = np.empty_like(perm)
+    inv[perm] = np.arange(graph.N)
+    return PoseGraph(poses_gt=graph.poses_gt[inv], ei=perm[graph.ei].astype(np.int32),
+                     ej=perm[graph.ej].astype(np.int32), noise=graph.noise.copy(), info=graph.info.copy(),
+                     drift=graph.drift[inv], name=graph.name + "-relabelled")
 
 
 def pose_graph_config(which: str) -> PoseGraph:

@@ -245,6 +245,26 @@ def test_lm_trace_matches_the_oracle(solver):
     assert abs(F - pgo.cost(pgo.poses_to_matrices(poses), g.ei, g.ej, Tms, infos)) <= 1e-12 * F
 
 
+def test_cholesky_on_a_shuffled_numbering_matches_the_oracle():
+    """sphere100 with its poses renumbered at random: the band of the node
+    order is then nearly the whole matrix and the Cholesky solver factors in
+    its reverse Cuthill-McKee order; the 8-trial trace against the
+    oracle's (which solves in the node order)."""
+    g = scenegen.relabel(scenegen.pose_graph_config("sphere100"), seed=4)
+    Ts, Tms, infos, _, P7, M7 = _inputs(g)
+    fixed = (int(np.argmin(np.abs(np.arange(g.N) - 50))),)
+    T_ref, ref = pgo.lm(Ts, g.ei, g.ej, Tms, infos, 8, LMOptions(solver="cholesky"), _mask(g.N, fixed))
+    with _make(g, P7, M7, fixed=fixed, solver="cholesky") as pg:
+        pg.solve(8)
+        st = pg.stats()
+        poses = pg.poses().cpu().numpy()
+    for t, (a, b) in enumerate(zip(st, ref)):
+        assert a["accepted"] == b["accepted"], t
+        for key in ("cost", "cost_trial", "model"):
+            assert abs(a[key] - b[key]) <= 1e-9 * abs(b["cost"]), (t, key, a[key], b[key])
+    assert np.max(np.abs(pgo.poses_to_matrices(poses) - T_ref)) < 1e-8
+
+
 def test_noise_free_graph_reaches_the_truth():
     g = _graph(noise=False)
     Ts, Tms, infos, Tg, P7, M7 = _inputs(g)
