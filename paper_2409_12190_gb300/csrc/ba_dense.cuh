@@ -15,7 +15,8 @@
 //   k_dense_mask     S -> m S m + (I - m) for frozen parameters.
 //   k_chol_diag      factor the diagonal DB x DB block of the current block
 //                    column (one CTA, in shared memory).
-//   k_chol_panel     L_ik = A_ik L_kk^{-T} for the block rows below.
+//   k_chol_panel     L_ik = A_ik L_kk^{-T} for the block rows below (one
+//                    warp per block of rows; k_chol_panel4: four warps).
 //   k_chol_update    A_IJ -= L_Ik L_Jk^T on the trailing lower triangle.
 //   k_dense_solve    L L^T x = b (one CTA: forward then backward
 //                    substitution, column by column), x into the PCG
@@ -143,22 +144,28 @@ k_chol_diag(int n, int kb, double* __restrict__ A, int* __restrict__ fail) {
   }
   __syncthreads();
   for (int c = 0; c < nb; ++c) {
+    // the pivot's reciprocal square root: one FP64 sequence on the
+    // column's critical path, then multiplications (a division per entry
+    // and a square root cost as much each on this GPU's FP64 pipe)
     const double d = L[c][c];
     const bool ok = d > 0.0 && isfinite(d);
-    const double piv = ok ? sqrt(d) : 1.0;
+    const double rs = ok ? rsqrt(d) : 1.0;
     __syncthreads();
     if (tid == 0) {
-      L[c][c] = piv;
+      L[c][c] = ok ? d * rs : 1.0;
       if (!ok) *fail = 1;
     }
     // column below the pivot
-    for (int r = c + 1 + tid; r < nb; r += blockDim.x) L[r][c] /= piv;
+    for (int r = c + 1 + tid; r < nb; r += blockDim.x) L[r][c] *= rs;
     __syncthreads();
-    // rank-1 update of the trailing lower triangle
+    // rank-1 update of the trailing lower triangle (its m (m + 1) / 2 entries)
     const int m = nb - c - 1;
-    for (int e = tid; e < m * m; e += blockDim.x) {
-      const int r = c + 1 + e / m, cc = c + 1 + e % m;
-      if (cc <= r) L[r][cc] -= L[r][c] * L[cc][c];
+    for (int e = tid; e < m * (m + 1) / 2; e += blockDim.x) {
+      int r = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);  // FP32 guess, corrected below
+      while ((r + 1) * (r + 2) / 2 <= e) ++r;
+      while (r * (r + 1) / 2 > e) --r;
+      const int cc = e - r * (r + 1) / 2;  // 0 <= cc <= r
+      L[c + 1 + r][c + 1 + cc] -= L[c + 1 + r][c] * L[c + 1 + cc][c];
     }
     __syncthreads();
   }
@@ -199,6 +206,41 @@ k_chol_panel(int n, int kb, double* __restrict__ A) {
     if (c < nb) A[(long long)r * n + k + c] = x[c];
 }
 
+// The same panel solve with four warps per block of DB rows (one lane per
+// row): column by column (right-looking), x_c = a_c / L_cc by warp 0 with
+// the pivot's reciprocal, then the four warps subtract x_c L_c'c from the
+// columns c' > c, a quarter each.  Spreads the FP64 work of a row block
+// over four warps instead of one.
+static __global__ void __launch_bounds__(4 * DB)
+k_chol_panel4(int n, int kb, double* __restrict__ A) {
+  __shared__ double Lk[DB][DB + 1];
+  __shared__ double xs[DB][DB + 1];
+  __shared__ double ri[DB];
+  const int k = kb * DB;
+  const int nb = min(DB, n - k);
+  const int r0 = k + nb + blockIdx.x * DB;
+  const int tid = threadIdx.x, lane = tid % DB, w = tid / DB;
+  for (int e = tid; e < DB * DB; e += blockDim.x) {
+    const int rr = e / DB, cc = e % DB;
+    Lk[rr][cc] = (rr < nb && cc <= rr) ? A[(long long)(k + rr) * n + k + cc] : 0.0;
+    xs[rr][cc] = (r0 + rr < n && cc < nb) ? A[(long long)(r0 + rr) * n + k + cc] : 0.0;
+  }
+  __syncthreads();
+  if (tid < nb) ri[tid] = 1.0 / Lk[tid][tid];
+  __syncthreads();
+  for (int c = 0; c < nb; ++c) {
+    if (w == 0) xs[lane][c] *= ri[c];
+    __syncthreads();
+    const double xc = xs[lane][c];
+    for (int cp = c + 1 + w; cp < nb; cp += 4) xs[lane][cp] -= xc * Lk[cp][c];
+    __syncthreads();
+  }
+  for (int e = tid; e < DB * DB; e += blockDim.x) {
+    const int rr = e / DB, cc = e % DB;
+    if (r0 + rr < n && cc < nb) A[(long long)(r0 + rr) * n + k + cc] = xs[rr][cc];
+  }
+}
+
 // A_IJ -= L_Ik L_Jk^T for the trailing tiles I >= J (DB x DB each) below
 // block column kb; blockIdx.x enumerates the lower-triangular tiles.
 static __global__ void __launch_bounds__(DB * DB / 4)
@@ -233,9 +275,9 @@ k_chol_update(int n, int kb, double* __restrict__ A) {
 }
 
 // x = (L L^T)^{-1} b (b = r, the reduced right-hand side); one CTA, by
-// blocks of DB unknowns: solve a block's DB x DB triangle (one thread, in
-// order), then update every remaining right-hand-side entry with the block
-// (coalesced rows of L).  bw: the half-bandwidth of L (L_ij = 0 for
+// blocks of DB unknowns: solve a block's DB x DB triangle (one warp, column
+// by column, with the reciprocals of its diagonal), then update every
+// remaining right-hand-side entry with the block (coalesced rows of L).  bw: the half-bandwidth of L (L_ij = 0 for
 // i - j > bw; n - 1 for a dense matrix), which bounds those updates.  With a
 // failed factorisation x = 0 (the LM trial is then a rejection) and the
 // failure is counted in st->fallbacks.  Writes the solve's statistics.
@@ -243,21 +285,41 @@ static __global__ void __launch_bounds__(1024)
 k_dense_solve(int n, int bw, const double* __restrict__ L, const double* __restrict__ b, double* __restrict__ y,
               double* __restrict__ x, const int* __restrict__ fail, DevState* st) {
   __shared__ double sb[DB];
+  __shared__ double tl[DB][DB + 1];  // the diagonal block's triangle
+  __shared__ double ri[DB];          // reciprocals of its diagonal
   const int tid = threadIdx.x;
+  const int lane = tid % 32;
   const bool bad = *fail != 0;
   for (int i = tid; i < n; i += blockDim.x) y[i] = bad ? 0.0 : b[i];
   __syncthreads();
   const int nblk = (n + DB - 1) / DB;
+  // stage block kb's triangle and the reciprocals of its diagonal
+  auto stage = [&](int k, int nb) {
+    for (int e = tid; e < DB * DB; e += blockDim.x) {
+      const int rr = e / DB, cc = e % DB;
+      tl[rr][cc] = (rr < nb && cc <= rr) ? L[(long long)(k + rr) * n + k + cc] : 0.0;
+    }
+    __syncthreads();
+    if (tid < nb) ri[tid] = 1.0 / tl[tid][tid];
+    __syncthreads();
+  };
   if (!bad) {
-    // forward: L y = b
+    // forward: L y = b.  A block's triangle is solved column by column by
+    // warp 0 (lane r holds y_r; y_c = y_c / L_cc, then every lane r > c
+    // subtracts L_rc y_c)
     for (int kb = 0; kb < nblk; ++kb) {
       const int k = kb * DB, nb = min(DB, n - k);
-      if (tid == 0) {
-        for (int r = 0; r < nb; ++r) {
-          double v = y[k + r];
-          for (int c = 0; c < r; ++c) v -= L[(long long)(k + r) * n + k + c] * sb[c];
-          sb[r] = v / L[(long long)(k + r) * n + k + r];
-          y[k + r] = sb[r];
+      stage(k, nb);
+      if (tid < 32) {
+        double v = lane < nb ? y[k + lane] : 0.0;
+        for (int c = 0; c < nb; ++c) {
+          const double yc = __shfl_sync(0xffffffffu, v * ri[c], c);
+          if (lane > c) v -= tl[lane][c] * yc;
+          if (lane == c) v = yc;
+        }
+        if (lane < nb) {
+          sb[lane] = v;
+          y[k + lane] = v;
         }
       }
       __syncthreads();
@@ -269,15 +331,21 @@ k_dense_solve(int n, int bw, const double* __restrict__ L, const double* __restr
       }
       __syncthreads();
     }
-    // backward: L^T x = y
+    // backward: L^T x = y (column by column from the last: x_c = y_c / L_cc,
+    // then every lane r < c subtracts L_cr x_c)
     for (int kb = nblk - 1; kb >= 0; --kb) {
       const int k = kb * DB, nb = min(DB, n - k);
-      if (tid == 0) {
-        for (int r = nb - 1; r >= 0; --r) {
-          double v = y[k + r];
-          for (int c = r + 1; c < nb; ++c) v -= L[(long long)(k + c) * n + k + r] * sb[c];
-          sb[r] = v / L[(long long)(k + r) * n + k + r];
-          y[k + r] = sb[r];
+      stage(k, nb);
+      if (tid < 32) {
+        double v = lane < nb ? y[k + lane] : 0.0;
+        for (int c = nb - 1; c >= 0; --c) {
+          const double xc = __shfl_sync(0xffffffffu, v * ri[c], c);
+          if (lane < c) v -= tl[c][lane] * xc;
+          if (lane == c) v = xc;
+        }
+        if (lane < nb) {
+          sb[lane] = v;
+          y[k + lane] = v;
         }
       }
       __syncthreads();

@@ -349,7 +349,7 @@ ba_status enqueue_solve(ba_pgo* h, const double* lam_ptr, int maxiter, double to
       k_chol_diag<<<1, DB * DB / 4, 0, s>>>(n, kb, h->dS, h->dfail);
       const int rows_below = std::min(n - (kb + 1) * DB, bw);
       if (rows_below > 0) {
-        k_chol_panel<<<(rows_below + DB - 1) / DB, DB, 0, s>>>(n, kb, h->dS);
+        k_chol_panel4<<<(rows_below + DB - 1) / DB, 4 * DB, 0, s>>>(n, kb, h->dS);
         const long long T_ = (rows_below + DB - 1) / DB;
         k_chol_update<<<(unsigned)(T_ * (T_ + 1) / 2), DB * DB / 4, 0, s>>>(n, kb, h->dS);
         count_launch(2);
