@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--backend", choices=["nccl", "gloo"], default="nccl",
+                    help="torch.distributed backend of the exchanges under torchrun (gloo: ranks may share a GPU)")
     ap.add_argument("--e2e-steps", type=int, default=0,
                     help="trials of the end-to-end leg (default: --steps, the timed trials)")
     ap.add_argument("--profile-trials", type=int, default=4)
@@ -625,11 +627,15 @@ def run_ours(args):
     from paper_2409_12190_gb300 import build as bbuild
 
     rank, world, local = dist_env()
+    local = local % max(1, torch.cuda.device_count())  # ranks share the GPUs when there are fewer
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     if world > 1:
         import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=dev)
+        if args.backend == "nccl":
+            dist.init_process_group("nccl", device_id=dev)
+        else:
+            dist.init_process_group("gloo")
     bbuild.build()
 
     def barrier():
@@ -693,11 +699,15 @@ def run_batch(args):
     from paper_2409_12190_gb300 import build as bbuild
 
     rank, world, local = dist_env()
+    local = local % max(1, torch.cuda.device_count())
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     if world > 1:
         import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=dev)
+        if args.backend == "nccl":
+            dist.init_process_group("nccl", device_id=dev)
+        else:
+            dist.init_process_group("gloo")
     bbuild.build()
     n_prob = args.batch_problems
     scenes = scenegen.batch_scenes(n_prob, seed=batch_seed(rank))

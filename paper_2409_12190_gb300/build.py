@@ -49,10 +49,14 @@ def build(verbose: bool = False, ptxas_verbose: bool = False, force: bool = Fals
         obj = os.path.join(BUILD, unit.replace(".cu", ".o"))
         if not force and not ptxas_verbose and os.path.exists(obj) and os.path.getmtime(obj) >= newest:
             return obj, ""
-        cmd = [nvcc, *_flags(extra), "-c", os.path.join(CSRC, unit), "-o", obj]
+        # a per-process temporary, then an atomic rename: processes that
+        # build at the same time (the ranks of one job) never see a torn file
+        tmp_obj = f"{obj}.{os.getpid()}.tmp"
+        cmd = [nvcc, *_flags(extra), "-c", os.path.join(CSRC, unit), "-o", tmp_obj]
         res = subprocess.run(cmd, capture_output=True, text=True)
         if res.returncode != 0:
             raise RuntimeError(f"nvcc failed for {unit}:\n{' '.join(cmd)}\n{res.stdout}\n{res.stderr}")
+        os.replace(tmp_obj, obj)
         return obj, res.stdout + res.stderr
 
     with cf.ThreadPoolExecutor(max_workers=len(UNITS)) as ex:
@@ -60,7 +64,7 @@ def build(verbose: bool = False, ptxas_verbose: bool = False, force: bool = Fals
     logs = "".join(r[1] for r in results)
     objs = [r[0] for r in results]
     if force or not os.path.exists(LIB) or any(os.path.getmtime(o) > os.path.getmtime(LIB) for o in objs):
-        tmp = LIB + ".tmp"
+        tmp = f"{LIB}.{os.getpid()}.tmp"
         cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "static"]
         res = subprocess.run(cmd, capture_output=True, text=True)
         if res.returncode != 0:
