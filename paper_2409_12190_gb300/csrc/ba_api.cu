@@ -330,7 +330,13 @@ void enqueue_dense_solve(ba_problem* h, const double* lam_ptr) {
 }
 
 template <typename T, bool MF>
-void enqueue_solve(ba_problem* h, const double* lam_ptr, int maxiter, double tol, bool learned = false) {
+// chunk > 0 (direct launches only: not under capture, not a partitioned
+// problem): enqueue the PCG iterations chunk at a time and stop once the
+// device reports convergence, instead of enqueueing all maxiter of them
+// (the iterations after convergence return at once, but each is still
+// several launches).
+void enqueue_solve(ba_problem* h, const double* lam_ptr, int maxiter, double tol, bool learned = false,
+                   int chunk = 0) {
   cudaStream_t s = h->s;
   const double dmin = h->opt.diag_min, dmax = h->opt.diag_max;
   {
@@ -377,7 +383,15 @@ void enqueue_solve(ba_problem* h, const double* lam_ptr, int maxiter, double tol
   if (h->opt.solver == BA_SOLVER_CHOLESKY) {
     enqueue_dense_solve<T, MF>(h, lam_ptr);
   } else {
-    for (int k = 0; k < maxiter; ++k) enqueue_pcg_iter<T, MF>(h, lam_ptr, k, tol);
+    for (int k = 0; k < maxiter; ++k) {
+      enqueue_pcg_iter<T, MF>(h, lam_ptr, k, tol);
+      if (chunk > 0 && !h->xch && (k + 1) % chunk == 0 && k + 1 < maxiter) {
+        int done = 0;
+        if (cudaMemcpyAsync(&done, &h->st->pcg_done, sizeof(int), cudaMemcpyDeviceToHost, s) == cudaSuccess &&
+            cudaStreamSynchronize(s) == cudaSuccess && done)
+          break;
+      }
+    }
   }
   {
     Prof pr(h, BA_K_OTHER);
@@ -487,7 +501,7 @@ void enqueue_backward(ba_problem* h, const double* lam_ptr, int maxiter, double 
   const long long n = std::max(9LL * h->C, 3LL * h->P);
   k_adj_rhs<T><<<nblk(n, 256), 256, 0, s>>>(h->C, h->P, (const T*)dLc, (const T*)dLp, h->pnew, h->gc, h->gp);
   count_launch();
-  enqueue_solve<T, MF>(h, lam_ptr, maxiter, tol);
+  enqueue_solve<T, MF>(h, lam_ptr, maxiter, tol, false, 16);
   const T delta = (T)(h->opt.huber_delta > 0 ? h->opt.huber_delta : 0.0);
   k_adjoint_cam<T, MF><<<h->npieces, PIECE_THREADS, 0, s>>>(
       h->piece_cam, h->piece_beg, h->piece_end, h->cm_pt, h->perm_cam, (const T*)h->cm_px, (const T*)h->Jcm,
