@@ -928,7 +928,7 @@ void enqueue_slow_probes(ba_problem* h, const double* lam_ptr, int n, const int*
                          float* zhat, double* xref) {
   cudaStream_t s = h->s;
   enqueue_collect<T, MF>(h, lam_ptr, 0, nullptr, h->Xf, nullptr, nullptr);  // scales D
-  enqueue_solve<T, MF>(h, lam_ptr, maxiter_ref, tol_ref, false);
+  enqueue_solve<T, MF>(h, lam_ptr, maxiter_ref, tol_ref, false, 16);
   cudaMemcpyAsync(xref, h->x, 72ull * h->C, cudaMemcpyDeviceToDevice, s);
   for (int j = 0; j < n; ++j) {
     enqueue_solve<T, MF>(h, lam_ptr, its[j], 0.0, false);
@@ -1378,7 +1378,7 @@ ba_status ba_damped_solve(ba_problem* h, double lambda, int maxiter, double tol,
   if (st != BA_OK) return st;
   const double* lp = &h->st->lam_probe;
   BA_DISPATCH(h, enqueue_lin, 1);
-  BA_DISPATCH(h, enqueue_solve, lp, maxiter, tol, h->learned);
+  BA_DISPATCH(h, enqueue_solve, lp, maxiter, tol, h->learned, 16);
   CU(cudaGetLastError());
   if (dc) CU(cudaMemcpyAsync(dc, h->x, 72ull * h->C, cudaMemcpyDeviceToDevice, h->s));
   if (dp) {
