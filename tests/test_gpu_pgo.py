@@ -436,16 +436,18 @@ def test_full_size_blocks_and_product_match_the_oracle(which):
     assert _rel(dx.cpu(), want) < 1e-9
 
 
-@pytest.mark.parametrize("which", ["sphere2500", "garage1661"])
-def test_full_size_lm_converges_to_a_stationary_point(which):
-    """The bench configuration run to convergence: the GPU's reported cost
-    equals the oracle's cost at the GPU's poses (1e-9), every accepted trial
-    lowered it, and the oracle's gradient there has fallen by 1e-4 of the
-    starting gradient (a stationarity certificate independent of the GPU's
-    own arithmetic)."""
+@pytest.mark.parametrize("which,solver", [("sphere2500", "pcg"), ("garage1661", "pcg"), ("sphere2500", "cholesky"),
+                                          ("garage1661", "cholesky")])
+def test_full_size_lm_converges_to_a_stationary_point(which, solver):
+    """The bench configuration run to convergence with either solver (the
+    banded Cholesky factors garage1661 in its reverse Cuthill-McKee order):
+    the GPU's reported cost equals the oracle's cost at the GPU's poses
+    (1e-9), every accepted trial lowered it, and the oracle's gradient there
+    has fallen by 1e-4 of the starting gradient (a stationarity certificate
+    independent of the GPU's own arithmetic)."""
     g = scenegen.pose_graph_config(which)
     Ts, Tms, infos, _, P7, M7 = _inputs(g)
-    with _make(g, P7, M7, pcg_tol=1e-6, pcg_maxiter=5000) as pg:
+    with _make(g, P7, M7, solver=solver, pcg_tol=1e-6, pcg_maxiter=5000) as pg:
         pg.solve(30)
         st = pg.stats()
         F, _ = pg.scalars()
