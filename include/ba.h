@@ -623,10 +623,14 @@ ba_status ba_mlp_train(float* params, float* adam_m, float* adam_v, int n, int K
  * product (H x)_i = sum_{e at i} B_e (x_i - x_other), B_e = A_e^T Omega_e
  * A_e, in one cooperative launch whose grid barriers wait at most about a
  * second (BA_ERR_TIMEOUT); BA_SOLVER_CHOLESKY factors the 6N x 6N system
- * H + D (stored dense, 6N <= BA_DENSE_MAX_DIM) within its band, in the node
- * order or a reverse Cuthill-McKee order computed at create when that is
- * narrower: half-bandwidth b = 6 max_e |pos(i) - pos(j)| + 5 unknowns, in
- * O(N b^2) (up to the dense O(N^3) for a graph with no narrow band).
+ * H + D within its band, in the node order or a reverse Cuthill-McKee order
+ * computed at create when that is narrower: half-bandwidth
+ * b = 6 max_e |pos(i) - pos(j)| + 5 unknowns.  Only the band is stored
+ * (32 x 32 tiles, about 6N (b + 64) doubles; BA_ERR_OOM at create when it
+ * does not fit), and the factorisation and both triangular solves run in one
+ * cooperative launch in O(N b^2) (up to the dense O(N^3) for a graph with no
+ * narrow band).  A pivot that is not positive, or a wait of that launch that
+ * runs out (about a second), gives dx = 0 for the trial (a rejection).
  * ------------------------------------------------------------------------ */
 typedef struct ba_pgo ba_pgo; /* opaque, owned by the library */
 

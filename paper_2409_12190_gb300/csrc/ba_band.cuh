@@ -1,0 +1,368 @@
+// Banded Cholesky of the damped pose-graph system (H + D) x = b and its two
+// triangular solves in one cooperative launch (the paper's sparse direct
+// solver, Sec. IV-C, "Sparse Direct Solver (Cholesky Factorization)", applied
+// to the pose-graph normal equations of Sec. IV-D).
+//
+// Storage.  In the factored order (reverse Cuthill-McKee when narrower) the
+// matrix has half-bandwidth bw unknowns, so its lower triangle lies in the
+// TB x TB tiles (I, J) with 0 <= I - J <= bwt = ceil(bw / TB).  Only those
+// tiles are stored: tile (I, J) at T + (J (bwt + 1) + I - J) TB^2, row-major.
+// The order is padded to nb TB unknowns with identity rows.  Cholesky keeps
+// the fill inside the band, so L takes the same tiles.
+//
+// Schedule.  The work is a dependency graph of tasks, handed out in a fixed
+// topological order by an atomic ticket:
+//   for J = 0 .. nb - 1:  tile tasks (J, J), (J + 1, J), ..., (J + bwt, J),
+//                         then the forward block F_J;
+//   then the backward blocks B_{nb-1}, ..., B_0.
+// A tile task (I, J) subtracts L_IK L_JK^T for every K < J in the band
+// (left-looking; it waits for the two tiles of column K), then factors the
+// tile (I = J) or solves X L_JJ^T = A_IJ (I > J, after L_JJ).  F_J computes
+// y_J = L_JJ^{-1} (b_J - sum_K L_JK y_K) and B_I computes
+// x_I = L_II^{-T} (y_I - sum_K L_KI^T x_K).  Every task waits only on tasks
+// with smaller tickets, which running blocks hold, so the smallest unfinished
+// ticket never waits and the schedule cannot deadlock; every wait is bounded
+// all the same (2^25 polls, about a second or more), and one that runs out
+// sets ctr[3], after which every block stops.  The forward solve runs under
+// the factorisation; only the backward blocks come after it.
+//
+// Each entry of L is a fixed-order sum (K ascending, then the tile's own
+// columns), so the result does not depend on the schedule.
+#pragma once
+
+#include <cuda/atomic>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ba_dense.cuh"
+
+namespace ba {
+
+constexpr int BAND_TB = DB;         // tile size (32)
+constexpr int BAND_THREADS = 256;   // threads per block
+constexpr int BAND_TRI = (BAND_TB - 1) * BAND_TB / 2;  // entries of the largest trailing triangle
+
+struct BandArgs {
+  int nb;             // block rows of the padded order (nb * TB >= n)
+  int bwt;            // half-bandwidth in tiles
+  int n;              // unknowns
+  double* T;          // band tiles, L on return
+  double* rsd;        // [nb TB] 1 / L_cc of every diagonal entry
+  const double* rhs;  // [n] b
+  double* y;          // [nb TB] y, then x
+  double* sol;        // [n] x
+  int* tflag;         // [nb (bwt + 1)] tile final
+  int* ctr;           // [0] ticket, [1] forward blocks done, [2] backward blocks done, [3] a wait ran out
+  int* fail;          // a pivot not positive or not finite
+};
+
+__device__ __forceinline__ double* band_tile(const BandArgs& a, int I, int J) {
+  return a.T + ((long long)J * (a.bwt + 1) + (I - J)) * (BAND_TB * BAND_TB);
+}
+
+__device__ __forceinline__ int* band_flag(const BandArgs& a, int I, int J) {
+  return a.tflag + (long long)J * (a.bwt + 1) + (I - J);
+}
+
+// Thread-0 wait until *flag >= v (acquire).  False when the wait ran out or
+// another one did (ctr[3]).
+__device__ __noinline__ bool band_wait(int* flag, int v, int* err) {
+  cuda::atomic_ref<int, cuda::thread_scope_device> f(*flag), e(*err);
+  unsigned int spins = 0;
+  while (f.load(cuda::memory_order_acquire) < v) {
+    if (e.load(cuda::memory_order_relaxed) || ++spins > (1u << 25)) {
+      e.store(1, cuda::memory_order_relaxed);
+      return false;
+    }
+    if (spins > 64) __nanosleep(64);
+  }
+  return true;
+}
+
+// Publish v after the block's writes (called by every thread).
+__device__ __forceinline__ void band_publish(int* flag, int v) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    cuda::atomic_ref<int, cuda::thread_scope_device> f(*flag);
+    f.store(v, cuda::memory_order_release);
+  }
+}
+
+// Stage a tile (row-major, TB x TB) into shared memory, through L2.
+__device__ __forceinline__ void band_stage(double (*s)[BAND_TB + 1], const double* __restrict__ g) {
+  for (int e = threadIdx.x; e < BAND_TB * BAND_TB; e += BAND_THREADS) s[e / BAND_TB][e % BAND_TB] = __ldcg(g + e);
+}
+
+struct BandSmem {
+  double A[BAND_TB][BAND_TB + 1];
+  double B[BAND_TB][BAND_TB + 1];
+  double rs[BAND_TB];
+  double d[BAND_TB];
+  double red[BAND_THREADS / 32][BAND_TB];
+  uint16_t tri[BAND_TRI];  // (r << 8) | c of the row-major lower triangle
+  int task;
+  int bad;
+};
+
+// Tile task (I, J).
+__device__ bool band_tile_task(const BandArgs& a, BandSmem& s, int I, int J) {
+  constexpr int TB = BAND_TB, E = TB * TB / BAND_THREADS;
+  const int tid = threadIdx.x, col = tid % TB, row0 = tid / TB;
+  double acc[E];
+  const double* Tij = band_tile(a, I, J);
+#pragma unroll
+  for (int m = 0; m < E; ++m) acc[m] = __ldcg(Tij + (row0 + m * (BAND_THREADS / TB)) * TB + col);
+  // acc -= L_IK L_JK^T, K ascending
+  for (int K = max(0, I - a.bwt); K < J; ++K) {
+    int w = 1;
+    if (tid == 0) w = band_wait(band_flag(a, I, K), 1, a.ctr + 3) && band_wait(band_flag(a, J, K), 1, a.ctr + 3);
+    if (!__syncthreads_and(w)) return false;
+    band_stage(s.A, band_tile(a, I, K));
+    if (I != J) band_stage(s.B, band_tile(a, J, K));
+    __syncthreads();
+    const double(*LJ)[TB + 1] = (I != J) ? s.B : s.A;
+#pragma unroll 8
+    for (int k = 0; k < TB; ++k) {
+      const double b = LJ[col][k];
+#pragma unroll
+      for (int m = 0; m < E; ++m) acc[m] = fma(-s.A[row0 + m * (BAND_THREADS / TB)][k], b, acc[m]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int m = 0; m < E; ++m) s.A[row0 + m * (BAND_THREADS / TB)][col] = acc[m];
+  __syncthreads();
+  double* out = band_tile(a, I, J);
+  if (I == J) {
+    // factor the diagonal tile: right-looking, the trailing triangle's
+    // entries spread over the block; the scaling of column c is deferred
+    // (a_rc' -= a_rc a_c'c / d_c), and the thread that updates the next
+    // pivot takes its reciprocal square root at once
+    if (tid == 0) {
+      const double d0 = s.A[0][0];
+      const bool ok = d0 > 0.0 && isfinite(d0);
+      s.d[0] = ok ? d0 : 1.0;
+      s.rs[0] = ok ? rsqrt(d0) : 1.0;
+      s.bad = ok ? 0 : 1;
+    }
+    __syncthreads();
+    for (int c = 0; c < TB - 1; ++c) {
+      const int m = TB - 1 - c, ne = m * (m + 1) / 2;
+      const double rs = s.rs[c];
+      const double inv = rs * rs;
+      for (int e = tid; e < ne; e += BAND_THREADS) {
+        const int rr = c + 1 + (s.tri[e] >> 8), cc = c + 1 + (s.tri[e] & 0xff);
+        const double v = fma(-(s.A[rr][c] * inv), s.A[cc][c], s.A[rr][cc]);
+        s.A[rr][cc] = v;
+        if (e == 0) {  // (c + 1, c + 1): the next pivot
+          const bool ok = v > 0.0 && isfinite(v);
+          s.d[c + 1] = ok ? v : 1.0;
+          s.rs[c + 1] = ok ? rsqrt(v) : 1.0;
+          if (!ok) s.bad = 1;
+        }
+      }
+      __syncthreads();
+    }
+    for (int e = tid; e < TB * TB; e += BAND_THREADS) {
+      const int rr = e / TB, cc = e % TB;
+      out[e] = rr > cc ? s.A[rr][cc] * s.rs[cc] : (rr == cc ? s.d[cc] * s.rs[cc] : 0.0);
+    }
+    if (tid < TB) a.rsd[(long long)J * TB + tid] = s.rs[tid];
+    if (tid == 0 && s.bad) atomicExch(a.fail, 1);
+  } else {
+    // X L_JJ^T = A: column by column, x_rc = a_rc / L_cc, then
+    // a_rc' -= x_rc L_c'c for c' > c (L's column c prescaled by 1 / L_cc)
+    int w = 1;
+    if (tid == 0) w = band_wait(band_flag(a, J, J), 1, a.ctr + 3);
+    if (!__syncthreads_and(w)) return false;
+    band_stage(s.B, band_tile(a, J, J));
+    if (tid < TB) s.rs[tid] = __ldcg(a.rsd + (long long)J * TB + tid);
+    __syncthreads();
+    for (int e = tid; e < TB * TB; e += BAND_THREADS) {
+      const int rr = e / TB, cc = e % TB;
+      if (rr > cc) s.B[rr][cc] *= s.rs[cc];
+    }
+    __syncthreads();
+    const int lane = tid % 32, wp = tid / 32;
+    for (int c = 0; c < TB - 1; ++c) {
+      const double x = s.A[lane][c];
+      for (int cp = c + 1 + wp; cp < TB; cp += BAND_THREADS / 32) s.A[lane][cp] = fma(-x, s.B[cp][c], s.A[lane][cp]);
+      __syncthreads();
+    }
+    for (int e = tid; e < TB * TB; e += BAND_THREADS) {
+      const int rr = e / TB, cc = e % TB;
+      out[e] = s.A[rr][cc] * s.rs[cc];
+    }
+  }
+  band_publish(band_flag(a, I, J), 1);
+  return true;
+}
+
+__device__ __forceinline__ int band_load(int* p) {
+  cuda::atomic_ref<int, cuda::thread_scope_device> f(*p);
+  return f.load(cuda::memory_order_acquire);
+}
+
+// Thread 0: wait until the counter *p reaches v; *known caches the last value
+// read, so a satisfied wait costs no load.
+__device__ __forceinline__ bool band_wait_count(int* p, int v, int* known, int* err) {
+  if (*known >= v) return true;
+  *known = band_load(p);
+  if (*known >= v) return true;
+  if (!band_wait(p, v, err)) return false;
+  *known = v;
+  return true;
+}
+
+// Forward block F_J: y_J = L_JJ^{-1} (b_J - sum_{K < J} L_JK y_K).
+__device__ bool band_forward_task(const BandArgs& a, BandSmem& s, int J) {
+  constexpr int TB = BAND_TB;
+  const int tid = threadIdx.x, r = tid / 8, q = tid % 8;  // row r, columns 4q .. 4q + 3
+  int known = 0;                                         // forward blocks known done (thread 0)
+  double part = 0.0;
+  for (int K = max(0, J - a.bwt); K < J; ++K) {
+    int w = 1;
+    if (tid == 0)
+      w = band_wait(band_flag(a, J, K), 1, a.ctr + 3) && band_wait_count(a.ctr + 1, K + 1, &known, a.ctr + 3);
+    if (!__syncthreads_and(w)) return false;
+    const double* L = band_tile(a, J, K) + r * TB + 4 * q;
+    const double* yk = a.y + (long long)K * TB + 4 * q;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) part = fma(__ldcg(L + c), __ldcg(yk + c), part);
+  }
+  part += __shfl_xor_sync(0xffffffffu, part, 4);
+  part += __shfl_xor_sync(0xffffffffu, part, 2);
+  part += __shfl_xor_sync(0xffffffffu, part, 1);
+  const long long row = (long long)J * TB + r;
+  if (q == 0) s.red[0][r] = (row < a.n ? a.rhs[row] : 0.0) - part;
+  int w = 1;
+  if (tid == 0) w = band_wait(band_flag(a, J, J), 1, a.ctr + 3);
+  if (!__syncthreads_and(w)) return false;
+  band_stage(s.B, band_tile(a, J, J));
+  if (tid < TB) s.rs[tid] = __ldcg(a.rsd + (long long)J * TB + tid);
+  __syncthreads();
+  if (tid < 32) {
+    // L_JJ y = v, column by column: y_c = v_c / L_cc, then v_r -= L_rc y_c
+    const int lane = tid;
+    double v = s.red[0][lane];
+#pragma unroll 4
+    for (int c = 0; c < TB; ++c) {
+      const double yc = __shfl_sync(0xffffffffu, v * s.rs[c], c);
+      if (lane > c) v = fma(-s.B[lane][c], yc, v);
+      else if (lane == c) v = yc;
+    }
+    a.y[(long long)J * TB + lane] = v;
+  }
+  // blocks are published in order (F_{J-1} first)
+  w = 1;
+  if (tid == 0) w = band_wait_count(a.ctr + 1, J, &known, a.ctr + 3);
+  if (!__syncthreads_and(w)) return false;
+  band_publish(a.ctr + 1, J + 1);
+  return true;
+}
+
+// Backward block B_I: x_I = L_II^{-T} (y_I - sum_{K > I} L_KI^T x_K); x
+// overwrites y.
+__device__ bool band_backward_task(const BandArgs& a, BandSmem& s, int I) {
+  constexpr int TB = BAND_TB;
+  const int tid = threadIdx.x, lane = tid % 32, wp = tid / 32;  // x row lane; L rows wp, wp + 8, ...
+  int known = 0;                                                // backward blocks known done (thread 0)
+  int w = 1;
+  if (tid == 0) w = band_wait(a.ctr + 1, a.nb, a.ctr + 3);  // every tile and y final
+  if (!__syncthreads_and(w)) return false;
+  double part = 0.0;
+  for (int K = min(a.nb - 1, I + a.bwt); K > I; --K) {
+    w = 1;
+    if (tid == 0) w = band_wait_count(a.ctr + 2, a.nb - K, &known, a.ctr + 3);
+    if (!__syncthreads_and(w)) return false;
+    const double* L = band_tile(a, K, I);
+    const double* xk = a.y + (long long)K * TB;
+#pragma unroll
+    for (int m = 0; m < TB / (BAND_THREADS / 32); ++m) {
+      const int c = wp + m * (BAND_THREADS / 32);
+      part = fma(__ldcg(L + c * TB + lane), __ldcg(xk + c), part);
+    }
+  }
+  s.red[wp][lane] = part;
+  band_stage(s.B, band_tile(a, I, I));
+  if (tid < TB) s.rs[tid] = __ldcg(a.rsd + (long long)I * TB + tid);
+  __syncthreads();
+  if (tid < 32) {
+    double v = __ldcg(a.y + (long long)I * TB + lane);
+#pragma unroll
+    for (int k = 0; k < BAND_THREADS / 32; ++k) v -= s.red[k][lane];
+    // L_II^T x = v, from the last column: x_c = v_c / L_cc, then v_r -= L_cr x_c
+#pragma unroll 4
+    for (int c = TB - 1; c >= 0; --c) {
+      const double xc = __shfl_sync(0xffffffffu, v * s.rs[c], c);
+      if (lane < c) v = fma(-s.B[c][lane], xc, v);
+      else if (lane == c) v = xc;
+    }
+    const long long row = (long long)I * TB + lane;
+    a.y[row] = v;
+    if (row < a.n) a.sol[row] = v;
+  }
+  w = 1;
+  if (tid == 0) w = band_wait_count(a.ctr + 2, a.nb - 1 - I, &known, a.ctr + 3);
+  if (!__syncthreads_and(w)) return false;
+  band_publish(a.ctr + 2, a.nb - I);
+  return true;
+}
+
+// The whole factorisation and both solves; launched cooperatively so that
+// every block is resident.
+static __global__ void __launch_bounds__(BAND_THREADS, 1) k_band_chol(BandArgs a) {
+  __shared__ BandSmem s;
+  for (int e = threadIdx.x; e < BAND_TRI; e += BAND_THREADS) {
+    int r = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);  // FP32 guess, corrected below
+    while ((r + 1) * (r + 2) / 2 <= e) ++r;
+    while (r * (r + 1) / 2 > e) --r;
+    s.tri[e] = (uint16_t)((r << 8) | (e - r * (r + 1) / 2));
+  }
+  const int ntile = a.nb * (a.bwt + 2), ntask = ntile + a.nb;
+  for (;;) {
+    if (threadIdx.x == 0) s.task = band_load(a.ctr + 3) ? ntask : atomicAdd(a.ctr, 1);
+    __syncthreads();
+    const int q = s.task;
+    __syncthreads();
+    if (q >= ntask) break;
+    bool ok = true;
+    if (q < ntile) {
+      const int J = q / (a.bwt + 2), d = q % (a.bwt + 2);
+      if (d <= a.bwt) {
+        if (J + d < a.nb) ok = band_tile_task(a, s, J + d, J);
+      } else {
+        ok = band_forward_task(a, s, J);
+      }
+    } else {
+      ok = band_backward_task(a, s, a.nb - 1 - (q - ntile));
+    }
+    if (!ok) break;
+  }
+}
+
+// Identity rows of the padding (n .. nb TB - 1) on the zeroed tiles.
+static __global__ void k_band_pad(int n, int nb, int bwt, double* __restrict__ T) {
+  const int R = n + blockIdx.x * blockDim.x + threadIdx.x;
+  if (R >= nb * BAND_TB) return;
+  const int I = R / BAND_TB;
+  T[(long long)I * (bwt + 1) * (BAND_TB * BAND_TB) + (R % BAND_TB) * (BAND_TB + 1)] = 1.0;
+}
+
+// After k_band_chol: a failed factorisation (a pivot not positive or not
+// finite) or a wait that ran out gives x = 0, counted; the solve's statistics.
+static __global__ void k_band_finish(int n, const int* __restrict__ fail, const int* __restrict__ ctr,
+                                     double* __restrict__ sol, DevState* st) {
+  const bool bad = *fail != 0 || ctr[3] != 0;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (bad && i < n) sol[i] = 0.0;
+  if (i == 0) {
+    st->pcg_done = 1;
+    st->pcg_iters = 0;
+    st->pcg_rel = bad ? 1.0 : 0.0;
+    if (bad) st->fallbacks += 1;
+  }
+}
+
+}  // namespace ba

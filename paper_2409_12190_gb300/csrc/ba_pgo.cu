@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -169,9 +170,14 @@ struct ba_pgo {
   double *B = nullptr, *qv = nullptr, *Hd = nullptr, *g = nullptr, *D = nullptr, *Minv = nullptr;
   double *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
   double *pcg_part = nullptr, *dpart = nullptr, *gpart = nullptr, *epart = nullptr;
-  uint8_t *fixed = nullptr, *fixed6 = nullptr;
-  double *dS = nullptr, *dy = nullptr;
-  int* dfail = nullptr;
+  uint8_t* fixed = nullptr;
+  // Cholesky: the band tiles of H + D (then L), 1 / L_cc, y / x in the
+  // padded factored order, and the flags (tile final [bnb (bwt + 1)],
+  // counters [4], failure [1]) of the factorisation's schedule
+  int bnb = 0, bwt = 0, band_grid = 0;
+  size_t bT_bytes = 0, bflag_count = 0;
+  double *bT = nullptr, *brs = nullptr, *dy = nullptr;
+  int* bflag = nullptr;
   int* derr = nullptr;
   GridBar* bar = nullptr;
   DevState* st = nullptr;
@@ -326,11 +332,18 @@ ba_status enqueue_solve(ba_pgo* h, const double* lam_ptr, int maxiter, double to
   if (h->opt.solver == BA_SOLVER_CHOLESKY) {
     // H + D is banded in the factored order (node order, or a reverse
     // Cuthill-McKee order when that is narrower; half-bandwidth h->band):
-    // only the tiles within the band are factored, and the solve stays in it
+    // its band tiles are assembled, then factored and solved in one
+    // cooperative launch (ba_band.cuh)
     const int n = 6 * h->N;
-    const int bw = h->band;
-    k_pgo_dense<<<h->N, 256, 0, s>>>(h->N, h->rowptr, h->inc, h->ei, h->ej, h->B, h->Hd, h->D, h->pos, h->dS);
+    PCU(cudaMemsetAsync(h->bT, 0, h->bT_bytes, s));
+    PCU(cudaMemsetAsync(h->bflag, 0, sizeof(int) * h->bflag_count, s));
+    k_pgo_band<<<h->N, 64, 0, s>>>(h->N, h->rowptr, h->inc, h->ei, h->ej, h->B, h->Hd, h->D, h->pos, h->fixed,
+                                   h->bwt, h->bT);
     count_launch();
+    if (h->bnb * BAND_TB > n) {
+      k_band_pad<<<1, BAND_TB, 0, s>>>(n, h->bnb, h->bwt, h->bT);
+      count_launch();
+    }
     const double* rhs = h->r;
     double* sol = h->x;
     if (h->pos) {
@@ -339,25 +352,12 @@ ba_status enqueue_solve(ba_pgo* h, const double* lam_ptr, int maxiter, double to
       rhs = h->rp;
       sol = h->xp;
     }
-    if (h->fixed) {
-      k_dense_mask<<<nb((long long)n * n, 256), 256, 0, s>>>(n, h->fixed6, h->dS);
-      count_launch();
-    }
-    PCU(cudaMemsetAsync(h->dfail, 0, sizeof(int), s));
-    const int nblk_d = (n + DB - 1) / DB;
-    for (int kb = 0; kb < nblk_d; ++kb) {
-      k_chol_diag<<<1, DB * DB / 4, 0, s>>>(n, kb, h->dS, h->dfail);
-      const int rows_below = std::min(n - (kb + 1) * DB, bw);
-      if (rows_below > 0) {
-        k_chol_panel4<<<(rows_below + DB - 1) / DB, 4 * DB, 0, s>>>(n, kb, h->dS);
-        const long long T_ = (rows_below + DB - 1) / DB;
-        k_chol_update<<<(unsigned)(T_ * (T_ + 1) / 2), DB * DB / 4, 0, s>>>(n, kb, h->dS);
-        count_launch(2);
-      }
-      count_launch();
-    }
-    k_dense_solve<<<1, 1024, 0, s>>>(n, bw, h->dS, rhs, h->dy, sol, h->dfail, h->st);
-    count_launch();
+    int* ctr = h->bflag + (size_t)h->bnb * (h->bwt + 1);
+    BandArgs ba_{h->bnb, h->bwt, n, h->bT, h->brs, rhs, h->dy, sol, h->bflag, ctr, ctr + 4};
+    void* args[] = {&ba_};
+    PCU(cudaLaunchCooperativeKernel((const void*)k_band_chol, dim3(h->band_grid), dim3(BAND_THREADS), args, 0, s));
+    k_band_finish<<<nb(n, 256), 256, 0, s>>>(n, ctr + 4, ctr, sol, h->st);
+    count_launch(2);
     if (h->pos) {
       k_pgo_permute<<<nb(n, 256), 256, 0, s>>>(h->N, h->pos, 1, h->xp, h->x);
       count_launch();
@@ -433,8 +433,6 @@ ba_status ba_pgo_create(ba_pgo** out, int N, int E, const double* poses, const i
   else ba_options_default(&o);
   ba_status st = check_pgo_options(&o);
   if (st != BA_OK) return st;
-  if (o.solver == BA_SOLVER_CHOLESKY && 6LL * N > BA_DENSE_MAX_DIM)
-    return set_error(BA_ERR_INVALID_ARG, "BA_SOLVER_CHOLESKY needs 6N <= %d (N = %d)", BA_DENSE_MAX_DIM, N);
   int dev = 0, coop = 0, nsm = 0, occ = 0;
   PCU(cudaGetDevice(&dev));
   PCU(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
@@ -491,15 +489,7 @@ ba_status ba_pgo_create(ba_pgo** out, int N, int E, const double* poses, const i
   A(&h->bar, sizeof(GridBar));
   A(&h->st, sizeof(DevState));
   A(&h->stats, sizeof(ba_iter_stats) * (size_t)o.max_stats);
-  if (fixed) {
-    A(&h->fixed, (size_t)N);
-    A(&h->fixed6, (size_t)n6);
-  }
-  if (o.solver == BA_SOLVER_CHOLESKY) {
-    A(&h->dS, 8ull * n6 * n6);
-    A(&h->dy, 8ull * n6);
-    A(&h->dfail, sizeof(int));
-  }
+  if (fixed) A(&h->fixed, (size_t)N);
   std::vector<int32_t> hpos;  // Cholesky: block position of each node, empty for the node order
   int32_t* keys = nullptr;
   int32_t* perm = nullptr;
@@ -546,6 +536,28 @@ ba_status ba_pgo_create(ba_pgo** out, int N, int E, const double* poses, const i
       } else {
         hpos.clear();  // node order
       }
+      // the band tiles and the schedule's flags
+      h->bnb = (int)((n6 + BAND_TB - 1) / BAND_TB);
+      h->bwt = std::min(h->bnb - 1, (h->band + BAND_TB - 1) / BAND_TB);
+      const long long ntask = (long long)h->bnb * (h->bwt + 2) + h->bnb;
+      if (ntask >= INT32_MAX)
+        return bail(set_error(BA_ERR_INVALID_ARG, "the band of H is too wide for BA_SOLVER_CHOLESKY (%d x %d tiles)",
+                              h->bnb, h->bwt + 1));
+      h->bT_bytes = (size_t)h->bnb * (h->bwt + 1) * (BAND_TB * BAND_TB) * sizeof(double);
+      h->bflag_count = (size_t)h->bnb * (h->bwt + 1) + 5;
+      int occb = 0;
+      if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occb, k_band_chol, BAND_THREADS, 0)) != cudaSuccess ||
+          occb < 1)
+        return bail(set_error(BA_ERR_CUDA, "the Cholesky kernel cannot be resident"));
+      // one block per SM: a task on the critical path (a diagonal tile, the
+      // next column's first solve) then has its SM's FP64 pipe to itself
+      h->band_grid = (int)std::max(1LL, std::min<long long>(ntask, nsm));
+      if ((e = h->alloc(&h->bT, h->bT_bytes)) != cudaSuccess ||
+          (e = h->alloc(&h->brs, 8ull * h->bnb * BAND_TB)) != cudaSuccess ||
+          (e = h->alloc(&h->dy, 8ull * h->bnb * BAND_TB)) != cudaSuccess ||
+          (e = h->alloc(&h->bflag, sizeof(int) * h->bflag_count)) != cudaSuccess)
+        return bail(set_error(e == cudaErrorMemoryAllocation ? BA_ERR_OOM : BA_ERR_CUDA,
+                              "allocation of the band (%zu bytes) failed", h->bT_bytes));
     }
   }
   // incidence CSR: stable sort of [ei..., ej...] by node
@@ -584,16 +596,6 @@ ba_status ba_pgo_create(ba_pgo** out, int N, int E, const double* poses, const i
   count_launch(2);
   if (fixed) {
     if ((st = copy_in(h->fixed, fixed, (size_t)N, s)) != BA_OK) return bail(st);
-    std::vector<uint8_t> hf(N), hf6(n6);
-    if ((e = cudaMemcpyAsync(hf.data(), h->fixed, (size_t)N, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
-        (e = cudaStreamSynchronize(s)) != cudaSuccess)
-      return bail(set_error(BA_ERR_CUDA, "copy of the fixed mask failed"));
-    for (long long k = 0; k < n6; ++k) {
-      const long long i = k / 6;
-      hf6[hpos.empty() ? k : 6LL * hpos[i] + k % 6] = hf[i] ? 1 : 0;
-    }
-    if ((e = cudaMemcpyAsync(h->fixed6, hf6.data(), (size_t)n6, cudaMemcpyHostToDevice, s)) != cudaSuccess)
-      return bail(set_error(BA_ERR_CUDA, "copy of the fixed mask failed"));
   }
   {
     DevState init{};

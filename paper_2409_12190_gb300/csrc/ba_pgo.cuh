@@ -25,14 +25,15 @@
 //   k_pgo_edge_cost  per edge: 1/2 r^T Omega r at the trial (or current)
 //                    poses and 1/2 u^T B u, u = delta_j - delta_i
 //   k_pgo_control    the gain ratio and the LM decision (shared rule)
-//   k_pgo_dense      block row i of H + D, for the dense Cholesky solver
+//   k_pgo_band       block row i of H + D into the band tiles of the Cholesky
+//                    solver (ba_band.cuh)
 #pragma once
 
 #include <cuda/atomic>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "ba_dense.cuh"
+#include "ba_band.cuh"
 #include "ba_kernels.cuh"
 
 namespace ba {
@@ -1021,39 +1022,39 @@ static __global__ void k_pgo_control(int nbe, const double* __restrict__ epart, 
   st->trials = t + 1;
 }
 
-// Block row i (6 rows of the dense 6N x 6N matrix H + D, at block position
-// pos[i] of the factored order, or i without pos): zero, H_ii + D_i on the
-// diagonal block, then -B_e into block (i, other(e)) for each incident edge
-// in CSR order (one thread per block entry: parallel edges between the same
-// two nodes accumulate in order).
-static __global__ void __launch_bounds__(256)
-k_pgo_dense(int N, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ inc,
-            const int32_t* __restrict__ ei, const int32_t* __restrict__ ej, const double* __restrict__ B,
-            const double* __restrict__ Hd, const double* __restrict__ D, const int32_t* __restrict__ pos,
-            double* __restrict__ S) {
-  const int i = blockIdx.x;
-  const long long n = 6LL * N;
-  const int pi = pos ? pos[i] : i;  // node i's block position in the factored order
-  double* row = S + 6LL * pi * n;
-  for (long long k = threadIdx.x; k < 6 * n; k += blockDim.x) row[k] = 0.0;
-  __syncthreads();
-  const int t = threadIdx.x;
-  if (t < 36) {
-    const int a = t / 6, b = t % 6;
-    double* dst = row + (long long)a * n + 6LL * pi + b;
-    *dst = Hd[21LL * i + (a <= b ? sym6(a, b) : sym6(b, a))] + (a == b ? D[6LL * i + a] : 0.0);
-  }
-  __syncthreads();
-  if (t < 36) {
-    const int a = t / 6, b = t % 6;
-    const int end = rowptr[i + 1];
-    for (int s = rowptr[i]; s < end; ++s) {
-      const int code = inc[s];
-      const int e = code >> 1;
-      const int other = (code & 1) ? ei[e] : ej[e];
-      const int po = pos ? pos[other] : other;
-      row[(long long)a * n + 6LL * po + b] -= B[36LL * e + 6 * a + b];
-    }
+// Block row i of H + D (6 rows, at block position pi = pos[i] of the
+// factored order, or i without pos) into the band tiles of the banded
+// Cholesky (tile size BAND_TB, half-bandwidth bwt tiles), lower triangle
+// only: H_ii + D_i on the diagonal block, then -B_e at block (pi, po) for
+// each incident edge whose other node comes earlier (po < pi), parallel
+// edges summed in CSR order (one thread per block entry).  The rows and
+// columns of a fixed node stay zero and its diagonal is 1.  The tiles are
+// zeroed before.
+static __global__ void __launch_bounds__(64)
+k_pgo_band(int N, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ inc,
+           const int32_t* __restrict__ ei, const int32_t* __restrict__ ej, const double* __restrict__ B,
+           const double* __restrict__ Hd, const double* __restrict__ D, const int32_t* __restrict__ pos,
+           const uint8_t* __restrict__ fixed, int bwt, double* __restrict__ T) {
+  const int i = blockIdx.x, t = threadIdx.x;
+  if (t >= 36) return;
+  const int a = t / 6, b = t % 6;
+  const int pi = pos ? pos[i] : i;
+  const int R = 6 * pi + a;
+  const bool fi = fixed && fixed[i];
+  auto at = [&](int C) -> double& {
+    const int I = R / BAND_TB, J = C / BAND_TB;
+    return T[((long long)J * (bwt + 1) + (I - J)) * (BAND_TB * BAND_TB) + (R % BAND_TB) * BAND_TB + C % BAND_TB];
+  };
+  if (b <= a) at(6 * pi + b) = fi ? (a == b ? 1.0 : 0.0)
+                                   : Hd[21LL * i + sym6(b, a)] + (a == b ? D[6LL * i + a] : 0.0);
+  if (fi) return;
+  const int end = rowptr[i + 1];
+  for (int s = rowptr[i]; s < end; ++s) {
+    const int code = inc[s];
+    const int e = code >> 1;
+    const int other = (code & 1) ? ei[e] : ej[e];
+    const int po = pos ? pos[other] : other;
+    if (po < pi && !(fixed && fixed[other])) at(6 * po + b) -= B[36LL * e + 6 * a + b];
   }
 }
 

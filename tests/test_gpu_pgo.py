@@ -402,10 +402,27 @@ def test_invalid_inputs_are_reported():
         PoseGraph(P7, g.ei, g.ej, M7, g.info, options=ba.Options(huber_delta=1.0))
     with pytest.raises(ValueError):
         PoseGraph(P7, g.ei, g.ej, M7, g.info, options=ba.Options(precision="f32"))
-    big = scenegen.sphere_graph(62, 50, seed=1, name="big")  # 6N = 18600 > 18432
-    with pytest.raises(ba.BAError, match="INVALID_ARG"):
-        PoseGraph(big.poses_gt, big.ei, big.ej, np.tile([0, 0, 0, 0, 0, 0, 1.0], (big.E, 1)), big.info,
-                  options=ba.Options(solver="cholesky"))
+
+
+def test_banded_cholesky_on_a_graph_larger_than_a_dense_factorisation_takes():
+    """A 62 x 50 sphere (3,100 poses, 18,600 unknowns, more than
+    BA_DENSE_MAX_DIM): only the band tiles are stored.  One damped solve
+    with pose 0 fixed: (H + D) dx = -g to 1e-10 over the free poses, and dx
+    against PCG run to 1e-12 on the same graph."""
+    big = scenegen.sphere_graph(62, 50, seed=1, name="big")
+    _, _, _, _, P7, M7 = _inputs(big)
+    lam = 1e-3
+    with _make(big, P7, M7, solver="cholesky") as pc:
+        dx, its, rel = pc.damped_solve(lam, 0, 0.0)
+        g = pc.linearize()["g"]
+        y = pc.matvec(lam, dx)
+    with _make(big, P7, M7, pcg_tol=1e-12, pcg_maxiter=20000) as pp:
+        dx_p, _, rel_p = pp.damped_solve(lam, 20000, 1e-12)
+    assert its == 0 and rel == 0.0 and rel_p <= 1e-12
+    res = (y + g)[1:].cpu().numpy()
+    assert np.max(np.abs(res)) <= 1e-10 * float(g[1:].abs().max())
+    assert np.all(dx[0].cpu().numpy() == 0.0)
+    assert _rel(dx.cpu(), dx_p.cpu()) < 1e-6
 
 
 # --------------------------------------------------------------------------
