@@ -10,21 +10,27 @@
 // The order is padded to nb TB unknowns with identity rows.  Cholesky keeps
 // the fill inside the band, so L takes the same tiles.
 //
-// Schedule.  The work is a dependency graph of tasks, handed out in a fixed
-// topological order by an atomic ticket:
-//   for J = 0 .. nb - 1:  tile tasks (J, J), (J + 1, J), ..., (J + bwt, J),
-//                         then the forward block F_J;
-//   then the backward blocks B_{nb-1}, ..., B_0.
-// A tile task (I, J) subtracts L_IK L_JK^T for every K < J in the band
-// (left-looking; it waits for the two tiles of column K), then factors the
-// tile (I = J) or solves X L_JJ^T = A_IJ (I > J, after L_JJ).  F_J computes
-// y_J = L_JJ^{-1} (b_J - sum_K L_JK y_K) and B_I computes
-// x_I = L_II^{-T} (y_I - sum_K L_KI^T x_K).  Every task waits only on tasks
-// with smaller tickets, which running blocks hold, so the smallest unfinished
-// ticket never waits and the schedule cannot deadlock; every wait is bounded
-// all the same (2^25 polls, about a second or more), and one that runs out
-// sets ctr[3], after which every block stops.  The forward solve runs under
-// the factorisation; only the backward blocks come after it.
+// Tasks (a dependency graph; K0(I) = max(0, I - bwt) is the first column
+// that reaches row I):
+//   D_J     the diagonal chain: L_{J,J-1} = A_{J,J-1} L_{J-1,J-1}^{-T}, then
+//           A_JJ -= L_{J,J-1} L_{J,J-1}^T and L_JJ = chol(A_JJ);
+//   U       A_IJ -= L_IK L_JK^T for K in [Ka, Ka + cnt): the updates of a
+//           tile, in ascending K (tile (J, J) leaves K = J - 1 to D_J);
+//   T       L_IJ = A_IJ L_JJ^{-T} for I >= J + 2;
+//   F_J     y_J = L_JJ^{-1} (b_J - sum_K L_JK y_K);
+//   B_I     x_I = L_II^{-T} (y_I - sum_K L_KI^T x_K).
+// The chain D_0, D_1, ... is the critical path; one D_J is a triangular
+// solve, a symmetric update and a factorisation of single tiles, while the U
+// and T tasks of later columns run beside it.  The host orders the tasks by
+// a list-scheduling simulation (a topological order) and splits them into two
+// pools: the near-diagonal tasks that feed the chain, run by a few blocks of
+// their own, and the bulk, run by the rest; each pool's blocks take its tasks
+// in order from an atomic ticket.  A task waits only on tasks earlier in the
+// simulated order.  The earliest unfinished task of that order has every
+// predecessor done; if no block holds it, every block of its pool holds an
+// earlier task of the same pool, which is impossible.  So the schedule cannot
+// deadlock; every wait is bounded all the same (2^25 polls, about a second or
+// more), and one that runs out sets ctr[3], after which every block stops.
 //
 // Each entry of L is a fixed-order sum (K ascending, then the tile's own
 // columns), so the result does not depend on the schedule.
@@ -38,31 +44,47 @@
 
 namespace ba {
 
-constexpr int BAND_TB = DB;         // tile size (32)
-constexpr int BAND_THREADS = 256;   // threads per block
-constexpr int BAND_TRI = (BAND_TB - 1) * BAND_TB / 2;  // entries of the largest trailing triangle
+constexpr int BAND_TB = DB;        // tile size (32)
+constexpr int BAND_THREADS = 256;  // threads per block
+constexpr int BAND_TRI = BAND_TB * (BAND_TB + 1) / 2;  // entries of a tile's lower triangle
+enum { BAND_D = 0, BAND_U = 1, BAND_T = 2, BAND_F = 3, BAND_B = 4 };
+constexpr int BAND_CRIT_BLOCKS = 4;  // blocks of the near-diagonal pool
 
+// One task: x = type + 8 count (count: U's updates), y = I, z = J, w = Ka
+// (U) - for D, F: y = z = J; for B: y = z = I.
 struct BandArgs {
   int nb;             // block rows of the padded order (nb * TB >= n)
   int bwt;            // half-bandwidth in tiles
   int n;              // unknowns
+  int ntask;          // tasks
+  int ncrit;          // the near-diagonal pool's tasks (the first ncrit of the list)
+  int ncta_crit;      // blocks 0 .. ncta_crit - 1 run that pool
+  const int4* task;   // [ntask] in ticket order, per pool
   double* T;          // band tiles, L on return
   double* rsd;        // [nb TB] 1 / L_cc of every diagonal entry
   const double* rhs;  // [n] b
   double* y;          // [nb TB] y, then x
   double* sol;        // [n] x
-  int* tflag;         // [nb (bwt + 1)] tile final
-  int* ctr;           // [0] ticket, [1] forward blocks done, [2] backward blocks done, [3] a wait ran out
+  int* tflag;         // [nb (bwt + 1)] tile final (L)
+  int* tprog;         // [nb (bwt + 1)] updates applied to the tile
+  int* ctr;           // [0] bulk ticket, [1] forward blocks done, [2] backward blocks done, [3] a wait ran out,
+                      // [4] near-diagonal ticket
   int* fail;          // a pivot not positive or not finite
 };
 
-__device__ __forceinline__ double* band_tile(const BandArgs& a, int I, int J) {
-  return a.T + ((long long)J * (a.bwt + 1) + (I - J)) * (BAND_TB * BAND_TB);
+__device__ __forceinline__ long long band_index(const BandArgs& a, int I, int J) {
+  return (long long)J * (a.bwt + 1) + (I - J);
 }
 
-__device__ __forceinline__ int* band_flag(const BandArgs& a, int I, int J) {
-  return a.tflag + (long long)J * (a.bwt + 1) + (I - J);
+__device__ __forceinline__ double* band_tile(const BandArgs& a, int I, int J) {
+  return a.T + band_index(a, I, J) * (BAND_TB * BAND_TB);
 }
+
+__device__ __forceinline__ int* band_flag(const BandArgs& a, int I, int J) { return a.tflag + band_index(a, I, J); }
+
+__device__ __forceinline__ int* band_prog(const BandArgs& a, int I, int J) { return a.tprog + band_index(a, I, J); }
+
+__device__ __forceinline__ int band_k0(const BandArgs& a, int I) { return max(0, I - a.bwt); }
 
 // Thread-0 wait until *flag >= v (acquire).  False when the wait ran out or
 // another one did (ctr[3]).
@@ -89,14 +111,19 @@ __device__ __forceinline__ void band_publish(int* flag, int v) {
   }
 }
 
+typedef double BandTile[BAND_TB][BAND_TB + 1];
+
 // Stage a tile (row-major, TB x TB) into shared memory, through L2.
-__device__ __forceinline__ void band_stage(double (*s)[BAND_TB + 1], const double* __restrict__ g) {
+__device__ __forceinline__ void band_stage(BandTile& s, const double* __restrict__ g) {
   for (int e = threadIdx.x; e < BAND_TB * BAND_TB; e += BAND_THREADS) s[e / BAND_TB][e % BAND_TB] = __ldcg(g + e);
 }
 
+__device__ __forceinline__ void band_store(double* __restrict__ g, const BandTile& t) {
+  for (int e = threadIdx.x; e < BAND_TB * BAND_TB; e += BAND_THREADS) g[e] = t[e / BAND_TB][e % BAND_TB];
+}
+
 struct BandSmem {
-  double A[BAND_TB][BAND_TB + 1];
-  double B[BAND_TB][BAND_TB + 1];
+  BandTile A, B, C;
   double rs[BAND_TB];
   double d[BAND_TB];
   double red[BAND_THREADS / 32][BAND_TB];
@@ -105,96 +132,170 @@ struct BandSmem {
   int bad;
 };
 
-// Tile task (I, J).
-__device__ bool band_tile_task(const BandArgs& a, BandSmem& s, int I, int J) {
-  constexpr int TB = BAND_TB, E = TB * TB / BAND_THREADS;
-  const int tid = threadIdx.x, col = tid % TB, row0 = tid / TB;
-  double acc[E];
-  const double* Tij = band_tile(a, I, J);
-#pragma unroll
-  for (int m = 0; m < E; ++m) acc[m] = __ldcg(Tij + (row0 + m * (BAND_THREADS / TB)) * TB + col);
-  // acc -= L_IK L_JK^T, K ascending
-  for (int K = max(0, I - a.bwt); K < J; ++K) {
+// X L^T = A in place (s.A = A on entry, X on return), L = the staged tile
+// s.B with 1 / L_cc in s.rs: column by column, x_rc = a_rc / L_cc, then
+// a_rc' -= x_rc L_c'c for c' > c (L's column c prescaled by 1 / L_cc; the
+// prescaling overwrites s.B).
+__device__ void band_trsm(BandSmem& s) {
+  constexpr int TB = BAND_TB;
+  const int tid = threadIdx.x, lane = tid % 32, wp = tid / 32;
+  for (int e = tid; e < TB * TB; e += BAND_THREADS) {
+    const int rr = e / TB, cc = e % TB;
+    if (rr > cc) s.B[rr][cc] *= s.rs[cc];
+  }
+  __syncthreads();
+  for (int c = 0; c < TB - 1; ++c) {
+    const double x = s.A[lane][c];
+    for (int cp = c + 1 + wp; cp < TB; cp += BAND_THREADS / 32) s.A[lane][cp] = fma(-x, s.B[cp][c], s.A[lane][cp]);
+    __syncthreads();
+  }
+  for (int e = tid; e < TB * TB; e += BAND_THREADS) s.A[e / TB][e % TB] *= s.rs[e % TB];
+  __syncthreads();
+}
+
+// Factor the diagonal tile in s.C (lower triangle) into L, in place, with
+// 1 / L_cc in s.rs: right-looking, one barrier per column; the scaling of
+// column c is deferred (a_rc' -= a_rc a_c'c / d_c).  Lane 0 of warp 0
+// updates each next pivot and takes its reciprocal square root, the serial
+// chain of the factorisation; the other entries of the trailing triangle go
+// to warps 1-3 and 5-7, so that the chain's FP64 instructions do not queue
+// behind theirs (warps w and w + 4 share a scheduler).  A pivot that is not
+// positive or not finite is replaced by 1 and counted in s.bad.
+__device__ void band_potrf(BandSmem& s) {
+  constexpr int TB = BAND_TB, NU = BAND_THREADS - 64;  // updating threads
+  const int tid = threadIdx.x, wp = tid / 32;
+  const bool pivot = tid == 0;
+  const bool upd = wp % 4 != 0;
+  const int u = (wp < 4 ? wp - 1 : wp - 2) * 32 + tid % 32;  // 0 .. NU - 1 for the updating warps
+  if (pivot) {
+    const double d0 = s.C[0][0];
+    const bool ok = d0 > 0.0 && isfinite(d0);
+    s.d[0] = ok ? d0 : 1.0;
+    s.rs[0] = ok ? rsqrt(d0) : 1.0;
+    s.bad = ok ? 0 : 1;
+  }
+  __syncthreads();
+  for (int c = 0; c < TB - 1; ++c) {
+    const int m = TB - 1 - c, ne = m * (m + 1) / 2;
+    const double inv = s.rs[c] * s.rs[c];
+    if (pivot) {  // (c + 1, c + 1): the next pivot
+      const double a = s.C[c + 1][c];
+      const double v = fma(-(a * inv), a, s.C[c + 1][c + 1]);
+      s.C[c + 1][c + 1] = v;
+      const bool ok = v > 0.0 && isfinite(v);
+      s.d[c + 1] = ok ? v : 1.0;
+      s.rs[c + 1] = ok ? rsqrt(v) : 1.0;
+      if (!ok) s.bad = 1;
+    } else if (upd) {
+      for (int e = 1 + u; e < ne; e += NU) {
+        const int rr = c + 1 + (s.tri[e] >> 8), cc = c + 1 + (s.tri[e] & 0xff);
+        s.C[rr][cc] = fma(-(s.C[rr][c] * inv), s.C[cc][c], s.C[rr][cc]);
+      }
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < TB * TB; e += BAND_THREADS) {
+    const int rr = e / TB, cc = e % TB;
+    s.C[rr][cc] = rr > cc ? s.C[rr][cc] * s.rs[cc] : (rr == cc ? s.d[cc] * s.rs[cc] : 0.0);
+  }
+  __syncthreads();
+}
+
+// D_J: the subdiagonal tile's solve, the last update of the diagonal tile
+// and its factorisation.
+__device__ bool band_task_D(const BandArgs& a, BandSmem& s, int J) {
+  constexpr int TB = BAND_TB;
+  const int tid = threadIdx.x;
+  if (J >= 1 && a.bwt >= 1) {
+    // tiles (J, J - 1) and (J, J) hold every update before K = J - 1
+    // (the two tiles of row J usually finish first: stage them while
+    // L_{J-1,J-1} is still being factored)
+    const int nupd = (J - 1) - band_k0(a, J);
     int w = 1;
+    if (tid == 0)
+      w = band_wait(band_prog(a, J, J - 1), nupd, a.ctr + 3) && band_wait(band_prog(a, J, J), nupd, a.ctr + 3);
+    if (!__syncthreads_and(w)) return false;
+    band_stage(s.A, band_tile(a, J, J - 1));
+    band_stage(s.C, band_tile(a, J, J));
+    w = 1;
+    if (tid == 0) w = band_wait(band_flag(a, J - 1, J - 1), 1, a.ctr + 3);
+    if (!__syncthreads_and(w)) return false;
+    band_stage(s.B, band_tile(a, J - 1, J - 1));
+    if (tid < TB) s.rs[tid] = __ldcg(a.rsd + (long long)(J - 1) * TB + tid);
+    __syncthreads();
+    band_trsm(s);  // s.A = L_{J,J-1}
+    band_store(band_tile(a, J, J - 1), s.A);
+    band_publish(band_flag(a, J, J - 1), 1);
+    // A_JJ -= L_{J,J-1} L_{J,J-1}^T on the lower triangle
+    for (int e = tid; e < BAND_TRI; e += BAND_THREADS) {
+      const int r = s.tri[e] >> 8, c = s.tri[e] & 0xff;
+      double v = s.C[r][c];
+#pragma unroll 8
+      for (int k = 0; k < TB; ++k) v = fma(-s.A[r][k], s.A[c][k], v);
+      s.C[r][c] = v;
+    }
+    __syncthreads();
+  } else {
+    band_stage(s.C, band_tile(a, J, J));
+    __syncthreads();
+  }
+  band_potrf(s);  // s.C = L_JJ
+  band_store(band_tile(a, J, J), s.C);
+  if (tid < TB) a.rsd[(long long)J * TB + tid] = s.rs[tid];
+  if (tid == 0 && s.bad) atomicExch(a.fail, 1);
+  band_publish(band_flag(a, J, J), 1);
+  return true;
+}
+
+// U: A_IJ -= L_IK L_JK^T for K = Ka .. Ka + cnt - 1, after the tile's
+// earlier updates.
+__device__ bool band_task_U(const BandArgs& a, BandSmem& s, int I, int J, int Ka, int cnt) {
+  constexpr int TB = BAND_TB, E = TB * TB / BAND_THREADS, RS = BAND_THREADS / TB;
+  const int tid = threadIdx.x, col = tid % TB, row0 = tid / TB;
+  const int k0 = band_k0(a, I);
+  int w = 1;
+  if (tid == 0) w = band_wait(band_prog(a, I, J), Ka - k0, a.ctr + 3);
+  if (!__syncthreads_and(w)) return false;
+  double* Tij = band_tile(a, I, J);
+  double acc[E];
+#pragma unroll
+  for (int m = 0; m < E; ++m) acc[m] = __ldcg(Tij + (row0 + m * RS) * TB + col);
+  for (int K = Ka; K < Ka + cnt; ++K) {
+    w = 1;
     if (tid == 0) w = band_wait(band_flag(a, I, K), 1, a.ctr + 3) && band_wait(band_flag(a, J, K), 1, a.ctr + 3);
     if (!__syncthreads_and(w)) return false;
     band_stage(s.A, band_tile(a, I, K));
     if (I != J) band_stage(s.B, band_tile(a, J, K));
     __syncthreads();
-    const double(*LJ)[TB + 1] = (I != J) ? s.B : s.A;
+    const BandTile& LJ = (I != J) ? s.B : s.A;
 #pragma unroll 8
     for (int k = 0; k < TB; ++k) {
       const double b = LJ[col][k];
 #pragma unroll
-      for (int m = 0; m < E; ++m) acc[m] = fma(-s.A[row0 + m * (BAND_THREADS / TB)][k], b, acc[m]);
+      for (int m = 0; m < E; ++m) acc[m] = fma(-s.A[row0 + m * RS][k], b, acc[m]);
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int m = 0; m < E; ++m) s.A[row0 + m * (BAND_THREADS / TB)][col] = acc[m];
+  for (int m = 0; m < E; ++m) Tij[(row0 + m * RS) * TB + col] = acc[m];
+  band_publish(band_prog(a, I, J), Ka + cnt - k0);
+  return true;
+}
+
+// T: L_IJ = A_IJ L_JJ^{-T} (I >= J + 2) after the tile's updates.
+__device__ bool band_task_T(const BandArgs& a, BandSmem& s, int I, int J) {
+  constexpr int TB = BAND_TB;
+  const int tid = threadIdx.x;
+  int w = 1;
+  if (tid == 0)
+    w = band_wait(band_flag(a, J, J), 1, a.ctr + 3) && band_wait(band_prog(a, I, J), J - band_k0(a, I), a.ctr + 3);
+  if (!__syncthreads_and(w)) return false;
+  band_stage(s.A, band_tile(a, I, J));
+  band_stage(s.B, band_tile(a, J, J));
+  if (tid < TB) s.rs[tid] = __ldcg(a.rsd + (long long)J * TB + tid);
   __syncthreads();
-  double* out = band_tile(a, I, J);
-  if (I == J) {
-    // factor the diagonal tile: right-looking, the trailing triangle's
-    // entries spread over the block; the scaling of column c is deferred
-    // (a_rc' -= a_rc a_c'c / d_c), and the thread that updates the next
-    // pivot takes its reciprocal square root at once
-    if (tid == 0) {
-      const double d0 = s.A[0][0];
-      const bool ok = d0 > 0.0 && isfinite(d0);
-      s.d[0] = ok ? d0 : 1.0;
-      s.rs[0] = ok ? rsqrt(d0) : 1.0;
-      s.bad = ok ? 0 : 1;
-    }
-    __syncthreads();
-    for (int c = 0; c < TB - 1; ++c) {
-      const int m = TB - 1 - c, ne = m * (m + 1) / 2;
-      const double rs = s.rs[c];
-      const double inv = rs * rs;
-      for (int e = tid; e < ne; e += BAND_THREADS) {
-        const int rr = c + 1 + (s.tri[e] >> 8), cc = c + 1 + (s.tri[e] & 0xff);
-        const double v = fma(-(s.A[rr][c] * inv), s.A[cc][c], s.A[rr][cc]);
-        s.A[rr][cc] = v;
-        if (e == 0) {  // (c + 1, c + 1): the next pivot
-          const bool ok = v > 0.0 && isfinite(v);
-          s.d[c + 1] = ok ? v : 1.0;
-          s.rs[c + 1] = ok ? rsqrt(v) : 1.0;
-          if (!ok) s.bad = 1;
-        }
-      }
-      __syncthreads();
-    }
-    for (int e = tid; e < TB * TB; e += BAND_THREADS) {
-      const int rr = e / TB, cc = e % TB;
-      out[e] = rr > cc ? s.A[rr][cc] * s.rs[cc] : (rr == cc ? s.d[cc] * s.rs[cc] : 0.0);
-    }
-    if (tid < TB) a.rsd[(long long)J * TB + tid] = s.rs[tid];
-    if (tid == 0 && s.bad) atomicExch(a.fail, 1);
-  } else {
-    // X L_JJ^T = A: column by column, x_rc = a_rc / L_cc, then
-    // a_rc' -= x_rc L_c'c for c' > c (L's column c prescaled by 1 / L_cc)
-    int w = 1;
-    if (tid == 0) w = band_wait(band_flag(a, J, J), 1, a.ctr + 3);
-    if (!__syncthreads_and(w)) return false;
-    band_stage(s.B, band_tile(a, J, J));
-    if (tid < TB) s.rs[tid] = __ldcg(a.rsd + (long long)J * TB + tid);
-    __syncthreads();
-    for (int e = tid; e < TB * TB; e += BAND_THREADS) {
-      const int rr = e / TB, cc = e % TB;
-      if (rr > cc) s.B[rr][cc] *= s.rs[cc];
-    }
-    __syncthreads();
-    const int lane = tid % 32, wp = tid / 32;
-    for (int c = 0; c < TB - 1; ++c) {
-      const double x = s.A[lane][c];
-      for (int cp = c + 1 + wp; cp < TB; cp += BAND_THREADS / 32) s.A[lane][cp] = fma(-x, s.B[cp][c], s.A[lane][cp]);
-      __syncthreads();
-    }
-    for (int e = tid; e < TB * TB; e += BAND_THREADS) {
-      const int rr = e / TB, cc = e % TB;
-      out[e] = s.A[rr][cc] * s.rs[cc];
-    }
-  }
+  band_trsm(s);
+  band_store(band_tile(a, I, J), s.A);
   band_publish(band_flag(a, I, J), 1);
   return true;
 }
@@ -320,23 +421,23 @@ static __global__ void __launch_bounds__(BAND_THREADS, 1) k_band_chol(BandArgs a
     while (r * (r + 1) / 2 > e) --r;
     s.tri[e] = (uint16_t)((r << 8) | (e - r * (r + 1) / 2));
   }
-  const int ntile = a.nb * (a.bwt + 2), ntask = ntile + a.nb;
+  const bool near = blockIdx.x < a.ncta_crit;
+  const int lim = near ? a.ncrit : a.ntask;
   for (;;) {
-    if (threadIdx.x == 0) s.task = band_load(a.ctr + 3) ? ntask : atomicAdd(a.ctr, 1);
+    if (threadIdx.x == 0)
+      s.task = band_load(a.ctr + 3) ? lim : (near ? 0 : a.ncrit) + atomicAdd(a.ctr + (near ? 4 : 0), 1);
     __syncthreads();
     const int q = s.task;
     __syncthreads();
-    if (q >= ntask) break;
+    if (q >= lim) break;
+    const int4 t = a.task[q];
     bool ok = true;
-    if (q < ntile) {
-      const int J = q / (a.bwt + 2), d = q % (a.bwt + 2);
-      if (d <= a.bwt) {
-        if (J + d < a.nb) ok = band_tile_task(a, s, J + d, J);
-      } else {
-        ok = band_forward_task(a, s, J);
-      }
-    } else {
-      ok = band_backward_task(a, s, a.nb - 1 - (q - ntile));
+    switch (t.x & 7) {
+      case BAND_D: ok = band_task_D(a, s, t.z); break;
+      case BAND_U: ok = band_task_U(a, s, t.y, t.z, t.w, t.x >> 3); break;
+      case BAND_T: ok = band_task_T(a, s, t.y, t.z); break;
+      case BAND_F: ok = band_forward_task(a, s, t.z); break;
+      default: ok = band_backward_task(a, s, t.z); break;
     }
     if (!ok) break;
   }
