@@ -17,8 +17,10 @@
 //   U       A_IJ -= L_IK L_JK^T for K in [Ka, Ka + cnt): the updates of a
 //           tile, in ascending K (tile (J, J) leaves K = J - 1 to D_J);
 //   T       L_IJ = A_IJ L_JJ^{-T} for I >= J + 2;
-//   F_J     y_J = L_JJ^{-1} (b_J - sum_K L_JK y_K);
-//   B_I     x_I = L_II^{-T} (y_I - sum_K L_KI^T x_K).
+//   I_J     U_J = L_JJ^{-T} (the same solve with A = identity), so that the
+//           triangular solves below are products, not serial substitutions;
+//   F_J     y_J = U_J^T (b_J - sum_K L_JK y_K);
+//   B_I     x_I = U_I (y_I - sum_K L_KI^T x_K).
 // The chain D_0, D_1, ... is the critical path; one D_J is a triangular
 // solve, a symmetric update and a factorisation of single tiles, while the U
 // and T tasks of later columns run beside it.  The host orders the tasks by
@@ -47,7 +49,7 @@ namespace ba {
 constexpr int BAND_TB = DB;        // tile size (32)
 constexpr int BAND_THREADS = 256;  // threads per block
 constexpr int BAND_TRI = BAND_TB * (BAND_TB + 1) / 2;  // entries of a tile's lower triangle
-enum { BAND_D = 0, BAND_U = 1, BAND_T = 2, BAND_F = 3, BAND_B = 4 };
+enum { BAND_D = 0, BAND_U = 1, BAND_T = 2, BAND_F = 3, BAND_B = 4, BAND_I = 5 };
 constexpr int BAND_CRIT_BLOCKS = 4;  // blocks of the near-diagonal pool
 
 // One task: x = type + 8 count (count: U's updates), y = I, z = J, w = Ka
@@ -62,6 +64,7 @@ struct BandArgs {
   const int4* task;   // [ntask] in ticket order, per pool
   double* T;          // band tiles, L on return
   double* rsd;        // [nb TB] 1 / L_cc of every diagonal entry
+  double* Ui;         // [nb TB TB] U_J = L_JJ^{-T}, row-major (upper triangular)
   const double* rhs;  // [n] b
   double* y;          // [nb TB] y, then x
   double* sol;        // [n] x
@@ -70,6 +73,7 @@ struct BandArgs {
   int* ctr;           // [0] bulk ticket, [1] forward blocks done, [2] backward blocks done, [3] a wait ran out,
                       // [4] near-diagonal ticket
   int* fail;          // a pivot not positive or not finite
+  int* iflag;         // [nb] U_J final
 };
 
 __device__ __forceinline__ long long band_index(const BandArgs& a, int I, int J) {
@@ -300,6 +304,23 @@ __device__ bool band_task_T(const BandArgs& a, BandSmem& s, int I, int J) {
   return true;
 }
 
+// I_J: U_J = L_JJ^{-T}, the solution of X L_JJ^T = identity.
+__device__ bool band_task_I(const BandArgs& a, BandSmem& s, int J) {
+  constexpr int TB = BAND_TB;
+  const int tid = threadIdx.x;
+  int w = 1;
+  if (tid == 0) w = band_wait(band_flag(a, J, J), 1, a.ctr + 3);
+  if (!__syncthreads_and(w)) return false;
+  band_stage(s.B, band_tile(a, J, J));
+  if (tid < TB) s.rs[tid] = __ldcg(a.rsd + (long long)J * TB + tid);
+  for (int e = tid; e < TB * TB; e += BAND_THREADS) s.A[e / TB][e % TB] = (e / TB == e % TB) ? 1.0 : 0.0;
+  __syncthreads();
+  band_trsm(s);
+  band_store(a.Ui + (long long)J * TB * TB, s.A);
+  band_publish(a.iflag + J, 1);
+  return true;
+}
+
 __device__ __forceinline__ int band_load(int* p) {
   cuda::atomic_ref<int, cuda::thread_scope_device> f(*p);
   return f.load(cuda::memory_order_acquire);
@@ -336,24 +357,29 @@ __device__ bool band_forward_task(const BandArgs& a, BandSmem& s, int J) {
   part += __shfl_xor_sync(0xffffffffu, part, 2);
   part += __shfl_xor_sync(0xffffffffu, part, 1);
   const long long row = (long long)J * TB + r;
-  if (q == 0) s.red[0][r] = (row < a.n ? a.rhs[row] : 0.0) - part;
+  if (q == 0) s.d[r] = (row < a.n ? a.rhs[row] : 0.0) - part;
   int w = 1;
-  if (tid == 0) w = band_wait(band_flag(a, J, J), 1, a.ctr + 3);
+  if (tid == 0) w = band_wait(a.iflag + J, 1, a.ctr + 3);
   if (!__syncthreads_and(w)) return false;
-  band_stage(s.B, band_tile(a, J, J));
-  if (tid < TB) s.rs[tid] = __ldcg(a.rsd + (long long)J * TB + tid);
-  __syncthreads();
-  if (tid < 32) {
-    // L_JJ y = v, column by column: y_c = v_c / L_cc, then v_r -= L_rc y_c
-    const int lane = tid;
-    double v = s.red[0][lane];
-#pragma unroll 4
-    for (int c = 0; c < TB; ++c) {
-      const double yc = __shfl_sync(0xffffffffu, v * s.rs[c], c);
-      if (lane > c) v = fma(-s.B[lane][c], yc, v);
-      else if (lane == c) v = yc;
+  {
+    // y = U_J^T v: lane r, rows c = wp, wp + 8, ... of U_J, summed over the
+    // warps in order
+    const int lane = tid % 32, wp = tid / 32;
+    const double* U = a.Ui + (long long)J * TB * TB;
+    double p = 0.0;
+#pragma unroll
+    for (int m = 0; m < TB / (BAND_THREADS / 32); ++m) {
+      const int c = wp + m * (BAND_THREADS / 32);
+      p = fma(__ldcg(U + c * TB + lane), s.d[c], p);
     }
-    a.y[(long long)J * TB + lane] = v;
+    s.red[wp][lane] = p;
+    __syncthreads();
+    if (tid < 32) {
+      double v = 0.0;
+#pragma unroll
+      for (int k = 0; k < BAND_THREADS / 32; ++k) v += s.red[k][lane];
+      a.y[(long long)J * TB + lane] = v;
+    }
   }
   // blocks are published in order (F_{J-1} first)
   w = 1;
@@ -386,23 +412,30 @@ __device__ bool band_backward_task(const BandArgs& a, BandSmem& s, int I) {
     }
   }
   s.red[wp][lane] = part;
-  band_stage(s.B, band_tile(a, I, I));
-  if (tid < TB) s.rs[tid] = __ldcg(a.rsd + (long long)I * TB + tid);
   __syncthreads();
   if (tid < 32) {
     double v = __ldcg(a.y + (long long)I * TB + lane);
 #pragma unroll
     for (int k = 0; k < BAND_THREADS / 32; ++k) v -= s.red[k][lane];
-    // L_II^T x = v, from the last column: x_c = v_c / L_cc, then v_r -= L_cr x_c
-#pragma unroll 4
-    for (int c = TB - 1; c >= 0; --c) {
-      const double xc = __shfl_sync(0xffffffffu, v * s.rs[c], c);
-      if (lane < c) v = fma(-s.B[c][lane], xc, v);
-      else if (lane == c) v = xc;
+    s.d[lane] = v;
+  }
+  __syncthreads();
+  {
+    // x = U_I v: row r of U_I, columns 4q .. 4q + 3, summed over the 8
+    // threads of the row
+    const int r = tid / 8, q = tid % 8;
+    const double* U = a.Ui + (long long)I * TB * TB + r * TB + 4 * q;
+    double p = 0.0;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) p = fma(__ldcg(U + c), s.d[4 * q + c], p);
+    p += __shfl_xor_sync(0xffffffffu, p, 4);
+    p += __shfl_xor_sync(0xffffffffu, p, 2);
+    p += __shfl_xor_sync(0xffffffffu, p, 1);
+    const long long row = (long long)I * TB + r;
+    if (q == 0) {
+      a.y[row] = p;
+      if (row < a.n) a.sol[row] = p;
     }
-    const long long row = (long long)I * TB + lane;
-    a.y[row] = v;
-    if (row < a.n) a.sol[row] = v;
   }
   w = 1;
   if (tid == 0) w = band_wait_count(a.ctr + 2, a.nb - 1 - I, &known, a.ctr + 3);
@@ -436,6 +469,7 @@ static __global__ void __launch_bounds__(BAND_THREADS, 1) k_band_chol(BandArgs a
       case BAND_D: ok = band_task_D(a, s, t.z); break;
       case BAND_U: ok = band_task_U(a, s, t.y, t.z, t.w, t.x >> 3); break;
       case BAND_T: ok = band_task_T(a, s, t.y, t.z); break;
+      case BAND_I: ok = band_task_I(a, s, t.z); break;
       case BAND_F: ok = band_forward_task(a, s, t.z); break;
       default: ok = band_backward_task(a, s, t.z); break;
     }

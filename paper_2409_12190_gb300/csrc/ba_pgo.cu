@@ -172,12 +172,13 @@ struct ba_pgo {
   double *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
   double *pcg_part = nullptr, *dpart = nullptr, *gpart = nullptr, *epart = nullptr;
   uint8_t* fixed = nullptr;
-  // Cholesky: the band tiles of H + D (then L), 1 / L_cc, y / x in the
-  // padded factored order, and the flags (tile final [bnb (bwt + 1)],
-  // counters [4], failure [1]) of the factorisation's schedule
+  // Cholesky: the band tiles of H + D (then L), 1 / L_cc, the inverses
+  // L_JJ^{-T}, y / x in the padded factored order, and the flags of the
+  // factorisation's schedule (tile final and tile updates [bnb (bwt + 1)]
+  // each, counters [5], failure [1], inverse final [bnb])
   int bnb = 0, bwt = 0, band_grid = 0, band_crit = 0, bntask = 0, bncrit = 0;
   size_t bT_bytes = 0, bflag_count = 0;
-  double *bT = nullptr, *brs = nullptr, *dy = nullptr;
+  double *bT = nullptr, *brs = nullptr, *bUi = nullptr, *dy = nullptr;
   int* bflag = nullptr;
   int4* btask = nullptr;  // the factorisation's tasks in ticket order
   int* derr = nullptr;
@@ -208,14 +209,14 @@ ba_status copy_in(void* dst, const void* src, size_t bytes, cudaStream_t s) {
 }
 
 // The banded Cholesky's tasks (ba_band.cuh) in ticket order.
-//  1. A topological enumeration by step s = 0 .. nb - 1: D_s; the update
+//  1. A topological enumeration by step s = 0 .. nb - 1: D_s; I_s; the update
 //     segments whose last column is s - 1; the solves T(I, s); F_s; then
 //     B_{nb-1} .. B_0.  Each task's predecessors are listed; D_J's
 //     subdiagonal tile L_{J,J-1} is published early (after its solve, before
 //     the update and factorisation of L_JJ).
 //  2. Each task's longest path to the end (its priority), from rough
 //     durations in microseconds (D 20, of which 8 before the early output;
-//     U 12 per column; T 7; F and B 4; 1 per dependency).
+//     U 12 per column; T 7; I 8; F and B 4; 1 per dependency).
 //  3. A list-scheduling simulation on `workers` blocks: a free block takes
 //     the ready task of highest priority.  The tickets follow the simulated
 //     start times.  A task starts after its predecessors' outputs, which
@@ -235,7 +236,7 @@ std::vector<int4> band_tasks(int nb, int bwt, int s_upd, int workers, int crit_w
       seg0[tix(I, J) + 1] = (u + s_upd - 1) / s_upd;
     }
   for (long long t = 0; t < ntile; ++t) seg0[t + 1] += seg0[t];
-  std::vector<int> segid(seg0[ntile], -1), idD(nb), idF(nb), idB(nb), idT(ntile, -1);
+  std::vector<int> segid(seg0[ntile], -1), idD(nb), idI(nb), idF(nb), idB(nb), idT(ntile, -1);
   std::vector<int4> task;
   std::vector<double> dur;
   std::vector<int> pbeg(1, 0), pred;  // predecessors: id * 2 + (1: D's early output)
@@ -265,6 +266,8 @@ std::vector<int4> band_tasks(int nb, int bwt, int s_upd, int workers, int crit_w
       }
     }
     idD[st] = add(BAND_D, 0, st, st, 0, 20.0);
+    dep(2 * idD[st]);
+    idI[st] = add(BAND_I, 0, st, st, 0, 8.0);
     for (int J = st; J < std::min(nb, st + bwt); ++J)
       for (int I = J; I < std::min(nb, st + bwt); ++I) {
         const int K = st - 1, a0 = k0(I), e = kend(I, J);
@@ -286,6 +289,7 @@ std::vector<int4> band_tasks(int nb, int bwt, int s_upd, int workers, int crit_w
     }
     if (st >= 1) dep(2 * idF[st - 1]);
     for (int K = k0(st); K <= st; ++K) dep(prod(st, K));
+    dep(2 * idI[st]);
     idF[st] = add(BAND_F, 0, st, st, 0, 4.0);
   }
   for (int I = nb - 1; I >= 0; --I) {
@@ -535,8 +539,8 @@ ba_status enqueue_solve(ba_pgo* h, const double* lam_ptr, int maxiter, double to
     }
     const size_t ntile = (size_t)h->bnb * (h->bwt + 1);
     int* ctr = h->bflag + 2 * ntile;
-    BandArgs ba_{h->bnb, h->bwt, n, h->bntask, h->bncrit, h->band_crit, h->btask, h->bT, h->brs, rhs, h->dy, sol,
-                 h->bflag, h->bflag + ntile, ctr, ctr + 5};
+    BandArgs ba_{h->bnb, h->bwt, n, h->bntask, h->bncrit, h->band_crit, h->btask, h->bT, h->brs, h->bUi, rhs,
+                 h->dy, sol, h->bflag, h->bflag + ntile, ctr, ctr + 5, ctr + 6};
     void* args[] = {&ba_};
     PCU(cudaLaunchCooperativeKernel((const void*)k_band_chol, dim3(h->band_grid), dim3(BAND_THREADS), args, 0, s));
     k_band_finish<<<nb(n, 256), 256, 0, s>>>(n, ctr + 5, ctr, sol, h->st);
@@ -735,13 +739,14 @@ ba_status ba_pgo_create(ba_pgo** out, int N, int E, const double* poses, const i
       const std::vector<int4> tasks = band_tasks(h->bnb, h->bwt, s_upd, h->band_grid, h->band_crit, &h->bncrit);
       h->bntask = (int)tasks.size();
       h->bT_bytes = (size_t)h->bnb * (h->bwt + 1) * (BAND_TB * BAND_TB) * sizeof(double);
-      h->bflag_count = 2 * (size_t)h->bnb * (h->bwt + 1) + 6;
+      h->bflag_count = 2 * (size_t)h->bnb * (h->bwt + 1) + 6 + h->bnb;
       int occb = 0;
       if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occb, k_band_chol, BAND_THREADS, 0)) != cudaSuccess ||
           occb < 1)
         return bail(set_error(BA_ERR_CUDA, "the Cholesky kernel cannot be resident"));
       if ((e = h->alloc(&h->bT, h->bT_bytes)) != cudaSuccess ||
           (e = h->alloc(&h->brs, 8ull * h->bnb * BAND_TB)) != cudaSuccess ||
+          (e = h->alloc(&h->bUi, 8ull * h->bnb * BAND_TB * BAND_TB)) != cudaSuccess ||
           (e = h->alloc(&h->dy, 8ull * h->bnb * BAND_TB)) != cudaSuccess ||
           (e = h->alloc(&h->bflag, sizeof(int) * h->bflag_count)) != cudaSuccess ||
           (e = h->alloc(&h->btask, sizeof(int4) * tasks.size())) != cudaSuccess ||
