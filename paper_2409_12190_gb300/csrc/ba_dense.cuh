@@ -16,7 +16,7 @@
 //   k_chol_diag      factor the diagonal DB x DB block of the current block
 //                    column (one CTA, in shared memory).
 //   k_chol_panel     L_ik = A_ik L_kk^{-T} for the block rows below (one
-//                    warp per block of rows; k_chol_panel4: four warps).
+//                    warp per block of rows).
 //   k_chol_update    A_IJ -= L_Ik L_Jk^T on the trailing lower triangle.
 //   k_dense_solve    L L^T x = b (one CTA: forward then backward
 //                    substitution, column by column), x into the PCG
@@ -204,41 +204,6 @@ k_chol_panel(int n, int kb, double* __restrict__ A) {
 #pragma unroll
   for (int c = 0; c < DB; ++c)
     if (c < nb) A[(long long)r * n + k + c] = x[c];
-}
-
-// The same panel solve with four warps per block of DB rows (one lane per
-// row): column by column (right-looking), x_c = a_c / L_cc by warp 0 with
-// the pivot's reciprocal, then the four warps subtract x_c L_c'c from the
-// columns c' > c, a quarter each.  Spreads the FP64 work of a row block
-// over four warps instead of one.
-static __global__ void __launch_bounds__(4 * DB)
-k_chol_panel4(int n, int kb, double* __restrict__ A) {
-  __shared__ double Lk[DB][DB + 1];
-  __shared__ double xs[DB][DB + 1];
-  __shared__ double ri[DB];
-  const int k = kb * DB;
-  const int nb = min(DB, n - k);
-  const int r0 = k + nb + blockIdx.x * DB;
-  const int tid = threadIdx.x, lane = tid % DB, w = tid / DB;
-  for (int e = tid; e < DB * DB; e += blockDim.x) {
-    const int rr = e / DB, cc = e % DB;
-    Lk[rr][cc] = (rr < nb && cc <= rr) ? A[(long long)(k + rr) * n + k + cc] : 0.0;
-    xs[rr][cc] = (r0 + rr < n && cc < nb) ? A[(long long)(r0 + rr) * n + k + cc] : 0.0;
-  }
-  __syncthreads();
-  if (tid < nb) ri[tid] = 1.0 / Lk[tid][tid];
-  __syncthreads();
-  for (int c = 0; c < nb; ++c) {
-    if (w == 0) xs[lane][c] *= ri[c];
-    __syncthreads();
-    const double xc = xs[lane][c];
-    for (int cp = c + 1 + w; cp < nb; cp += 4) xs[lane][cp] -= xc * Lk[cp][c];
-    __syncthreads();
-  }
-  for (int e = tid; e < DB * DB; e += blockDim.x) {
-    const int rr = e / DB, cc = e % DB;
-    if (r0 + rr < n && cc < nb) A[(long long)(r0 + rr) * n + k + cc] = xs[rr][cc];
-  }
 }
 
 // A_IJ -= L_Ik L_Jk^T for the trailing tiles I >= J (DB x DB each) below
