@@ -42,6 +42,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "ba_band_sched.h"
 #include "ba_dense.cuh"
 
 namespace ba {
@@ -49,8 +50,6 @@ namespace ba {
 constexpr int BAND_TB = DB;        // tile size (32)
 constexpr int BAND_THREADS = 256;  // threads per block
 constexpr int BAND_TRI = BAND_TB * (BAND_TB + 1) / 2;  // entries of a tile's lower triangle
-enum { BAND_D = 0, BAND_U = 1, BAND_T = 2, BAND_F = 3, BAND_B = 4, BAND_I = 5 };
-constexpr int BAND_CRIT_BLOCKS = 4;  // blocks of the near-diagonal pool
 
 // One task: x = type + 8 count (count: U's updates), y = I, z = J, w = Ka
 // (U) - for D, F: y = z = J; for B: y = z = I.
