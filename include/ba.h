@@ -66,10 +66,13 @@ enum { BA_JAC_AUTO = 0, BA_JAC_RECOMPUTE = 1, BA_JAC_STORE = 2 };
  * the paper offers PCG and a sparse direct solver, a Cholesky
  * factorisation).  BA_SOLVER_PCG: block-Jacobi PCG with the implicit S x
  * product (pcg_maxiter, pcg_tol).  BA_SOLVER_CHOLESKY: S formed explicitly
- * as a dense 9C x 9C FP64 matrix and factored by a blocked Cholesky on the
- * GPU, for problems with 9C <= BA_DENSE_MAX_DIM (the matrix takes 81 C^2 x 8
- * bytes); a trial whose S is not positive definite in FP64 takes a zero step
- * (rejected, counted in ba_iter_stats.precond_fallbacks). */
+ * as a dense 9C x 9C FP64 matrix and factored by a tiled Cholesky on the
+ * GPU (the factorisation and both triangular solves in one cooperative
+ * launch), for problems with 9C <= BA_DENSE_MAX_DIM (the matrix and its
+ * tiles take 81 C^2 x 8 bytes each, plus up to 8 partial copies of S while
+ * it is built for small C); a trial whose S is not positive definite in
+ * FP64 takes a zero step (rejected, counted in
+ * ba_iter_stats.precond_fallbacks). */
 enum { BA_SOLVER_PCG = 0, BA_SOLVER_CHOLESKY = 1 };
 #define BA_DENSE_MAX_DIM 18432
 
@@ -92,7 +95,8 @@ typedef struct {
   double diag_max;     /* 1e32 */
   int pcg_maxiter;     /* PCG iterations per LM trial, 250 */
   double pcg_tol;      /* stop when |r|_2 <= pcg_tol |b|_2, 1e-4 */
-  int use_graph;       /* 1: ba_solve replays a captured CUDA graph */
+  int use_graph;       /* 1: ba_solve replays a captured CUDA graph (not with
+                          BA_SOLVER_CHOLESKY: its trials are direct launches) */
   int max_stats;       /* capacity of the per-trial statistics ring, 4096 */
   int jacobian_mode;   /* BA_JAC_AUTO, BA_JAC_RECOMPUTE or BA_JAC_STORE */
   int solver;          /* BA_SOLVER_PCG or BA_SOLVER_CHOLESKY */

@@ -15,7 +15,7 @@
 
 #include "ba.h"
 #include "ba_internal.h"
-#include "ba_dense.cuh"
+#include "ba_band.cuh"
 #include "ba_kernels.cuh"
 #include "ba_learn.cuh"
 #include "ba_problem.h"
@@ -290,43 +290,35 @@ void enqueue_coupling(ba_problem* h, const double* lam_ptr) {
   }
 }
 
-// The direct solve of the reduced system (BA_SOLVER_CHOLESKY): explicit S,
-// blocked Cholesky, triangular solves; dc into h->x as the PCG would leave it.
+// The direct solve of the reduced system (BA_SOLVER_CHOLESKY): explicit S in
+// nseg partials, summed into the band tiles, then the factorisation and both
+// triangular solves in one cooperative launch (ba_band.cuh); dc into h->x as
+// the PCG would leave it.
 template <typename T, bool MF>
 void enqueue_dense_solve(ba_problem* h, const double* lam_ptr) {
   cudaStream_t s = h->s;
   const int n = 9 * h->C;
-  {
-    Prof pr(h, BA_K_OTHER);
-    k_schur_dense<T, MF><<<h->C, DENSE_THREADS, 0, s>>>(
-        h->C, h->rowptr_cam, h->cm_pt, h->rowptr_pt, h->pm_cam, h->pm2cm, (const T*)h->Jcm, (const T*)h->cm_sw,
-        (const T*)h->camtab, (const T*)h->pts, h->st, h->P, h->O, (const T*)h->Vinv, h->U, lam_ptr, h->opt.diag_min,
-        h->opt.diag_max, h->dS);
+  Prof pr(h, BA_K_OTHER);
+  k_schur_dense<T, MF><<<h->C * h->nseg, DENSE_THREADS, 0, s>>>(
+      h->C, h->rowptr_cam, h->cm_pt, h->rowptr_pt, h->pm_cam, h->pm2cm, (const T*)h->Jcm, (const T*)h->cm_sw,
+      (const T*)h->camtab, (const T*)h->pts, h->st, h->P, h->O, (const T*)h->Vinv, h->nseg, h->Spart);
+  cudaMemsetAsync(h->bT, 0, h->bT_bytes, s);
+  cudaMemsetAsync(h->bflag, 0, sizeof(int) * h->bflag_count, s);
+  k_schur_to_band<<<n, 256, 0, s>>>(h->C, h->nseg, h->Spart, h->U, lam_ptr, h->opt.diag_min, h->opt.diag_max,
+                                    h->fixed, h->bwt, h->bT);
+  count_launch(2);
+  if (h->bnb * BAND_TB > n) {
+    k_band_pad<<<1, BAND_TB, 0, s>>>(n, h->bnb, h->bwt, h->bT);
     count_launch();
   }
-  if (h->fixed) {
-    k_dense_mask<<<nblk((long long)n * n, 256), 256, 0, s>>>(n, h->fixed, h->dS);
-    count_launch();
-  }
-  cudaMemsetAsync(h->dfail, 0, sizeof(int), s);
-  const int nblk_d = (n + DB - 1) / DB;
-  for (int kb = 0; kb < nblk_d; ++kb) {
-    Prof pr(h, BA_K_OTHER);
-    k_chol_diag<<<1, DB * DB / 4, 0, s>>>(n, kb, h->dS, h->dfail);
-    const int rows_below = n - (kb + 1) * DB;
-    if (rows_below > 0) {
-      k_chol_panel<<<(rows_below + DB - 1) / DB, DB, 0, s>>>(n, kb, h->dS);
-      const long long T_ = nblk_d - kb - 1;
-      k_chol_update<<<(unsigned)(T_ * (T_ + 1) / 2), DB * DB / 4, 0, s>>>(n, kb, h->dS);
-      count_launch(2);
-    }
-    count_launch();
-  }
-  {
-    Prof pr(h, BA_K_OTHER);
-    k_dense_solve<<<1, 1024, 0, s>>>(n, n - 1, h->dS, h->r, h->dy, h->x, h->dfail, h->st);
-    count_launch();
-  }
+  const size_t ntile = (size_t)h->bnb * (h->bwt + 1);
+  int* ctr = h->bflag + 2 * ntile;
+  BandArgs ba_{h->bnb, h->bwt, n, h->bntask, h->bncrit, h->band_crit, h->btask, h->bT, h->brs, h->bUi, h->r,
+               h->dy, h->x, h->bflag, h->bflag + ntile, ctr, ctr + 5, ctr + 6};
+  void* args[] = {&ba_};
+  cudaLaunchCooperativeKernel((const void*)k_band_chol, dim3(h->band_grid), dim3(BAND_THREADS), args, 0, s);
+  k_band_finish<<<nblk(n, 256), 256, 0, s>>>(n, ctr + 5, ctr, h->x, h->st);
+  count_launch(2);
 }
 
 template <typename T, bool MF>
@@ -798,10 +790,36 @@ ba_status create_impl(ba_problem* h, const void* cams, const void* points, const
   CU(h->alloc(&h->part, (size_t)PART * std::max(h->npieces, 1) * 8));
   h->ncb = (int)nblk(C, CAM_THREADS);
   if (h->opt.solver == BA_SOLVER_CHOLESKY) {
+    // the direct solve: partial copies of S so that about every resident
+    // slot of the build kernel holds a share of a camera's observations
+    // (at most 8 copies); the band tiles of the whole lower triangle; the
+    // factorisation's task list (ba_band_sched.h) for one block per SM
     const size_t n = 9 * (size_t)C;
-    CU(h->alloc(&h->dS, n * n * 8));
-    CU(h->alloc(&h->dy, n * 8));
-    CU(h->alloc(&h->dfail, 16));
+    int dev = 0, nsm = 1, occ = 1;
+    CU(cudaGetDevice(&dev));
+    CU(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_schur_dense<double, false>, DENSE_THREADS, 0));
+    h->nseg = (int)std::max(1LL, std::min(8LL, (long long)occ * nsm / std::max(1LL, (long long)C)));
+    CU(h->alloc(&h->Spart, (size_t)h->nseg * n * n * 8));
+    h->bnb = (int)((n + BAND_TB - 1) / BAND_TB);
+    h->bwt = h->bnb - 1;
+    const long long nupd = (long long)h->bnb * h->bwt * (h->bwt + 1) / 2;
+    const int s_upd = (int)std::max(1LL, (nupd + (4LL << 20) - 1) / (4LL << 20));
+    h->band_grid = std::max(1, nsm);
+    h->band_crit = h->band_grid >= 2 ? std::min(BAND_CRIT_BLOCKS, std::max(1, h->band_grid / 8)) : 0;
+    const std::vector<BandTask> tasks = band_tasks(h->bnb, h->bwt, s_upd, h->band_grid, h->band_crit, &h->bncrit);
+    static_assert(sizeof(BandTask) == sizeof(int4), "a task is read as an int4");
+    if (h->bncrit == 0) h->band_crit = 0;
+    h->bntask = (int)tasks.size();
+    h->bT_bytes = (size_t)h->bnb * (h->bwt + 1) * (BAND_TB * BAND_TB) * sizeof(double);
+    h->bflag_count = 2 * (size_t)h->bnb * (h->bwt + 1) + 6 + h->bnb;
+    CU(h->alloc(&h->bT, h->bT_bytes));
+    CU(h->alloc(&h->brs, 8ull * h->bnb * BAND_TB));
+    CU(h->alloc(&h->bUi, 8ull * h->bnb * BAND_TB * BAND_TB));
+    CU(h->alloc(&h->dy, 8ull * h->bnb * BAND_TB));
+    CU(h->alloc(&h->bflag, sizeof(int) * h->bflag_count));
+    CU(h->alloc(&h->btask, sizeof(int4) * tasks.size()));
+    CU(cudaMemcpy(h->btask, tasks.data(), sizeof(int4) * tasks.size(), cudaMemcpyHostToDevice));
   }
   h->npb = (int)nblk(P, PT_THREADS);
   CU(h->alloc(&h->dot_pq, h->ncb * 8));
@@ -1140,7 +1158,9 @@ ba_status ba_solve(ba_problem* h, int iters, void* stream) {
       return fail(BA_ERR_CUDA, h->xerr == 2 ? "the exchange callback failed" : "exchange buffer too small or copy failed");
     return leave(h, stream);
   }
-  if (!h->opt.use_graph) {
+  // the direct solver's factorisation is a cooperative launch: its trials
+  // run as direct launches
+  if (!h->opt.use_graph || h->opt.solver == BA_SOLVER_CHOLESKY) {
     for (int i = 0; i < iters; ++i) enqueue_trial_any(h);
     CU(cudaGetLastError());
     return leave(h, stream);

@@ -91,7 +91,7 @@ __device__ __forceinline__ int band_k0(const BandArgs& a, int I) { return max(0,
 
 // Thread-0 wait until *flag >= v (acquire).  False when the wait ran out or
 // another one did (ctr[3]).
-__device__ __noinline__ bool band_wait(int* flag, int v, int* err) {
+static __device__ __noinline__ bool band_wait(int* flag, int v, int* err) {
   cuda::atomic_ref<int, cuda::thread_scope_device> f(*flag), e(*err);
   unsigned int spins = 0;
   while (f.load(cuda::memory_order_acquire) < v) {
@@ -139,7 +139,7 @@ struct BandSmem {
 // s.B with 1 / L_cc in s.rs: column by column, x_rc = a_rc / L_cc, then
 // a_rc' -= x_rc L_c'c for c' > c (L's column c prescaled by 1 / L_cc; the
 // prescaling overwrites s.B).
-__device__ void band_trsm(BandSmem& s) {
+static __device__ void band_trsm(BandSmem& s) {
   constexpr int TB = BAND_TB;
   const int tid = threadIdx.x, lane = tid % 32, wp = tid / 32;
   for (int e = tid; e < TB * TB; e += BAND_THREADS) {
@@ -164,7 +164,7 @@ __device__ void band_trsm(BandSmem& s) {
 // to warps 1-3 and 5-7, so that the chain's FP64 instructions do not queue
 // behind theirs (warps w and w + 4 share a scheduler).  A pivot that is not
 // positive or not finite is replaced by 1 and counted in s.bad.
-__device__ void band_potrf(BandSmem& s) {
+static __device__ void band_potrf(BandSmem& s) {
   constexpr int TB = BAND_TB, NU = BAND_THREADS - 64;  // updating threads
   const int tid = threadIdx.x, wp = tid / 32;
   const bool pivot = tid == 0;
@@ -206,7 +206,7 @@ __device__ void band_potrf(BandSmem& s) {
 
 // D_J: the subdiagonal tile's solve, the last update of the diagonal tile
 // and its factorisation.
-__device__ bool band_task_D(const BandArgs& a, BandSmem& s, int J) {
+static __device__ bool band_task_D(const BandArgs& a, BandSmem& s, int J) {
   constexpr int TB = BAND_TB;
   const int tid = threadIdx.x;
   if (J >= 1 && a.bwt >= 1) {
@@ -252,7 +252,7 @@ __device__ bool band_task_D(const BandArgs& a, BandSmem& s, int J) {
 
 // U: A_IJ -= L_IK L_JK^T for K = Ka .. Ka + cnt - 1, after the tile's
 // earlier updates.
-__device__ bool band_task_U(const BandArgs& a, BandSmem& s, int I, int J, int Ka, int cnt) {
+static __device__ bool band_task_U(const BandArgs& a, BandSmem& s, int I, int J, int Ka, int cnt) {
   constexpr int TB = BAND_TB, E = TB * TB / BAND_THREADS, RS = BAND_THREADS / TB;
   const int tid = threadIdx.x, col = tid % TB, row0 = tid / TB;
   const int k0 = band_k0(a, I);
@@ -286,7 +286,7 @@ __device__ bool band_task_U(const BandArgs& a, BandSmem& s, int I, int J, int Ka
 }
 
 // T: L_IJ = A_IJ L_JJ^{-T} (I >= J + 2) after the tile's updates.
-__device__ bool band_task_T(const BandArgs& a, BandSmem& s, int I, int J) {
+static __device__ bool band_task_T(const BandArgs& a, BandSmem& s, int I, int J) {
   constexpr int TB = BAND_TB;
   const int tid = threadIdx.x;
   int w = 1;
@@ -304,7 +304,7 @@ __device__ bool band_task_T(const BandArgs& a, BandSmem& s, int I, int J) {
 }
 
 // I_J: U_J = L_JJ^{-T}, the solution of X L_JJ^T = identity.
-__device__ bool band_task_I(const BandArgs& a, BandSmem& s, int J) {
+static __device__ bool band_task_I(const BandArgs& a, BandSmem& s, int J) {
   constexpr int TB = BAND_TB;
   const int tid = threadIdx.x;
   int w = 1;
@@ -337,7 +337,7 @@ __device__ __forceinline__ bool band_wait_count(int* p, int v, int* known, int* 
 }
 
 // Forward block F_J: y_J = L_JJ^{-1} (b_J - sum_{K < J} L_JK y_K).
-__device__ bool band_forward_task(const BandArgs& a, BandSmem& s, int J) {
+static __device__ bool band_forward_task(const BandArgs& a, BandSmem& s, int J) {
   constexpr int TB = BAND_TB;
   const int tid = threadIdx.x, r = tid / 8, q = tid % 8;  // row r, columns 4q .. 4q + 3
   int known = 0;                                         // forward blocks known done (thread 0)
@@ -390,7 +390,7 @@ __device__ bool band_forward_task(const BandArgs& a, BandSmem& s, int J) {
 
 // Backward block B_I: x_I = L_II^{-T} (y_I - sum_{K > I} L_KI^T x_K); x
 // overwrites y.
-__device__ bool band_backward_task(const BandArgs& a, BandSmem& s, int I) {
+static __device__ bool band_backward_task(const BandArgs& a, BandSmem& s, int I) {
   constexpr int TB = BAND_TB;
   const int tid = threadIdx.x, lane = tid % 32, wp = tid / 32;  // x row lane; L rows wp, wp + 8, ...
   int known = 0;                                                // backward blocks known done (thread 0)

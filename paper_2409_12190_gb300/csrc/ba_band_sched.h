@@ -15,7 +15,8 @@ namespace ba {
 // solve, F / B the forward / backward block solves, I a diagonal tile's
 // inverse transpose.
 enum { BAND_D = 0, BAND_U = 1, BAND_T = 2, BAND_F = 3, BAND_B = 4, BAND_I = 5 };
-constexpr int BAND_CRIT_BLOCKS = 4;  // blocks of the near-diagonal pool
+constexpr int BAND_CRIT_BLOCKS = 4;             // blocks of the near-diagonal pool
+constexpr long long BAND_SIM_MAX_TASKS = 2000000;  // longest list that is simulated
 
 // One task, as the device reads it (an int4): x = type + 8 count (count:
 // U's columns), y = I, z = J, w = Ka (U's first column); for D, I, F:
@@ -39,8 +40,10 @@ struct BandTask {
 //     come after their starts, so the order is topological.
 // s_upd: columns per update segment; workers blocks in all, crit_workers
 // of them for the near-diagonal pool; *ncrit: that pool's tasks (the list's
-// first ones).
-inline std::vector<BandTask> band_tasks(int nb, int bwt, int s_upd, int workers, int crit_workers, int* ncrit) {
+// first ones).  A list of more than sim_max tasks is returned in the
+// enumeration's order (topological), in one pool (*ncrit = 0).
+inline std::vector<BandTask> band_tasks(int nb, int bwt, int s_upd, int workers, int crit_workers, int* ncrit,
+                                        long long sim_max = BAND_SIM_MAX_TASKS) {
   const long long ntile = (long long)nb * (bwt + 1);
   auto k0 = [&](int I) { return std::max(0, I - bwt); };
   auto tix = [&](int I, int J) { return (long long)J * (bwt + 1) + (I - J); };
@@ -52,6 +55,9 @@ inline std::vector<BandTask> band_tasks(int nb, int bwt, int s_upd, int workers,
       seg0[tix(I, J) + 1] = (u + s_upd - 1) / s_upd;
     }
   for (long long t = 0; t < ntile; ++t) seg0[t + 1] += seg0[t];
+  // a list too long to simulate keeps the enumeration's order, in one pool
+  const bool simulate = seg0[ntile] + 6LL * nb <= sim_max;
+  if (!simulate) crit_workers = 0;
   std::vector<int> segid(seg0[ntile], -1), idD(nb), idI(nb), idF(nb), idB(nb), idT(ntile, -1);
   std::vector<BandTask> task;
   std::vector<double> dur;
@@ -64,7 +70,7 @@ inline std::vector<BandTask> band_tasks(int nb, int bwt, int s_upd, int workers,
     return seg0[t + 1] > seg0[t] ? segid[seg0[t + 1] - 1] : -1;
   };
   auto dep = [&](int p2) {
-    if (p2 >= 0) pred.push_back(p2);
+    if (p2 >= 0 && simulate) pred.push_back(p2);
   };
   auto add = [&](int type, int cnt, int I, int J, int Ka, double d) {
     task.push_back(BandTask{type + 8 * cnt, I, J, Ka});
@@ -114,6 +120,10 @@ inline std::vector<BandTask> band_tasks(int nb, int bwt, int s_upd, int workers,
     idB[I] = add(BAND_B, 0, I, I, 0, 4.0);
   }
   const int nt = (int)task.size();
+  if (!simulate) {
+    *ncrit = 0;
+    return task;
+  }
   const double lat = 1.0, early = 8.0;
   auto out_time = [&](int p2, double start_or_len) { return (p2 & 1) ? early : start_or_len; };
   // longest path to the end

@@ -556,6 +556,7 @@ ba_status ba_pgo_create(ba_pgo** out, int N, int E, const double* poses, const i
       h->band_crit = h->band_grid >= 2 ? std::min(BAND_CRIT_BLOCKS, std::max(1, h->band_grid / 8)) : 0;
       const std::vector<BandTask> tasks = band_tasks(h->bnb, h->bwt, s_upd, h->band_grid, h->band_crit, &h->bncrit);
       static_assert(sizeof(BandTask) == sizeof(int4), "a task is read as an int4");
+      if (h->bncrit == 0) h->band_crit = 0;
       h->bntask = (int)tasks.size();
       h->bT_bytes = (size_t)h->bnb * (h->bwt + 1) * (BAND_TB * BAND_TB) * sizeof(double);
       h->bflag_count = 2 * (size_t)h->bnb * (h->bwt + 1) + 6 + h->bnb;

@@ -74,11 +74,18 @@ struct ba_problem {
   float* Ef = nullptr;      // [C][45] network output
   double* Dsc = nullptr;    // [C][9] scales diag(S_ii)
   double* kap = nullptr;    // [C] coupling sums of the probes (feature 93)
-  // direct solver (BA_SOLVER_CHOLESKY): dense S / its factor, work vector,
-  // failure flag
-  double* dS = nullptr;
-  double* dy = nullptr;
-  int* dfail = nullptr;
+  // direct solver (BA_SOLVER_CHOLESKY): nseg partial copies of S, the band
+  // tiles of S (then L; the band is the whole lower triangle), 1 / L_cc,
+  // L_JJ^{-T}, the work vector, the factorisation's flags (tile final and
+  // tile updates [bnb bnb] each, counters [5], failure [1], inverse final
+  // [bnb]) and its task list
+  double* Spart = nullptr;
+  int nseg = 1;
+  double *bT = nullptr, *brs = nullptr, *bUi = nullptr, *dy = nullptr;
+  int* bflag = nullptr;
+  int4* btask = nullptr;
+  int bnb = 0, bwt = 0, bntask = 0, bncrit = 0, band_grid = 0, band_crit = 0;
+  size_t bT_bytes = 0, bflag_count = 0;
   ba::DevState* st = nullptr;
   ba_iter_stats* stats = nullptr;
   int cap = 0;

@@ -28,9 +28,11 @@ def scheduler(tmp_path_factory):
                     os.path.join(ROOT, "paper_2409_12190_gb300", "csrc"),
                     os.path.join(ROOT, "tests", "c", "band_schedule.cpp"), "-o", str(exe)], check=True)
 
-    def run(nb, bwt, s_upd, workers, crit):
-        out = subprocess.run([str(exe), str(nb), str(bwt), str(s_upd), str(workers), str(crit)],
-                             capture_output=True, text=True, check=True).stdout.splitlines()
+    def run(nb, bwt, s_upd, workers, crit, sim_max=None):
+        argv = [str(exe), str(nb), str(bwt), str(s_upd), str(workers), str(crit)]
+        if sim_max is not None:
+            argv.append(str(sim_max))
+        out = subprocess.run(argv, capture_output=True, text=True, check=True).stdout.splitlines()
         ncrit = int(out[0].split()[1])
         tasks = [tuple(int(v) for v in line.split()) for line in out[1:]]
         return ncrit, tasks
@@ -171,7 +173,7 @@ def _execute(machine, ncrit, tasks, workers, crit, seed):
         done += 1
 
 
-CASES = [  # nb, bwt, columns per update task, blocks, near-diagonal blocks
+CASES = [  # nb, bwt, columns per update task, blocks, near-diagonal blocks[, longest simulated list]
     (7, 3, 1, 8, 2),
     (11, 10, 1, 16, 3),   # dense lower triangle
     (16, 5, 2, 12, 2),    # update segments of two columns
@@ -180,12 +182,19 @@ CASES = [  # nb, bwt, columns per update task, blocks, near-diagonal blocks
     (1, 0, 1, 2, 1),      # one block
     (20, 4, 1, 152, 4),
     (9, 8, 1, 1, 0),      # one block for everything (no near-diagonal pool)
+    (10, 9, 2, 6, 2, 0),  # too long to simulate: the enumeration's order, one pool
 ]
 
 
-@pytest.mark.parametrize("nb,bwt,s_upd,workers,crit", CASES)
-def test_task_list_covers_the_factorisation_once(scheduler, nb, bwt, s_upd, workers, crit):
-    ncrit, tasks = scheduler(nb, bwt, s_upd, workers, crit)
+def _case(c):
+    return c + (None,) * (6 - len(c))
+
+
+@pytest.mark.parametrize("nb,bwt,s_upd,workers,crit,sim_max", [_case(c) for c in CASES])
+def test_task_list_covers_the_factorisation_once(scheduler, nb, bwt, s_upd, workers, crit, sim_max):
+    ncrit, tasks = scheduler(nb, bwt, s_upd, workers, crit, sim_max)
+    if sim_max == 0:
+        assert ncrit == 0
     assert len(set(tasks)) == len(tasks)
     types = [t[0] & 7 for t in tasks]
     for typ in (D, INV, F, B):
@@ -204,12 +213,12 @@ def test_task_list_covers_the_factorisation_once(scheduler, nb, bwt, s_upd, work
     for x, I, J, Ka in tasks[:ncrit]:
         typ = x & 7
         assert typ == D or (typ == U and I <= Ka + (x >> 3) + 1) or (typ == T and I == J + 2)
-    assert (ncrit == 0) == (crit == 0) or types.count(D) == 0
+    assert (ncrit == 0) == (crit == 0 or sim_max == 0) or types.count(D) == 0
 
 
-@pytest.mark.parametrize("nb,bwt,s_upd,workers,crit", CASES)
-def test_two_pool_execution_never_deadlocks_and_solves(scheduler, nb, bwt, s_upd, workers, crit):
-    ncrit, tasks = scheduler(nb, bwt, s_upd, workers, crit)
+@pytest.mark.parametrize("nb,bwt,s_upd,workers,crit,sim_max", [_case(c) for c in CASES])
+def test_two_pool_execution_never_deadlocks_and_solves(scheduler, nb, bwt, s_upd, workers, crit, sim_max):
+    ncrit, tasks = scheduler(nb, bwt, s_upd, workers, crit, sim_max)
     rng = np.random.default_rng(nb * 100 + bwt)
     n = nb * TB - 5 if nb > 1 else 20   # ragged: the padding's identity rows
     bw = min(n - 1, max(0, bwt * TB - 7))
