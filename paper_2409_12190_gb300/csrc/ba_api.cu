@@ -299,9 +299,12 @@ void enqueue_dense_solve(ba_problem* h, const double* lam_ptr) {
   cudaStream_t s = h->s;
   const int n = 9 * h->C;
   Prof pr(h, BA_K_OTHER);
-  k_schur_dense<T, MF><<<h->C * h->nseg, DENSE_THREADS, 0, s>>>(
-      h->C, h->rowptr_cam, h->cm_pt, h->rowptr_pt, h->pm_cam, h->pm2cm, (const T*)h->Jcm, (const T*)h->cm_sw,
-      (const T*)h->camtab, (const T*)h->pts, h->st, h->P, h->O, (const T*)h->Vinv, h->nseg, h->Spart);
+  k_dense_w<T, MF><<<nblk(h->P, DENSE_THREADS), DENSE_THREADS, 0, s>>>(
+      h->P, h->rowptr_pt, h->pm_cam, h->pm2cm, (const T*)h->Jcm, (const T*)h->cm_sw, (const T*)h->camtab,
+      (const T*)h->pts, h->st, h->O, h->Wd);
+  k_schur_dense<T><<<h->C * h->nseg, DENSE_THREADS, 0, s>>>(
+      h->C, h->nseg, h->rowptr_cam, h->cm_pt, h->rowptr_pt, h->pm_cam, h->pm2cm, h->Wd, (const T*)h->Vinv, h->Spart);
+  count_launch();
   cudaMemsetAsync(h->bT, 0, h->bT_bytes, s);
   cudaMemsetAsync(h->bflag, 0, sizeof(int) * h->bflag_count, s);
   k_schur_to_band<<<n, 256, 0, s>>>(h->C, h->nseg, h->Spart, h->U, lam_ptr, h->opt.diag_min, h->opt.diag_max,
@@ -790,16 +793,16 @@ ba_status create_impl(ba_problem* h, const void* cams, const void* points, const
   CU(h->alloc(&h->part, (size_t)PART * std::max(h->npieces, 1) * 8));
   h->ncb = (int)nblk(C, CAM_THREADS);
   if (h->opt.solver == BA_SOLVER_CHOLESKY) {
-    // the direct solve: partial copies of S so that about every resident
-    // slot of the build kernel holds a share of a camera's observations
-    // (at most 8 copies); the band tiles of the whole lower triangle; the
+    // the direct solve: W of every observation; partial copies of S (as
+    // many as fit in 64 MB, at most 8, at least 1: one CTA per camera and
+    // copy builds them); the band tiles of the whole lower triangle; the
     // factorisation's task list (ba_band_sched.h) for one block per SM
     const size_t n = 9 * (size_t)C;
-    int dev = 0, nsm = 1, occ = 1;
+    int dev = 0, nsm = 1;
     CU(cudaGetDevice(&dev));
     CU(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_schur_dense<double, false>, DENSE_THREADS, 0));
-    h->nseg = (int)std::max(1LL, std::min(8LL, (long long)occ * nsm / std::max(1LL, (long long)C)));
+    h->nseg = (int)std::max<size_t>(1, std::min<size_t>(8, (64ull << 20) / (n * n * 8)));
+    CU(h->alloc(&h->Wd, 27ull * 8 * (size_t)std::max<long long>(O, 1)));
     CU(h->alloc(&h->Spart, (size_t)h->nseg * n * n * 8));
     h->bnb = (int)((n + BAND_TB - 1) / BAND_TB);
     h->bwt = h->bnb - 1;

@@ -79,6 +79,7 @@ struct ba_problem {
   // L_JJ^{-T}, the work vector, the factorisation's flags (tile final and
   // tile updates [bnb bnb] each, counters [5], failure [1], inverse final
   // [bnb]) and its task list
+  double* Wd = nullptr;     // [O][27] W = Jc^T Jp per observation
   double* Spart = nullptr;
   int nseg = 1;
   double *bT = nullptr, *brs = nullptr, *bUi = nullptr, *dy = nullptr;
