@@ -793,15 +793,19 @@ ba_status create_impl(ba_problem* h, const void* cams, const void* points, const
   CU(h->alloc(&h->part, (size_t)PART * std::max(h->npieces, 1) * 8));
   h->ncb = (int)nblk(C, CAM_THREADS);
   if (h->opt.solver == BA_SOLVER_CHOLESKY) {
-    // the direct solve: W of every observation; partial copies of S (as
-    // many as fit in 64 MB, at most 8, at least 1: one CTA per camera and
-    // copy builds them); the band tiles of the whole lower triangle; the
-    // factorisation's task list (ba_band_sched.h) for one block per SM
+    // the direct solve: W of every observation; partial copies of S, one
+    // CTA per camera and copy building them (as many copies as keep every
+    // CTA resident and fit in 96 MB, so in L2; at most 8, at least 1); the
+    // band tiles of the whole lower triangle; the factorisation's task list
+    // (ba_band_sched.h) for one block per SM
     const size_t n = 9 * (size_t)C;
-    int dev = 0, nsm = 1;
+    int dev = 0, nsm = 1, occ = 1;
     CU(cudaGetDevice(&dev));
     CU(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    h->nseg = (int)std::max<size_t>(1, std::min<size_t>(8, (64ull << 20) / (n * n * 8)));
+    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_schur_dense<double>, DENSE_THREADS, 0));
+    const size_t by_slots = (size_t)std::max(1, occ) * (size_t)nsm / (size_t)std::max<long long>(1, C);
+    const size_t by_bytes = (96ull << 20) / (n * n * 8);
+    h->nseg = (int)std::max<size_t>(1, std::min<size_t>(8, std::min(by_slots, by_bytes)));
     CU(h->alloc(&h->Wd, 27ull * 8 * (size_t)std::max<long long>(O, 1)));
     CU(h->alloc(&h->Spart, (size_t)h->nseg * n * n * 8));
     h->bnb = (int)((n + BAND_TB - 1) / BAND_TB);
