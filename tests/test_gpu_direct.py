@@ -1,5 +1,5 @@
 """The direct solver of the reduced camera system (the paper's Cholesky
-variant, Sec. IV-C): S formed explicitly on the GPU, a blocked FP64
+variant, Sec. IV-C): S formed explicitly on the GPU, a tiled FP64
 Cholesky factorisation and triangular solves, against the oracle's explicit
 Schur complement and dense Cholesky (oracle.solve_damped with
 solver="cholesky"), which its pins tie to the dense solve of Eq. 2."""
