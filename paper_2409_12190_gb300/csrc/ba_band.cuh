@@ -1,11 +1,14 @@
-// Banded Cholesky of the damped pose-graph system (H + D) x = b and its two
-// triangular solves in one cooperative launch (the paper's sparse direct
-// solver, Sec. IV-C, "Sparse Direct Solver (Cholesky Factorization)", applied
-// to the pose-graph normal equations of Sec. IV-D).
+// Banded Cholesky of an SPD system A x = b and its two triangular solves in
+// one cooperative launch (the paper's sparse direct solver, Sec. IV-C,
+// "Sparse Direct Solver (Cholesky Factorization)").  It solves the damped
+// pose-graph system H + D (Sec. IV-D), whose band is narrow, and the
+// bundle-adjustment reduced camera system S (Eq. 2), whose band is the
+// whole lower triangle.
 //
-// Storage.  In the factored order (reverse Cuthill-McKee when narrower) the
-// matrix has half-bandwidth bw unknowns, so its lower triangle lies in the
-// TB x TB tiles (I, J) with 0 <= I - J <= bwt = ceil(bw / TB).  Only those
+// Storage.  In the factored order (for the pose graphs, reverse
+// Cuthill-McKee when narrower) the matrix has half-bandwidth bw unknowns, so
+// its lower triangle lies in the TB x TB tiles (I, J) with
+// 0 <= I - J <= bwt = ceil(bw / TB).  Only those
 // tiles are stored: tile (I, J) at T + (J (bwt + 1) + I - J) TB^2, row-major.
 // The order is padded to nb TB unknowns with identity rows.  Cholesky keeps
 // the fill inside the band, so L takes the same tiles.
@@ -51,8 +54,8 @@ constexpr int BAND_TB = DB;        // tile size (32)
 constexpr int BAND_THREADS = 256;  // threads per block
 constexpr int BAND_TRI = BAND_TB * (BAND_TB + 1) / 2;  // entries of a tile's lower triangle
 
-// One task: x = type + 8 count (count: U's updates), y = I, z = J, w = Ka
-// (U) - for D, F: y = z = J; for B: y = z = I.
+// The launch's arguments; the tasks are ba_band_sched.h's BandTask records,
+// read as int4.
 struct BandArgs {
   int nb;             // block rows of the padded order (nb * TB >= n)
   int bwt;            // half-bandwidth in tiles
